@@ -1,0 +1,378 @@
+"""CPU oracle for the sector Lanczos method -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, obviously correct restatement of Schnack, Hage and Schmidt,
+"Optimized implementation of the Lanczos method for magnetic systems"
+(arXiv:0706.3293).  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of
+``bench.py`` may import it.  It shares no code with the CUDA library in
+``paper_0706_3293_gb300``; both sides meet only in the seeded input generators of
+``paper_0706_3293_gb300.workloads`` (which hold none of the method's arithmetic) and in
+SplitMix64, which each side implements on its own from the published definition.
+
+Two layers:
+
+* ``hm_oracle.c`` (plain C, openMP over rows like the paper, Sec. 4): the D(N, A) table
+  (Eq. E-3-c), decode (Sec. 3.1), encode (Sec. 3.2), successor (Sec. 3.1), the row
+  matvec (Eq. E-4-b) of the Heisenberg model (Eq. E-2-1), bond correlations, the plain
+  Lanczos recurrence and a Sturm bisection for the tridiagonal matrix.
+* this module: ctypes bindings plus pure-Python/numpy brute force for tiny systems
+  (stored sorted basis and binary search, Sec. 3.1 / Sec. 1; dense H built from
+  Kronecker products of spin matrices), the ground-state gradient and the
+  finite-temperature Lanczos estimator.  Library primitives used as single steps:
+  ``numpy.linalg.eigh``/``eigvalsh`` and ``scipy.linalg.eigh_tridiagonal``.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` against
+closed forms, worked examples of the paper, brute force, or invariants; none is
+"parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from typing import Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+# breakdown threshold of the Lanczos recurrence (relative to the largest |alpha|, beta)
+LANCZOS_TOL = 1e-12
+
+
+def build(force: bool = False) -> str:
+    """Compile hm_oracle.c into liboracle.so next to it (gcc, -O2, openMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        c_p, i64, i32, f64p = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        L.orc_basis_new.restype = c_p
+        L.orc_basis_new.argtypes = [i32, i32, i32]
+        L.orc_basis_free.argtypes = [c_p]
+        L.orc_basis_dim.restype = i64
+        L.orc_basis_dim.argtypes = [c_p]
+        L.orc_table.restype = i64
+        L.orc_table.argtypes = [c_p, i32, i32]
+        L.orc_decode.restype = i32
+        L.orc_decode.argtypes = [c_p, i64, c_p]
+        L.orc_encode.restype = i64
+        L.orc_encode.argtypes = [c_p, c_p]
+        L.orc_successor.restype = i32
+        L.orc_successor.argtypes = [i32, i32, c_p]
+        L.orc_matvec.restype = i32
+        L.orc_matvec.argtypes = [c_p, i32, c_p, c_p, c_p, f64p, f64p]
+        L.orc_matvec_rows.restype = i32
+        L.orc_matvec_rows.argtypes = [c_p, i32, c_p, c_p, c_p, f64p, f64p, i64, i64]
+        L.orc_count_nnz.restype = i64
+        L.orc_count_nnz.argtypes = [c_p, i32, c_p, c_p, i64, i64]
+        L.orc_bond_corr.restype = i32
+        L.orc_bond_corr.argtypes = [c_p, i32, c_p, c_p, f64p, f64p, f64p]
+        L.orc_lanczos.restype = i32
+        L.orc_lanczos.argtypes = [c_p, i32, c_p, c_p, c_p, f64p, i32, ctypes.c_double,
+                                  f64p, f64p, f64p, f64p]
+        L.orc_tridiag_lowest.argtypes = [i32, f64p, f64p, i32, f64p]
+        L.orc_splitmix.restype = ctypes.c_uint64
+        L.orc_splitmix.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        L.orc_start_uniform.argtypes = [ctypes.c_uint64, i64, f64p]
+        L.orc_start_pm1.argtypes = [ctypes.c_uint64, i64, f64p]
+        L.orc_stream_seed.restype = ctypes.c_uint64
+        L.orc_stream_seed.argtypes = [ctypes.c_uint64, i32, i32]
+        L.orc_num_threads.restype = i32
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def sector_A(n_sites: int, two_s: int, two_m: int) -> int:
+    """A = N s - M (Sec. 3); two_s = 2s, two_m = 2M must make N*2s - 2M even."""
+    t = n_sites * two_s - two_m
+    if t % 2 or t < 0 or t > 2 * n_sites * two_s:
+        raise ValueError("M is not a magnetic quantum number of this system")
+    return t // 2
+
+
+class Bonds:
+    """A bond list (u, v, J): the terms -J s_u.s_v of Eq. (E-2-1), each listed once."""
+
+    def __init__(self, u: Sequence[int], v: Sequence[int], J: Sequence[float]):
+        self.u = np.ascontiguousarray(u, dtype=np.int32)
+        self.v = np.ascontiguousarray(v, dtype=np.int32)
+        self.J = np.ascontiguousarray(J, dtype=np.float64)
+        assert self.u.shape == self.v.shape == self.J.shape
+
+    def __len__(self):
+        return int(self.u.shape[0])
+
+
+class Basis:
+    """One sector H(M) of N spins s with the paper's D-table coding (Sec. 3)."""
+
+    def __init__(self, n_sites: int, two_s: int, A: int):
+        self.N, self.S2, self.A = n_sites, two_s, A
+        self._h = lib().orc_basis_new(n_sites, two_s, A)
+        if not self._h:
+            raise ValueError("invalid basis or table overflow")
+        self.dim = int(lib().orc_basis_dim(self._h))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_basis_free(h)
+            self._h = None
+
+    def D(self, k: int, a: int) -> int:
+        return int(lib().orc_table(self._h, k, a))
+
+    def decode(self, i: int) -> np.ndarray:
+        d = np.zeros(self.N, dtype=np.int32)
+        if lib().orc_decode(self._h, int(i), _ptr(d)) != 0:
+            raise IndexError(i)
+        return d
+
+    def encode(self, digits: Sequence[int]) -> int:
+        d = np.ascontiguousarray(digits, dtype=np.int32)
+        assert d.shape == (self.N,)
+        return int(lib().orc_encode(self._h, _ptr(d)))
+
+    def matvec(self, bonds: Bonds, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty(self.dim, dtype=np.float64)
+        rc = lib().orc_matvec(self._h, len(bonds), _ptr(bonds.u), _ptr(bonds.v), _ptr(bonds.J),
+                              _ptr(x), _ptr(y))
+        if rc:
+            raise ValueError("bad bond list")
+        return y
+
+    def matvec_rows(self, bonds: Bonds, x: np.ndarray, r0: int, r1: int) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty(r1 - r0, dtype=np.float64)
+        rc = lib().orc_matvec_rows(self._h, len(bonds), _ptr(bonds.u), _ptr(bonds.v),
+                                   _ptr(bonds.J), _ptr(x), _ptr(y), r0, r1)
+        if rc:
+            raise ValueError("bad bond list or row range")
+        return y
+
+    def count_nnz(self, bonds: Bonds, r0: int = 0, r1: int | None = None) -> int:
+        r1 = self.dim if r1 is None else r1
+        return int(lib().orc_count_nnz(self._h, len(bonds), _ptr(bonds.u), _ptr(bonds.v), r0, r1))
+
+    def bond_corr(self, bonds: Bonds, g: np.ndarray, x: np.ndarray) -> np.ndarray:
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.empty(len(bonds), dtype=np.float64)
+        rc = lib().orc_bond_corr(self._h, len(bonds), _ptr(bonds.u), _ptr(bonds.v), _ptr(g),
+                                 _ptr(x), _ptr(out))
+        if rc:
+            raise ValueError("bad bond list")
+        return out
+
+    def lanczos(self, bonds: Bonds, v0: np.ndarray, steps: int, tol: float = LANCZOS_TOL,
+                coef: np.ndarray | None = None):
+        """Plain Lanczos; returns (alpha, beta) of the steps done, and psi if coef given."""
+        v0 = np.ascontiguousarray(v0, dtype=np.float64)
+        al = np.zeros(steps)
+        be = np.zeros(steps)
+        psi = None
+        cptr = None
+        if coef is not None:
+            coef = np.ascontiguousarray(np.pad(coef, (0, steps - len(coef))), dtype=np.float64)
+            psi = np.empty(self.dim)
+            cptr = _ptr(coef)
+        done = lib().orc_lanczos(self._h, len(bonds), _ptr(bonds.u), _ptr(bonds.v), _ptr(bonds.J),
+                                 _ptr(v0), steps, tol, _ptr(al), _ptr(be), cptr,
+                                 _ptr(psi) if psi is not None else None)
+        if done < 1:
+            raise ValueError("lanczos failed")
+        if coef is not None:
+            return al[:done], be[:done], psi
+        return al[:done], be[:done]
+
+
+def successor(digits: Sequence[int], two_s: int):
+    """Sec. 3.1 successor; returns the next digits or None for the last state."""
+    d = np.ascontiguousarray(digits, dtype=np.int32).copy()
+    ok = lib().orc_successor(len(d), two_s, _ptr(d))
+    return d if ok else None
+
+
+def tridiag_lowest(alpha: np.ndarray, beta: np.ndarray, k: int) -> np.ndarray:
+    """k lowest eigenvalues of T(alpha, beta[:m-1]) by Sturm bisection."""
+    al = np.ascontiguousarray(alpha, dtype=np.float64)
+    m = len(al)
+    be = np.ascontiguousarray(beta[: max(m - 1, 0)], dtype=np.float64)
+    if be.size == 0:
+        be = np.zeros(1)
+    out = np.zeros(min(k, m))
+    lib().orc_tridiag_lowest(m, _ptr(al), _ptr(be), len(out), _ptr(out))
+    return out
+
+
+def splitmix(seed: int, t: int) -> int:
+    return int(lib().orc_splitmix(seed & (2**64 - 1), t))
+
+
+def start_uniform(seed: int, n: int) -> np.ndarray:
+    out = np.empty(n)
+    lib().orc_start_uniform(seed & (2**64 - 1), n, _ptr(out))
+    return out
+
+
+def start_pm1(seed: int, n: int) -> np.ndarray:
+    out = np.empty(n)
+    lib().orc_start_pm1(seed & (2**64 - 1), n, _ptr(out))
+    return out
+
+
+def stream_seed(seed: int, A: int, r: int) -> int:
+    return int(lib().orc_stream_seed(seed & (2**64 - 1), A, r))
+
+
+# ----------------------------------------------------------------------------------------
+# Brute force for tiny systems: independent of the D-table coding.
+# ----------------------------------------------------------------------------------------
+
+def full_basis_sorted(n_sites: int, two_s: int, A: int) -> list[tuple]:
+    """The sector states in the paper's lexicographic order, by the "stored basis"
+    route of Sec. 3.1: run through the full product basis (Eq. E-3-a: a_1 varies
+    fastest, i.e. the natural number with base 2s+1 and a_N most significant) and keep
+    the states with digit sum A."""
+    base = two_s + 1
+    out = []
+    for code in range(base ** n_sites):
+        d, c = [], code
+        for _ in range(n_sites):
+            d.append(c % base)
+            c //= base
+        if sum(d) == A:
+            out.append(tuple(d))
+    return out
+
+
+def spin_matrices(two_s: int):
+    """(sz, s+, s-) in the basis |a = 0..2s> with m = s - a (textbook matrices)."""
+    s = two_s / 2.0
+    n = two_s + 1
+    m = np.array([s - a for a in range(n)])
+    sz = np.diag(m)
+    sp = np.zeros((n, n))
+    for a in range(1, n):          # s+ |m> = sqrt(s(s+1) - m(m+1)) |m+1>; m+1 <-> a-1
+        mm = m[a]
+        sp[a - 1, a] = math.sqrt(s * (s + 1) - mm * (mm + 1))
+    return sz, sp, sp.T.copy()
+
+
+def dense_hamiltonian_full(n_sites: int, two_s: int, bonds: Bonds) -> np.ndarray:
+    """H = -sum_b J_b s_u.s_v on the full product space from Kronecker products.
+    Basis index of |a_1..a_N> = sum_k a_k (2s+1)^(k-1) (Eq. E-3-a)."""
+    sz, sp, sm = spin_matrices(two_s)
+    n = two_s + 1
+    eye = np.eye(n)
+
+    def site_op(op, k):
+        # a_1 varies fastest -> it is the last factor of the Kronecker product
+        mats = [eye] * n_sites
+        mats[k] = op
+        out = np.array([[1.0]])
+        for q in reversed(range(n_sites)):
+            out = np.kron(out, mats[q])
+        return out
+
+    dimf = n ** n_sites
+    H = np.zeros((dimf, dimf))
+    for u, v, J in zip(bonds.u, bonds.v, bonds.J):
+        ss = (site_op(sz, u) @ site_op(sz, v)
+              + 0.5 * (site_op(sp, u) @ site_op(sm, v) + site_op(sm, u) @ site_op(sp, v)))
+        H -= J * ss
+    return H
+
+
+def dense_hamiltonian_sector(n_sites: int, two_s: int, A: int, bonds: Bonds) -> np.ndarray:
+    """The block of dense_hamiltonian_full on the sorted sector states."""
+    Hf = dense_hamiltonian_full(n_sites, two_s, bonds)
+    base = two_s + 1
+    idx = [sum(d[k] * base ** k for k in range(n_sites))
+           for d in full_basis_sorted(n_sites, two_s, A)]
+    return Hf[np.ix_(idx, idx)]
+
+
+# ----------------------------------------------------------------------------------------
+# Ground state, its gradient, and the finite-temperature Lanczos estimator
+# ----------------------------------------------------------------------------------------
+
+def ground_state(basis: Basis, bonds: Bonds, v0: np.ndarray, steps: int):
+    """Lanczos E0 and psi0: a first pass gives T, a library eigensolver gives its lowest
+    eigenvector c, a second pass accumulates psi0 = sum_j c_j v_j (normalised)."""
+    from scipy.linalg import eigh_tridiagonal
+    al, be = basis.lanczos(bonds, v0, steps)
+    m = len(al)
+    if m == 1:
+        w, c = np.array([al[0]]), np.ones((1, 1))
+    else:
+        w, c = eigh_tridiagonal(al, be[: m - 1])
+    al2, be2, psi = basis.lanczos(bonds, v0, m, coef=c[:, 0])
+    psi = psi / np.linalg.norm(psi)
+    return float(tridiag_lowest(al, be, 1)[0]), psi, (al, be)
+
+
+def e0_grad(basis: Basis, bonds: Bonds, v0: np.ndarray, steps: int):
+    """dE0/dJ_b = -<psi0| s_u.s_v |psi0> (Hellmann-Feynman on Eq. E-2-1)."""
+    e0, psi, _ = ground_state(basis, bonds, v0, steps)
+    return e0, -basis.bond_corr(bonds, psi, psi)
+
+
+def ftlm_sector(basis: Basis, bonds: Bonds, seed: int, R: int, steps: int):
+    """Per start vector r of one sector: Ritz values theta_j and weights tau_j (squared
+    first components of T's eigenvectors), the start vector being the +-1 vector of
+    stream (seed, A, r)."""
+    from scipy.linalg import eigh_tridiagonal
+    res = []
+    for r in range(R):
+        v0 = start_pm1(stream_seed(seed, basis.A, r), basis.dim)
+        al, be = basis.lanczos(bonds, v0, steps)
+        m = len(al)
+        if m == 1:
+            th, c = np.array([al[0]]), np.ones((1, 1))
+        else:
+            th, c = eigh_tridiagonal(al, be[: m - 1])
+        res.append((th, c[0, :] ** 2, al, be))
+    return res
+
+
+def ftlm_thermo(per_sector: list, temps: Sequence[float]):
+    """Finite-temperature Lanczos (Jaklic-Prelovsek) estimator over sectors:
+    Z(T) = sum_A (D_A/R) sum_r sum_j tau_rj exp(-theta_rj/T),
+    E(T) = [same with theta_rj inside] / Z.  per_sector is a list of (D_A, results) with
+    results a list of (theta, tau, ...) per start vector.  Energies are shifted by the
+    lowest Ritz value for the exponentials; returns (Z, E, e_ref) with the true
+    Z = Z * exp(-e_ref / T)."""
+    e_ref = min(float(np.min(th)) for (_, lst) in per_sector for (th, tau, *_) in lst)
+    Z = np.zeros(len(temps))
+    EZ = np.zeros(len(temps))
+    for (dim, lst) in per_sector:
+        R = len(lst)
+        for (th, tau, *_) in lst:
+            for k, T in enumerate(temps):
+                wgt = tau * np.exp(-(th - e_ref) / T)
+                Z[k] += dim / R * float(np.sum(wgt))
+                EZ[k] += dim / R * float(np.sum(wgt * th))
+    return Z, EZ / Z, e_ref
