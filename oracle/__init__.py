@@ -319,12 +319,33 @@ def dense_hamiltonian_sector(n_sites: int, two_s: int, A: int, bonds: Bonds) -> 
 # Ground state, its gradient, and the finite-temperature Lanczos estimator
 # ----------------------------------------------------------------------------------------
 
+def converged_length(al: np.ndarray, be: np.ndarray, tol: float = 1e-10) -> int:
+    """Shortest leading T_k whose lowest Ritz pair has converged: the residual norm of a
+    Ritz pair of T_k is beta_k |s_k| (s_k the last component of its normalised
+    eigenvector); take the first k with beta_k |s_k| <= tol * max(1, |theta|), else m.
+    Stopping there keeps ghost copies of the ground state (which appear after
+    convergence without re-orthogonalisation) out of T."""
+    from scipy.linalg import eigh_tridiagonal
+    m = len(al)
+    for k in range(1, m + 1):
+        if k == 1:
+            th, s = al[0], 1.0
+        else:
+            w, c = eigh_tridiagonal(al[:k], be[: k - 1], select="i", select_range=(0, 0))
+            th, s = w[0], c[k - 1, 0]
+        if be[k - 1] * abs(s) <= tol * max(1.0, abs(th)):
+            return k
+    return m
+
+
 def ground_state(basis: Basis, bonds: Bonds, v0: np.ndarray, steps: int):
-    """Lanczos E0 and psi0: a first pass gives T, a library eigensolver gives its lowest
-    eigenvector c, a second pass accumulates psi0 = sum_j c_j v_j (normalised)."""
+    """Lanczos E0 and psi0: a first pass gives T, cut at the converged length (see
+    converged_length); a library eigensolver gives its lowest eigenvector c, a second pass
+    accumulates psi0 = sum_j c_j v_j (normalised)."""
     from scipy.linalg import eigh_tridiagonal
     al, be = basis.lanczos(bonds, v0, steps)
-    m = len(al)
+    m = converged_length(al, be)
+    al, be = al[:m], be[:m]
     if m == 1:
         w, c = np.array([al[0]]), np.ones((1, 1))
     else:
