@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark: Lanczos steps on the s = 1/2 J1-J2 ring N = 32 (J1 = -1, J2 = -0.5),
+sector M = 0 (dim C(32,16) = 601,080,390), FP64 vectors.
+
+A step is one full Lanczos iteration through the C ABI: the row matvec with its fused
+epilogue (u = H v_j - beta v_{j-1}, alpha_j partials), the alpha reduction, the update
+(w = u - alpha v_j, |w|^2 partials) and the beta reduction.  The metric is Gnnz/s: the
+non-zero matrix elements one product applies (20,456,122,950 here) per step, over the
+timed steps.  The vectors (2 x 4.8 GB) are far larger than L2, so no L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload j1j2_ring32|ring24_randJ|ring16]
+
+--impl reference times the CPU oracle (test infrastructure, the only baseline: the paper
+ships no code) on the host cores, on bounded row samples of the same workload.
+Under torchrun (N > 1) every rank runs an independent replica (the sector product needs
+no exchange between replicas); value = all ranks' work / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H(M) matvec Gnnz/s"
+UNIT = "Gnnz/s"
+
+WORKLOADS = {
+    # name: (factory, nnz per product); nnz = dim + number of allowed exchange hops
+    "j1j2_ring32": ("j1j2_ring32", 20456122950),
+    "ring24_randJ": ("ring24_randJ", 70425628),
+    "ring16": ("ring16", 122694),
+}
+
+# bytes one product must move at minimum: read x once, write y once (FP64)
+ALGO_BYTES_PER_ROW = 16
+
+
+def instance(name):
+    from paper_0706_3293_gb300 import workloads as W
+    return {"j1j2_ring32": W.j1j2_ring32, "ring24_randJ": W.ring24_random_j, "ring16": W.ring16}[name]()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_0706_3293_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def read_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes of the kernel from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = kernel_source_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[3] == cur:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        def rd():
+            for line in self.proc.stdout:
+                self.rows.append([c.strip() for c in line.split(",")])
+        self.thread = threading.Thread(target=rd, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[4 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(inst, nnz_total, target_s=15.0):
+    """The oracle's row matvec on a bounded contiguous sample of rows, all host cores."""
+    import numpy as np
+    import oracle
+    ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
+    bonds = oracle.Bonds(inst.u, inst.v, inst.J)
+    x = oracle.start_uniform(inst.seed, ob.dim)
+    mid = ob.dim // 3
+    pilot = min(ob.dim, 200000)
+    t0 = time.perf_counter()
+    ob.matvec_rows(bonds, x, mid if mid + pilot <= ob.dim else 0, (mid if mid + pilot <= ob.dim else 0) + pilot)
+    rate = pilot / max(time.perf_counter() - t0, 1e-6)
+    n = int(min(ob.dim, max(pilot, rate * target_s)))
+    r0 = min(mid, ob.dim - n)
+    t0 = time.perf_counter()
+    ob.matvec_rows(bonds, x, r0, r0 + n)
+    dt = time.perf_counter() - t0
+    nnz = ob.count_nnz(bonds, r0, r0 + n)
+    del x
+    return {"value": nnz / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"rows [{r0}, {r0 + n}) of one FP64 product ({n} of {ob.dim} rows, "
+                      f"{nnz} nnz, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    inst = instance(args.workload)
+    ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
+    bonds = oracle.Bonds(inst.u, inst.v, inst.J)
+    x = oracle.start_uniform(inst.seed, ob.dim)
+    # one step = one oracle product over a bounded row sample sized to ~3 s
+    pilot = min(ob.dim, 100000)
+    r0 = ob.dim // 3 if ob.dim // 3 + pilot <= ob.dim else 0
+    t0 = time.perf_counter()
+    ob.matvec_rows(bonds, x, r0, r0 + pilot)
+    rate = pilot / max(time.perf_counter() - t0, 1e-6)
+    n = int(min(ob.dim, max(pilot, rate * 3.0)))
+    r0 = min(r0, ob.dim - n)
+    nnz = ob.count_nnz(bonds, r0, r0 + n)
+    for _ in range(args.warmup):
+        ob.matvec_rows(bonds, x, r0, r0 + n)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ob.matvec_rows(bonds, x, r0, r0 + n)
+    dt = time.perf_counter() - t0
+    val = nnz * args.steps / dt / 1e9
+    sample = f"rows [{r0}, {r0 + n}) of {ob.dim} per step ({nnz} nnz), FP64"
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": inst.name, "dim": ob.dim, "n_sites": inst.n_sites,
+                                          "two_s": inst.two_s, "two_m": inst.two_m, "l2": "inputs larger than L2"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0706_3293_gb300 import api
+
+    inst = instance(args.workload)
+    nnz = WORKLOADS[args.workload][1]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    b = api.Basis(inst.n_sites, inst.two_s, inst.two_m)
+    bl = api.bonds_of(inst)
+    total = args.warmup + args.steps
+    st = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing ----
+    run = api.LanczosRun(b, bl, total, seed=inst.seed)
+    for _ in range(args.warmup):
+        run.step()
+    barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    ev[0].record(st)
+    for k in range(args.steps):
+        run.substep(0)
+        ev[2 * k + 1].record(st)
+        run.substep(1)
+        ev[2 * k + 2].record(st)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    total_ms = ev[0].elapsed_time(ev[-1])
+    mv_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
+    al, be, rc = run.read()
+    run.close()
+    del run
+    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    t_max = float(t_local.item())
+    value = nnz * args.steps * ws / (t_max * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers ----
+    x_host = torch.empty(b.dim, dtype=torch.float64, pin_memory=True)
+    x_host.copy_(api.start_vector(b, inst.seed).cpu())
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    v0 = x_host.to(dev, non_blocking=True)
+    run2 = api.LanczosRun(b, bl, args.steps, v0=v0)
+    d2h = 0
+    for k in range(args.steps):
+        run2.step()
+        a2, b2, _ = run2.read()      # the step's result (alpha_j, beta_j) back on the host
+        d2h += 16
+    e1.record(st)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    run2.close()
+    del run2, v0
+    t_e2e = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_val = nnz * args.steps * ws / (float(t_e2e.item()) * 1e-3) / 1e9
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    peak, peak_src = read_peaks()
+    mv_mean = float(np.mean(mv_ms))
+    achieved = ALGO_BYTES_PER_ROW * b.dim / (mv_mean * 1e-3) / 1e9
+    traffic = read_traffic("k_lz_matvec", inst.name)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": inst.name, "n_sites": inst.n_sites, "two_s": inst.two_s,
+                   "two_m": inst.two_m, "dim": b.dim, "nnz_per_product": nnz,
+                   "bonds": inst.n_bonds, "start_seed": inst.seed, "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (2 x %.1f GB vectors)" % (b.dim * 8 / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_lz_matvec", "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": ALGO_BYTES_PER_ROW * b.dim,
+                     "mean_launch_ms": mv_mean},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": b.dim * 8 / args.steps,
+                "d2h_bytes_per_step": 16},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "lanczos": {"alpha_last": float(al[-1]) if len(al) else None,
+                    "steps_done": int(len(al)), "status": int(rc)},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(inst, nnz)
+    print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="j1j2_ring32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

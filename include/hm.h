@@ -1,0 +1,179 @@
+/*
+ * hm.h -- C ABI of the GB300 sector Lanczos library (libhm.so).
+ *
+ * Implements the hot path of Schnack, Hage and Schmidt, "Optimized implementation of the
+ * Lanczos method for magnetic systems" (arXiv:0706.3293): the matrix-free product
+ * y = H x of the isotropic Heisenberg Hamiltonian, Eq. (E-2-1),
+ *     H = - sum_b J_b s_{u_b} . s_{v_b},
+ * restricted to one sector H(M) of fixed total magnetic quantum number (Sec. 3), in the
+ * row-oriented form of Eq. (E-4-b) (Sec. 4), with the basis states numbered by the
+ * paper's direct coding built on the dimension table D(N, A), Eq. (E-3-c), and the
+ * decode/encode rules of Sec. 3.1 and 3.2; and the Lanczos recurrence built on it.
+ *
+ * Conventions shared by every entry point
+ *   - Status: every function returns an int: HM_OK (0) on success, a positive
+ *     informational code (HM_BREAKDOWN, HM_DEGENERATE) when the result is valid but
+ *     noteworthy, a negative HM_E* code on error.  hm_last_error() returns a message for
+ *     the last failing call of the calling host thread.  After HM_ECUDA the CUDA context
+ *     may be unusable (a sticky device error).
+ *   - Sites are numbered 0..n_sites-1.  A state is the digit string a_k = s - m_k in
+ *     0..2s (Sec. 2); site k is digit position k, position n_sites-1 the most
+ *     significant of the lexicographic order (Eq. E-3-a: a_1 varies fastest).
+ *   - Sector: two_s = 2s (1..7), two_m = 2M; n_sites*two_s - two_m must be even and
+ *     |M| <= N s.  The digit sum is A = N s - M.
+ *   - Indices are 0-based (the paper's index minus one), dimension < 2^63.
+ *   - Bonds: n_bonds entries (u[b], v[b], J[b]), 0 <= u, v < n_sites, u != v, at most
+ *     HM_MAX_BONDS; each entry is one term -J_b s_u.s_v (a pair listed twice is summed).
+ *     Bond arrays and all outputs documented "host" are host memory.
+ *   - Vectors ("device") are caller-owned device memory on the current CUDA device,
+ *     dense, row-major [dim][nvec], element type HM_F64 (double) or HM_F32 (float),
+ *     aligned to the element size (16 bytes for nvec > 1).  Input and output vectors
+ *     must not overlap.
+ *   - stream is a cudaStream_t passed as void* (NULL: the legacy default stream).
+ *     Calls without host results only enqueue work; calls with host results
+ *     synchronise that stream before returning.
+ *   - Workspace: functions that need scratch take a caller-owned device buffer
+ *     (work, work_bytes); the matching *_workspace function gives the size.  The
+ *     library allocates device memory only for the small per-basis tables
+ *     (basis_build) and never frees caller memory.
+ */
+#ifndef HM_H
+#define HM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HM_OK = 0,
+    HM_BREAKDOWN = 1,     /* Lanczos stopped early: beta_j below the breakdown threshold */
+    HM_DEGENERATE = 2,    /* ground state (near-)degenerate: dE0/dJ is not unique       */
+    HM_EINVAL = -1,       /* bad argument                                               */
+    HM_EPARITY = -2,      /* N*2s - 2M odd, or |M| > N s                                */
+    HM_EOVERFLOW = -3,    /* a dimension or table entry does not fit in 63 bits         */
+    HM_ECUDA = -4,        /* a CUDA runtime call failed                                 */
+    HM_ENOMEM = -5,       /* host allocation failed                                     */
+    HM_ETIMEOUT = -6,     /* a device-side wait gave up (bounded spin) -- no hang       */
+    HM_EWORKSPACE = -7    /* workspace missing or too small                             */
+};
+
+enum { HM_F64 = 0, HM_F32 = 1 };
+
+#define HM_MAX_BONDS 512
+#define HM_MAX_SITES 64
+
+typedef struct hm_basis hm_basis;      /* library-owned: tables of one sector      */
+typedef struct hm_lanczos hm_lanczos;  /* library-owned: state of one Lanczos run  */
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *hm_last_error(void);
+
+/* ---- host-only helpers (no GPU needed) ---------------------------------------------- */
+
+/* D(N, A) of Eq. (E-3-c) for the sector (n_sites, two_s, two_m): the number of basis
+ * states of H(M) (Sec. 3).  HM_EPARITY / HM_EINVAL / HM_EOVERFLOW as above. */
+int basis_dim_query(int n_sites, int two_s, int two_m, int64_t *dim);
+
+/* Validates a bond list against n_sites (ranges, u != v, count, finite J). */
+int bonds_check(int n_sites, int n_bonds, const int32_t *u, const int32_t *v, const double *J);
+
+/* ---- basis (Sec. 3) ------------------------------------------------------------------- */
+
+/* Builds D(k, a) by Eq. (E-3-c) and the per-position rank tables
+ * CD[p][S][a] = sum_{n<a} D(p, S - n) (the inner sums of the Sec. 3.2 encoding) on the
+ * host, and uploads them to the current device.  *out is library-owned; free it with
+ * basis_free. */
+int basis_build(int n_sites, int two_s, int two_m, hm_basis **out);
+int basis_free(hm_basis *basis);
+int basis_dim(const hm_basis *basis, int64_t *dim);
+
+/* Test hooks of the codec (Sec. 3.1 decode, Sec. 3.2 encode).  States are packed
+ * digits: digit k in bits [k*b, k*b+b) of a uint64, b = 1 for 2s = 1, 2 for 2s <= 3,
+ * 4 otherwise.  idx (device int64[n]) <-> states (device uint64[n]).  decode of an index
+ * outside [0, dim) and encode of a state outside the sector give -1 / ~0ull. */
+int basis_encode(const hm_basis *basis, const uint64_t *states, int64_t *idx, int64_t n,
+                 void *stream);
+int basis_decode(const hm_basis *basis, const int64_t *idx, uint64_t *states, int64_t n,
+                 void *stream);
+
+/* ---- the product y = H x: Eq. (E-4-b) ------------------------------------------------ */
+
+/* y = H(J) x for nvec vectors at once (row-major [dim][nvec], 1 <= nvec <= 64).  Each
+ * output row decodes its own index, applies every bond to its own state and gathers x
+ * at the encoded targets (Sec. 4); rows never write each other's output.  dtype HM_F64
+ * or HM_F32 for both x and y. */
+int matvec(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
+           const double *J, const void *x, void *y, int dtype, int nvec, void *stream);
+
+/* Adjoint of the coupling dependence: out[b] = sum_i g_i [(s_u . s_v) x]_i for every
+ * bond b (device double[n_bonds]), so that d(g^T H x)/dJ_b = -out[b] (H is linear in
+ * J, Eq. E-2-1).  g, x: device vectors of dtype; nvec must be 1.  Deterministic:
+ * fixed-order two-stage reduction in double.  work: bond_corr_workspace bytes. */
+int bond_corr_workspace(const hm_basis *basis, int n_bonds, size_t *bytes);
+int bond_corr(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
+              const void *g, const void *x, double *out, int dtype, void *work,
+              size_t work_bytes, void *stream);
+
+/* Seeded start vectors (device, dtype, nvec = 1).  kind 0: uniform on [-1, 1),
+ * x_t = 2 (o_t >> 11) 2^-53 - 1; kind 1: +-1, x_t = -1 if bit 63 of o_t is set;
+ * o_t = output t of SplitMix64 (Steele, Lea, Flood 2014) seeded with seed.  HM_F32
+ * rounds the double value to nearest. */
+int start_vector(const hm_basis *basis, uint64_t seed, int kind, void *x, int dtype,
+                 void *stream);
+
+/* ---- Lanczos --------------------------------------------------------------------------- */
+/* Recurrence (three-term, Paige order, no re-orthogonalisation):
+ *   v_1 = v0/|v0|;  u = H v_j - beta_{j-1} v_{j-1};  alpha_j = v_j . u;
+ *   w = u - alpha_j v_j;  beta_j = |w|;  v_{j+1} = w / beta_j.
+ * Breakdown after step j when beta_j <= 1e-12 * max(|alpha_1..alpha_j|,
+ * beta_1..beta_{j-1}); the run then stops with steps_done = j (status HM_BREAKDOWN).
+ * Vectors are stored in dtype; alpha, beta and all reductions are double (fixed-order,
+ * run-to-run deterministic); the tridiagonal eigensolve runs on the device in double. */
+
+/* Workspace bytes of a Lanczos run with at most max_steps steps. */
+int lanczos_workspace(const hm_basis *basis, int dtype, int max_steps, size_t *bytes);
+
+/* Creates a run: copies the bonds, sets v_1 from v0 (device vector of dtype, or NULL
+ * for the seeded uniform start vector), using caller workspace 'work'. */
+int lanczos_init(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
+                 const double *J, const void *v0, uint64_t seed, int dtype, int max_steps,
+                 void *work, size_t work_bytes, void *stream, hm_lanczos **out);
+/* Enqueues one fused step (matvec + alpha + update + beta) on stream; no host sync. */
+int lanczos_step(hm_lanczos *run, void *stream);
+/* One phase of a step: phase 0 = the product with its fused epilogue and alpha_j
+ * (u = H v_j - beta_{j-1} v_{j-1}), phase 1 = the update and beta_j (w, v_{j+1}).
+ * lanczos_step is phase 0 then phase 1; the split lets a caller time the product alone.
+ * Phases must alternate starting with 0. */
+int lanczos_substep(hm_lanczos *run, int phase, void *stream);
+/* Copies alpha[0..steps_done), beta[0..steps_done) (host) and steps_done; syncs. */
+int lanczos_read(hm_lanczos *run, double *alpha, double *beta, int *steps_done, void *stream);
+int lanczos_free(hm_lanczos *run);
+
+/* A whole run: steps steps captured in one CUDA graph and launched once, then the
+ * n_ritz lowest eigenvalues of T (Sturm bisection on the device).  Host outputs:
+ * alpha[steps], beta[steps], *steps_done, ritz[n_ritz].  Returns HM_OK or
+ * HM_BREAKDOWN. */
+int lanczos_run(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
+                const double *J, const void *v0, uint64_t seed, int steps, int dtype,
+                void *work, size_t work_bytes, double *alpha, double *beta,
+                int *steps_done, double *ritz, int n_ritz, void *stream);
+
+/* Ground energy and its coupling gradient dE0/dJ_b = -<psi0| s_u.s_v |psi0>
+ * (Hellmann-Feynman on Eq. E-2-1).  A first Lanczos pass gives T, its lowest
+ * eigenvector c is found on the device (bisection + inverse iteration), a second pass
+ * regenerates the same v_j and accumulates psi0 = sum_j c_j v_j, which is normalised;
+ * then bond_corr(psi0, psi0).  Host outputs: *e0, dE0_dJ[n_bonds]; psi_out (device,
+ * double[dim]) optional.  Returns HM_DEGENERATE when the gap to the second Ritz value is
+ * below 1e-8 |E0| (the gradient is then one of many).  Workspace: e0_grad_workspace. */
+int e0_grad_workspace(const hm_basis *basis, int n_bonds, int steps, size_t *bytes);
+int e0_grad(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
+            const double *J, const void *v0, uint64_t seed, int steps, void *work,
+            size_t work_bytes, double *e0, double *dE0_dJ, double *psi_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HM_H */

@@ -1,0 +1,204 @@
+// hm_internal.cuh -- shared definitions of libhm.so (not part of the C ABI).
+//
+// Sector tables, bond parameters, error reporting, the device codec (Sec. 3.1/3.2 of
+// Schnack, Hage, Schmidt) and deterministic block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hm.h"
+
+// ---------------------------------------------------------------------------------------
+// error reporting (thread-local message, see hm_last_error)
+// ---------------------------------------------------------------------------------------
+namespace hm {
+int fail(int code, const char *fmt, ...);   // records the message, returns code
+int cuda_fail(cudaError_t e, const char *what);
+}  // namespace hm
+
+#define HM_CUDA(call)                                                      \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return hm::cuda_fail(e_, #call);            \
+    } while (0)
+
+#define HM_TRY(call)                                                       \
+    do {                                                                   \
+        int rc_ = (call);                                                  \
+        if (rc_ < 0) return rc_;                                           \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------
+// sector tables
+// ---------------------------------------------------------------------------------------
+namespace hm {
+// CD[p][S][a] = sum_{n<a} D(p, S - n) for positions p = 0..N-1, prefix digit sums
+// S = 0..A and digits a = 0..2s+1 (the last entry is the total D(p+1, S)).  With
+// S_p = a_0 + ... + a_p, the 0-based index of a state is sum_{p>=1} CD[p][S_p][a_p]
+// (Sec. 3.2), and decode walks p = N-1..1 choosing the digit whose cumulative range
+// holds the residual index (Sec. 3.1).
+struct SectorView {
+    int N, S2, A, bits;     // bits per digit: 1, 2 or 4
+    int cd_w;               // S2 + 2
+    int cd_rowlen;          // (A + 1) * (S2 + 2)
+    int cd_len;             // N * cd_rowlen
+    int idx64;              // 1 when dim >= 2^32 (64-bit index arithmetic)
+    uint64_t dim;
+    const void *cd;         // device table, uint32_t (idx64 = 0) or uint64_t
+};
+
+}  // namespace hm
+
+struct hm_basis {
+    hm::SectorView view;
+    std::vector<uint64_t> D;        // host D(k, a), (N+1) x (S2*N+1)
+    std::vector<uint64_t> cd;       // host CD, cd_len entries
+    void *d_cd = nullptr;           // device copy (owned)
+    int device = 0;
+};
+
+namespace hm {
+
+int digit_bits(int two_s);
+// host helpers shared by the translation units
+int build_tables(int n_sites, int two_s, int two_m, hm_basis *b);
+int check_sector(int n_sites, int two_s, int two_m, int *A);
+
+// ---------------------------------------------------------------------------------------
+// bonds, normalised to p < q, passed to kernels by value
+// ---------------------------------------------------------------------------------------
+struct BondParams {
+    int nb;
+    int S2;
+    unsigned char p[HM_MAX_BONDS], q[HM_MAX_BONDS];
+    double jm[HM_MAX_BONDS];        // -J_b
+    // exchange factors 1/2 sqrt(radicand product), indexed [a_p * 8 + a_q]:
+    //   pdn: s+_p s-_q (a_p -> a_p - 1, a_q -> a_q + 1), radicand a_p(2s-a_p+1)(2s-a_q)(a_q+1)
+    //   pup: s-_p s+_q (a_p -> a_p + 1, a_q -> a_q - 1), radicand (2s-a_p)(a_p+1)a_q(2s-a_q+1)
+    double hs_pdn[64], hs_pup[64];
+};
+
+int make_bonds(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v,
+               const double *J, BondParams *out);
+
+// ---------------------------------------------------------------------------------------
+// device codec
+// ---------------------------------------------------------------------------------------
+#ifdef __CUDA_ARCH__
+#define HM_POPC64(x) __popcll(x)
+#else
+#define HM_POPC64(x) __builtin_popcountll(x)
+#endif
+
+__host__ __device__ __forceinline__ int dig(uint64_t w, int p, int bits) {
+    return (int)((w >> (p * bits)) & ((1u << bits) - 1u));
+}
+
+// sum of the digits at positions < p
+__host__ __device__ __forceinline__ int prefix_sum_below(uint64_t w, int p, int bits) {
+    uint64_t m = (p * bits >= 64) ? ~0ull : ((1ull << (p * bits)) - 1ull);
+    uint64_t x = w & m;
+    if (bits == 1) return HM_POPC64(x);
+    if (bits == 2) {
+        x = (x & 0x3333333333333333ull) + ((x >> 2) & 0x3333333333333333ull);
+        x = (x + (x >> 4)) & 0x0F0F0F0F0F0F0F0Full;
+        return (int)((x * 0x0101010101010101ull) >> 56);
+    }
+    // bits == 4: byte sums fit (<= 30), total <= 16*15 = 240 fits a byte
+    x = (x & 0x0F0F0F0F0F0F0F0Full) + ((x >> 4) & 0x0F0F0F0F0F0F0F0Full);
+    return (int)((x * 0x0101010101010101ull) >> 56);
+}
+
+template <class I>
+struct Codec {
+    const I *cd;   // shared or global copy of CD
+    int N, S2, A, bits, cd_w, cd_rowlen;
+
+    __host__ __device__ __forceinline__ I at(int p, int S, int a) const {
+        return cd[p * cd_rowlen + S * cd_w + a];
+    }
+
+    // Sec. 3.1: index -> packed digits
+    __host__ __device__ __forceinline__ uint64_t decode(I i) const {
+        uint64_t w = 0;
+        int S = A;
+        I r = i;
+        for (int p = N - 1; p >= 1; --p) {
+            const I *row = cd + p * cd_rowlen + S * cd_w;
+            int amax = S < S2 ? S : S2;
+            int a = 0;
+            while (a < amax && row[a + 1] <= r) ++a;
+            r -= row[a];
+            S -= a;
+            w |= (uint64_t)a << (p * bits);
+        }
+        return w | (uint64_t)S;
+    }
+
+    // Sec. 3.2: packed digits -> index
+    __host__ __device__ __forceinline__ I encode(uint64_t w) const {
+        int S = dig(w, 0, bits);
+        I r = 0;
+        for (int p = 1; p < N; ++p) {
+            int a = dig(w, p, bits);
+            S += a;
+            r += at(p, S, a);
+        }
+        return r;
+    }
+
+    // index change when the digit at p moves by dp (+1/-1) and the digit at q > p by -dp:
+    // only the rank terms of positions p..q change (prefix sums between them shift by dp)
+    __host__ __device__ __forceinline__ I delta(uint64_t w, int p, int q, int dp) const {
+        int S = prefix_sum_below(w, p, bits);
+        I d = 0;
+        for (int r = p; r <= q; ++r) {
+            int a = dig(w, r, bits);
+            S += a;
+            int a2 = a + (r == p ? dp : (r == q ? -dp : 0));
+            int S2n = S + (r < q ? dp : 0);
+            d += at(r, S2n, a2) - at(r, S, a);
+        }
+        return d;
+    }
+};
+
+// ---------------------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): output t of the generator seeded with s
+// is mix(s + (t+1) * 0x9E3779B97F4A7C15).
+// ---------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t sm64(uint64_t seed, uint64_t t) {
+    uint64_t z = seed + (t + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------------------------------
+// deterministic block reduction of doubles (fixed shuffle tree + fixed warp order)
+// ---------------------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *sh /* >= NT/32 */) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NT / 32; ++k) t += sh[k];
+    return t;  // valid in thread 0
+}
+
+// number of blocks used by grid-stride kernels: fixed per device so reductions are
+// reproducible run to run
+int grid_blocks(uint64_t rows, int threads);
+int sm_count();
+
+cudaStream_t as_stream(void *s);
+
+}  // namespace hm

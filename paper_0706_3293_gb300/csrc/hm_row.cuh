@@ -1,0 +1,69 @@
+// hm_row.cuh -- the per-row kernel body of Eq. (E-4-b): apply every bond term of
+// Eq. (E-2-1) to the row's own basis state, encode each target, gather x there.
+#pragma once
+
+#include "hm_internal.cuh"
+
+namespace hm {
+
+// Tables one CTA needs in shared memory: the exchange factors, then the rank table CD.
+template <class I>
+__device__ __forceinline__ I *stage_tables(const SectorView &sv, const BondParams &bp,
+                                           unsigned char *smem_raw, const double **pdn,
+                                           const double **pup) {
+    double *hs = reinterpret_cast<double *>(smem_raw);
+    I *cd = reinterpret_cast<I *>(smem_raw + 128 * sizeof(double));
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) {
+        hs[k] = bp.hs_pdn[k];
+        hs[64 + k] = bp.hs_pup[k];
+    }
+    for (int k = threadIdx.x; k < sv.cd_len; k += blockDim.x) cd[k] = ((const I *)sv.cd)[k];
+    __syncthreads();
+    *pdn = hs;
+    *pup = hs + 64;
+    return cd;
+}
+
+template <class I>
+__host__ __forceinline__ size_t row_smem_bytes(const SectorView &sv) {
+    return 128 * sizeof(double) + (size_t)sv.cd_len * sizeof(I);
+}
+
+// (H x)_i for NV vector columns of a row-major [dim][ld] array starting at column c0.
+// T is the storage type, Acc the accumulation type.  Returns the diagonal element in
+// *diag_out (as Acc) and the off-diagonal sum in acc[]; the caller forms
+// y = diag * x_i + acc, the same association as the oracle's row.
+template <class I, class T, class Acc, int NV>
+__device__ __forceinline__ void row_apply(const Codec<I> &c, const BondParams &bp,
+                                          const double *hs_pdn, const double *hs_pup,
+                                          I i, uint64_t w, const T *__restrict__ x, int ld,
+                                          int c0, Acc *acc, Acc *diag_out) {
+    const int S2 = c.S2, bits = c.bits;
+    const double half = 0.5 * S2;
+    double dg = 0.0;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = Acc(0);
+    for (int t = 0; t < bp.nb; ++t) {
+        const int p = bp.p[t], q = bp.q[t];
+        const int ap = dig(w, p, bits), aq = dig(w, q, bits);
+        const double jm = bp.jm[t];
+        dg += jm * (half - ap) * (half - aq);
+        if (ap >= 1 && aq < S2) {          // s+_p s-_q
+            const I j = i + c.delta(w, p, q, -1);
+            const Acc cf = (Acc)(jm * hs_pdn[ap * 8 + aq]);
+            const T *xr = x + (size_t)j * ld + c0;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += cf * (Acc)xr[k];
+        }
+        if (ap < S2 && aq >= 1) {          // s-_p s+_q
+            const I j = i + c.delta(w, p, q, +1);
+            const Acc cf = (Acc)(jm * hs_pup[ap * 8 + aq]);
+            const T *xr = x + (size_t)j * ld + c0;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += cf * (Acc)xr[k];
+        }
+    }
+    *diag_out = (Acc)dg;
+}
+
+}  // namespace hm

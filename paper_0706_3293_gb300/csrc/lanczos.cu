@@ -1,0 +1,638 @@
+// lanczos.cu -- the Lanczos recurrence around the row matvec, the tridiagonal
+// eigensolvers on the device, lanczos_run (one CUDA graph) and e0_grad.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "hm_row.cuh"
+
+namespace hm {
+
+int matvec_dev(const hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype,
+               int nvec, cudaStream_t st);
+int bond_corr_dev(const hm_basis *b, const BondParams &bp, const void *g, const void *x,
+                  double *out, int dtype, void *work, size_t work_bytes, double sign,
+                  const double *div, cudaStream_t st);
+size_t bond_corr_bytes(const hm_basis *b, int n_bonds);
+int start_vector_dev(uint64_t n, uint64_t seed, int kind, void *x, int dtype, cudaStream_t st);
+
+constexpr double LZ_TOL = 1e-12;     // breakdown: beta_j <= LZ_TOL * max(|alpha|, beta)
+constexpr int NT = 256;
+
+struct LzScalars {
+    double sigma_cur;    // v_j = sigma_cur * q_cur (stored vectors are unnormalised)
+    double sigma_prev;
+    double beta_prev;
+    double scale;        // max(|alpha_1..alpha_j|, beta_1..beta_{j-1})
+    double nrm2;         // scratch for norms
+    int j;               // steps done
+    int done;
+    int status;
+    int mconv;           // e0_grad: Krylov length used
+};
+
+// workspace carve-up (all segments 256-byte aligned)
+struct LzLayout {
+    size_t buf[2], part, sc, alpha, beta, ritz, psi, coef, res, gout, tri, bpart, total;
+};
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad, int nb) {
+    LzLayout L{};
+    const uint64_t dim = b->view.dim;
+    const size_t es = dtype == HM_F64 ? 8 : 4;
+    const int nblk = grid_blocks(dim, NT);
+    size_t o = 0;
+    L.buf[0] = o; o += al256(dim * es);
+    L.buf[1] = o; o += al256(dim * es);
+    L.part = o; o += al256((size_t)nblk * sizeof(double));
+    L.sc = o; o += al256(sizeof(LzScalars));
+    L.alpha = o; o += al256((size_t)max_steps * 8);
+    L.beta = o; o += al256((size_t)max_steps * 8);
+    L.ritz = o; o += al256(64 * 8);
+    if (grad) {
+        L.psi = o; o += al256(dim * 8);
+        L.coef = o; o += al256((size_t)max_steps * 8);
+        L.res = o; o += al256((size_t)max_steps * 8);
+        L.gout = o; o += al256((size_t)(nb > 0 ? nb : 1) * 8);
+        // per-length convergence scratch: max_steps x (5 * max_steps) doubles
+        L.tri = o; o += al256((size_t)max_steps * (5 * (size_t)max_steps + 4) * 8);
+        L.bpart = o; o += al256(bond_corr_bytes(b, nb));
+    }
+    L.total = o;
+    return L;
+}
+
+}  // namespace hm
+
+struct hm_lanczos {
+    const hm_basis *basis;
+    hm::BondParams bp;
+    int dtype, max_steps, host_j, next_phase;
+    unsigned char *work;
+    hm::LzLayout L;
+    hm::LzScalars *sc;
+    double *alpha, *beta, *part, *psi, *coef;
+};
+
+namespace hm {
+
+// ---------------------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(NT) k_sumsq(const T *__restrict__ q, uint64_t n, double *__restrict__ part) {
+    __shared__ double red[NT / 32];
+    double s = 0.0;
+    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
+        double v = (double)q[r];
+        s += v * v;
+    }
+    s = block_sum<NT>(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_lz_start(LzScalars *S, const double *__restrict__ part, int nblk) {
+    __shared__ double red[NT / 32];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += NT) s += part[k];
+    s = block_sum<NT>(s, red);
+    if (threadIdx.x == 0) {
+        S->sigma_cur = 1.0 / sqrt(s);
+        S->sigma_prev = 0.0;
+        S->beta_prev = 0.0;
+        S->scale = 0.0;
+        S->j = 0;
+        S->done = (s > 0.0) ? 0 : 1;
+        S->status = (s > 0.0) ? HM_OK : HM_EINVAL;
+        S->mconv = 0;
+    }
+}
+
+// u = sigma_cur * H q_cur - beta_prev * sigma_prev * q_prev, written over q_prev;
+// part[blk] = sum (sigma_cur q_cur) . u
+template <class I, class T, class Acc>
+__global__ void __launch_bounds__(NT)
+k_lz_matvec(SectorView sv, BondParams bp, const T *__restrict__ qc, T *__restrict__ qp,
+            const LzScalars *__restrict__ S, double *__restrict__ part) {
+    if (S->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[NT / 32];
+    const double *pdn, *pup;
+    const I *cd = stage_tables<I>(sv, bp, smem_raw, &pdn, &pup);
+    Codec<I> c{cd, sv.N, sv.S2, sv.A, sv.bits, sv.cd_w, sv.cd_rowlen};
+    const double sc = S->sigma_cur, bp_ = S->beta_prev * S->sigma_prev;
+    double dot = 0.0;
+    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < sv.dim; r += (uint64_t)gridDim.x * NT) {
+        const I i = (I)r;
+        const uint64_t w = c.decode(i);
+        Acc acc[1], dg;
+        row_apply<I, T, Acc, 1>(c, bp, pdn, pup, i, w, qc, 1, 0, acc, &dg);
+        const Acc hv = dg * (Acc)qc[r] + acc[0];
+        const T u = (T)(sc * (double)hv - bp_ * (double)qp[r]);
+        qp[r] = u;
+        dot += (sc * (double)qc[r]) * (double)u;
+    }
+    dot = block_sum<NT>(dot, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = dot;
+}
+
+__global__ void k_lz_alpha(LzScalars *S, const double *__restrict__ part, int nblk, double *alpha) {
+    if (S->done) return;
+    __shared__ double red[NT / 32];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += NT) s += part[k];
+    s = block_sum<NT>(s, red);
+    if (threadIdx.x == 0) {
+        alpha[S->j] = s;
+        S->scale = fmax(S->scale, fabs(s));
+    }
+}
+
+// w = u - alpha_j sigma_cur q_cur over q_prev; part = sum w^2; psi += coef_j v_j if psi
+template <class T>
+__global__ void __launch_bounds__(NT)
+k_lz_update(const T *__restrict__ qc, T *__restrict__ qp, uint64_t n, const LzScalars *__restrict__ S,
+            const double *__restrict__ alpha, double *__restrict__ part, double *__restrict__ psi,
+            const double *__restrict__ coef) {
+    if (S->done) return;
+    __shared__ double red[NT / 32];
+    const double as = alpha[S->j] * S->sigma_cur;
+    const double cj = psi ? coef[S->j] * S->sigma_cur : 0.0;
+    double s = 0.0;
+    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
+        const double q = (double)qc[r];
+        const T w = (T)((double)qp[r] - as * q);
+        qp[r] = w;
+        const double wd = (double)w;
+        s += wd * wd;
+        if (psi) psi[r] += cj * q;
+    }
+    s = block_sum<NT>(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_lz_beta(LzScalars *S, const double *__restrict__ part, int nblk, double *beta) {
+    if (S->done) return;
+    __shared__ double red[NT / 32];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += NT) s += part[k];
+    s = block_sum<NT>(s, red);
+    if (threadIdx.x == 0) {
+        const double b = sqrt(s);
+        beta[S->j] = b;
+        S->j += 1;
+        if (b <= LZ_TOL * S->scale) {
+            S->done = 1;
+            S->status = HM_BREAKDOWN;
+        } else {
+            S->scale = fmax(S->scale, b);
+            S->sigma_prev = S->sigma_cur;
+            S->sigma_cur = 1.0 / b;
+            S->beta_prev = b;
+        }
+    }
+}
+
+// ---- tridiagonal T (diagonal al[0..m), off-diagonal be[0..m-1)) ------------------------
+
+__device__ int sturm_count(int m, const double *al, const double *be, double x, double pivmin) {
+    int c = 0;
+    double q = al[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+        q = (al[i] - x) - be[i - 1] * be[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        if (q < 0) ++c;
+    }
+    return c;
+}
+
+// e-th lowest eigenvalue (1-based) by bisection of the Sturm count on the Gershgorin
+// interval, until the midpoint no longer moves
+__device__ double tri_eig(int m, const double *al, const double *be, int e) {
+    double lo = 1e308, hi = -1e308, bmax = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i < m - 1 ? fabs(be[i]) : 0.0);
+        lo = fmin(lo, al[i] - r);
+        hi = fmax(hi, al[i] + r);
+        if (i < m - 1) bmax = fmax(bmax, fabs(be[i]));
+    }
+    const double pivmin = 2.2250738585072014e-308 * fmax(1.0, bmax * bmax);
+    const double pad = 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + pivmin;
+    double a = lo - pad, c = hi + pad;
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (a + c);
+        if (mid <= a || mid >= c) break;
+        if (sturm_count(m, al, be, mid, pivmin) >= e) c = mid; else a = mid;
+    }
+    return 0.5 * (a + c);
+}
+
+// eigenvector of T for eigenvalue th by inverse iteration: three solves of
+// (T - th I) z = b with Gaussian elimination and partial pivoting (one extra
+// super-diagonal of fill-in); z normalised, returned in z[0..m)
+__device__ void tri_vec(int m, const double *al, const double *be, double th, double *z,
+                        double *d, double *du, double *du2, double *dl) {
+    if (m == 1) { z[0] = 1.0; return; }
+    double tnorm = 0.0;
+    for (int i = 0; i < m; ++i) tnorm = fmax(tnorm, fabs(al[i]) + (i > 0 ? fabs(be[i - 1]) : 0.0) + (i < m - 1 ? fabs(be[i]) : 0.0));
+    const double tiny = fmax(tnorm, 1e-300) * 2.220446049250313e-16;
+    for (int i = 0; i < m; ++i) z[i] = 1.0 / sqrt((double)m) * (1.0 + 1e-3 * (double)(i % 7));
+    for (int it = 0; it < 3; ++it) {
+        for (int i = 0; i < m; ++i) d[i] = al[i] - th;
+        for (int i = 0; i < m - 1; ++i) { du[i] = be[i]; dl[i] = be[i]; }
+        for (int i = 0; i < m; ++i) du2[i] = 0.0;
+        double *b = z;
+        for (int i = 0; i < m - 1; ++i) {
+            if (fabs(d[i]) >= fabs(dl[i])) {
+                if (d[i] == 0.0) d[i] = tiny;
+                const double f = dl[i] / d[i];
+                d[i + 1] -= f * du[i];
+                b[i + 1] -= f * b[i];
+            } else {
+                const double f = d[i] / dl[i];
+                d[i] = dl[i];
+                const double t = d[i + 1];
+                d[i + 1] = du[i] - f * t;
+                du[i] = t;
+                if (i < m - 2) {
+                    du2[i] = du[i + 1];
+                    du[i + 1] = -f * du[i + 1];
+                }
+                const double tb = b[i];
+                b[i] = b[i + 1];
+                b[i + 1] = tb - f * b[i + 1];
+            }
+        }
+        if (d[m - 1] == 0.0) d[m - 1] = tiny;
+        b[m - 1] = b[m - 1] / d[m - 1];
+        b[m - 2] = (b[m - 2] - du[m - 2] * b[m - 1]) / d[m - 2];
+        for (int i = m - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / d[i];
+        double nn = 0.0;
+        for (int i = 0; i < m; ++i) nn += b[i] * b[i];
+        nn = 1.0 / sqrt(nn);
+        for (int i = 0; i < m; ++i) b[i] *= nn;
+    }
+}
+
+__global__ void k_ritz(const LzScalars *S, const double *alpha, const double *beta, int n_ritz, double *ritz) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = S->j;
+    if (e >= n_ritz) return;
+    ritz[e] = (m >= 1 && e < m) ? tri_eig(m, alpha, beta, e + 1) : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// Convergence of the lowest Ritz pair of every leading T_k (k = 1..m): thread k computes
+// theta_1(T_k) and the last component s_k of its eigenvector; the residual norm of the
+// Ritz pair is beta_k |s_k|.  res[k-1] = beta_k |s_k| / max(1, |theta|).
+__global__ void k_conv_scan(const LzScalars *S, const double *alpha, const double *beta,
+                            double *scratch, int max_steps, double *res) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int m = S->j;
+    if (k > m) return;
+    double *z = scratch + (size_t)(k - 1) * (5 * (size_t)max_steps + 4);
+    double *d = z + max_steps, *du = d + max_steps, *du2 = du + max_steps, *dl = du2 + max_steps;
+    const double th = tri_eig(k, alpha, beta, 1);
+    tri_vec(k, alpha, beta, th, z, d, du, du2, dl);
+    res[k - 1] = beta[k - 1] * fabs(z[k - 1]) / fmax(1.0, fabs(th));
+}
+
+// picks the shortest converged Krylov length (res <= tol), or m; computes the lowest
+// eigenvector of T_mconv into coef, and e0 / e1 into ritz[0], ritz[1]
+__global__ void k_pick_and_vec(LzScalars *S, const double *alpha, const double *beta,
+                               double *scratch, int max_steps, const double *res, double tol,
+                               double *coef, double *ritz) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int m = S->j;
+    int mc = m;
+    for (int k = 1; k <= m; ++k)
+        if (res[k - 1] <= tol) { mc = k; break; }
+    S->mconv = mc;
+    double *d = scratch, *du = d + max_steps, *du2 = du + max_steps, *dl = du2 + max_steps;
+    const double th = tri_eig(mc, alpha, beta, 1);
+    ritz[0] = th;
+    ritz[1] = mc >= 2 ? tri_eig(mc, alpha, beta, 2) : __longlong_as_double(0x7ff0000000000000ll);
+    tri_vec(mc, alpha, beta, th, coef, d, du, du2, dl);
+    for (int k = mc; k < max_steps; ++k) coef[k] = 0.0;
+}
+
+__global__ void k_scale(double *__restrict__ v, uint64_t n, const LzScalars *S) {
+    const double f = 1.0 / sqrt(S->nrm2);
+    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) v[r] *= f;
+}
+
+__global__ void k_store_nrm2(LzScalars *S, const double *__restrict__ part, int nblk) {
+    __shared__ double red[NT / 32];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += NT) s += part[k];
+    s = block_sum<NT>(s, red);
+    if (threadIdx.x == 0) S->nrm2 = s;
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+template <class I, class T, class Acc>
+static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st) {
+    const SectorView &sv = R->basis->view;
+    T *b0 = (T *)(R->work + R->L.buf[0]);
+    T *b1 = (T *)(R->work + R->L.buf[1]);
+    T *qc = parity ? b1 : b0;
+    T *qp = parity ? b0 : b1;
+    const int nblk = grid_blocks(sv.dim, NT);
+    if (phase == 0) {
+        const size_t sm = row_smem_bytes<I>(sv);
+        k_lz_matvec<I, T, Acc><<<nblk, NT, sm, st>>>(sv, R->bp, qc, qp, R->sc, R->part);
+        k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->alpha);
+    } else {
+        k_lz_update<T><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, R->psi, R->coef);
+        k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta);
+    }
+    HM_CUDA(cudaGetLastError());
+    return HM_OK;
+}
+
+// raises the dynamic shared-memory limit of the product kernel (outside any capture)
+template <class I, class T, class Acc>
+static int prepare_t(const hm_basis *b) {
+    HM_CUDA(cudaFuncSetAttribute(k_lz_matvec<I, T, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)row_smem_bytes<I>(b->view)));
+    return HM_OK;
+}
+
+static int prepare(const hm_basis *b, int dtype) {
+    const bool i64 = b->view.idx64 != 0;
+    if (dtype == HM_F64) return i64 ? prepare_t<uint64_t, double, double>(b) : prepare_t<uint32_t, double, double>(b);
+    return i64 ? prepare_t<uint64_t, float, float>(b) : prepare_t<uint32_t, float, float>(b);
+}
+
+static int enqueue_phase(hm_lanczos *R, int phase, cudaStream_t st) {
+    const int parity = R->host_j & 1;
+    const bool i64 = R->basis->view.idx64 != 0;
+    int rc;
+    if (R->dtype == HM_F64)
+        rc = i64 ? enqueue_phase_t<uint64_t, double, double>(R, parity, phase, st)
+                 : enqueue_phase_t<uint32_t, double, double>(R, parity, phase, st);
+    else
+        rc = i64 ? enqueue_phase_t<uint64_t, float, float>(R, parity, phase, st)
+                 : enqueue_phase_t<uint32_t, float, float>(R, parity, phase, st);
+    if (rc == HM_OK && phase == 1) R->host_j += 1;
+    return rc;
+}
+
+static int enqueue_step(hm_lanczos *R, cudaStream_t st) {
+    HM_TRY(enqueue_phase(R, 0, st));
+    return enqueue_phase(R, 1, st);
+}
+
+// (re)starts the recurrence: q_cur = v0 (or seeded), q_prev = 0, sigma = 1/|v0|
+static int enqueue_start(hm_lanczos *R, const void *v0, uint64_t seed, cudaStream_t st) {
+    const SectorView &sv = R->basis->view;
+    const size_t es = R->dtype == HM_F64 ? 8 : 4;
+    void *b0 = R->work + R->L.buf[0];
+    void *b1 = R->work + R->L.buf[1];
+    if (v0) HM_CUDA(cudaMemcpyAsync(b0, v0, sv.dim * es, cudaMemcpyDeviceToDevice, st));
+    else HM_TRY(start_vector_dev(sv.dim, seed, 0, b0, R->dtype, st));
+    HM_CUDA(cudaMemsetAsync(b1, 0, sv.dim * es, st));
+    const int nblk = grid_blocks(sv.dim, NT);
+    if (R->dtype == HM_F64) k_sumsq<double><<<nblk, NT, 0, st>>>((const double *)b0, sv.dim, R->part);
+    else k_sumsq<float><<<nblk, NT, 0, st>>>((const float *)b0, sv.dim, R->part);
+    k_lz_start<<<1, NT, 0, st>>>(R->sc, R->part, nblk);
+    HM_CUDA(cudaGetLastError());
+    R->host_j = 0;
+    R->next_phase = 0;
+    return HM_OK;
+}
+
+static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v,
+                     const double *J, int dtype, int max_steps, void *work, size_t work_bytes,
+                     bool grad, hm_lanczos **out) {
+    if (!b || !out) return fail(HM_EINVAL, "NULL argument");
+    if (dtype != HM_F64 && dtype != HM_F32) return fail(HM_EINVAL, "bad dtype");
+    if (max_steps < 1 || max_steps > 100000) return fail(HM_EINVAL, "steps must be in 1..100000");
+    hm_lanczos *R = new (std::nothrow) hm_lanczos();
+    if (!R) return fail(HM_ENOMEM, "host allocation failed");
+    int rc = make_bonds(b, n_bonds, u, v, J, &R->bp);
+    if (rc < 0) { delete R; return rc; }
+    R->basis = b;
+    R->dtype = dtype;
+    R->max_steps = max_steps;
+    R->L = lz_layout(b, dtype, max_steps, grad, n_bonds);
+    if (!work || work_bytes < R->L.total || ((uintptr_t)work & 255)) {
+        size_t need = R->L.total;
+        delete R;
+        return fail(HM_EWORKSPACE, "workspace must be >= %zu bytes, 256-byte aligned", need);
+    }
+    rc = prepare(b, dtype);
+    if (rc < 0) { delete R; return rc; }
+    R->work = (unsigned char *)work;
+    R->sc = (LzScalars *)(R->work + R->L.sc);
+    R->alpha = (double *)(R->work + R->L.alpha);
+    R->beta = (double *)(R->work + R->L.beta);
+    R->part = (double *)(R->work + R->L.part);
+    R->psi = nullptr;
+    R->coef = grad ? (double *)(R->work + R->L.coef) : nullptr;
+    *out = R;
+    return HM_OK;
+}
+
+// steps launched as one captured graph (the recurrence state lives on the device, so
+// no host round trip is needed between steps)
+static int run_steps_graph(hm_lanczos *R, int steps, cudaStream_t st) {
+    cudaStream_t cap;
+    HM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    int rc = HM_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < steps && rc == HM_OK; ++k) rc = enqueue_step(R, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (rc == HM_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
+    } else {
+        rc = cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    if (rc == HM_OK) {
+        e = cudaGraphInstantiate(&ge, g, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+    }
+    if (rc == HM_OK) {
+        e = cudaGraphLaunch(ge, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphLaunch");
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    return rc;
+}
+
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" {
+
+int lanczos_workspace(const hm_basis *b, int dtype, int max_steps, size_t *bytes) {
+    if (!b || !bytes) return fail(HM_EINVAL, "NULL argument");
+    if (dtype != HM_F64 && dtype != HM_F32) return fail(HM_EINVAL, "bad dtype");
+    if (max_steps < 1) return fail(HM_EINVAL, "max_steps must be >= 1");
+    *bytes = lz_layout(b, dtype, max_steps, false, 0).total;
+    return HM_OK;
+}
+
+int e0_grad_workspace(const hm_basis *b, int n_bonds, int steps, size_t *bytes) {
+    if (!b || !bytes) return fail(HM_EINVAL, "NULL argument");
+    if (steps < 1) return fail(HM_EINVAL, "steps must be >= 1");
+    *bytes = lz_layout(b, HM_F64, steps, true, n_bonds).total;
+    return HM_OK;
+}
+
+int lanczos_init(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v,
+                 const double *J, const void *v0, uint64_t seed, int dtype, int max_steps,
+                 void *work, size_t work_bytes, void *stream, hm_lanczos **out) {
+    if (out) *out = nullptr;
+    hm_lanczos *R = nullptr;
+    HM_TRY(lz_create(b, n_bonds, u, v, J, dtype, max_steps, work, work_bytes, false, &R));
+    int rc = enqueue_start(R, v0, seed, as_stream(stream));
+    if (rc < 0) { delete R; return rc; }
+    *out = R;
+    return HM_OK;
+}
+
+int lanczos_step(hm_lanczos *R, void *stream) {
+    if (!R) return fail(HM_EINVAL, "run is NULL");
+    if (R->host_j >= R->max_steps) return fail(HM_EINVAL, "max_steps (%d) reached", R->max_steps);
+    if (R->next_phase != 0) return fail(HM_EINVAL, "a step is half done (phase 1 pending)");
+    return enqueue_step(R, as_stream(stream));
+}
+
+int lanczos_substep(hm_lanczos *R, int phase, void *stream) {
+    if (!R) return fail(HM_EINVAL, "run is NULL");
+    if (phase != 0 && phase != 1) return fail(HM_EINVAL, "phase must be 0 or 1");
+    if (phase != R->next_phase) return fail(HM_EINVAL, "phases must alternate 0, 1, 0, ...");
+    if (R->host_j >= R->max_steps) return fail(HM_EINVAL, "max_steps (%d) reached", R->max_steps);
+    HM_TRY(enqueue_phase(R, phase, as_stream(stream)));
+    R->next_phase = 1 - phase;
+    return HM_OK;
+}
+
+int lanczos_read(hm_lanczos *R, double *alpha, double *beta, int *steps_done, void *stream) {
+    if (!R) return fail(HM_EINVAL, "run is NULL");
+    cudaStream_t st = as_stream(stream);
+    LzScalars S;
+    HM_CUDA(cudaMemcpyAsync(&S, R->sc, sizeof S, cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    if (steps_done) *steps_done = S.j;
+    if (alpha && S.j > 0) HM_CUDA(cudaMemcpy(alpha, R->alpha, S.j * 8, cudaMemcpyDeviceToHost));
+    if (beta && S.j > 0) HM_CUDA(cudaMemcpy(beta, R->beta, S.j * 8, cudaMemcpyDeviceToHost));
+    if (S.status < 0) return fail(S.status, "Lanczos start vector has zero norm");
+    return S.status;
+}
+
+int lanczos_free(hm_lanczos *R) {
+    delete R;
+    return HM_OK;
+}
+
+int lanczos_run(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v,
+                const double *J, const void *v0, uint64_t seed, int steps, int dtype,
+                void *work, size_t work_bytes, double *alpha, double *beta, int *steps_done,
+                double *ritz, int n_ritz, void *stream) {
+    if (n_ritz < 0 || n_ritz > 64 || (n_ritz > 0 && !ritz)) return fail(HM_EINVAL, "n_ritz must be in 0..64");
+    hm_lanczos *R = nullptr;
+    HM_TRY(lanczos_init(b, n_bonds, u, v, J, v0, seed, dtype, steps, work, work_bytes, stream, &R));
+    cudaStream_t st = as_stream(stream);
+    int rc = run_steps_graph(R, steps, st);
+    double *d_ritz = (double *)(R->work + R->L.ritz);
+    if (rc == HM_OK && n_ritz > 0) {
+        k_ritz<<<1, 64, 0, st>>>(R->sc, R->alpha, R->beta, n_ritz, d_ritz);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "k_ritz");
+    }
+    if (rc == HM_OK) rc = lanczos_read(R, alpha, beta, steps_done, stream);
+    if (rc >= 0 && n_ritz > 0) {
+        cudaError_t e = cudaMemcpy(ritz, d_ritz, n_ritz * 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "ritz copy");
+    }
+    delete R;
+    return rc;
+}
+
+int e0_grad(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, const double *J,
+            const void *v0, uint64_t seed, int steps, void *work, size_t work_bytes, double *e0,
+            double *dE0_dJ, double *psi_out, void *stream) {
+    if (!e0 || (n_bonds > 0 && !dE0_dJ)) return fail(HM_EINVAL, "NULL output");
+    hm_lanczos *R = nullptr;
+    HM_TRY(lz_create(b, n_bonds, u, v, J, HM_F64, steps, work, work_bytes, true, &R));
+    cudaStream_t st = as_stream(stream);
+    const SectorView &sv = b->view;
+    const int nblk = grid_blocks(sv.dim, NT);
+    double *d_ritz = (double *)(R->work + R->L.ritz);
+    double *tri = (double *)(R->work + R->L.tri);
+    double *res = (double *)(R->work + R->L.res);
+    int rc = HM_OK;
+    // pass 1: T
+    rc = enqueue_start(R, v0, seed, st);
+    for (int k = 0; k < steps && rc == HM_OK; ++k) rc = enqueue_step(R, st);
+    if (rc == HM_OK) {
+        // residual of the lowest Ritz pair of every leading T_k, then the shortest
+        // converged length and the eigenvector of T there (no ghost copies yet)
+        k_conv_scan<<<(steps + 63) / 64, 64, 0, st>>>(R->sc, R->alpha, R->beta, tri, steps, res);
+        k_pick_and_vec<<<1, 1, 0, st>>>(R->sc, R->alpha, R->beta, tri, steps, res, 1e-10, R->coef, d_ritz);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "e0_grad: eigenvector");
+    }
+    // pass 2: the same recurrence from the same start, accumulating psi = sum_j c_j v_j
+    LzScalars S1{};
+    if (rc == HM_OK) {
+        cudaError_t e = cudaMemcpyAsync(&S1, R->sc, sizeof S1, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "e0_grad: read pass 1");
+        if (rc == HM_OK && S1.status < 0) rc = fail(S1.status, "Lanczos start vector has zero norm");
+    }
+    if (rc == HM_OK) {
+        R->psi = (double *)(R->work + R->L.psi);
+        cudaError_t e = cudaMemsetAsync(R->psi, 0, sv.dim * 8, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "memset psi");
+        if (rc == HM_OK) rc = enqueue_start(R, v0, seed, st);
+        for (int k = 0; k < S1.mconv && rc == HM_OK; ++k) rc = enqueue_step(R, st);
+    }
+    if (rc == HM_OK) {
+        k_sumsq<double><<<nblk, NT, 0, st>>>(R->psi, sv.dim, R->part);
+        k_store_nrm2<<<1, NT, 0, st>>>(R->sc, R->part, nblk);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "e0_grad: norm");
+    }
+    // dE0/dJ_b = -<psi| s_u.s_v |psi> / <psi|psi>
+    double *d_out = (double *)(R->work + R->L.gout);
+    if (rc == HM_OK && n_bonds > 0) {
+        std::vector<double> ones(n_bonds, 1.0);
+        BondParams bp1;
+        rc = make_bonds(b, n_bonds, u, v, ones.data(), &bp1);
+        if (rc == HM_OK)
+            rc = bond_corr_dev(b, bp1, R->psi, R->psi, d_out, HM_F64, R->work + R->L.bpart,
+                               bond_corr_bytes(b, n_bonds), -1.0, &R->sc->nrm2, st);
+    }
+    if (rc == HM_OK && psi_out) {
+        k_scale<<<nblk, NT, 0, st>>>(R->psi, sv.dim, R->sc);
+        cudaError_t e = cudaMemcpyAsync(psi_out, R->psi, sv.dim * 8, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "psi copy");
+    }
+    double rz[2] = {0, 0};
+    if (rc == HM_OK) {
+        cudaError_t e = cudaMemcpyAsync(rz, d_ritz, 16, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && n_bonds > 0) e = cudaMemcpyAsync(dE0_dJ, d_out, n_bonds * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "e0_grad: results");
+    }
+    delete R;
+    if (rc < 0) return rc;
+    *e0 = rz[0];
+    if (std::isfinite(rz[1]) && rz[1] - rz[0] < 1e-8 * std::fabs(rz[0])) return HM_DEGENERATE;
+    return HM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,317 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the same seeded
+inputs.  Tolerances: indices and states bit-exact; FP64 rows ||dy||/||y|| <= 1e-12;
+FP32 rows (FP32 storage and accumulation) ||dy||/||y|| <= 1e-5; E0 <= 1e-10 relative."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0706_3293_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL_F64 = 1e-12
+TOL_F32 = 1e-5
+TOL_E0 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def hm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0706_3293_gb300 import build
+    build.build()
+    from paper_0706_3293_gb300 import api
+    return api
+
+
+def obonds(inst):
+    return oracle.Bonds(inst.u, inst.v, inst.J)
+
+
+def pack(digits, bits):
+    w = 0
+    for k, a in enumerate(digits):
+        w |= int(a) << (k * bits)
+    return w
+
+
+def bits_of(two_s):
+    return 1 if two_s == 1 else (2 if two_s <= 3 else 4)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+SMALL = [
+    W.ring16(),
+    W.small_ring(18, -1.0, -0.5),
+    W.s1_random_graph(10, 21),
+    W.s1_random_graph_small(),
+    W.Instance("s32_N8_A6", 8, 3, 0, np.array([0, 1, 2, 3, 4, 5, 6, 7, 0, 2], np.int32),
+               np.array([1, 2, 3, 4, 5, 6, 7, 0, 5, 6], np.int32),
+               np.linspace(-1.2, 0.9, 10)),
+    W.Instance("s2_N6", 6, 4, 2, np.array([0, 1, 2, 3, 4, 5, 0], np.int32),
+               np.array([1, 2, 3, 4, 5, 0, 3], np.int32), np.linspace(-1.0, 0.5, 7)),
+]
+
+
+# ---- codec -------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("inst", SMALL[:5], ids=lambda i: i.name)
+def test_codec_all_indices(hm, inst):
+    b = hm.Basis(inst.n_sites, inst.two_s, inst.two_m)
+    ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
+    assert b.dim == ob.dim
+    idx = torch.arange(b.dim, dtype=torch.int64, device="cuda")
+    st = b.decode(idx).cpu().numpy()
+    bits = bits_of(inst.two_s)
+    step = max(1, b.dim // 3000)
+    for i in list(range(0, b.dim, step)) + [b.dim - 1]:
+        assert int(st[i]) == pack(ob.decode(i), bits), i
+    back = b.encode(torch.from_numpy(st).cuda()).cpu().numpy()
+    assert np.array_equal(back, np.arange(b.dim))
+
+
+def test_codec_worked_example(hm):
+    """Sec. 3.2 example: N = 4, s = 3/2, A = 6, |1,0,2,3> has 0-based index 41."""
+    b = hm.Basis(4, 3, 0)
+    st = torch.tensor([pack([1, 0, 2, 3], 2)], dtype=torch.int64, device="cuda")
+    assert int(b.encode(st)[0]) == 41
+    assert int(b.decode(torch.tensor([41], device="cuda"))[0]) == pack([1, 0, 2, 3], 2)
+
+
+def test_codec_rejects_outside(hm):
+    b = hm.Basis(6, 1, 0)
+    out = b.decode(torch.tensor([-1, b.dim, 0], dtype=torch.int64, device="cuda")).cpu()
+    assert int(out[0]) == -1 and int(out[1]) == -1
+    bad = torch.tensor([0b111, 0b1000111, 0b111000], dtype=torch.int64, device="cuda")
+    e = b.encode(bad).cpu()
+    assert int(e[0]) == 0 and int(e[1]) == -1 and int(e[2]) >= 0
+
+
+@pytest.mark.parametrize("n,two_s,two_m", [(32, 1, 0), (20, 2, 0)])
+def test_codec_full_size_sampled(hm, n, two_s, two_m):
+    b = hm.Basis(n, two_s, two_m)
+    ob = oracle.Basis(n, two_s, (n * two_s - two_m) // 2)
+    rng = np.random.default_rng(1)
+    idx = np.concatenate([[0, 1, 2, b.dim - 2, b.dim - 1], rng.integers(0, b.dim, 3000)])
+    st = b.decode(torch.from_numpy(idx).cuda()).cpu().numpy()
+    bits = bits_of(two_s)
+    for i, s in zip(idx, st):
+        assert int(s) == pack(ob.decode(int(i)), bits)
+    assert np.array_equal(b.encode(torch.from_numpy(st).cuda()).cpu().numpy(), idx)
+
+
+# ---- start vectors -----------------------------------------------------------------------
+
+def test_start_vectors_bitwise(hm):
+    b = hm.Basis(16, 1, 0)
+    for kind, ref in [(0, oracle.start_uniform(1001, b.dim)), (1, oracle.start_pm1(77, b.dim))]:
+        seed = 1001 if kind == 0 else 77
+        x = hm.start_vector(b, seed, kind).cpu().numpy()
+        assert np.array_equal(x, ref)
+        xf = hm.start_vector(b, seed, kind, dtype=torch.float32).cpu().numpy()
+        assert np.array_equal(xf, ref.astype(np.float32))
+
+
+# ---- matvec ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("inst", SMALL, ids=lambda i: i.name)
+def test_matvec_f64(hm, inst):
+    b = hm.Basis(inst.n_sites, inst.two_s, inst.two_m)
+    ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
+    x = oracle.start_uniform(5, b.dim)
+    ref = ob.matvec(obonds(inst), x)
+    y = hm.matvec(b, hm.bonds_of(inst), torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, ref) <= TOL_F64
+    assert np.max(np.abs(y - ref)) <= TOL_F64 * np.max(np.abs(ref)) * 10
+
+
+@pytest.mark.parametrize("inst", SMALL, ids=lambda i: i.name)
+def test_matvec_f32(hm, inst):
+    b = hm.Basis(inst.n_sites, inst.two_s, inst.two_m)
+    ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
+    x32 = oracle.start_uniform(6, b.dim).astype(np.float32)
+    ref = ob.matvec(obonds(inst), x32.astype(np.float64))
+    y = hm.matvec(b, hm.bonds_of(inst), torch.from_numpy(x32).cuda()).cpu().numpy()
+    assert rel(y.astype(np.float64), ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("nvec", [2, 5, 32, 37])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_matvec_batched(hm, nvec, dtype):
+    inst = W.small_ring(14, -1.0, -0.3)
+    b = hm.Basis(14, 1, 0)
+    ob = oracle.Basis(14, 1, 7)
+    X = np.stack([oracle.start_pm1(100 + r, b.dim) * oracle.start_uniform(200 + r, b.dim)
+                  for r in range(nvec)], axis=1)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    Xt = torch.from_numpy(X).to(tdt).cuda()
+    Y = hm.matvec(b, hm.bonds_of(inst), Xt).cpu().numpy().astype(np.float64)
+    Xr = Xt.cpu().numpy().astype(np.float64)
+    for r in range(nvec):
+        ref = ob.matvec(obonds(inst), Xr[:, r].copy())
+        assert rel(Y[:, r], ref) <= (TOL_F64 if dtype == "f64" else TOL_F32)
+
+
+def test_matvec_empty_bonds_and_tiny_sectors(hm):
+    """No bonds: y = 0.  A dim-1 sector: y = E x with E = -s^2 sum J."""
+    b = hm.Basis(6, 1, 6)
+    assert b.dim == 1
+    inst = W.small_ring(6, 0.8)
+    y = hm.matvec(b, hm.bonds_of(inst), torch.tensor([2.0], dtype=torch.float64, device="cuda"))
+    assert abs(float(y[0]) - 2.0 * (-0.25 * 6 * 0.8)) < 1e-15
+    b2 = hm.Basis(10, 1, 0)
+    y2 = hm.matvec(b2, hm.BondList.make([], [], []), torch.ones(b2.dim, dtype=torch.float64, device="cuda"))
+    assert float(y2.abs().max()) == 0.0
+
+
+def test_matvec_full_size_sampled_rows(hm):
+    """The 601,080,390-row J1-J2 ring sector in FP64: sampled rows of one product,
+    computed one by one by the oracle, in the launch configuration the benchmark uses."""
+    inst = W.j1j2_ring32()
+    b = hm.Basis(32, 1, 0)
+    ob = oracle.Basis(32, 1, 16)
+    x = oracle.start_uniform(inst.seed, b.dim)
+    xt = torch.from_numpy(x).cuda()
+    y = hm.matvec(b, hm.bonds_of(inst), xt)
+    rng = np.random.default_rng(7)
+    starts = np.concatenate([[0, b.dim - 256], rng.integers(0, b.dim - 256, 12)])
+    for r0 in starts:
+        r0 = int(r0)
+        ref = ob.matvec_rows(obonds(inst), x, r0, r0 + 256)
+        got = y[r0:r0 + 256].cpu().numpy()
+        assert rel(got, ref) <= TOL_F64
+    del y, xt
+
+
+# ---- bond correlations / autograd -------------------------------------------------------
+
+@pytest.mark.parametrize("inst", [SMALL[1], SMALL[3], SMALL[4]], ids=lambda i: i.name)
+def test_bond_corr(hm, inst):
+    b = hm.Basis(inst.n_sites, inst.two_s, inst.two_m)
+    ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
+    g, x = oracle.start_uniform(8, b.dim), oracle.start_uniform(9, b.dim)
+    ref = ob.bond_corr(obonds(inst), g, x)
+    got = hm.bond_corr(b, hm.bonds_of(inst), torch.from_numpy(g).cuda(), torch.from_numpy(x).cuda())
+    np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+def test_autograd_matvec(hm):
+    from paper_0706_3293_gb300.autograd import HeisenbergMatvec
+    inst = W.small_ring(16, -1.0, -0.4)
+    rng = np.random.default_rng(3)
+    Jn = rng.uniform(-1.2, -0.8, inst.n_bonds)
+    b = hm.Basis(16, 1, 0)
+    ob = oracle.Basis(16, 1, 8)
+    x = torch.from_numpy(oracle.start_uniform(1, b.dim)).cuda().requires_grad_(True)
+    J = torch.tensor(Jn, dtype=torch.float64, requires_grad=True)
+    w = torch.from_numpy(oracle.start_uniform(2, b.dim)).cuda()
+    y = HeisenbergMatvec.apply(x, J, b, inst.u, inst.v)
+    loss = (w * y).sum() + 0.5 * (y * y).sum()
+    loss.backward()
+    ob_b = oracle.Bonds(inst.u, inst.v, Jn)
+    yr = ob.matvec(ob_b, x.detach().cpu().numpy())
+    g = w.cpu().numpy() + yr
+    np.testing.assert_allclose(x.grad.cpu().numpy(), ob.matvec(ob_b, g), rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(J.grad.numpy(), -ob.bond_corr(ob_b, g, x.detach().cpu().numpy()),
+                               rtol=1e-10)
+    # directional finite difference in J (L is quadratic in J: central difference exact up
+    # to rounding)
+    d = rng.standard_normal(inst.n_bonds)
+    h = 1e-4
+
+    def L(Jv):
+        yv = ob.matvec(oracle.Bonds(inst.u, inst.v, Jv), x.detach().cpu().numpy())
+        return w.cpu().numpy() @ yv + 0.5 * yv @ yv
+    fd = (L(Jn + h * d) - L(Jn - h * d)) / (2 * h)
+    assert abs(fd - J.grad.numpy() @ d) < 1e-6 * abs(fd)
+
+
+# ---- Lanczos -----------------------------------------------------------------------------
+
+def test_lanczos_ring16_config(hm):
+    """16-site ring, M = 0, FP64, uniform start seed 1001, 100 steps: E0 and the lowest 5
+    Ritz values against the oracle run on the same start vector."""
+    inst = W.ring16()
+    b = hm.Basis(16, 1, 0)
+    ob = oracle.Basis(16, 1, 8)
+    res = hm.lanczos_run(b, hm.bonds_of(inst), inst.steps, seed=inst.seed, n_ritz=5)
+    al, be = ob.lanczos(obonds(inst), oracle.start_uniform(inst.seed, b.dim), inst.steps)
+    assert res.steps_done == len(al) == 100
+    np.testing.assert_allclose(res.alpha[:30], al[:30], rtol=0, atol=1e-11)
+    np.testing.assert_allclose(res.beta[:30], be[:30], rtol=0, atol=1e-11)
+    ref = oracle.tridiag_lowest(al, be, 5)
+    assert abs(res.ritz[0] - ref[0]) <= TOL_E0 * abs(ref[0])
+    assert abs(res.ritz[0] - (-7.142296360617)) < 1e-10
+    # Ritz values of T from the GPU's own alpha/beta, bisection on host vs device
+    np.testing.assert_allclose(res.ritz, oracle.tridiag_lowest(res.alpha, res.beta, 5), rtol=0, atol=1e-13)
+
+
+def test_lanczos_s1_small_f64_f32(hm):
+    """s = 1, N = 12 random 4-regular graph (dim 73,789): FP64 Lanczos against the oracle
+    and FP32 vectors against FP64 (|dE0/E0| <= 1e-6)."""
+    inst = W.s1_random_graph_small()
+    b = hm.Basis(12, 2, 0)
+    ob = oracle.Basis(12, 2, 12)
+    r64 = hm.lanczos_run(b, hm.bonds_of(inst), 80, seed=inst.seed, n_ritz=1)
+    al, be = ob.lanczos(obonds(inst), oracle.start_uniform(inst.seed, b.dim), 80)
+    e_ref = oracle.tridiag_lowest(al, be, 1)[0]
+    assert abs(r64.ritz[0] - e_ref) <= TOL_E0 * abs(e_ref)
+    r32 = hm.lanczos_run(b, hm.bonds_of(inst), 80, seed=inst.seed, n_ritz=1, dtype=torch.float32)
+    assert abs(r32.ritz[0] - e_ref) <= 1e-6 * abs(e_ref)
+
+
+def test_lanczos_stepwise_equals_graph(hm):
+    inst = W.small_ring(14, -1.0, -0.3)
+    b = hm.Basis(14, 1, 0)
+    run = hm.LanczosRun(b, hm.bonds_of(inst), 40, seed=3)
+    run.step(40)
+    al, be, rc = run.read()
+    res = hm.lanczos_run(b, hm.bonds_of(inst), 40, seed=3, n_ritz=1)
+    assert np.array_equal(al, res.alpha) and np.array_equal(be, res.beta)
+
+
+def test_lanczos_breakdown_small_sectors(hm):
+    inst = W.small_ring(8, -1.0, -0.3)
+    for two_m, dim in [(8, 1), (6, 8), (4, 28)]:
+        b = hm.Basis(8, 1, two_m)
+        assert b.dim == dim
+        res = hm.lanczos_run(b, hm.bonds_of(inst), 60, seed=11, n_ritz=1)
+        ob = oracle.Basis(8, 1, (8 - two_m) // 2)
+        al, be = ob.lanczos(obonds(inst), oracle.start_uniform(11, dim), 60)
+        assert res.steps_done == len(al) <= dim
+        assert res.status == 1    # HM_BREAKDOWN
+        assert abs(res.ritz[0] - oracle.tridiag_lowest(al, be, 1)[0]) < 1e-12
+
+
+def test_lanczos_user_start_vector(hm):
+    inst = W.small_ring(12, -1.0)
+    b = hm.Basis(12, 1, 0)
+    ob = oracle.Basis(12, 1, 6)
+    v0 = oracle.start_pm1(5, b.dim) * 0.25
+    res = hm.lanczos_run(b, hm.bonds_of(inst), 30, v0=torch.from_numpy(v0).cuda(), n_ritz=2)
+    al, be = ob.lanczos(obonds(inst), v0, 30)
+    np.testing.assert_allclose(res.alpha[:10], al[:10], atol=1e-12)
+
+
+# ---- ground-state gradient -------------------------------------------------------------
+
+def test_e0_grad_vs_oracle(hm):
+    inst = W.small_ring(14, -1.0, -0.3)
+    rng = np.random.default_rng(12)
+    J = rng.uniform(-1.2, -0.8, inst.n_bonds)
+    b = hm.Basis(14, 1, 0)
+    ob = oracle.Basis(14, 1, 7)
+    bl = hm.BondList.make(inst.u, inst.v, J)
+    e0, g, psi, rc = hm.e0_grad(b, bl, 120, seed=21, want_psi=True)
+    oe0, og = oracle.e0_grad(ob, oracle.Bonds(inst.u, inst.v, J), oracle.start_uniform(21, b.dim), 120)
+    assert abs(e0 - oe0) <= TOL_E0 * abs(oe0)
+    np.testing.assert_allclose(g, og, rtol=0, atol=1e-8)
+    assert abs(np.dot(J, g) - e0) < 1e-8        # Euler
+    assert abs(float(torch.linalg.norm(psi)) - 1.0) < 1e-12
