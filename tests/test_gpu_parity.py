@@ -254,16 +254,20 @@ def test_lanczos_ring16_config(hm):
 
 
 def test_lanczos_s1_small_f64_f32(hm):
-    """s = 1, N = 12 random 4-regular graph (dim 73,789): FP64 Lanczos against the oracle
-    and FP32 vectors against FP64 (|dE0/E0| <= 1e-6)."""
+    """s = 1, N = 12 random 4-regular graph (dim 73,789), 140 steps (E0 converged): FP64
+    Lanczos against the oracle (first steps to 1e-12, E0 to 1e-10) and FP32 vectors
+    against FP64 (|dE0/E0| <= 1e-6).  Before convergence two valid runs drift apart by
+    amplified rounding, so E0 is compared where it has converged."""
     inst = W.s1_random_graph_small()
     b = hm.Basis(12, 2, 0)
     ob = oracle.Basis(12, 2, 12)
-    r64 = hm.lanczos_run(b, hm.bonds_of(inst), 80, seed=inst.seed, n_ritz=1)
-    al, be = ob.lanczos(obonds(inst), oracle.start_uniform(inst.seed, b.dim), 80)
+    r64 = hm.lanczos_run(b, hm.bonds_of(inst), 140, seed=inst.seed, n_ritz=1)
+    al, be = ob.lanczos(obonds(inst), oracle.start_uniform(inst.seed, b.dim), 140)
+    np.testing.assert_allclose(r64.alpha[:20], al[:20], rtol=0, atol=1e-12 * np.abs(al).max())
+    np.testing.assert_allclose(r64.beta[:20], be[:20], rtol=0, atol=1e-12 * np.abs(al).max())
     e_ref = oracle.tridiag_lowest(al, be, 1)[0]
     assert abs(r64.ritz[0] - e_ref) <= TOL_E0 * abs(e_ref)
-    r32 = hm.lanczos_run(b, hm.bonds_of(inst), 80, seed=inst.seed, n_ritz=1, dtype=torch.float32)
+    r32 = hm.lanczos_run(b, hm.bonds_of(inst), 140, seed=inst.seed, n_ritz=1, dtype=torch.float32)
     assert abs(r32.ritz[0] - e_ref) <= 1e-6 * abs(e_ref)
 
 
@@ -278,15 +282,20 @@ def test_lanczos_stepwise_equals_graph(hm):
 
 
 def test_lanczos_breakdown_small_sectors(hm):
+    """Sectors of dim 1 and 8 exhaust their Krylov space: beta falls far below the
+    breakdown threshold and both sides stop at the same step with the same Ritz value.
+    The dim-28 sector loses orthogonality before beta gets that small (floating point);
+    there only E0 is compared."""
     inst = W.small_ring(8, -1.0, -0.3)
-    for two_m, dim in [(8, 1), (6, 8), (4, 28)]:
+    for two_m, dim, clean in [(8, 1, True), (6, 8, True), (4, 28, False)]:
         b = hm.Basis(8, 1, two_m)
         assert b.dim == dim
         res = hm.lanczos_run(b, hm.bonds_of(inst), 60, seed=11, n_ritz=1)
         ob = oracle.Basis(8, 1, (8 - two_m) // 2)
         al, be = ob.lanczos(obonds(inst), oracle.start_uniform(11, dim), 60)
-        assert res.steps_done == len(al) <= dim
-        assert res.status == 1    # HM_BREAKDOWN
+        if clean:
+            assert res.steps_done == len(al) <= dim
+            assert res.status == 1    # HM_BREAKDOWN
         assert abs(res.ritz[0] - oracle.tridiag_lowest(al, be, 1)[0]) < 1e-12
 
 
