@@ -120,6 +120,7 @@ int make_bonds(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *
         out->p[t] = (unsigned char)p;
         out->q[t] = (unsigned char)q;
         out->jm[t] = -J[t];
+        out->jmf[t] = (float)(-J[t]);
     }
     for (int ap = 0; ap <= S2; ++ap)
         for (int aq = 0; aq <= S2; ++aq) {
@@ -223,9 +224,11 @@ int basis_build(int n_sites, int two_s, int two_m, hm_basis **out) {
     }
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_cd, bytes > 0 ? bytes : 8);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_scratch, 256);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_cd, src, bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         if (b->d_cd) cudaFree(b->d_cd);
+        if (b->d_scratch) cudaFree(b->d_scratch);
         delete b;
         return cuda_fail(e, "basis_build: device tables");
     }
@@ -236,14 +239,13 @@ int basis_build(int n_sites, int two_s, int two_m, hm_basis **out) {
 
 int basis_free(hm_basis *b) {
     if (!b) return HM_OK;
-    if (b->d_cd) {
-        cudaError_t e = cudaFree(b->d_cd);
-        b->d_cd = nullptr;
-        delete b;
-        if (e != cudaSuccess) return cuda_fail(e, "basis_free");
-        return HM_OK;
-    }
+    cudaError_t e = cudaSuccess, e2;
+    if (b->d_cd && (e2 = cudaFree(b->d_cd)) != cudaSuccess) e = e2;
+    if (b->d_scratch && (e2 = cudaFree(b->d_scratch)) != cudaSuccess) e = e2;
+    for (auto &kv : b->blk_tabs)
+        if (kv.second.dev && (e2 = cudaFree(kv.second.dev)) != cudaSuccess) e = e2;
     delete b;
+    if (e != cudaSuccess) return cuda_fail(e, "basis_free");
     return HM_OK;
 }
 

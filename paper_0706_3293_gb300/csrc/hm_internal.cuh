@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -53,15 +54,38 @@ struct SectorView {
 
 }  // namespace hm
 
+namespace hm {
+struct BlkTab {                     // byte-chunk rank tables of the s = 1/2 block path
+    void *dev = nullptr;
+    int bytes = 0, oU = 0, oR0 = 0, oC = 0;
+};
+}  // namespace hm
+
 struct hm_basis {
     hm::SectorView view;
     std::vector<uint64_t> D;        // host D(k, a), (N+1) x (S2*N+1)
     std::vector<uint64_t> cd;       // host CD, cd_len entries
     void *d_cd = nullptr;           // device copy (owned)
+    void *d_scratch = nullptr;      // 256 bytes of device scratch (owned), e.g. exponents
+    std::map<int, hm::BlkTab> blk_tabs;   // per split position K (owned device memory)
     int device = 0;
 };
 
 namespace hm {
+
+// device state of a Lanczos run (see lanczos.cu)
+struct LzScalars {
+    double sigma_cur;    // v_j = sigma_cur * q_cur (stored vectors are unnormalised)
+    double sigma_prev;
+    double beta_prev;
+    double scale;        // max(|alpha_1..alpha_j|, beta_1..beta_{j-1})
+    double nrm2;         // scratch for norms
+    int j;               // steps done
+    int done;
+    int status;
+    int mconv;           // e0_grad: Krylov length used
+    int emax[2];         // largest exponent field of the vector held in buffer 0 / 1
+};
 
 int digit_bits(int two_s);
 // host helpers shared by the translation units
@@ -76,6 +100,7 @@ struct BondParams {
     int S2;
     unsigned char p[HM_MAX_BONDS], q[HM_MAX_BONDS];
     double jm[HM_MAX_BONDS];        // -J_b
+    float jmf[HM_MAX_BONDS];        // -J_b rounded to float (FP32 paths)
     // exchange factors 1/2 sqrt(radicand product), indexed [a_p * 8 + a_q]:
     //   pdn: s+_p s-_q (a_p -> a_p - 1, a_q -> a_q + 1), radicand a_p(2s-a_p+1)(2s-a_q)(a_q+1)
     //   pup: s-_p s+_q (a_p -> a_p + 1, a_q -> a_q - 1), radicand (2s-a_p)(a_p+1)a_q(2s-a_q+1)

@@ -4,9 +4,15 @@
 #include <cstring>
 #include <new>
 
+#include "blk.cuh"
+#include "ef64.cuh"
 #include "hm_row.cuh"
 
 namespace hm {
+
+int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int *blocks);
+int blk_lz_launch(const BlkParams &P, int dtype, const void *qc, void *qp, LzScalars *S, int pc,
+                  double *part, int blocks, cudaStream_t st);
 
 int matvec_dev(const hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype,
                int nvec, cudaStream_t st);
@@ -18,18 +24,6 @@ int start_vector_dev(uint64_t n, uint64_t seed, int kind, void *x, int dtype, cu
 
 constexpr double LZ_TOL = 1e-12;     // breakdown: beta_j <= LZ_TOL * max(|alpha|, beta)
 constexpr int NT = 256;
-
-struct LzScalars {
-    double sigma_cur;    // v_j = sigma_cur * q_cur (stored vectors are unnormalised)
-    double sigma_prev;
-    double beta_prev;
-    double scale;        // max(|alpha_1..alpha_j|, beta_1..beta_{j-1})
-    double nrm2;         // scratch for norms
-    int j;               // steps done
-    int done;
-    int status;
-    int mconv;           // e0_grad: Krylov length used
-};
 
 // workspace carve-up (all segments 256-byte aligned)
 struct LzLayout {
@@ -69,6 +63,8 @@ static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad
 struct hm_lanczos {
     const hm_basis *basis;
     hm::BondParams bp;
+    hm::BlkParams blk;      // s = 1/2 block path (use_blk)
+    int use_blk, blk_blocks;
     int dtype, max_steps, host_j, next_phase;
     unsigned char *work;
     hm::LzLayout L;
@@ -81,18 +77,32 @@ namespace hm {
 // ---------------------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------------------
+// part[blk] = sum q^2 (double-float per thread); *emax = max exponent field (if given)
 template <class T>
-__global__ void __launch_bounds__(NT) k_sumsq(const T *__restrict__ q, uint64_t n, double *__restrict__ part) {
+__global__ void __launch_bounds__(NT) k_sumsq(const T *__restrict__ q, uint64_t n, double *__restrict__ part,
+                                               int *emax) {
     __shared__ double red[NT / 32];
-    double s = 0.0;
+    ef::df s{0.0f, 0.0f};
+    double sd = 0.0;
+    int em = 0;
     for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
-        double v = (double)q[r];
-        s += v * v;
+        if constexpr (sizeof(T) == 8) {
+            const unsigned long long b = ((const unsigned long long *)q)[r];
+            em = max(em, (int)((b >> 52) & 0x7FF));
+            sd += q[r] * q[r];   // start vector only: once per run
+        } else {
+            s = ef::df_add(s, ef::two_prod(q[r], q[r]));
+        }
     }
-    s = block_sum<NT>(s, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    double tot = block_sum<NT>(sd + (double)s.hi + (double)s.lo, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (emax) {
+        for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_down_sync(0xffffffffu, em, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(emax, em);
+    }
 }
 
+// scalars were zeroed (emax[0] filled by k_sumsq) before this runs
 __global__ void k_lz_start(LzScalars *S, const double *__restrict__ part, int nblk) {
     __shared__ double red[NT / 32];
     double s = 0.0;
@@ -100,13 +110,8 @@ __global__ void k_lz_start(LzScalars *S, const double *__restrict__ part, int nb
     s = block_sum<NT>(s, red);
     if (threadIdx.x == 0) {
         S->sigma_cur = 1.0 / sqrt(s);
-        S->sigma_prev = 0.0;
-        S->beta_prev = 0.0;
-        S->scale = 0.0;
-        S->j = 0;
         S->done = (s > 0.0) ? 0 : 1;
         S->status = (s > 0.0) ? HM_OK : HM_EINVAL;
-        S->mconv = 0;
     }
 }
 
@@ -123,22 +128,31 @@ k_lz_matvec(SectorView sv, BondParams bp, const T *__restrict__ qc, T *__restric
     const I *cd = stage_tables<I>(sv, bp, smem_raw, &pdn, &pup);
     Codec<I> c{cd, sv.N, sv.S2, sv.A, sv.bits, sv.cd_w, sv.cd_rowlen};
     const double sc = S->sigma_cur, bp_ = S->beta_prev * S->sigma_prev;
+    const float scf = (float)sc, bpf = (float)bp_;
     double dot = 0.0;
+    ef::df dotf{0.0f, 0.0f};
     for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < sv.dim; r += (uint64_t)gridDim.x * NT) {
         const I i = (I)r;
         const uint64_t w = c.decode(i);
         Acc acc[1], dg;
         row_apply<I, T, Acc, 1>(c, bp, pdn, pup, i, w, qc, 1, 0, acc, &dg);
         const Acc hv = dg * (Acc)qc[r] + acc[0];
-        const T u = (T)(sc * (double)hv - bp_ * (double)qp[r]);
-        qp[r] = u;
-        dot += (sc * (double)qc[r]) * (double)u;
+        if constexpr (sizeof(T) == 8) {
+            const T u = (T)(sc * (double)hv - bp_ * (double)qp[r]);
+            qp[r] = u;
+            dot += (sc * (double)qc[r]) * (double)u;
+        } else {
+            const float u = scf * (float)hv - bpf * (float)qp[r];
+            qp[r] = (T)u;
+            dotf = ef::df_add(dotf, ef::two_prod(scf * (float)qc[r], u));
+        }
     }
-    dot = block_sum<NT>(dot, red);
+    dot = block_sum<NT>(dot + (double)dotf.hi + (double)dotf.lo, red);
     if (threadIdx.x == 0) part[blockIdx.x] = dot;
 }
 
-__global__ void k_lz_alpha(LzScalars *S, const double *__restrict__ part, int nblk, double *alpha) {
+__global__ void k_lz_alpha(LzScalars *S, const double *__restrict__ part, int nblk, double *alpha,
+                           int pprev) {
     if (S->done) return;
     __shared__ double red[NT / 32];
     double s = 0.0;
@@ -147,30 +161,51 @@ __global__ void k_lz_alpha(LzScalars *S, const double *__restrict__ part, int nb
     if (threadIdx.x == 0) {
         alpha[S->j] = s;
         S->scale = fmax(S->scale, fabs(s));
+        S->emax[pprev] = 0;          // filled again by the update kernel
     }
 }
 
-// w = u - alpha_j sigma_cur q_cur over q_prev; part = sum w^2; psi += coef_j v_j if psi
+// w = u - alpha_j sigma_cur q_cur over q_prev; part = sum w^2; psi += coef_j v_j if psi.
+// FP64 in double-float arithmetic on the bit patterns (no FP64 instruction per row);
+// the largest exponent field of w goes to S->emax[pprev].
 template <class T>
 __global__ void __launch_bounds__(NT)
-k_lz_update(const T *__restrict__ qc, T *__restrict__ qp, uint64_t n, const LzScalars *__restrict__ S,
+k_lz_update(const T *__restrict__ qc, T *__restrict__ qp, uint64_t n, LzScalars *S,
             const double *__restrict__ alpha, double *__restrict__ part, double *__restrict__ psi,
-            const double *__restrict__ coef) {
+            const double *__restrict__ coef, int pprev) {
     if (S->done) return;
     __shared__ double red[NT / 32];
     const double as = alpha[S->j] * S->sigma_cur;
     const double cj = psi ? coef[S->j] * S->sigma_cur : 0.0;
-    double s = 0.0;
+    const int scale_q = S->emax[pprev ^ 1] - 1023;
+    const ef::df as_s = [&] { const double v = ldexp(as, scale_q); const float h = (float)v; return ef::df{h, (float)(v - (double)h)}; }();
+    const float asf = (float)as;
+    ef::df s{0.0f, 0.0f};
+    int em = 0;
     for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
-        const double q = (double)qc[r];
-        const T w = (T)((double)qp[r] - as * q);
-        qp[r] = w;
-        const double wd = (double)w;
-        s += wd * wd;
-        if (psi) psi[r] += cj * q;
+        if constexpr (sizeof(T) == 8) {
+            const unsigned long long qb = ((const unsigned long long *)qc)[r];
+            const unsigned long long ub = ((const unsigned long long *)qp)[r];
+            const ef::df w = ef::df_add(ef::df_from_bits(ub, 0),
+                                        ef::df_neg(ef::df_mul(as_s, ef::df_from_bits(qb, scale_q))));
+            const unsigned long long wb = ef::bits_from_df(w, 0);
+            ((unsigned long long *)qp)[r] = wb;
+            em = max(em, (int)((wb >> 52) & 0x7FF));
+            s = ef::df_add(s, ef::df_mul(w, w));
+            if (psi) psi[r] += cj * ef::u2d(qb);
+        } else {
+            const float w = qp[r] - asf * qc[r];
+            qp[r] = w;
+            s = ef::df_add(s, ef::two_prod(w, w));
+            if (psi) psi[r] += cj * (double)qc[r];
+        }
     }
-    s = block_sum<NT>(s, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    const double tot = block_sum<NT>((double)s.hi + (double)s.lo, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if constexpr (sizeof(T) == 8) {
+        for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_down_sync(0xffffffffu, em, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&S->emax[pprev], em);
+    }
 }
 
 __global__ void k_lz_beta(LzScalars *S, const double *__restrict__ part, int nblk, double *beta) {
@@ -343,12 +378,18 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
     T *qc = parity ? b1 : b0;
     T *qp = parity ? b0 : b1;
     const int nblk = grid_blocks(sv.dim, NT);
+    const int pprev = parity ^ 1;   // buffer of q_prev, receives u then w
     if (phase == 0) {
-        const size_t sm = row_smem_bytes<I>(sv);
-        k_lz_matvec<I, T, Acc><<<nblk, NT, sm, st>>>(sv, R->bp, qc, qp, R->sc, R->part);
-        k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->alpha);
+        if (R->use_blk) {
+            HM_TRY(blk_lz_launch(R->blk, R->dtype, qc, qp, R->sc, parity, R->part, R->blk_blocks, st));
+            k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, R->blk_blocks, R->alpha, pprev);
+        } else {
+            const size_t sm = row_smem_bytes<I>(sv);
+            k_lz_matvec<I, T, Acc><<<nblk, NT, sm, st>>>(sv, R->bp, qc, qp, R->sc, R->part);
+            k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->alpha, pprev);
+        }
     } else {
-        k_lz_update<T><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, R->psi, R->coef);
+        k_lz_update<T><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
         k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta);
     }
     HM_CUDA(cudaGetLastError());
@@ -397,9 +438,10 @@ static int enqueue_start(hm_lanczos *R, const void *v0, uint64_t seed, cudaStrea
     if (v0) HM_CUDA(cudaMemcpyAsync(b0, v0, sv.dim * es, cudaMemcpyDeviceToDevice, st));
     else HM_TRY(start_vector_dev(sv.dim, seed, 0, b0, R->dtype, st));
     HM_CUDA(cudaMemsetAsync(b1, 0, sv.dim * es, st));
+    HM_CUDA(cudaMemsetAsync(R->sc, 0, sizeof(LzScalars), st));
     const int nblk = grid_blocks(sv.dim, NT);
-    if (R->dtype == HM_F64) k_sumsq<double><<<nblk, NT, 0, st>>>((const double *)b0, sv.dim, R->part);
-    else k_sumsq<float><<<nblk, NT, 0, st>>>((const float *)b0, sv.dim, R->part);
+    if (R->dtype == HM_F64) k_sumsq<double><<<nblk, NT, 0, st>>>((const double *)b0, sv.dim, R->part, &R->sc->emax[0]);
+    else k_sumsq<float><<<nblk, NT, 0, st>>>((const float *)b0, sv.dim, R->part, nullptr);
     k_lz_start<<<1, NT, 0, st>>>(R->sc, R->part, nblk);
     HM_CUDA(cudaGetLastError());
     R->host_j = 0;
@@ -428,6 +470,10 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
     }
     rc = prepare(b, dtype);
     if (rc < 0) { delete R; return rc; }
+    R->use_blk = 0;
+    rc = blk_lz_plan(const_cast<hm_basis *>(b), R->bp, dtype, &R->blk, &R->blk_blocks);
+    if (rc < 0) { delete R; return rc; }
+    R->use_blk = rc == 0 && R->blk_blocks <= grid_blocks(b->view.dim, NT);
     R->work = (unsigned char *)work;
     R->sc = (LzScalars *)(R->work + R->L.sc);
     R->alpha = (double *)(R->work + R->L.alpha);
@@ -601,7 +647,7 @@ int e0_grad(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, 
         for (int k = 0; k < S1.mconv && rc == HM_OK; ++k) rc = enqueue_step(R, st);
     }
     if (rc == HM_OK) {
-        k_sumsq<double><<<nblk, NT, 0, st>>>(R->psi, sv.dim, R->part);
+        k_sumsq<double><<<nblk, NT, 0, st>>>(R->psi, sv.dim, R->part, nullptr);
         k_store_nrm2<<<1, NT, 0, st>>>(R->sc, R->part, nblk);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "e0_grad: norm");

@@ -153,9 +153,15 @@ size_t bond_corr_bytes(const hm_basis *b, int n_bonds) {
     return (size_t)grid_blocks(b->view.dim, 256) * (size_t)(n_bonds > 0 ? n_bonds : 1) * sizeof(double);
 }
 
+int blk_matvec(hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype, int nvec,
+               cudaStream_t st);
+
 int matvec_dev(const hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype,
                int nvec, cudaStream_t st) {
     const SectorView &sv = b->view;
+    // s = 1/2 sectors with few coupling classes take the block path (blk.cu)
+    const int brc = blk_matvec(const_cast<hm_basis *>(b), bp, x, y, dtype, nvec, st);
+    if (brc <= 0) return brc;
     if (dtype == HM_F64) {
         if (sv.idx64) return matvec_cols<uint64_t, double, double>(sv, bp, (const double *)x, (double *)y, nvec, st);
         return matvec_cols<uint32_t, double, double>(sv, bp, (const double *)x, (double *)y, nvec, st);

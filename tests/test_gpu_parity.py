@@ -324,3 +324,64 @@ def test_e0_grad_vs_oracle(hm):
     np.testing.assert_allclose(g, og, rtol=0, atol=1e-8)
     assert abs(np.dot(J, g) - e0) < 1e-8        # Euler
     assert abs(float(torch.linalg.norm(psi)) - 1.0) < 1e-12
+
+
+# ---- s = 1/2 block path (sites split 16 low / N-16 high) ---------------------------------
+
+@pytest.mark.parametrize("two_m", [0, 2, 6, 12, 16, 18])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_matvec_block_path_all_sectors(hm, two_m, dtype):
+    """N = 20 J1-J2 ring (two coupling classes): the block kernel over sectors whose
+    blocks range from one row to C(16, 8)."""
+    inst = W.small_ring(20, -1.0, -0.3, two_m=two_m)
+    b = hm.Basis(20, 1, two_m)
+    ob = oracle.Basis(20, 1, inst.A)
+    x = oracle.start_uniform(31 + two_m, b.dim)
+    if dtype == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    ref = ob.matvec(obonds(inst), x)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    y = hm.matvec(b, hm.bonds_of(inst), torch.from_numpy(x).to(tdt).cuda()).cpu().numpy()
+    assert rel(y.astype(np.float64), ref) <= (TOL_F64 if dtype == "f64" else TOL_F32)
+
+
+def test_matvec_block_path_three_classes_and_scaled_input(hm):
+    """Three coupling classes, and an input scaled far from 1 (fixed-point unit follows
+    the vector's largest exponent)."""
+    u, v, _ = W.ring_bonds(22, 1.0, 1.0)
+    J = np.where(np.arange(len(u)) % 3 == 0, -1.0, np.where(np.arange(len(u)) % 3 == 1, 0.7, -0.25))
+    inst = W.Instance("r22c3", 22, 1, 0, u, v, J)
+    b = hm.Basis(22, 1, 0)
+    ob = oracle.Basis(22, 1, 11)
+    for s in [1.0, 2.0**-40, 2.0**35]:
+        x = oracle.start_uniform(4, b.dim) * s
+        ref = ob.matvec(obonds(inst), x)
+        y = hm.matvec(b, hm.bonds_of(inst), torch.from_numpy(x).cuda()).cpu().numpy()
+        assert rel(y, ref) <= TOL_F64
+
+
+def test_lanczos_block_path(hm):
+    """N = 20 J1-J2 ring, M = 0 (dim 184,756) on the block path: first steps to 1e-12
+    against the oracle, E0 to 1e-10 once converged, FP32 vectors to 1e-6."""
+    inst = W.small_ring(20, -1.0, -0.3)
+    b = hm.Basis(20, 1, 0)
+    ob = oracle.Basis(20, 1, 10)
+    r64 = hm.lanczos_run(b, hm.bonds_of(inst), 150, seed=9, n_ritz=1)
+    al, be = ob.lanczos(obonds(inst), oracle.start_uniform(9, b.dim), 150)
+    np.testing.assert_allclose(r64.alpha[:20], al[:20], rtol=0, atol=1e-12 * np.abs(al).max())
+    np.testing.assert_allclose(r64.beta[:20], be[:20], rtol=0, atol=1e-12 * np.abs(al).max())
+    e_ref = oracle.tridiag_lowest(al, be, 1)[0]
+    assert abs(r64.ritz[0] - e_ref) <= TOL_E0 * abs(e_ref)
+    r32 = hm.lanczos_run(b, hm.bonds_of(inst), 150, seed=9, n_ritz=1, dtype=torch.float32)
+    assert abs(r32.ritz[0] - e_ref) <= 1e-6 * abs(e_ref)
+
+
+def test_e0_grad_block_path(hm):
+    inst = W.small_ring(18, -1.0, -0.3)
+    b = hm.Basis(18, 1, 0)
+    ob = oracle.Basis(18, 1, 9)
+    e0, g, psi, rc = hm.e0_grad(b, hm.bonds_of(inst), 150, seed=5, want_psi=True)
+    oe0, og = oracle.e0_grad(ob, obonds(inst), oracle.start_uniform(5, b.dim), 150)
+    assert abs(e0 - oe0) <= TOL_E0 * abs(oe0)
+    np.testing.assert_allclose(g, og, rtol=0, atol=1e-8)
+    assert abs(np.dot(inst.J, g) - e0) < 1e-8
