@@ -96,6 +96,12 @@ def j1j2_ring32() -> Instance:
     return Instance("j1j2_ring32_s12_M0", 32, 1, 0, u, v, J, steps=60, seed=1002)
 
 
+def j1j2_ring(n_sites: int, j2: float = -0.5, seed: int = 1002) -> Instance:
+    """s = 1/2 J1-J2 ring of any even N (J1 = -1), M = 0 -- mid-size cases for profiling."""
+    u, v, J = ring_bonds(n_sites, -1.0, j2)
+    return Instance(f"j1j2_ring{n_sites}_s12_M0", n_sites, 1, 0, u, v, J, steps=60, seed=seed)
+
+
 def s1_random_graph(n_sites: int = 20, graph_seed: int = 3) -> Instance:
     """s = 1, each site bonded to 4 random partners, J ~ U[-1.5, -0.5], M = 0, 80 steps."""
     a, b = random_regular_graph(n_sites, 4, graph_seed)
