@@ -41,6 +41,9 @@ _lib = None
 
 # breakdown threshold of the Lanczos recurrence (relative to the largest |alpha|, beta)
 LANCZOS_TOL = 1e-12
+# finite-temperature runs: exhausted sectors are detected above the FP32 noise floor, and
+# no run exceeds the sector dimension (a D-dimensional space holds at most D Lanczos vectors)
+FTLM_TOL = 1e-5
 
 
 def build(force: bool = False) -> str:
@@ -364,12 +367,13 @@ def e0_grad(basis: Basis, bonds: Bonds, v0: np.ndarray, steps: int):
 def ftlm_sector(basis: Basis, bonds: Bonds, seed: int, R: int, steps: int):
     """Per start vector r of one sector: Ritz values theta_j and weights tau_j (squared
     first components of T's eigenvectors), the start vector being the +-1 vector of
-    stream (seed, A, r)."""
+    stream (seed, A, r).  A run stops at beta_j <= FTLM_TOL max(|alpha|, beta) or after
+    dim steps."""
     from scipy.linalg import eigh_tridiagonal
     res = []
     for r in range(R):
         v0 = start_pm1(stream_seed(seed, basis.A, r), basis.dim)
-        al, be = basis.lanczos(bonds, v0, steps)
+        al, be = basis.lanczos(bonds, v0, min(steps, basis.dim), tol=FTLM_TOL)
         m = len(al)
         if m == 1:
             th, c = np.array([al[0]]), np.ones((1, 1))
