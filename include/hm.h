@@ -128,8 +128,9 @@ int start_vector(const hm_basis *basis, uint64_t seed, int kind, void *x, int dt
 /* Recurrence (three-term, Paige order, no re-orthogonalisation):
  *   v_1 = v0/|v0|;  u = H v_j - beta_{j-1} v_{j-1};  alpha_j = v_j . u;
  *   w = u - alpha_j v_j;  beta_j = |w|;  v_{j+1} = w / beta_j.
- * Breakdown after step j when beta_j <= 1e-12 * max(|alpha_1..alpha_j|,
- * beta_1..beta_{j-1}); the run then stops with steps_done = j (status HM_BREAKDOWN).
+ * Breakdown after step j when beta_j <= tol * max(|alpha_1..alpha_j|,
+ * beta_1..beta_{j-1}), tol = 1e-12 for HM_F64 vectors and 1e-5 for HM_F32 vectors (the
+ * FP32 rounding floor); the run then stops with steps_done = j (status HM_BREAKDOWN).
  * Vectors are stored in dtype; alpha, beta and all reductions are double (fixed-order,
  * run-to-run deterministic); the tridiagonal eigensolve runs on the device in double. */
 
@@ -172,6 +173,31 @@ int e0_grad_workspace(const hm_basis *basis, int n_bonds, int steps, size_t *byt
 int e0_grad(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
             const double *J, const void *v0, uint64_t seed, int steps, void *work,
             size_t work_bytes, double *e0, double *dE0_dJ, double *psi_out, void *stream);
+
+/* ---- finite-temperature Lanczos over all sectors ---------------------------------------- */
+/* Jaklic-Prelovsek estimator (cited by the paper, Sec. 1, as an application of the Lanczos
+ * machinery) for s = 1/2 (two_s = 1), 10 <= n_sites <= 32, at most 4 distinct couplings and
+ * 64 bonds.  Every sector A = N/2 - M (0..N) runs R (1..32) Lanczos runs of up to `steps`
+ * steps from the +-1 vectors of SplitMix64 streams: stream seed = output #(A*2^20 + r) of
+ * the generator seeded with `seed`, element t = -1 if bit 63 of output #t of that stream is
+ * set, else +1.  Vectors are FP32 (row-major [rows][32], all sectors back to back),
+ * reductions double-float then double; a run stops at beta_j <= 1e-5 * max(|alpha|, beta)
+ * (above the FP32 noise floor) or after D_A steps (a sector of dimension D_A holds at most
+ * D_A Lanczos vectors).  Everything runs in one CUDA graph: start vectors, one
+ * cooperative persistent kernel for all steps (grid barriers wait at most 5 s, then the
+ * call returns HM_ETIMEOUT), and the tridiagonal eigensolves on the device.  Outputs (host):
+ * e_ref = lowest Ritz value; for each temperature T = temps[i]:
+ *   Z[i] = sum_A (D_A/R) sum_r sum_j tau_j e^{-(theta_j - e_ref)/T}  (partition function
+ *          divided by e^{-e_ref/T}),  E[i] = energy expectation;
+ * optional theta/tau [(A*32 + r)*steps + j] and mlen [A*32 + r] (Krylov length).
+ * vt: vectors per lane of the product (1, 2, 4), 0 = autotune (timed once per shape).
+ * Returns the tiling used (> 0) or an error. */
+int ftlm_workspace(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_t *v,
+                   const double *J, int R, int steps, int n_t, size_t *bytes);
+int ftlm_run(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_t *v,
+             const double *J, int R, int steps, uint64_t seed, const double *temps, int n_t,
+             double *Z, double *E, double *e_ref, double *theta, double *tau, int *mlen, int vt,
+             void *work, size_t work_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,7 @@ EXPORTS = [
     "hm_last_error", "basis_dim_query", "bonds_check", "basis_build", "basis_free", "basis_dim",
     "basis_encode", "basis_decode", "matvec", "bond_corr_workspace", "bond_corr", "start_vector",
     "lanczos_workspace", "lanczos_init", "lanczos_step", "lanczos_substep", "lanczos_read", "lanczos_free",
-    "lanczos_run", "e0_grad_workspace", "e0_grad",
+    "lanczos_run", "e0_grad_workspace", "e0_grad", "ftlm_workspace", "ftlm_run",
 ]
 
 _lib = None
@@ -69,6 +69,9 @@ def load() -> ctypes.CDLL:
                               i32, vp]),
         "e0_grad_workspace": (i32, [vp, i32, i32, szp]),
         "e0_grad": (i32, [vp, i32, vp, vp, vp, vp, u64, i32, vp, sz, dp, dp, vp, vp]),
+        "ftlm_workspace": (i32, [i32, i32, i32, vp, vp, vp, i32, i32, i32, szp]),
+        "ftlm_run": (i32, [i32, i32, i32, vp, vp, vp, i32, i32, u64, vp, i32, vp, vp, dp, vp, vp,
+                           vp, i32, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -244,3 +244,38 @@ def e0_grad(basis: Basis, bonds: BondList, steps: int, v0: torch.Tensor | None =
                          g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                          _vp(psi) if psi is not None else None, _stream()))
     return e0.value, g[: len(bonds)], psi, rc
+
+
+@dataclass
+class FTLMResult:
+    Z: np.ndarray          # partition function / e^{-e_ref / T}
+    E: np.ndarray          # energy expectation
+    e_ref: float
+    theta: np.ndarray      # [sector, 32, steps] Ritz values
+    tau: np.ndarray        # [sector, 32, steps] weights
+    mlen: np.ndarray       # [sector, 32] Krylov lengths
+    vt: int                # vectors per lane used by the product
+
+
+def ftlm_run(n_sites: int, bonds: BondList, R: int, steps: int, seed: int, temps, vt: int = 0,
+             device="cuda") -> FTLMResult:
+    """Finite-temperature Lanczos over all sectors of an s = 1/2 system (one graph)."""
+    L = _capi.load()
+    temps = np.ascontiguousarray(temps, dtype=np.float64)
+    n_t = int(temps.shape[0])
+    n = ctypes.c_size_t()
+    check(L.ftlm_workspace(n_sites, 1, *bonds.args(), R, steps, n_t, ctypes.byref(n)))
+    work = _workspace(n.value, device)
+    nsec = n_sites + 1
+    Z = np.zeros(max(n_t, 1))
+    E = np.zeros(max(n_t, 1))
+    eref = ctypes.c_double()
+    theta = np.zeros(nsec * 32 * steps)
+    tau = np.zeros(nsec * 32 * steps)
+    mlen = np.zeros(nsec * 32, dtype=np.int32)
+    dp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = check(L.ftlm_run(n_sites, 1, *bonds.args(), R, steps, seed & (2**64 - 1), dp(temps), n_t,
+                          dp(Z), dp(E), ctypes.byref(eref), dp(theta), dp(tau), dp(mlen), vt,
+                          _vp(work), work.numel(), _stream()))
+    return FTLMResult(Z[:n_t], E[:n_t], eref.value, theta.reshape(nsec, 32, steps),
+                      tau.reshape(nsec, 32, steps), mlen.reshape(nsec, 32), rc)

@@ -2,14 +2,16 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <cmath>
 #include <map>
 #include <tuple>
+#include <type_traits>
 
 #include "blk.cuh"
 
 namespace hm {
 
-constexpr int BLK_NT = 1024;
+constexpr int BLK_NT = 512;
 
 __host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -114,14 +116,44 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
         P->gq[c] = (float)g;
     }
     for (int t = 0; t < bp.nb; ++t) P->ntot[bc[t]]++;
-    // low groups keyed by (class, d, type); high and cross bonds by class
+    // integer-ratio classes: every -J_c/4 an exact small multiple of the smallest one
+    P->iratio = 0;
+    if (!cls.empty()) {
+        double g0 = 0.0;
+        for (double J : cls) {
+            const double g = std::fabs(J / 4.0);
+            if (g > 0.0 && (g0 == 0.0 || g < g0)) g0 = g;
+        }
+        bool ok = g0 > 0.0;
+        long weight = 0;
+        for (int c = 0; c < (int)cls.size() && ok; ++c) {
+            const double g = -cls[c] / 4.0;
+            const double kr = g / g0;
+            const long ki = std::lround(kr);
+            if ((double)ki != kr || std::labs(ki) > 64 || (double)ki * g0 != g) ok = false;
+            P->Kc[c] = (int)ki;
+            weight += std::labs(ki) * P->ntot[c];
+        }
+        // |T_c| < 3 n_c 2^53 per row: the weighted sum must stay below 2^63
+        if (ok && weight * 3 < 1000) {
+            P->iratio = 1;
+            P->g0 = g0;
+            P->g0_hi = (float)g0;
+            P->g0_lo = (float)(g0 - (double)P->g0_hi);
+            int ex = 0;
+            const double fr = std::frexp(g0, &ex);
+            P->g0_pow2 = fr == 0.5 ? 1 : 0;
+            P->g0_exp = ex - 1;                       // g0 = 2^(ex-1) when a power of two
+        }
+    }
+    // low groups keyed by (class, type, d); high and cross bonds by class
     std::map<std::tuple<int, int, int>, uint32_t> groups;
     std::vector<std::pair<int, int>> hi[HM_BLK_MAXC], cr[HM_BLK_MAXC];
     for (int t = 0; t < bp.nb; ++t) {
         const int p = bp.p[t], q = bp.q[t];  // p < q
         if (q < K) {
             const int type = q < 8 ? 0 : (p >= 8 ? 1 : 2);
-            groups[std::make_tuple(bc[t], q - p, type)] |= 1u << p;
+            groups[std::make_tuple(bc[t], type, q - p)] |= 1u << p;
         } else if (p >= K) {
             hi[bc[t]].push_back({p - K, q - K});
         } else {
@@ -130,26 +162,27 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
     }
     if ((int)groups.size() > HM_BLK_MAXG) return 1;
     int g = 0;
-    for (int c = 0; c < P->nc; ++c) {
-        P->lg_start[c] = g;
-        for (auto &kv : groups)
-            if (std::get<0>(kv.first) == c) {
-                P->lg_mask[g] = kv.second;
-                P->lg_d[g] = (uint8_t)std::get<1>(kv.first);
-                P->lg_type[g] = (uint8_t)std::get<2>(kv.first);
-                ++g;
-            }
-    }
-    for (int c = P->nc; c <= HM_BLK_MAXC; ++c) P->lg_start[c] = g;
+    for (int c = 0; c < HM_BLK_MAXC; ++c)
+        for (int ty = 0; ty < 3; ++ty) {
+            P->lg_cs[3 * c + ty] = g;
+            for (auto &kv : groups)
+                if (std::get<0>(kv.first) == c && std::get<1>(kv.first) == ty) {
+                    P->lg_mask[g] = kv.second;
+                    P->lg_d[g] = (uint8_t)std::get<2>(kv.first);
+                    ++g;
+                }
+        }
+    P->lg_cs[3 * HM_BLK_MAXC] = g;
     P->nlg = g;
     int nh = 0, ncr = 0;
-    for (int c = 0; c < P->nc; ++c) {
+    for (int c = 0; c < HM_BLK_MAXC; ++c) {
         P->hb_start[c] = nh;
         for (auto &e : hi[c]) { P->hb_p[nh] = (uint8_t)e.first; P->hb_q[nh] = (uint8_t)e.second; ++nh; }
         P->cb_start[c] = ncr;
         for (auto &e : cr[c]) { P->cb_p[ncr] = (uint8_t)e.first; P->cb_q[ncr] = (uint8_t)e.second; ++ncr; }
     }
-    for (int c = P->nc; c <= HM_BLK_MAXC; ++c) { P->hb_start[c] = nh; P->cb_start[c] = ncr; }
+    P->hb_start[HM_BLK_MAXC] = nh;
+    P->cb_start[HM_BLK_MAXC] = ncr;
     P->nhb = nh;
     P->ncb = ncr;
     // largest block: max over the low popcounts that occur of C(K, k)
@@ -167,156 +200,88 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
     return 0;
 }
 
-// shared memory: tables | low words (uint16) | staged values | per-block hop lists
+// shared memory: tables | staged rows | BlkShared
 size_t blk_smem_bytes(const BlkParams &P, int stage_bytes_per_row, int nvec) {
-    size_t o = al16(P.tab_bytes);
-    o += al16((size_t)P.max_block * 2);
-    o += al16((size_t)P.max_block * stage_bytes_per_row * nvec);
-    o += al16(HM_BLK_MAXB * 4) * 2 + al16(HM_BLK_MAXB) * 2;
-    return o;
+    return al16(P.tab_bytes) + al16((size_t)P.max_block * stage_bytes_per_row * nvec) +
+           blk_shared_bytes(P.max_block);
 }
 
 // ---------------------------------------------------------------------------------------
-// the kernel
+// gathers: how a row value is read from global memory
 // ---------------------------------------------------------------------------------------
-template <class T> struct Stage;
-template <> struct Stage<double> { using type = int64_t; };
-template <> struct Stage<float> { using type = float; };
-
-__device__ __forceinline__ uint32_t gosper8(uint32_t v) {   // next byte with the same popcount
-    const uint32_t t = v | (v - 1);
-    return (t + 1) | (((~t & (t + 1)) - 1) >> (__ffs(v)));
-}
-
-template <class T>
-__device__ __forceinline__ typename Stage<T>::type stage_val(const T *x, uint32_t j, int E) {
-    if constexpr (sizeof(T) == 8) {
-        const unsigned long long bits = __ldg((const unsigned long long *)x + j);
-        return ef::fix_from_bits(bits, E);
-    } else {
-        return __ldg(x + j);
-    }
-}
-
-// Per-block setup, shared by every block kernel: computes the block offset, the hop
-// lists and the low words, stages the block's own x.  Returns the row count n.
-template <class T>
-struct BlkBlock {
-    uint32_t off;
-    int k, n;
+struct GatherF64 {          // binary64 -> fixed point on the fly (vector exponent E)
+    const unsigned long long *x;
+    int E;
+    __device__ __forceinline__ int64_t operator()(uint32_t j) const { return ef::fix_from_bits(__ldg(x + j), E); }
+};
+struct GatherFix {          // precomputed fixed-point copy
+    const long long *x;
+    __device__ __forceinline__ int64_t operator()(uint32_t j) const { return (int64_t)__ldg(x + j); }
+};
+struct GatherF32 {
+    const float *x;
+    __device__ __forceinline__ float operator()(uint32_t j) const { return __ldg(x + j); }
 };
 
-template <class T, int NC>
-__device__ __forceinline__ void blk_setup(const BlkParams &P, const BlkTabs &tb, uint32_t h, int k,
-                                          const T *__restrict__ x, int E, uint16_t *list,
-                                          typename Stage<T>::type *Xs, int *hdelta, uint32_t *coff,
-                                          int8_t *ck, uint8_t *cbq, uint32_t *off_out, int *n_out) {
-    const uint32_t off = blk_off(P, tb, h, k);
-    const int n = (int)tb.C[P.K * (P.A + 1) + k];
-    for (int e = threadIdx.x; e < P.nhb; e += blockDim.x) {
-        const int p = P.hb_p[e], q = P.hb_q[e];
-        const bool valid = ((h >> p) ^ (h >> q)) & 1u;
-        hdelta[e] = valid ? (int)(blk_off(P, tb, h ^ ((1u << p) | (1u << q)), k) - off) : INT_MIN;
-    }
-    for (int e = threadIdx.x; e < P.ncb; e += blockDim.x) {
-        const int q = P.cb_q[e];
-        const uint32_t bq = (h >> q) & 1u;
-        const int k2 = k + (bq ? 1 : -1);
-        const bool ok = k2 >= 0 && k2 <= P.K;
-        cbq[e] = (uint8_t)bq;
-        ck[e] = (int8_t)(ok ? k2 : -1);
-        coff[e] = ok ? blk_off(P, tb, h ^ (1u << q), k2) : 0u;
-    }
-    for (int b1 = threadIdx.x; b1 < P.nb1; b1 += blockDim.x) {
-        const int c0 = k - __popc(b1);
-        if (c0 < 0 || c0 > 8) continue;
-        int base = tb.U[k * P.nb1 + b1];
-        uint32_t b0 = (1u << c0) - 1u;
-        const uint32_t hib = (uint32_t)b1 << 8;
-        if (c0 == 0) { list[base] = (uint16_t)hib; continue; }
-        while (b0 < 256u) {
-            list[base++] = (uint16_t)(hib | b0);
-            b0 = gosper8(b0);
-        }
-    }
-    for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = stage_val<T>(x, off + r, E);
-    *off_out = off;
-    *n_out = n;
-}
-
-// Hop sums of one row.  acc[c]: sum of x over the allowed exchanges of class c (fixed
-// point in FP64 mode), cnt[c]: their number.
-template <class T, int NC>
-__device__ __forceinline__ void blk_row(const BlkParams &P, const BlkTabs &tb, int k, uint32_t off,
-                                        int r, uint32_t l, const T *__restrict__ x, int E,
-                                        const typename Stage<T>::type *Xs, const int *hdelta,
-                                        const uint32_t *coff, const int8_t *ck, const uint8_t *cbq,
-                                        typename Stage<T>::type *acc, int *cnt) {
-    using S = typename Stage<T>::type;
-    const uint32_t R0own = tb.R0[l & 255u];
-    const uint32_t R1own = (uint32_t)r - R0own;
+// hop sums of one row: acc[c] = sum of x over the allowed exchanges of class c, cnt[c]
+// their number
+template <class Sv, int NC, class G>
+__device__ __forceinline__ void blk_row(const BlkParams &P, const BlkTabs &tb, int k, uint32_t off, int r,
+                                        uint32_t l, const Sv *Xs, const BlkShared &sh, const G &gx, Sv *acc,
+                                        int *cnt) {
     const uint16_t *Uk = tb.U + k * P.nb1;
+    const uint32_t i = off + (uint32_t)r;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        S a = S(0);
-        int m_cnt = 0;
-        // exchanges among the low positions: targets in this block (shared memory)
-        for (int g = P.lg_start[c]; g < P.lg_start[c + 1]; ++g) {
-            const int d = P.lg_d[g];
-            const int type = P.lg_type[g];
-            const uint32_t pat = 1u | (1u << d);
-            uint32_t m = ((l >> d) ^ l) & P.lg_mask[g];
-            while (m) {
-                const int p = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t l2 = l ^ (pat << p);
-                uint32_t r2;
-                if (type == 0) r2 = R1own + tb.R0[l2 & 255u];
-                else if (type == 1) r2 = R0own + Uk[l2 >> 8];
-                else r2 = (uint32_t)Uk[l2 >> 8] + tb.R0[l2 & 255u];
-                a += Xs[r2];
-                ++m_cnt;
-            }
+        Sv a = Sv(0);
+        int mc = blk_low_hops(P, tb, c, l, (uint32_t)r, Uk, [&](uint32_t r2) { a += Xs[r2]; });
+        mc += blk_cross_hops(P, tb, c, l, sh, [&](uint32_t j) { a += gx(j); });
+        // exchanges among the high positions: the same low word in another block
+        const int e0 = sh.hcs[c], e1 = sh.hcs[c + 1];
+        int e = e0;
+        for (; e + 4 <= e1; e += 4) {
+            const Sv v0 = gx(i + sh.hcd[e]), v1 = gx(i + sh.hcd[e + 1]);
+            const Sv v2 = gx(i + sh.hcd[e + 2]), v3 = gx(i + sh.hcd[e + 3]);
+            a += (v0 + v1) + (v2 + v3);
         }
-        // exchanges across the split: one bit flips on each side
-        for (int e = P.cb_start[c]; e < P.cb_start[c + 1]; ++e) {
-            const int p = P.cb_p[e];
-            if ((((l >> p) & 1u) != cbq[e]) && ck[e] >= 0) {
-                const uint32_t l2 = l ^ (1u << p);
-                const uint32_t j = coff[e] + rank_low(P, tb, l2, ck[e]);
-                a += stage_val<T>(x, j, E);
-                ++m_cnt;
-            }
-        }
-        // exchanges among the high positions: the same row of another block
-        for (int e = P.hb_start[c]; e < P.hb_start[c + 1]; ++e) {
-            const int dl = hdelta[e];
-            if (dl != INT_MIN) {
-                a += stage_val<T>(x, (uint32_t)((int)(off + (uint32_t)r) + dl), E);
-                ++m_cnt;
-            }
-        }
+        for (; e < e1; ++e) a += gx(i + sh.hcd[e]);
         acc[c] = a;
-        cnt[c] = m_cnt;
+        cnt[c] = mc + (e1 - e0);
     }
 }
 
-// y_i from the class sums: sum_c (-J_c/4) (2 acc_c + (ntot_c - 2 cnt_c) x_i)
+// T_c = 2 acc_c + (ntot_c - 2 cnt_c) x_i: the class sum of Eq. (E-2-1) rows in units of
+// -J_c / 4 (s = 1/2: s^z s^z = +-1/4, exchange element 1/2)
 template <int NC>
-__device__ __forceinline__ ef::df blk_combine_f64(const BlkParams &P, const int64_t *acc, const int *cnt,
-                                                  int64_t Xo, int E, int scale) {
+__device__ __forceinline__ void blk_classes(const BlkParams &P, const int64_t *acc, const int *cnt, int64_t Xo,
+                                            int64_t *T) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) T[c] = 2 * acc[c] + (int64_t)(P.ntot[c] - 2 * cnt[c]) * Xo;
+}
+
+// y (binary64 bits) of a row from its class sums; u = unit exponent of the fixed point.
+// Integer-ratio classes with a power-of-two g0 round the exact integer once.
+template <int NC>
+__device__ __forceinline__ unsigned long long blk_y_bits(const BlkParams &P, const int64_t *T, int u, int64_t *Tsum) {
+    if (P.iratio) {
+        int64_t s = 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s += (int64_t)P.Kc[c] * T[c];
+        *Tsum = s;
+        if (P.g0_pow2) return ef::bits_from_int(s, u + P.g0_exp);
+        const ef::df t = ef::df_from_fix(s, u + 1022 + ef::FIX_BITS, 0, 0);
+        return ef::bits_from_df(ef::df_mul(t, ef::df{P.g0_hi, P.g0_lo}), 0);
+    }
+    *Tsum = 0;
     ef::df y{0.0f, 0.0f};
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const int64_t Tc = 2 * acc[c] + (int64_t)(P.ntot[c] - 2 * cnt[c]) * Xo;
-        const ef::df t = ef::df_from_fix(Tc, E, 0, scale);
-        y = ef::df_add(y, ef::df_mul(t, ef::df{P.g_hi[c], P.g_lo[c]}));
-    }
-    return y;
+    for (int c = 0; c < NC; ++c)
+        y = ef::df_add(y, ef::df_mul(ef::df_from_fix(T[c], u + 1022 + ef::FIX_BITS, 0, 0), ef::df{P.g_hi[c], P.g_lo[c]}));
+    return ef::bits_from_df(y, 0);
 }
 
 template <int NC>
-__device__ __forceinline__ float blk_combine_f32(const BlkParams &P, const float *acc, const int *cnt, float xo) {
+__device__ __forceinline__ float blk_y_f32(const BlkParams &P, const float *acc, const int *cnt, float xo) {
     float y = 0.0f;
 #pragma unroll
     for (int c = 0; c < NC; ++c) y += P.gq[c] * (2.0f * acc[c] + (float)(P.ntot[c] - 2 * cnt[c]) * xo);
@@ -332,39 +297,45 @@ __global__ void k_max_exp(const unsigned long long *__restrict__ x, uint64_t n, 
     if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
+// ---------------------------------------------------------------------------------------
+// y = H x (matvec API)
+// ---------------------------------------------------------------------------------------
 template <class T, int NC>
-__global__ void __launch_bounds__(BLK_NT, 1)
+__global__ void __launch_bounds__(BLK_NT)
 k_blk_matvec(BlkParams P, const T *__restrict__ x, T *__restrict__ y, const int *__restrict__ Eptr) {
-    using S = typename Stage<T>::type;
+    using Sv = typename std::conditional<sizeof(T) == 8, int64_t, float>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     const BlkTabs tb = stage_blk_tables(P, smem);
-    size_t o = al16(P.tab_bytes);
-    uint16_t *list = (uint16_t *)(smem + o); o += al16((size_t)P.max_block * 2);
-    S *Xs = (S *)(smem + o); o += al16((size_t)P.max_block * sizeof(S));
-    int *hdelta = (int *)(smem + o); o += al16(HM_BLK_MAXB * 4);
-    uint32_t *coff = (uint32_t *)(smem + o); o += al16(HM_BLK_MAXB * 4);
-    int8_t *ck = (int8_t *)(smem + o); o += al16(HM_BLK_MAXB);
-    uint8_t *cbq = (uint8_t *)(smem + o);
+    Sv *Xs = (Sv *)(smem + al16(P.tab_bytes));
+    const BlkShared sh = blk_carve(smem + al16(P.tab_bytes) + al16((size_t)P.max_block * sizeof(Sv)), P.max_block);
     const int E = Eptr ? *Eptr : 0;
-    const int scale = E - 1023;
+    const int u = E - 1022 - ef::FIX_BITS;
     for (uint32_t h = blockIdx.x; h < (1u << P.H); h += gridDim.x) {
         const int k = P.A - __popc(h);
         if (k < 0 || k > P.K) continue;
         __syncthreads();    // previous block done with the shared buffers
         uint32_t off;
-        int n;
-        blk_setup<T, NC>(P, tb, h, k, x, E, list, Xs, hdelta, coff, ck, cbq, &off, &n);
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += blockDim.x) {
-            const uint32_t l = list[r];
-            S acc[NC];
-            int cnt[NC];
-            blk_row<T, NC>(P, tb, k, off, r, l, x, E, Xs, hdelta, coff, ck, cbq, acc, cnt);
-            if constexpr (sizeof(T) == 8) {
-                const ef::df v = blk_combine_f64<NC>(P, acc, cnt, Xs[r], E, scale);
-                ((unsigned long long *)y)[off + r] = ef::bits_from_df(v, scale);
-            } else {
-                y[off + r] = blk_combine_f32<NC>(P, acc, cnt, Xs[r]);
+        const int n = blk_setup_block(P, tb, h, k, sh, &off);
+        if constexpr (sizeof(T) == 8) {
+            const GatherF64 gx{(const unsigned long long *)x, E};
+            for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = gx(off + r);
+            __syncthreads();
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                int64_t acc[NC], Tc[NC], ts;
+                int cnt[NC];
+                blk_row<int64_t, NC>(P, tb, k, off, r, sh.list[r], Xs, sh, gx, acc, cnt);
+                blk_classes<NC>(P, acc, cnt, Xs[r], Tc);
+                ((unsigned long long *)y)[off + r] = blk_y_bits<NC>(P, Tc, u, &ts);
+            }
+        } else {
+            const GatherF32 gx{(const float *)x};
+            for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = gx(off + r);
+            __syncthreads();
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                float acc[NC];
+                int cnt[NC];
+                blk_row<float, NC>(P, tb, k, off, r, sh.list[r], Xs, sh, gx, acc, cnt);
+                y[off + r] = blk_y_f32<NC>(P, acc, cnt, Xs[r]);
             }
         }
     }
@@ -372,7 +343,7 @@ k_blk_matvec(BlkParams P, const T *__restrict__ x, T *__restrict__ y, const int 
 
 template <class T, int NC>
 static int launch_blk_matvec(hm_basis *b, const BlkParams &P, const T *x, T *y, cudaStream_t st) {
-    const size_t sm = blk_smem_bytes(P, sizeof(typename Stage<T>::type), 1);
+    const size_t sm = blk_smem_bytes(P, sizeof(T) == 8 ? 8 : 4, 1);
     HM_CUDA(cudaFuncSetAttribute(k_blk_matvec<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int *Ed = nullptr;
     if constexpr (sizeof(T) == 8) {
@@ -381,124 +352,161 @@ static int launch_blk_matvec(hm_basis *b, const BlkParams &P, const T *x, T *y, 
         k_max_exp<<<grid_blocks(P.dim, 256), 256, 0, st>>>((const unsigned long long *)x, P.dim, Ed);
         HM_CUDA(cudaGetLastError());
     }
-    const int blocks = std::min<int>(sm_count(), 1 << P.H);
+    int per = 1;
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_matvec<T, NC>, BLK_NT, sm));
+    const int blocks = std::min<int>(sm_count() * std::max(per, 1), 1 << P.H);
     k_blk_matvec<T, NC><<<blocks, BLK_NT, sm, st>>>(P, x, y, Ed);
     HM_CUDA(cudaGetLastError());
     return HM_OK;
 }
 
+// split position: 15 low sites (blocks <= 6435 rows: three 512-thread CTAs per SM), or
+// the largest K <= 15 that leaves two high sites
+static int blk_K(const hm_basis *b) { return std::min(15, b->view.N - 2); }
+
 // ---------------------------------------------------------------------------------------
-// Lanczos product: u = sigma_cur H q_cur - beta_prev sigma_prev q_prev, written over
-// q_prev; part[blockIdx] = sum_i (sigma_cur q_cur,i) u_i.  Buffer parity pc holds q_cur.
-// FP64: the row result, u and the dot are double-float; no FP64 instruction per row.
+// Lanczos, FP64: y = H q_cur from the fixed-point copy Xc of q_cur (every gather an
+// integer load), written as binary64 to Y; the exact integer dots q.y and q.q_prev
+// (Xp: fixed-point copy of q_prev) give alpha without re-reading y.
+// part[blk] = (q . H q) and part[gridDim + blk] = (q . q_prev), both in true units.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ ef::df df_of_double(double v) {
-    const float hi = (float)v;
-    return ef::df{hi, (float)(v - (double)hi)};
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo = (unsigned long long)v;
+    return (double)hi * 18446744073709551616.0 + (double)lo;
 }
 
-template <class T, int NC>
-__global__ void __launch_bounds__(BLK_NT, 1)
-k_blk_lz(BlkParams P, const T *__restrict__ qc, T *__restrict__ qp, LzScalars *S, int pc,
-         double *__restrict__ part) {
-    using S_t = typename Stage<T>::type;
+template <int NC>
+__global__ void __launch_bounds__(BLK_NT)
+k_blk_lz64(BlkParams P, const long long *__restrict__ Xc, const long long *__restrict__ Xp,
+           unsigned long long *__restrict__ Y, LzScalars *S, int pc, double *__restrict__ part) {
     if (S->done) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[BLK_NT / 32];
     const BlkTabs tb = stage_blk_tables(P, smem);
-    size_t o = al16(P.tab_bytes);
-    uint16_t *list = (uint16_t *)(smem + o); o += al16((size_t)P.max_block * 2);
-    S_t *Xs = (S_t *)(smem + o); o += al16((size_t)P.max_block * sizeof(S_t));
-    int *hdelta = (int *)(smem + o); o += al16(HM_BLK_MAXB * 4);
-    uint32_t *coff = (uint32_t *)(smem + o); o += al16(HM_BLK_MAXB * 4);
-    int8_t *ck = (int8_t *)(smem + o); o += al16(HM_BLK_MAXB);
-    uint8_t *cbq = (uint8_t *)(smem + o);
-    const int E = S->emax[pc];
-    const int Ep = S->emax[pc ^ 1];
-    const int scale = E - 1023, scale_p = Ep - 1023;
-    // per-thread copies of the step scalars (a few FP64 operations per thread, not per row)
-    const ef::df sig_s = df_of_double(ldexp(S->sigma_cur, scale));
-    const ef::df gam_s = df_of_double(ldexp(S->beta_prev * S->sigma_prev, scale_p));
-    const float sig_f = (float)S->sigma_cur, gam_f = (float)(S->beta_prev * S->sigma_prev);
+    int64_t *Xs = (int64_t *)(smem + al16(P.tab_bytes));
+    const BlkShared sh = blk_carve(smem + al16(P.tab_bytes) + al16((size_t)P.max_block * 8), P.max_block);
+    const int E = S->emax[pc], Ep = S->emax[pc ^ 1];
+    const int u = E - 1022 - ef::FIX_BITS, up = Ep - 1022 - ef::FIX_BITS;
+    const GatherFix gx{Xc};
+    __int128 d1 = 0, d2 = 0;
+    ef::df d1f{0.0f, 0.0f};
+    for (uint32_t h = blockIdx.x; h < (1u << P.H); h += gridDim.x) {
+        const int k = P.A - __popc(h);
+        if (k < 0 || k > P.K) continue;
+        __syncthreads();
+        uint32_t off;
+        const int n = blk_setup_block(P, tb, h, k, sh, &off);
+        for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = gx(off + r);
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            int64_t acc[NC], Tc[NC], ts;
+            int cnt[NC];
+            blk_row<int64_t, NC>(P, tb, k, off, r, sh.list[r], Xs, sh, gx, acc, cnt);
+            const int64_t xo = Xs[r];
+            blk_classes<NC>(P, acc, cnt, xo, Tc);
+            const unsigned long long yb = blk_y_bits<NC>(P, Tc, u, &ts);
+            Y[off + r] = yb;
+            if (P.iratio) d1 += (__int128)xo * ts;
+            else d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
+            d2 += (__int128)xo * (int64_t)__ldg(Xp + off + r);
+        }
+    }
+    // true units: q.y = g0 2^(2u) sum X Tsum (integer ratios) or the double-float sum
+    // scaled back by 2^(2(E-1023)); q.q_prev = 2^(u+up) sum X Xp
+    const double q_y = P.iratio ? ldexp(i128_to_double(d1) * P.g0, 2 * u)
+                                : ldexp((double)d1f.hi + (double)d1f.lo, 2 * (E - 1023));
+    const double q_qp = ldexp(i128_to_double(d2), u + up);
+    const double s1 = block_sum<BLK_NT>(q_y, red);
+    __syncthreads();
+    const double s2 = block_sum<BLK_NT>(q_qp, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s1;
+        part[gridDim.x + blockIdx.x] = s2;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Lanczos, FP32: u = sigma H q - gamma q_prev over q_prev, dot in double-float
+// ---------------------------------------------------------------------------------------
+template <int NC>
+__global__ void __launch_bounds__(BLK_NT)
+k_blk_lz32(BlkParams P, const float *__restrict__ qc, float *__restrict__ qp, LzScalars *S, double *__restrict__ part) {
+    if (S->done) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[BLK_NT / 32];
+    const BlkTabs tb = stage_blk_tables(P, smem);
+    float *Xs = (float *)(smem + al16(P.tab_bytes));
+    const BlkShared sh = blk_carve(smem + al16(P.tab_bytes) + al16((size_t)P.max_block * 4), P.max_block);
+    const float sig = (float)S->sigma_cur, gam = (float)(S->beta_prev * S->sigma_prev);
+    const GatherF32 gx{qc};
     ef::df dot{0.0f, 0.0f};
     for (uint32_t h = blockIdx.x; h < (1u << P.H); h += gridDim.x) {
         const int k = P.A - __popc(h);
         if (k < 0 || k > P.K) continue;
         __syncthreads();
         uint32_t off;
-        int n;
-        blk_setup<T, NC>(P, tb, h, k, qc, E, list, Xs, hdelta, coff, ck, cbq, &off, &n);
+        const int n = blk_setup_block(P, tb, h, k, sh, &off);
+        for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = gx(off + r);
         __syncthreads();
         for (int r = threadIdx.x; r < n; r += blockDim.x) {
-            const uint32_t l = list[r];
-            S_t acc[NC];
+            float acc[NC];
             int cnt[NC];
-            blk_row<T, NC>(P, tb, k, off, r, l, qc, E, Xs, hdelta, coff, ck, cbq, acc, cnt);
-            if constexpr (sizeof(T) == 8) {
-                // H q in units of 2^scale (the vector's own scale), then
-                // u = (sigma 2^scale) hv - (gamma 2^scale_p) (q_prev 2^-scale_p)
-                const ef::df hv = blk_combine_f64<NC>(P, acc, cnt, Xs[r], E, scale);
-                const unsigned long long pb = ((const unsigned long long *)qp)[off + r];
-                const ef::df qpv = ef::df_from_bits(pb, scale_p);
-                const ef::df u = ef::df_add(ef::df_mul(sig_s, hv), ef::df_neg(ef::df_mul(gam_s, qpv)));
-                ((unsigned long long *)qp)[off + r] = ef::bits_from_df(u, 0);
-                const ef::df v = ef::df_mul(sig_s, ef::df_from_fix(Xs[r], E, 0, scale));
-                dot = ef::df_add(dot, ef::df_mul(v, u));
-            } else {
-                const float hv = blk_combine_f32<NC>(P, acc, cnt, Xs[r]);
-                const float u = sig_f * hv - gam_f * qp[off + r];
-                qp[off + r] = u;
-                dot = ef::df_add(dot, ef::two_prod(sig_f * Xs[r], u));
-            }
+            blk_row<float, NC>(P, tb, k, off, r, sh.list[r], Xs, sh, gx, acc, cnt);
+            const float hv = blk_y_f32<NC>(P, acc, cnt, Xs[r]);
+            const float uu = sig * hv - gam * qp[off + r];
+            qp[off + r] = uu;
+            dot = ef::df_add(dot, ef::two_prod(sig * Xs[r], uu));
         }
     }
-    double d = block_sum<BLK_NT>((double)dot.hi + (double)dot.lo, red);
+    const double d = block_sum<BLK_NT>((double)dot.hi + (double)dot.lo, red);
     if (threadIdx.x == 0) part[blockIdx.x] = d;
 }
 
-template <class T, int NC>
-static int launch_blk_lz(const BlkParams &P, const T *qc, T *qp, LzScalars *S, int pc, double *part,
-                         int blocks, cudaStream_t st) {
-    const size_t sm = blk_smem_bytes(P, sizeof(typename Stage<T>::type), 1);
-    k_blk_lz<T, NC><<<blocks, BLK_NT, sm, st>>>(P, qc, qp, S, pc, part);
-    HM_CUDA(cudaGetLastError());
-    return HM_OK;
-}
-
-template <class T, int NC>
-static int prep_blk_lz(const BlkParams &P) {
-    const size_t sm = blk_smem_bytes(P, sizeof(typename Stage<T>::type), 1);
-    HM_CUDA(cudaFuncSetAttribute(k_blk_lz<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+template <class K_t>
+static int set_smem(K_t kern, size_t sm) {
+    HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     return HM_OK;
 }
 
 // Lanczos hooks: plan (0 = block path usable), attribute setup, launch
 int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int *blocks) {
-    int rc = blk_plan(b, bp, 16, P);
+    int rc = blk_plan(b, bp, blk_K(b), P);
     if (rc != 0) return rc;
-    const size_t stage = dtype == HM_F64 ? 8 : 4;
-    if (blk_smem_bytes(*P, (int)stage, 1) > 227 * 1024) return 1;
-    *blocks = std::min<int>(sm_count(), 1 << P->H);
+    const size_t sm = blk_smem_bytes(*P, dtype == HM_F64 ? 8 : 4, 1);
+    if (sm > 227 * 1024) return 1;
+    int per = 1;
     if (dtype == HM_F64) {
-        if (P->nc == 1) return prep_blk_lz<double, 1>(*P);
-        if (P->nc == 2) return prep_blk_lz<double, 2>(*P);
-        return prep_blk_lz<double, 4>(*P);
+        if (P->nc == 1) { HM_TRY(set_smem(k_blk_lz64<1>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz64<1>, BLK_NT, sm)); }
+        else if (P->nc == 2) { HM_TRY(set_smem(k_blk_lz64<2>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz64<2>, BLK_NT, sm)); }
+        else { HM_TRY(set_smem(k_blk_lz64<4>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz64<4>, BLK_NT, sm)); }
+    } else {
+        if (P->nc == 1) { HM_TRY(set_smem(k_blk_lz32<1>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz32<1>, BLK_NT, sm)); }
+        else if (P->nc == 2) { HM_TRY(set_smem(k_blk_lz32<2>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz32<2>, BLK_NT, sm)); }
+        else { HM_TRY(set_smem(k_blk_lz32<4>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz32<4>, BLK_NT, sm)); }
     }
-    if (P->nc == 1) return prep_blk_lz<float, 1>(*P);
-    if (P->nc == 2) return prep_blk_lz<float, 2>(*P);
-    return prep_blk_lz<float, 4>(*P);
+    *blocks = std::min<int>(sm_count() * std::max(per, 1), 1 << P->H);
+    return 0;
 }
 
-int blk_lz_launch(const BlkParams &P, int dtype, const void *qc, void *qp, LzScalars *S, int pc,
-                  double *part, int blocks, cudaStream_t st) {
-    if (dtype == HM_F64) {
-        if (P.nc == 1) return launch_blk_lz<double, 1>(P, (const double *)qc, (double *)qp, S, pc, part, blocks, st);
-        if (P.nc == 2) return launch_blk_lz<double, 2>(P, (const double *)qc, (double *)qp, S, pc, part, blocks, st);
-        return launch_blk_lz<double, 4>(P, (const double *)qc, (double *)qp, S, pc, part, blocks, st);
-    }
-    if (P.nc == 1) return launch_blk_lz<float, 1>(P, (const float *)qc, (float *)qp, S, pc, part, blocks, st);
-    if (P.nc == 2) return launch_blk_lz<float, 2>(P, (const float *)qc, (float *)qp, S, pc, part, blocks, st);
-    return launch_blk_lz<float, 4>(P, (const float *)qc, (float *)qp, S, pc, part, blocks, st);
+int blk_lz64_launch(const BlkParams &P, const long long *Xc, const long long *Xp, unsigned long long *Y,
+                    LzScalars *S, int pc, double *part, int blocks, cudaStream_t st) {
+    const size_t sm = blk_smem_bytes(P, 8, 1);
+    if (P.nc == 1) k_blk_lz64<1><<<blocks, BLK_NT, sm, st>>>(P, Xc, Xp, Y, S, pc, part);
+    else if (P.nc == 2) k_blk_lz64<2><<<blocks, BLK_NT, sm, st>>>(P, Xc, Xp, Y, S, pc, part);
+    else k_blk_lz64<4><<<blocks, BLK_NT, sm, st>>>(P, Xc, Xp, Y, S, pc, part);
+    HM_CUDA(cudaGetLastError());
+    return HM_OK;
+}
+
+int blk_lz32_launch(const BlkParams &P, const float *qc, float *qp, LzScalars *S, double *part, int blocks,
+                    cudaStream_t st) {
+    const size_t sm = blk_smem_bytes(P, 4, 1);
+    if (P.nc == 1) k_blk_lz32<1><<<blocks, BLK_NT, sm, st>>>(P, qc, qp, S, part);
+    else if (P.nc == 2) k_blk_lz32<2><<<blocks, BLK_NT, sm, st>>>(P, qc, qp, S, part);
+    else k_blk_lz32<4><<<blocks, BLK_NT, sm, st>>>(P, qc, qp, S, part);
+    HM_CUDA(cudaGetLastError());
+    return HM_OK;
 }
 
 // returns 1 when the block path does not apply (caller falls back to the row kernel)
@@ -506,10 +514,9 @@ int blk_matvec(hm_basis *b, const BondParams &bp, const void *x, void *y, int dt
                cudaStream_t st) {
     if (nvec != 1) return 1;
     BlkParams P;
-    int rc = blk_plan(b, bp, 16, &P);
+    int rc = blk_plan(b, bp, blk_K(b), &P);
     if (rc != 0) return rc;
-    const size_t stage = dtype == HM_F64 ? 8 : 4;
-    if (blk_smem_bytes(P, (int)stage, 1) > 227 * 1024) return 1;
+    if (blk_smem_bytes(P, dtype == HM_F64 ? 8 : 4, 1) > 227 * 1024) return 1;
     if (dtype == HM_F64) {
         switch (P.nc) {
             case 1: return launch_blk_matvec<double, 1>(b, P, (const double *)x, (double *)y, st);

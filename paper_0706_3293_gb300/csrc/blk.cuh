@@ -22,6 +22,8 @@
 // in double-float arithmetic: no FP64 instruction runs per row.
 #pragma once
 
+#include <climits>
+
 #include "ef64.cuh"
 #include "hm_internal.cuh"
 
@@ -39,11 +41,18 @@ struct BlkParams {
     float g_hi[HM_BLK_MAXC], g_lo[HM_BLK_MAXC];   // FP64 mode: -J_c / 4 as double-float
     float gq[HM_BLK_MAXC];                        // FP32 mode: -J_c / 4
     int ntot[HM_BLK_MAXC];                        // bonds in class c
-    // low bonds grouped by (class, distance d, byte type): mask of start positions p;
-    // type 0: both ends in byte 0, 1: both in byte 1, 2: across the bytes
-    int nlg, lg_start[HM_BLK_MAXC + 1];
+    // integer-ratio classes: -J_c / 4 = Kc[c] * g0 exactly (small integers), so the row
+    // value is g0 * sum_c Kc T_c, one exact integer; g0 = +-2^g0_exp when g0_pow2
+    int iratio, g0_pow2, g0_exp;
+    int Kc[HM_BLK_MAXC];
+    double g0;
+    float g0_hi, g0_lo;
+    // low bonds grouped by (class, byte type, distance d): mask of start positions p;
+    // type 0: both ends in byte 0, 1: both in byte 1, 2: across the bytes.  Groups of
+    // class c and type t are [lg_cs[3c+t], lg_cs[3c+t+1]).
+    int nlg, lg_cs[3 * HM_BLK_MAXC + 1];
     uint32_t lg_mask[HM_BLK_MAXG];
-    uint8_t lg_d[HM_BLK_MAXG], lg_type[HM_BLK_MAXG];
+    uint8_t lg_d[HM_BLK_MAXG];
     // high bonds (positions relative to K) and cross bonds (p < K <= q), by class
     int nhb, hb_start[HM_BLK_MAXC + 1];
     uint8_t hb_p[HM_BLK_MAXB], hb_q[HM_BLK_MAXB];
@@ -93,6 +102,152 @@ __device__ __forceinline__ uint32_t blk_off(const BlkParams &P, const BlkTabs &T
 
 __device__ __forceinline__ uint32_t rank_low(const BlkParams &P, const BlkTabs &T, uint32_t l, int k) {
     return (uint32_t)T.U[k * P.nb1 + (l >> 8)] + (uint32_t)T.R0[l & 255u];
+}
+
+}  // namespace hm
+
+namespace hm {
+
+// ---- per-block setup shared by the block kernels -------------------------------------------
+// Shared scratch of one block: low words, compacted high-exchange offsets per class,
+// cross-exchange targets.
+struct BlkShared {
+    uint16_t *list;       // [max_block] low words in rank order
+    int *hcd;             // [HM_BLK_MAXB] offsets (target row - own row) of the valid high exchanges
+    int *hcs;             // [HM_BLK_MAXC + 1] class c owns hcd[hcs[c] .. hcs[c+1])
+    int *tmp;             // [HM_BLK_MAXB]
+    uint32_t *coff;       // [HM_BLK_MAXB] sector offset of the cross target block
+    int8_t *ck;           // [HM_BLK_MAXB] low popcount of the cross target (-1: none)
+    uint8_t *cbq;         // [HM_BLK_MAXB] bit q of h for the cross bond
+};
+
+__host__ __device__ __forceinline__ size_t blk_al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// bytes of BlkShared after the staged rows
+__host__ __device__ __forceinline__ size_t blk_shared_bytes(int max_block) {
+    return blk_al16((size_t)max_block * 2) + blk_al16(HM_BLK_MAXB * 4) + blk_al16((HM_BLK_MAXC + 1) * 4) +
+           blk_al16(HM_BLK_MAXB * 4) + blk_al16(HM_BLK_MAXB * 4) + blk_al16(HM_BLK_MAXB) * 2;
+}
+
+__device__ __forceinline__ BlkShared blk_carve(unsigned char *p, int max_block) {
+    BlkShared s;
+    s.list = (uint16_t *)p; p += blk_al16((size_t)max_block * 2);
+    s.hcd = (int *)p; p += blk_al16(HM_BLK_MAXB * 4);
+    s.hcs = (int *)p; p += blk_al16((HM_BLK_MAXC + 1) * 4);
+    s.tmp = (int *)p; p += blk_al16(HM_BLK_MAXB * 4);
+    s.coff = (uint32_t *)p; p += blk_al16(HM_BLK_MAXB * 4);
+    s.ck = (int8_t *)p; p += blk_al16(HM_BLK_MAXB);
+    s.cbq = (uint8_t *)p;
+    return s;
+}
+
+// Offsets of the block one exchange away (high and cross bonds) and the low words of the
+// block, for the block of high word h whose low part holds k ones.  Contains barriers:
+// every thread of the CTA must call it.  Returns the block's row count; *off_out = off(h).
+__device__ __forceinline__ int blk_setup_block(const BlkParams &P, const BlkTabs &tb, uint32_t h, int k,
+                                               const BlkShared &sh, uint32_t *off_out) {
+    const uint32_t off = blk_off(P, tb, h, k);
+    const int n = (int)tb.C[P.K * (P.A + 1) + k];
+    for (int e = threadIdx.x; e < P.nhb; e += blockDim.x) {
+        const int p = P.hb_p[e], q = P.hb_q[e];
+        const bool valid = ((h >> p) ^ (h >> q)) & 1u;
+        sh.tmp[e] = valid ? (int)(blk_off(P, tb, h ^ ((1u << p) | (1u << q)), k) - off) : INT_MIN;
+    }
+    for (int e = threadIdx.x; e < P.ncb; e += blockDim.x) {
+        const int q = P.cb_q[e];
+        const uint32_t bq = (h >> q) & 1u;
+        const int k2 = k + (bq ? 1 : -1);
+        const bool ok = k2 >= 0 && k2 <= P.K;
+        sh.cbq[e] = (uint8_t)bq;
+        sh.ck[e] = (int8_t)(ok ? k2 : -1);
+        sh.coff[e] = ok ? blk_off(P, tb, h ^ (1u << q), k2) : 0u;
+    }
+    for (int b1 = threadIdx.x; b1 < P.nb1; b1 += blockDim.x) {
+        const int c0 = k - __popc(b1);
+        if (c0 < 0 || c0 > 8) continue;
+        int bs = tb.U[k * P.nb1 + b1];
+        const uint32_t hib = (uint32_t)b1 << 8;
+        if (c0 == 0) { sh.list[bs] = (uint16_t)hib; continue; }
+        uint32_t b0 = (1u << c0) - 1u;
+        while (b0 < 256u) {                        // bytes of popcount c0 in increasing order
+            sh.list[bs++] = (uint16_t)(hib | b0);
+            const uint32_t t = b0 | (b0 - 1);
+            b0 = (t + 1) | (((~t & (t + 1)) - 1) >> (__ffs(b0)));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {                        // compact the valid high exchanges by class
+        int cnt = 0;
+        for (int c = 0; c < HM_BLK_MAXC; ++c) {
+            sh.hcs[c] = cnt;
+            for (int e = P.hb_start[c]; e < P.hb_start[c + 1]; ++e)
+                if (sh.tmp[e] != INT_MIN) sh.hcd[cnt++] = sh.tmp[e];
+        }
+        sh.hcs[HM_BLK_MAXC] = cnt;
+    }
+    *off_out = off;
+    return n;
+}
+
+// f(r2) for every allowed exchange of class c among the low positions (targets in the
+// same block); returns their number
+template <class F>
+__device__ __forceinline__ int blk_low_hops(const BlkParams &P, const BlkTabs &tb, int c, uint32_t l,
+                                            uint32_t r, const uint16_t *Uk, F &&f) {
+    const uint32_t R0own = tb.R0[l & 255u];
+    const uint32_t R1own = r - R0own;
+    int mc = 0;
+    for (int g = P.lg_cs[3 * c]; g < P.lg_cs[3 * c + 1]; ++g) {        // inside byte 0
+        const int d = P.lg_d[g];
+        const uint32_t pat = 1u | (1u << d);
+        uint32_t m = ((l >> d) ^ l) & P.lg_mask[g];
+        while (m) {
+            const int p = __ffs(m) - 1;
+            m &= m - 1;
+            f(R1own + tb.R0[(l ^ (pat << p)) & 255u]);
+            ++mc;
+        }
+    }
+    for (int g = P.lg_cs[3 * c + 1]; g < P.lg_cs[3 * c + 2]; ++g) {    // inside byte 1
+        const int d = P.lg_d[g];
+        const uint32_t pat = 1u | (1u << d);
+        uint32_t m = ((l >> d) ^ l) & P.lg_mask[g];
+        while (m) {
+            const int p = __ffs(m) - 1;
+            m &= m - 1;
+            f(R0own + Uk[(l ^ (pat << p)) >> 8]);
+            ++mc;
+        }
+    }
+    for (int g = P.lg_cs[3 * c + 2]; g < P.lg_cs[3 * c + 3]; ++g) {    // across the bytes
+        const int d = P.lg_d[g];
+        const uint32_t pat = 1u | (1u << d);
+        uint32_t m = ((l >> d) ^ l) & P.lg_mask[g];
+        while (m) {
+            const int p = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t l2 = l ^ (pat << p);
+            f((uint32_t)Uk[l2 >> 8] + tb.R0[l2 & 255u]);
+            ++mc;
+        }
+    }
+    return mc;
+}
+
+// f(j) (j: row inside the sector) for every allowed exchange of class c across the split
+template <class F>
+__device__ __forceinline__ int blk_cross_hops(const BlkParams &P, const BlkTabs &tb, int c, uint32_t l,
+                                              const BlkShared &sh, F &&f) {
+    int mc = 0;
+    for (int e = P.cb_start[c]; e < P.cb_start[c + 1]; ++e) {
+        const int p = P.cb_p[e];
+        if ((((l >> p) & 1u) != sh.cbq[e]) && sh.ck[e] >= 0) {
+            const uint32_t l2 = l ^ (1u << p);
+            f(sh.coff[e] + rank_low(P, tb, l2, sh.ck[e]));
+            ++mc;
+        }
+    }
+    return mc;
 }
 
 }  // namespace hm

@@ -205,21 +205,45 @@ EF_HD uint64_t bits_from_df(df v, int scale) {
 
 // ---- fixed point -----------------------------------------------------------------------
 // A vector whose largest biased exponent field is E (all |x| < 2^(E-1022)) is mapped to
-// int64 X = x * 2^(FIX_BITS - (E - 1022)), so |X| < 2^FIX_BITS; the 8 bits above leave
-// room for sums of up to 2^7 terms of either sign and a factor 2.
-constexpr int FIX_BITS = 55;
+// int64 X = x * 2^(FIX_BITS - (E - 1022)), so |X| < 2^FIX_BITS = 2^53: every double of
+// the vector keeps its significand down to 2^-53 of the largest one, and the 10 bits above
+// leave room for sums of up to 2^9 terms of either sign.
+constexpr int FIX_BITS = 53;
 
 // binary64 bits -> fixed point (truncated toward zero).  E: the vector's largest
 // exponent field (>= the exponent field of b).
 EF_HD int64_t fix_from_bits(uint64_t b, int E) {
     const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
     const int e = (int)((hw >> 20) & 0x7FF);
-    // significand with the implicit bit, shifted left 2: M < 2^55
-    const uint64_t M = ((((uint64_t)(hw & 0xFFFFFu)) | 0x100000ull) << 34) | ((uint64_t)lw << 2);
-    int sh = E - e;                     // X = M >> sh (sh >= 0 by the choice of E)
+    // significand with the implicit bit: M < 2^53; x = M 2^(e-1075), X = M >> (E - e)
+    const uint64_t M = ((((uint64_t)(hw & 0xFFFFFu)) | 0x100000ull) << 32) | (uint64_t)lw;
+    int sh = E - e;
     sh = sh > 63 ? 63 : (sh < 0 ? 0 : sh);
     const uint64_t mag = e == 0 ? 0ull : (M >> sh);
     return (hw & 0x80000000u) ? -(int64_t)mag : (int64_t)mag;
+}
+
+// T * 2^k as a binary64 bit pattern, rounded to nearest even (exact int -> double)
+EF_HD uint64_t bits_from_int(int64_t T, int k) {
+    if (T == 0) return 0ull;
+    const uint64_t sign = T < 0 ? (1ull << 63) : 0ull;
+    uint64_t a = T < 0 ? (uint64_t)(-T) : (uint64_t)T;
+    const int lead = 63 - clz64(a);
+    int e2 = lead + k;
+    uint64_t mant;
+    if (lead > 52) {
+        const int rs = lead - 52;
+        uint64_t q = a >> rs, rem = a & ((1ull << rs) - 1), half = 1ull << (rs - 1);
+        if (rem > half || (rem == half && (q & 1))) ++q;
+        if (q >> 53) { q >>= 1; ++e2; }
+        mant = q;
+    } else {
+        mant = a << (52 - lead);
+    }
+    const int be = e2 + 1023;
+    if (be <= 0) return sign;
+    if (be >= 2047) return sign | 0x7FF0000000000000ull;
+    return sign | ((uint64_t)be << 52) | (mant & 0xFFFFFFFFFFFFFull);
 }
 
 // fixed point (unit 2^(E - 1022 - FIX_BITS)) times 2^extra -> double-float, scaled by

@@ -1,0 +1,734 @@
+// ftlm.cu -- finite-temperature Lanczos over all sectors of an s = 1/2 system in one
+// persistent, cooperative launch (Jaklic and Prelovsek's estimator; the paper cites it
+// as an application of the Lanczos machinery, Sec. 1).
+//
+// For every sector A (digit sum, M = N/2 - A) and start vector r = 0..R-1 a Lanczos run
+// of up to `steps` steps starts from the +-1 vector of SplitMix64 stream (seed, A, r).
+// All R runs of a sector share one product: a row's R vector entries sit in one
+// 128-byte line (row-major [dim][32]), a warp serves VT rows with 32/VT lanes each, lane
+// l of a row holding vectors l*VT .. l*VT+VT-1, so the codec of a row runs once per
+// warp instruction for all of its vectors.  The rows of all sectors are cut into the
+// blocks of blk.cuh (one high word, all low words); a step is four phases separated by
+// grid barriers with bounded waits:
+//   A  u = sigma H q - beta_prev sigma_prev q_prev over q_prev, alpha partials
+//   B  alpha per (sector, vector)
+//   C  w = u - alpha sigma q over q_prev, |w|^2 partials
+//   D  beta, breakdown, sigma
+// Then per (sector, vector) the tridiagonal T is diagonalised on the device (implicit
+// symmetric QR with Wilkinson shifts, Golub and Van Loan, Matrix Computations, Sec. 8.3),
+// keeping the first row of the eigenvector matrix: Ritz values theta_j and weights
+// tau_j = (first component)^2.  Finally
+//   Z(T) = sum_A (D_A / R) sum_r sum_j tau e^{-(theta - e_ref)/T},
+//   E(T) = [same with theta inside] / Z(T)     (Z returned relative to e^{-e_ref/T}).
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "blk.cuh"
+
+namespace hm {
+
+int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *out);
+__host__ __device__ __forceinline__ size_t al16f(size_t x) { return (x + 15) & ~(size_t)15; }
+
+constexpr int FT_NT = 512;          // threads per CTA of the persistent kernel
+constexpr int FT_W = 32;            // row stride in floats (vectors per row, padded)
+constexpr int FT_MAXS = 65;         // sectors (N + 1 for s = 1/2, N <= 64)
+constexpr double FT_TOL = 1e-5;     // breakdown threshold (above the FP32 noise floor)
+
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    int abort;
+    int pad;
+};
+
+struct FtDev {
+    // per (sector, vector) state, index s * FT_W + v
+    double *sig_cur, *sig_prev, *beta_prev, *scale, *as;
+    int *done, *nsteps;
+    double *alpha, *beta;           // [(s * FT_W + v) * steps + j]
+    double *part;                   // [cta][s][v]
+    int *sec_active;                // [s]
+    GridBar *bar;
+    const uint32_t *items;          // (A << 16) | h, sorted by A
+    const uint64_t *rowoff;         // first global row of sector A
+    const uint32_t *secdim;         // D(N, A)
+    float *q0, *q1;                 // [rows][FT_W]
+    double *theta, *tau;            // [(s * FT_W + v) * steps + j]
+    int *mlen;                      // Krylov length per (s, v)
+    double *zsum, *esum, *eref;     // thermodynamics (n_t each), e_ref
+};
+
+struct FtParams {
+    BlkParams P;                    // block plan built with A = N (full binomial table)
+    FtDev d;
+    int nsec, R, steps, nitems;
+    unsigned nctas;
+    uint64_t seed;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// grid-wide barrier of a cooperative launch; gives up after limit_ns (sets abort) so a
+// lost CTA can never hang the GPU
+__device__ bool grid_sync(GridBar *gb, unsigned nctas, unsigned long long limit_ns) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &gb->gen;
+        volatile int *vab = &gb->abort;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&gb->count, 1u);
+        if (arrived == nctas - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            const unsigned long long t0 = globaltimer_ns();
+            while (*vgen == g) {
+                if (*vab) break;
+                if (globaltimer_ns() - t0 > limit_ns) { atomicExch(&gb->abort, 1); break; }
+                __nanosleep(200);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int *)&gb->abort == 0;
+}
+
+// ---- start vectors and state -----------------------------------------------------------
+__global__ void k_ft_init(FtParams F) {
+    const FtDev &d = F.d;
+    const uint64_t nrows = d.rowoff[F.nsec];
+    const uint64_t total = nrows * FT_W;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t row = t / FT_W;
+        const int v = (int)(t % FT_W);
+        int A = 0;
+        while (d.rowoff[A + 1] <= row) ++A;          // few sectors: linear search
+        float val = 0.0f;
+        if (v < F.R) {
+            const uint64_t stream = sm64(F.seed, ((uint64_t)A << 20) + (uint64_t)v);
+            val = (sm64(stream, row - d.rowoff[A]) >> 63) ? -1.0f : 1.0f;
+        }
+        d.q0[t] = val;
+        d.q1[t] = 0.0f;
+    }
+    const int nst = F.nsec * FT_W;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nst; t += gridDim.x * blockDim.x) {
+        const int s = t / FT_W, v = t % FT_W;
+        const bool on = v < F.R && d.secdim[s] > 0;
+        d.sig_cur[t] = on ? 1.0 / sqrt((double)d.secdim[s]) : 0.0;   // |+-1 vector| = sqrt(dim)
+        d.sig_prev[t] = 0.0;
+        d.beta_prev[t] = 0.0;
+        d.scale[t] = 0.0;
+        d.as[t] = 0.0;
+        d.done[t] = on ? 0 : 1;
+        d.nsteps[t] = 0;
+        d.mlen[t] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < FT_MAXS && (int)threadIdx.x < F.nsec) d.sec_active[threadIdx.x] = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) { d.bar->count = 0; d.bar->gen = 0; d.bar->abort = 0; }
+}
+
+// ---- the persistent kernel ---------------------------------------------------------------
+// shared layout: block tables | low words | staged rows [max_block][FT_W] floats |
+// hop lists | sigma/gamma of the item's sector | per-CTA accumulators [nsec][FT_W] (df)
+template <int NC, int VT>
+__global__ void __launch_bounds__(FT_NT, 1) k_ftlm(FtParams F) {
+    const BlkParams &P = F.P;
+    const FtDev &d = F.d;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const BlkTabs tb = stage_blk_tables(P, smem);
+    size_t o = al16f(P.tab_bytes);
+    float *Xs = (float *)(smem + o); o += al16f((size_t)P.max_block * FT_W * 4);
+    const BlkShared sh = blk_carve(smem + o, P.max_block); o += blk_shared_bytes(P.max_block);
+    float *sg = (float *)(smem + o); o += al16f(FT_W * 4 * 3);   // sigma, gamma, alpha*sigma
+    float *red = (float *)(smem + o); o += al16f((size_t)(FT_NT / 32) * 4 * 2 * FT_W * 4);   // [warp*VT+grp][v] df
+    ef::df *cacc = (ef::df *)(smem + o);                          // [nsec][FT_W]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lpr = 32 / VT;                       // lanes per row
+    const int grp = lane / lpr, li = lane % lpr;   // row group in the warp, lane in row
+    const int v0 = li * VT;                        // first vector of this lane
+    const int nwarps = FT_NT / 32;
+    const unsigned long long LIMIT = 5000000000ull;   // 5 s per barrier
+    for (int t = threadIdx.x; t < F.nsec * FT_W; t += FT_NT) cacc[t] = ef::df{0.0f, 0.0f};
+    __syncthreads();
+
+    for (int j = 0; j < F.steps; ++j) {
+        // ---------------- phase A: products ----------------
+        for (int it = blockIdx.x; it < F.nitems; it += gridDim.x) {
+            const uint32_t item = d.items[it];
+            const int A = (int)(item >> 16);
+            const uint32_t h = item & 0xFFFFu;
+            if (!d.sec_active[A]) continue;
+            const int k = A - __popc(h);
+            const uint64_t base = d.rowoff[A];
+            __syncthreads();
+            // block setup (offsets inside the sector; rows of the sector start at base)
+            uint32_t off;
+            const int n = blk_setup_block(P, tb, h, k, sh, &off);
+            const float4 *src = (const float4 *)((j & 1) ? d.q1 : d.q0) + (base + off) * (FT_W / 4);
+            for (int t = threadIdx.x; t < n * (FT_W / 4); t += FT_NT) ((float4 *)Xs)[t] = src[t];
+            if (threadIdx.x < FT_W) {
+                const int sv = A * FT_W + threadIdx.x;
+                sg[threadIdx.x] = (float)d.sig_cur[sv];
+                sg[FT_W + threadIdx.x] = (float)(d.beta_prev[sv] * d.sig_prev[sv]);
+            }
+            __syncthreads();
+            const float *qc = (j & 1) ? d.q1 : d.q0;
+            float *qp = (j & 1) ? d.q0 : d.q1;
+            const uint16_t *Uk = tb.U + k * P.nb1;
+            ef::df dot[VT];
+#pragma unroll
+            for (int q = 0; q < VT; ++q) dot[q] = ef::df{0.0f, 0.0f};
+            for (int r = warp * VT + grp; r < n; r += nwarps * VT) {
+                const uint32_t l = sh.list[r];
+                float acc[NC][VT];
+                int cnt[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    float *ac = acc[c];
+#pragma unroll
+                    for (int q = 0; q < VT; ++q) ac[q] = 0.0f;
+                    int mc = blk_low_hops(P, tb, c, l, (uint32_t)r, Uk, [&](uint32_t r2) {
+                        const float *xr = Xs + (size_t)r2 * FT_W + v0;
+#pragma unroll
+                        for (int q = 0; q < VT; ++q) ac[q] += xr[q];
+                    });
+                    mc += blk_cross_hops(P, tb, c, l, sh, [&](uint32_t jj) {
+                        const float *xr = qc + (base + jj) * FT_W + v0;
+#pragma unroll
+                        for (int q = 0; q < VT; ++q) ac[q] += __ldg(xr + q);
+                    });
+                    for (int e = sh.hcs[c]; e < sh.hcs[c + 1]; ++e) {
+                        const uint64_t jr = base + (uint64_t)((int64_t)(off + (uint32_t)r) + sh.hcd[e]);
+                        const float *xr = qc + jr * FT_W + v0;
+#pragma unroll
+                        for (int q = 0; q < VT; ++q) ac[q] += __ldg(xr + q);
+                    }
+                    cnt[c] = mc + (sh.hcs[c + 1] - sh.hcs[c]);
+                }
+                const uint64_t row = base + off + (uint32_t)r;
+#pragma unroll
+                for (int q = 0; q < VT; ++q) {
+                    const float xo = Xs[(size_t)r * FT_W + v0 + q];
+                    float y = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) y += P.gq[c] * (2.0f * acc[c][q] + (float)(P.ntot[c] - 2 * cnt[c]) * xo);
+                    const float u = sg[v0 + q] * y - sg[FT_W + v0 + q] * qp[row * FT_W + v0 + q];
+                    qp[row * FT_W + v0 + q] = u;
+                    dot[q] = ef::df_add(dot[q], ef::two_prod(sg[v0 + q] * xo, u));
+                }
+            }
+            // item reduction: per vector over warps and row groups, fixed order
+#pragma unroll
+            for (int q = 0; q < VT; ++q) {
+                red[((warp * VT + grp) * FT_W + v0 + q) * 2] = dot[q].hi;
+                red[((warp * VT + grp) * FT_W + v0 + q) * 2 + 1] = dot[q].lo;
+            }
+            __syncthreads();
+            if (threadIdx.x < FT_W) {
+                ef::df s = cacc[A * FT_W + threadIdx.x];
+                for (int w = 0; w < nwarps * VT; ++w)
+                    s = ef::df_add(s, ef::df{red[(w * FT_W + threadIdx.x) * 2], red[(w * FT_W + threadIdx.x) * 2 + 1]});
+                cacc[A * FT_W + threadIdx.x] = s;
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < F.nsec * FT_W; t += FT_NT) {
+            d.part[(size_t)blockIdx.x * F.nsec * FT_W + t] = (double)cacc[t].hi + (double)cacc[t].lo;
+            cacc[t] = ef::df{0.0f, 0.0f};
+        }
+        if (!grid_sync(d.bar, F.nctas, LIMIT)) return;
+        // ---------------- phase B: alpha ----------------
+        for (int t = blockIdx.x * FT_NT + threadIdx.x; t < F.nsec * FT_W; t += gridDim.x * FT_NT) {
+            if (d.done[t]) continue;
+            double a = 0.0;
+            for (unsigned c = 0; c < F.nctas; ++c) a += d.part[(size_t)c * F.nsec * FT_W + t];
+            d.alpha[(size_t)t * F.steps + j] = a;
+            d.scale[t] = fmax(d.scale[t], fabs(a));
+            d.as[t] = a * d.sig_cur[t];
+        }
+        if (!grid_sync(d.bar, F.nctas, LIMIT)) return;
+        // ---------------- phase C: update ----------------
+        for (int it = blockIdx.x; it < F.nitems; it += gridDim.x) {
+            const uint32_t item = d.items[it];
+            const int A = (int)(item >> 16);
+            const uint32_t h = item & 0xFFFFu;
+            if (!d.sec_active[A]) continue;
+            const int k = A - __popc(h);
+            const uint32_t off = blk_off(P, tb, h, k);
+            const int n = (int)tb.C[P.K * (P.A + 1) + k];
+            const uint64_t base = d.rowoff[A] + off;
+            __syncthreads();
+            if (threadIdx.x < FT_W) sg[2 * FT_W + threadIdx.x] = (float)d.as[A * FT_W + threadIdx.x];
+            __syncthreads();
+            const float *qc = (j & 1) ? d.q1 : d.q0;
+            float *qp = (j & 1) ? d.q0 : d.q1;
+            ef::df nn[VT];
+#pragma unroll
+            for (int q = 0; q < VT; ++q) nn[q] = ef::df{0.0f, 0.0f};
+            for (int r = warp * VT + grp; r < n; r += nwarps * VT) {
+                const uint64_t row = base + (uint32_t)r;
+#pragma unroll
+                for (int q = 0; q < VT; ++q) {
+                    const uint64_t ix = row * FT_W + v0 + q;
+                    const float w = qp[ix] - sg[2 * FT_W + v0 + q] * qc[ix];
+                    qp[ix] = w;
+                    nn[q] = ef::df_add(nn[q], ef::two_prod(w, w));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < VT; ++q) {
+                red[((warp * VT + grp) * FT_W + v0 + q) * 2] = nn[q].hi;
+                red[((warp * VT + grp) * FT_W + v0 + q) * 2 + 1] = nn[q].lo;
+            }
+            __syncthreads();
+            if (threadIdx.x < FT_W) {
+                ef::df s = cacc[A * FT_W + threadIdx.x];
+                for (int w = 0; w < nwarps * VT; ++w)
+                    s = ef::df_add(s, ef::df{red[(w * FT_W + threadIdx.x) * 2], red[(w * FT_W + threadIdx.x) * 2 + 1]});
+                cacc[A * FT_W + threadIdx.x] = s;
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < F.nsec * FT_W; t += FT_NT) {
+            d.part[(size_t)blockIdx.x * F.nsec * FT_W + t] = (double)cacc[t].hi + (double)cacc[t].lo;
+            cacc[t] = ef::df{0.0f, 0.0f};
+        }
+        if (!grid_sync(d.bar, F.nctas, LIMIT)) return;
+        // ---------------- phase D: beta ----------------
+        for (int t = blockIdx.x * FT_NT + threadIdx.x; t < F.nsec * FT_W; t += gridDim.x * FT_NT) {
+            bool act = false;
+            if (!d.done[t]) {
+                double s = 0.0;
+                for (unsigned c = 0; c < F.nctas; ++c) s += d.part[(size_t)c * F.nsec * FT_W + t];
+                const double b = sqrt(s);
+                d.beta[(size_t)t * F.steps + j] = b;
+                d.nsteps[t] = j + 1;
+                // stop when beta is at the noise floor or the sector is exhausted
+                if (b <= FT_TOL * d.scale[t] || (uint32_t)(j + 1) >= d.secdim[t / FT_W]) {
+                    d.done[t] = 1;
+                    d.sig_cur[t] = 0.0;
+                    d.sig_prev[t] = 0.0;
+                    d.beta_prev[t] = 0.0;
+                    d.as[t] = 0.0;
+                } else {
+                    d.scale[t] = fmax(d.scale[t], b);
+                    d.sig_prev[t] = d.sig_cur[t];
+                    d.sig_cur[t] = 1.0 / b;
+                    d.beta_prev[t] = b;
+                    act = true;
+                }
+            }
+            // a sector stays active while any of its vectors runs (a warp holds one sector)
+            const unsigned any = __ballot_sync(0xffffffffu, act);
+            if ((t & 31) == 0) d.sec_active[t / FT_W] = any != 0u;
+        }
+        if (!grid_sync(d.bar, F.nctas, LIMIT)) return;
+    }
+}
+
+// ---- tridiagonal eigen-decomposition with the first components -------------------------
+// Implicit symmetric QR with Wilkinson shifts (Golub and Van Loan, Sec. 8.3): each sweep
+// chases a bulge down the unreduced block with Givens rotations; the rotations are also
+// applied to z, the first row of the accumulated eigenvector matrix.
+__device__ void tri_ql_first(int m, double *dg, double *e, double *z) {
+    for (int i = 0; i < m; ++i) z[i] = i == 0 ? 1.0 : 0.0;
+    int hi = m - 1, guard = 0;
+    while (hi > 0 && guard < 60 * m) {
+        const double tol = 2.220446049250313e-16 * (fabs(dg[hi - 1]) + fabs(dg[hi]));
+        if (fabs(e[hi - 1]) <= tol) { e[hi - 1] = 0.0; --hi; continue; }
+        int lo = hi - 1;
+        while (lo > 0 && fabs(e[lo - 1]) > 2.220446049250313e-16 * (fabs(dg[lo - 1]) + fabs(dg[lo]))) --lo;
+        ++guard;
+        // Wilkinson shift: eigenvalue of the trailing 2x2 block closer to dg[hi]
+        const double dd = 0.5 * (dg[hi - 1] - dg[hi]);
+        const double eh = e[hi - 1];
+        const double den = dd + copysign(sqrt(dd * dd + eh * eh), dd == 0.0 ? 1.0 : dd);
+        const double mu = dg[hi] - eh * eh / den;
+        double x = dg[lo] - mu, y = e[lo];
+        for (int kk = lo; kk < hi; ++kk) {
+            const double r = hypot(x, y);
+            const double c = r == 0.0 ? 1.0 : x / r, s = r == 0.0 ? 0.0 : y / r;
+            if (kk > lo) e[kk - 1] = r;
+            const double a = dg[kk], b = e[kk], cc = dg[kk + 1];
+            dg[kk] = c * c * a + 2.0 * c * s * b + s * s * cc;
+            dg[kk + 1] = s * s * a - 2.0 * c * s * b + c * c * cc;
+            e[kk] = c * s * (cc - a) + (c * c - s * s) * b;
+            const double zk = z[kk], zk1 = z[kk + 1];
+            z[kk] = c * zk + s * zk1;
+            z[kk + 1] = -s * zk + c * zk1;
+            if (kk + 1 < hi) {
+                x = e[kk];
+                y = s * e[kk + 1];
+                e[kk + 1] = c * e[kk + 1];
+            }
+        }
+    }
+}
+
+__global__ void k_ft_eig(FtParams F, double *scratch) {
+    const FtDev &d = F.d;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= F.nsec * FT_W) return;
+    const int v = t % FT_W;
+    const int m = (v < F.R) ? d.nsteps[t] : 0;
+    d.mlen[t] = m;
+    if (m == 0) return;
+    double *dg = scratch + (size_t)t * 3 * F.steps, *e = dg + F.steps, *z = e + F.steps;
+    for (int i = 0; i < m; ++i) dg[i] = d.alpha[(size_t)t * F.steps + i];
+    for (int i = 0; i + 1 < m; ++i) e[i] = d.beta[(size_t)t * F.steps + i];
+    if (m > 1) e[m - 1] = 0.0;
+    tri_ql_first(m, dg, e, z);
+    for (int i = 0; i < m; ++i) {
+        d.theta[(size_t)t * F.steps + i] = dg[i];
+        d.tau[(size_t)t * F.steps + i] = z[i] * z[i];
+    }
+}
+
+// one block: e_ref = min theta, then Z and E sums for each temperature (fixed order)
+__global__ void k_ft_thermo(FtParams F, const double *temps, int n_t) {
+    const FtDev &d = F.d;
+    __shared__ double red[32];
+    __shared__ double s_ref;
+    const int nst = F.nsec * FT_W;
+    double mn = 1e308;
+    for (int t = threadIdx.x; t < nst; t += blockDim.x)
+        for (int i = 0; i < d.mlen[t]; ++i) mn = fmin(mn, d.theta[(size_t)t * F.steps + i]);
+    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 1e308;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmin(m, red[w]);
+        s_ref = m;
+        *d.eref = m;
+    }
+    __syncthreads();
+    const double e_ref = s_ref;
+    for (int it = 0; it < n_t; ++it) {
+        const double T = temps[it];
+        double z = 0.0, ez = 0.0;
+        for (int t = threadIdx.x; t < nst; t += blockDim.x) {
+            const int s = t / FT_W;
+            const double wgt = (double)d.secdim[s] / (double)F.R;
+            for (int i = 0; i < d.mlen[t]; ++i) {
+                const double th = d.theta[(size_t)t * F.steps + i];
+                const double b = d.tau[(size_t)t * F.steps + i] * exp(-(th - e_ref) / T) * wgt;
+                z += b;
+                ez += b * th;
+            }
+        }
+        __syncthreads();
+        double zs = block_sum<1024>(z, red);
+        __syncthreads();
+        double es = block_sum<1024>(ez, red);
+        if (threadIdx.x == 0) { d.zsum[it] = zs; d.esum[it] = es / zs; }
+        __syncthreads();
+    }
+}
+
+// ---- host --------------------------------------------------------------------------------
+struct FtLayout {
+    size_t q0, q1, st, ab, part, sec, bar, items, rowoff, secdim, theta, tau, mlen, therm, temps, eigs, total;
+};
+
+static int ft_choose_K(int N) {
+    // largest K (8..16, K <= N-2) whose biggest block of 32-float rows fits ~150 KB
+    int best = -1;
+    for (int K = 8; K <= 16 && K <= N - 2; ++K) {
+        uint64_t c = 1;
+        for (int i = 0; i < K / 2; ++i) c = c * (K - i) / (i + 1);
+        if (c * FT_W * 4 <= 150 * 1024) best = K;
+    }
+    return best;
+}
+
+static FtLayout ft_layout(int N, int nsec, int R, int steps, int nitems, int nctas, int n_t) {
+    (void)R;
+    FtLayout L{};
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const uint64_t rows = 1ull << N;     // sum of all sector dimensions for s = 1/2
+    const size_t nst = (size_t)nsec * FT_W;
+    size_t o = 0;
+    L.q0 = o; o += a(rows * FT_W * 4);
+    L.q1 = o; o += a(rows * FT_W * 4);
+    L.st = o; o += a(nst * 8 * 5 + nst * 4 * 2);
+    L.ab = o; o += a(nst * (size_t)steps * 8 * 2);
+    L.part = o; o += a((size_t)nctas * nst * 8);
+    L.sec = o; o += a(FT_MAXS * 4);
+    L.bar = o; o += a(sizeof(GridBar));
+    L.items = o; o += a((size_t)nitems * 4);
+    L.rowoff = o; o += a((size_t)(nsec + 1) * 8);
+    L.secdim = o; o += a((size_t)nsec * 4);
+    L.theta = o; o += a(nst * (size_t)steps * 8);
+    L.tau = o; o += a(nst * (size_t)steps * 8);
+    L.mlen = o; o += a(nst * 4);
+    L.therm = o; o += a((size_t)(2 * n_t + 1) * 8);
+    L.temps = o; o += a((size_t)(n_t > 0 ? n_t : 1) * 8);
+    L.eigs = o; o += a(nst * 3 * (size_t)steps * 8);
+    L.total = o;
+    return L;
+}
+
+template <int NC, int VT>
+static const void *ft_kernel() { return (const void *)k_ftlm<NC, VT>; }
+
+static const void *pick_kernel(int nc, int vt) {
+    if (nc == 1) return vt == 1 ? ft_kernel<1, 1>() : vt == 2 ? ft_kernel<1, 2>() : ft_kernel<1, 4>();
+    if (nc == 2) return vt == 1 ? ft_kernel<2, 1>() : vt == 2 ? ft_kernel<2, 2>() : ft_kernel<2, 4>();
+    return vt == 1 ? ft_kernel<4, 1>() : vt == 2 ? ft_kernel<4, 2>() : ft_kernel<4, 4>();
+}
+
+static size_t ft_smem(const BlkParams &P, int nsec) {
+    size_t o = al16f(P.tab_bytes);
+    o += al16f((size_t)P.max_block * FT_W * 4);
+    o += blk_shared_bytes(P.max_block);
+    o += al16f(FT_W * 4 * 3);
+    o += al16f((size_t)(FT_NT / 32) * 4 * 2 * FT_W * 4);
+    o += al16f((size_t)nsec * FT_W * sizeof(ef::df));
+    return o;
+}
+
+// vectors-per-lane tiling chosen by timing each candidate once per (N, bonds) shape
+static std::map<std::pair<int, int>, int> g_ft_tuned;
+
+struct FtSetup {
+    hm_basis full;                   // tables with the full binomial table (A = N)
+    FtParams F;
+    FtLayout L;
+    size_t smem;
+    int nctas;
+};
+
+static int ft_prepare(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_t *v,
+                      const double *J, int R, int steps, int n_t, FtSetup *S, std::vector<uint32_t> *items) {
+    if (two_s != 1) return fail(HM_EINVAL, "ftlm_run supports s = 1/2 (two_s = 1)");
+    if (R < 1 || R > FT_W) return fail(HM_EINVAL, "R must be in 1..%d", FT_W);
+    if (steps < 1 || steps > 2000) return fail(HM_EINVAL, "steps must be in 1..2000");
+    if (n_t < 0 || n_t > 4096) return fail(HM_EINVAL, "n_t must be in 0..4096");
+    const int K = ft_choose_K(n_sites);
+    if (K < 0 || n_sites > 32) return fail(HM_EINVAL, "ftlm_run needs 10 <= n_sites <= 32");
+    HM_TRY(build_tables(n_sites, 1, -n_sites, &S->full));      // A = N: full table
+    BondParams bp;
+    HM_TRY(make_bonds(&S->full, n_bonds, u, v, J, &bp));
+    memset(&S->F, 0, sizeof S->F);
+    const int prc = blk_plan(&S->full, bp, K, &S->F.P);
+    if (prc < 0) return prc;
+    if (prc > 0) return fail(HM_EINVAL, "ftlm_run: more than %d coupling classes or %d bonds", HM_BLK_MAXC, HM_BLK_MAXB);
+    // the plan's block size was taken for A = N; use the largest over all sectors
+    uint64_t mb = 1;
+    for (int i = 0; i < K / 2; ++i) mb = mb * (K - i) / (i + 1);
+    S->F.P.max_block = (int)mb;
+    const int nsec = n_sites + 1;
+    items->clear();
+    const int H = n_sites - K;
+    for (int A = 0; A <= n_sites; ++A)
+        for (uint32_t h = 0; h < (1u << H); ++h) {
+            const int k = A - __builtin_popcount(h);
+            if (k >= 0 && k <= K) items->push_back(((uint32_t)A << 16) | h);
+        }
+    S->F.nsec = nsec;
+    S->F.R = R;
+    S->F.steps = steps;
+    S->F.nitems = (int)items->size();
+    S->smem = ft_smem(S->F.P, nsec);
+    if (S->smem > 227 * 1024) return fail(HM_EINVAL, "ftlm_run: shared memory plan too large");
+    int per_sm = 0;
+    const void *kfn = pick_kernel(S->F.P.nc, 1);
+    HM_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem));
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, FT_NT, S->smem));
+    if (per_sm < 1) return fail(HM_EINVAL, "ftlm_run: kernel does not fit on an SM");
+    S->nctas = sm_count();   // one CTA per SM (cooperative: all resident)
+    S->F.nctas = (unsigned)S->nctas;
+    S->L = ft_layout(n_sites, nsec, R, steps, S->F.nitems, S->nctas, n_t);
+    return HM_OK;
+}
+
+static void ft_bind(FtSetup *S, unsigned char *w) {
+    const FtLayout &L = S->L;
+    FtDev &d = S->F.d;
+    const size_t nst = (size_t)S->F.nsec * FT_W;
+    d.q0 = (float *)(w + L.q0);
+    d.q1 = (float *)(w + L.q1);
+    double *st = (double *)(w + L.st);
+    d.sig_cur = st; d.sig_prev = st + nst; d.beta_prev = st + 2 * nst; d.scale = st + 3 * nst; d.as = st + 4 * nst;
+    d.done = (int *)(st + 5 * nst);
+    d.nsteps = d.done + nst;
+    d.alpha = (double *)(w + L.ab);
+    d.beta = d.alpha + nst * S->F.steps;
+    d.part = (double *)(w + L.part);
+    d.sec_active = (int *)(w + L.sec);
+    d.bar = (GridBar *)(w + L.bar);
+    d.items = (const uint32_t *)(w + L.items);
+    d.rowoff = (const uint64_t *)(w + L.rowoff);
+    d.secdim = (const uint32_t *)(w + L.secdim);
+    d.theta = (double *)(w + L.theta);
+    d.tau = (double *)(w + L.tau);
+    d.mlen = (int *)(w + L.mlen);
+    double *th = (double *)(w + L.therm);
+    d.zsum = th;
+    d.esum = th + 1;   // reassigned with n_t below
+    d.eref = th;
+}
+
+static int ft_launch_persistent(FtSetup *S, int vt, cudaStream_t st) {
+    const void *kfn = pick_kernel(S->F.P.nc, vt);
+    HM_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(S->nctas);
+    cfg.blockDim = dim3(FT_NT);
+    cfg.dynamicSmemBytes = S->smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    void *args[] = {(void *)&S->F};
+    HM_CUDA(cudaLaunchKernelExC(&cfg, kfn, args));
+    return HM_OK;
+}
+
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" {
+
+int ftlm_workspace(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_t *v,
+                   const double *J, int R, int steps, int n_t, size_t *bytes) {
+    if (!bytes) return fail(HM_EINVAL, "bytes is NULL");
+    FtSetup S;
+    std::vector<uint32_t> items;
+    HM_TRY(ft_prepare(n_sites, two_s, n_bonds, u, v, J, R, steps, n_t, &S, &items));
+    *bytes = S.L.total;
+    return HM_OK;
+}
+
+int ftlm_run(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_t *v, const double *J,
+             int R, int steps, uint64_t seed, const double *temps, int n_t, double *Z, double *E,
+             double *e_ref, double *theta, double *tau, int *mlen, int vt, void *work,
+             size_t work_bytes, void *stream) {
+    if (n_t > 0 && (!temps || !Z || !E)) return fail(HM_EINVAL, "temperature arrays are NULL");
+    if (vt != 0 && vt != 1 && vt != 2 && vt != 4) return fail(HM_EINVAL, "vt must be 0 (autotune), 1, 2 or 4");
+    FtSetup S;
+    std::vector<uint32_t> items;
+    HM_TRY(ft_prepare(n_sites, two_s, n_bonds, u, v, J, R, steps, n_t, &S, &items));
+    if (!work || work_bytes < S.L.total || ((uintptr_t)work & 255))
+        return fail(HM_EWORKSPACE, "ftlm_run needs %zu workspace bytes (256-byte aligned)", S.L.total);
+    cudaStream_t st = as_stream(stream);
+    unsigned char *w = (unsigned char *)work;
+    ft_bind(&S, w);
+    S.F.seed = seed;
+    double *therm = (double *)(w + S.L.therm);
+    S.F.d.eref = therm;
+    S.F.d.zsum = therm + 1;
+    S.F.d.esum = therm + 1 + n_t;
+    // host-built inputs: items, sector row offsets and dimensions
+    const int nsec = S.F.nsec;
+    std::vector<uint64_t> rowoff(nsec + 1, 0);
+    std::vector<uint32_t> dims(nsec);
+    {
+        const int W = S.full.view.S2 * n_sites + 1;
+        for (int A = 0; A < nsec; ++A) {
+            dims[A] = (uint32_t)S.full.D[(size_t)n_sites * W + A];
+            rowoff[A + 1] = rowoff[A] + dims[A];
+        }
+    }
+    HM_CUDA(cudaMemcpyAsync(w + S.L.items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(w + S.L.rowoff, rowoff.data(), rowoff.size() * 8, cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(w + S.L.secdim, dims.data(), dims.size() * 4, cudaMemcpyHostToDevice, st));
+    double *d_temps = (double *)(w + S.L.temps);
+    if (n_t > 0) HM_CUDA(cudaMemcpyAsync(d_temps, temps, n_t * 8, cudaMemcpyHostToDevice, st));
+    // autotune the vectors-per-lane tiling on a short run (2 steps), once per shape
+    int use_vt = vt;
+    if (use_vt == 0) {
+        auto key = std::make_pair(n_sites, S.F.P.nc * 1000 + S.F.P.nhb * 10 + R);
+        auto it = g_ft_tuned.find(key);
+        if (it != g_ft_tuned.end()) {
+            use_vt = it->second;
+        } else {
+            float best = 1e30f;
+            int bvt = 1;
+            FtParams keep = S.F;
+            S.F.steps = std::min(steps, 2);
+            cudaEvent_t e0, e1;
+            HM_CUDA(cudaEventCreate(&e0));
+            HM_CUDA(cudaEventCreate(&e1));
+            for (int cand : {1, 2, 4}) {
+                k_ft_init<<<sm_count() * 4, 256, 0, st>>>(S.F);
+                HM_CUDA(cudaGetLastError());
+                HM_CUDA(cudaEventRecord(e0, st));
+                HM_TRY(ft_launch_persistent(&S, cand, st));
+                HM_CUDA(cudaEventRecord(e1, st));
+                HM_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                HM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; bvt = cand; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            S.F = keep;
+            use_vt = bvt;
+            g_ft_tuned[key] = bvt;
+        }
+    }
+    // the run: init, persistent steps, eigen-decompositions, sums -- one captured graph
+    cudaStream_t cap;
+    HM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    int rc = HM_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) rc = cuda_fail(e, "ftlm capture");
+    if (rc == HM_OK) {
+        k_ft_init<<<sm_count() * 4, 256, 0, cap>>>(S.F);
+        if ((e = cudaGetLastError()) != cudaSuccess) rc = cuda_fail(e, "k_ft_init");
+        if (rc == HM_OK) rc = ft_launch_persistent(&S, use_vt, cap);
+        if (rc == HM_OK) {
+            const int nst = nsec * FT_W;
+            k_ft_eig<<<(nst + 127) / 128, 128, 0, cap>>>(S.F, (double *)(w + S.L.eigs));
+            if ((e = cudaGetLastError()) != cudaSuccess) rc = cuda_fail(e, "k_ft_eig");
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (rc == HM_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "ftlm end capture");
+    }
+    if (rc == HM_OK && (e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) rc = cuda_fail(e, "ftlm instantiate");
+    if (rc == HM_OK && (e = cudaGraphLaunch(ge, st)) != cudaSuccess) rc = cuda_fail(e, "ftlm graph launch");
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    HM_TRY(rc);
+    if (n_t > 0) {
+        k_ft_thermo<<<1, 1024, 0, st>>>(S.F, d_temps, n_t);
+        HM_CUDA(cudaGetLastError());
+    }
+    GridBar bar;
+    HM_CUDA(cudaMemcpyAsync(&bar, S.F.d.bar, sizeof bar, cudaMemcpyDeviceToHost, st));
+    std::vector<double> th(1 + 2 * (size_t)n_t);
+    HM_CUDA(cudaMemcpyAsync(th.data(), therm, th.size() * 8, cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    if (bar.abort) return fail(HM_ETIMEOUT, "ftlm_run: a grid barrier timed out");
+    if (e_ref) *e_ref = th[0];
+    for (int i = 0; i < n_t; ++i) { Z[i] = th[1 + i]; E[i] = th[1 + n_t + i]; }
+    const size_t nst = (size_t)nsec * FT_W;
+    if (theta) HM_CUDA(cudaMemcpy(theta, S.F.d.theta, nst * steps * 8, cudaMemcpyDeviceToHost));
+    if (tau) HM_CUDA(cudaMemcpy(tau, S.F.d.tau, nst * steps * 8, cudaMemcpyDeviceToHost));
+    if (mlen) HM_CUDA(cudaMemcpy(mlen, S.F.d.mlen, nst * 4, cudaMemcpyDeviceToHost));
+    return use_vt;   // > 0: the tiling that ran (informational)
+}
+
+}  // extern "C"

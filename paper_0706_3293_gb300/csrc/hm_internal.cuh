@@ -85,6 +85,7 @@ struct LzScalars {
     int status;
     int mconv;           // e0_grad: Krylov length used
     int emax[2];         // largest exponent field of the vector held in buffer 0 / 1
+    int emax_old;        // exponent of q_prev while its buffer receives w
 };
 
 int digit_bits(int two_s);

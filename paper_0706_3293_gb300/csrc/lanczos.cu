@@ -1,5 +1,6 @@
 // lanczos.cu -- the Lanczos recurrence around the row matvec, the tridiagonal
 // eigensolvers on the device, lanczos_run (one CUDA graph) and e0_grad.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -11,8 +12,10 @@
 namespace hm {
 
 int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int *blocks);
-int blk_lz_launch(const BlkParams &P, int dtype, const void *qc, void *qp, LzScalars *S, int pc,
-                  double *part, int blocks, cudaStream_t st);
+int blk_lz64_launch(const BlkParams &P, const long long *Xc, const long long *Xp, unsigned long long *Y,
+                    LzScalars *S, int pc, double *part, int blocks, cudaStream_t st);
+int blk_lz32_launch(const BlkParams &P, const float *qc, float *qp, LzScalars *S, double *part, int blocks,
+                    cudaStream_t st);
 
 int matvec_dev(const hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype,
                int nvec, cudaStream_t st);
@@ -22,12 +25,15 @@ int bond_corr_dev(const hm_basis *b, const BondParams &bp, const void *g, const 
 size_t bond_corr_bytes(const hm_basis *b, int n_bonds);
 int start_vector_dev(uint64_t n, uint64_t seed, int kind, void *x, int dtype, cudaStream_t st);
 
-constexpr double LZ_TOL = 1e-12;     // breakdown: beta_j <= LZ_TOL * max(|alpha|, beta)
+constexpr double LZ_TOL = 1e-12;     // breakdown: beta_j <= LZ_TOL * max(|alpha|, beta), FP64
+constexpr double LZ_TOL32 = 1e-5;    // FP32 vectors: above their rounding floor
 constexpr int NT = 256;
 
 // workspace carve-up (all segments 256-byte aligned)
 struct LzLayout {
     size_t buf[2], part, sc, alpha, beta, ritz, psi, coef, res, gout, tri, bpart, total;
+    size_t ybuf, xs[2];     // FP64 block path: y = H q and the fixed-point copies of q
+    bool shadow;
 };
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -40,7 +46,15 @@ static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad
     size_t o = 0;
     L.buf[0] = o; o += al256(dim * es);
     L.buf[1] = o; o += al256(dim * es);
-    L.part = o; o += al256((size_t)nblk * sizeof(double));
+    const size_t npart = std::max<size_t>((size_t)nblk, (size_t)sm_count() * 8);
+    L.part = o; o += al256(npart * 2 * sizeof(double));
+    // the s = 1/2 block path of FP64 runs needs y and two fixed-point copies
+    L.shadow = dtype == HM_F64 && b->view.S2 == 1 && b->view.N >= 10 && b->view.N <= 32 && !b->view.idx64;
+    if (L.shadow) {
+        L.ybuf = o; o += al256(dim * 8);
+        L.xs[0] = o; o += al256(dim * 8);
+        L.xs[1] = o; o += al256(dim * 8);
+    }
     L.sc = o; o += al256(sizeof(LzScalars));
     L.alpha = o; o += al256((size_t)max_steps * 8);
     L.beta = o; o += al256((size_t)max_steps * 8);
@@ -208,7 +222,69 @@ k_lz_update(const T *__restrict__ qc, T *__restrict__ qp, uint64_t n, LzScalars 
     }
 }
 
-__global__ void k_lz_beta(LzScalars *S, const double *__restrict__ part, int nblk, double *beta) {
+// fixed-point copy of q (FP64 block path), unit from the vector's largest exponent
+__global__ void __launch_bounds__(NT)
+k_fix(const unsigned long long *__restrict__ w, long long *__restrict__ X, uint64_t n, const LzScalars *S, int slot) {
+    if (S->done) return;
+    const int E = S->emax[slot];
+    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT)
+        X[r] = (long long)ef::fix_from_bits(w[r], E);
+}
+
+// alpha_j = sigma^2 (q.Hq) - sigma gamma (q.q_prev) from the two partial sums of the
+// FP64 block product (the Paige form v.(Hv - beta v_prev))
+__global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int nblk, double *alpha, int pprev) {
+    if (S->done) return;
+    __shared__ double red[NT / 32];
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += NT) { s1 += part[k]; s2 += part[nblk + k]; }
+    s1 = block_sum<NT>(s1, red);
+    __syncthreads();
+    s2 = block_sum<NT>(s2, red);
+    if (threadIdx.x == 0) {
+        const double sg = S->sigma_cur, gm = S->beta_prev * S->sigma_prev;
+        const double a = sg * sg * s1 - sg * gm * s2;
+        alpha[S->j] = a;
+        S->scale = fmax(S->scale, fabs(a));
+        S->emax_old = S->emax[pprev];
+        S->emax[pprev] = 0;          // filled again by the update kernel
+    }
+}
+
+// FP64 block path: w = sigma y - alpha sigma q - gamma q_prev over q_prev, in
+// double-float on the bit patterns; part = |w|^2; exponent of w to S->emax[pprev]
+__global__ void __launch_bounds__(NT)
+k_lz_update_y(const unsigned long long *__restrict__ Y, const unsigned long long *__restrict__ qc,
+              unsigned long long *__restrict__ qp, uint64_t n, LzScalars *S, const double *__restrict__ alpha,
+              double *__restrict__ part, double *__restrict__ psi, const double *__restrict__ coef, int pprev) {
+    if (S->done) return;
+    __shared__ double red[NT / 32];
+    const double sg = S->sigma_cur, gm = S->beta_prev * S->sigma_prev, as = alpha[S->j] * sg;
+    const double cj = psi ? coef[S->j] * sg : 0.0;
+    const int scale_q = S->emax[pprev ^ 1] - 1023, scale_p = S->emax_old - 1023;
+    auto todf = [](double v) { const float h = (float)v; return ef::df{h, (float)(v - (double)h)}; };
+    const ef::df sg_d = todf(sg), as_s = todf(ldexp(as, scale_q)), gm_s = todf(ldexp(gm, scale_p));
+    ef::df s{0.0f, 0.0f};
+    int em = 0;
+    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
+        const unsigned long long qb = qc[r];
+        const ef::df t1 = ef::df_mul(sg_d, ef::df_from_bits(Y[r], 0));
+        const ef::df t2 = ef::df_mul(as_s, ef::df_from_bits(qb, scale_q));
+        const ef::df t3 = ef::df_mul(gm_s, ef::df_from_bits(qp[r], scale_p));
+        const ef::df w = ef::df_add(t1, ef::df_neg(ef::df_add(t2, t3)));
+        const unsigned long long wb = ef::bits_from_df(w, 0);
+        qp[r] = wb;
+        em = max(em, (int)((wb >> 52) & 0x7FF));
+        s = ef::df_add(s, ef::df_mul(w, w));
+        if (psi) psi[r] += cj * ef::u2d(qb);
+    }
+    const double tot = block_sum<NT>((double)s.hi + (double)s.lo, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_down_sync(0xffffffffu, em, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&S->emax[pprev], em);
+}
+
+__global__ void k_lz_beta(LzScalars *S, const double *__restrict__ part, int nblk, double *beta, double tol) {
     if (S->done) return;
     __shared__ double red[NT / 32];
     double s = 0.0;
@@ -218,7 +294,7 @@ __global__ void k_lz_beta(LzScalars *S, const double *__restrict__ part, int nbl
         const double b = sqrt(s);
         beta[S->j] = b;
         S->j += 1;
-        if (b <= LZ_TOL * S->scale) {
+        if (b <= tol * S->scale) {
             S->done = 1;
             S->status = HM_BREAKDOWN;
         } else {
@@ -379,18 +455,30 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
     T *qp = parity ? b0 : b1;
     const int nblk = grid_blocks(sv.dim, NT);
     const int pprev = parity ^ 1;   // buffer of q_prev, receives u then w
+    const bool b64 = R->use_blk && R->dtype == HM_F64;
+    long long *xs[2] = {R->L.shadow ? (long long *)(R->work + R->L.xs[0]) : nullptr,
+                        R->L.shadow ? (long long *)(R->work + R->L.xs[1]) : nullptr};
+    unsigned long long *Y = R->L.shadow ? (unsigned long long *)(R->work + R->L.ybuf) : nullptr;
     if (phase == 0) {
-        if (R->use_blk) {
-            HM_TRY(blk_lz_launch(R->blk, R->dtype, qc, qp, R->sc, parity, R->part, R->blk_blocks, st));
+        if (b64) {
+            HM_TRY(blk_lz64_launch(R->blk, xs[parity], xs[pprev], Y, R->sc, parity, R->part, R->blk_blocks, st));
+            k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, R->part, R->blk_blocks, R->alpha, pprev);
+        } else if (R->use_blk) {
+            HM_TRY(blk_lz32_launch(R->blk, (const float *)qc, (float *)qp, R->sc, R->part, R->blk_blocks, st));
             k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, R->blk_blocks, R->alpha, pprev);
         } else {
             const size_t sm = row_smem_bytes<I>(sv);
             k_lz_matvec<I, T, Acc><<<nblk, NT, sm, st>>>(sv, R->bp, qc, qp, R->sc, R->part);
             k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->alpha, pprev);
         }
+    } else if (b64) {
+        k_lz_update_y<<<nblk, NT, 0, st>>>(Y, (const unsigned long long *)qc, (unsigned long long *)qp, sv.dim,
+                                           R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
+        k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
+        k_fix<<<nblk, NT, 0, st>>>((const unsigned long long *)qp, xs[pprev], sv.dim, R->sc, pprev);
     } else {
         k_lz_update<T><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
-        k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta);
+        k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
     }
     HM_CUDA(cudaGetLastError());
     return HM_OK;
@@ -443,6 +531,10 @@ static int enqueue_start(hm_lanczos *R, const void *v0, uint64_t seed, cudaStrea
     if (R->dtype == HM_F64) k_sumsq<double><<<nblk, NT, 0, st>>>((const double *)b0, sv.dim, R->part, &R->sc->emax[0]);
     else k_sumsq<float><<<nblk, NT, 0, st>>>((const float *)b0, sv.dim, R->part, nullptr);
     k_lz_start<<<1, NT, 0, st>>>(R->sc, R->part, nblk);
+    if (R->use_blk && R->dtype == HM_F64) {
+        k_fix<<<nblk, NT, 0, st>>>((const unsigned long long *)b0, (long long *)(R->work + R->L.xs[0]), sv.dim, R->sc, 0);
+        HM_CUDA(cudaMemsetAsync(R->work + R->L.xs[1], 0, sv.dim * 8, st));
+    }
     HM_CUDA(cudaGetLastError());
     R->host_j = 0;
     R->next_phase = 0;
@@ -473,7 +565,7 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
     R->use_blk = 0;
     rc = blk_lz_plan(const_cast<hm_basis *>(b), R->bp, dtype, &R->blk, &R->blk_blocks);
     if (rc < 0) { delete R; return rc; }
-    R->use_blk = rc == 0 && R->blk_blocks <= grid_blocks(b->view.dim, NT);
+    R->use_blk = rc == 0 && (dtype == HM_F32 || R->L.shadow);
     R->work = (unsigned char *)work;
     R->sc = (LzScalars *)(R->work + R->L.sc);
     R->alpha = (double *)(R->work + R->L.alpha);
