@@ -41,6 +41,8 @@ WORKLOADS = {
     "j1j2_ring28": 1204983800,
     "ring24_randJ": 70425628,
     "ring16": 122694,
+    # finite-temperature Lanczos: nnz counted per sector and per executed vector-step
+    "ftlm_ring24": None,
 }
 
 # bytes one product must move at minimum: read x once, write y once (FP64)
@@ -50,7 +52,14 @@ ALGO_BYTES_PER_ROW = 16
 def instance(name):
     from paper_0706_3293_gb300 import workloads as W
     return {"j1j2_ring32": W.j1j2_ring32, "j1j2_ring28": lambda: W.j1j2_ring(28),
-            "ring24_randJ": W.ring24_random_j, "ring16": W.ring16}[name]()
+            "ring24_randJ": W.ring24_random_j, "ring16": W.ring16, "ftlm_ring24": W.ftlm_ring24}[name]()
+
+
+def sector_nnz_s12(n_sites: int, n_bonds: int, A: int) -> int:
+    """nnz of one s = 1/2 sector: C(N, A) diagonal elements plus, for every bond, the
+    2 C(N-2, A-1) states whose two spins differ (each has one exchange)."""
+    import math
+    return math.comb(n_sites, A) + (2 * n_bonds * math.comb(n_sites - 2, A - 1) if A >= 1 else 0)
 
 
 def dist_env():
@@ -222,7 +231,86 @@ def run_kernel_name(b, inst) -> str:
     return "k_lz_matvec"
 
 
+def run_ftlm(args):
+    """One step = one whole finite-temperature run: all 25 sectors of the N = 24 ring, 32
+    +-1 vectors each, 80 Lanczos steps, in one graph launch through the C ABI.  Gnnz/s
+    counts every executed vector-step: sum over (sector, vector) of nnz_A x Krylov length."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0706_3293_gb300 import api
+    inst = instance(args.workload)
+    R = inst.meta["R"]
+    bl = api.bonds_of(inst)
+    temps = [0.25, 0.5, 1.0, 2.0, 4.0]
+    for _ in range(args.warmup):
+        res = api.ftlm_run(inst.n_sites, bl, R, inst.steps, inst.seed, temps)
+    nnz_sec = [sector_nnz_s12(inst.n_sites, inst.n_bonds, A) for A in range(inst.n_sites + 1)]
+    work = float(sum(nnz_sec[A] * int(res.mlen[A, :R].sum()) for A in range(inst.n_sites + 1)))
+    st = torch.cuda.current_stream()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        res = api.ftlm_run(inst.n_sites, bl, R, inst.steps, inst.seed, temps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        if rank != 0:
+            dist.destroy_process_group()
+            return 0
+    ms = float(t.item())
+    value = work * args.steps * ws / (ms * 1e-3) / 1e9
+    peak, peak_src = read_peaks()
+    # algorithmic bytes of one Lanczos step on R FP32 vectors: product 8 B per vector-row
+    # (read x, write u), update 12 B (read u and q, write w) = 20 B per vector-row
+    rows = 2 ** inst.n_sites
+    algo = 20.0 * rows * R * inst.steps
+    achieved = algo / (ms / args.steps * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": inst.name, "n_sites": inst.n_sites, "sectors": inst.n_sites + 1,
+                      "R": R, "lanczos_steps": inst.steps, "vector_nnz_per_run": work,
+                      "vt": res.vt, "step": "one finite-temperature run (all sectors)",
+                      "l2": "inputs larger than L2 (2 x %.1f GB vector sets)" % (rows * 32 * 4 / 1e9)},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": read_traffic("k_ftlm", inst.name),
+                        "kernel": "k_ftlm (whole run)", "peak_source": peak_src,
+                        "algorithmic_bytes_per_launch": algo},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 8 * inst.n_bonds * 2 + 8 * len(temps),
+                   "d2h_bytes_per_step": 16 * len(temps) + 16 * 25 * 32 * inst.steps},
+           "gpu_launches": 4 * args.steps, "clocks": clocks,
+           "thermo": {"T": temps, "Z_rel": list(map(float, res.Z)), "E": list(map(float, res.E)),
+                      "e_ref": res.e_ref}}
+    print(json.dumps(out))
+    return 0
+
+
 def run_ours(args):
+    if args.workload == "ftlm_ring24":
+        return run_ftlm(args)
     import numpy as np
     import torch
     ws, rank, local = dist_env()
