@@ -226,8 +226,8 @@ def run_kernel_name(b, inst) -> str:
     """Product kernel the library picks: the s = 1/2 block kernel for N = 18..32 with at
     most 4 coupling classes, else the general row kernel."""
     ncls = len(set(float(j) for j in inst.J))
-    if inst.two_s == 1 and 18 <= inst.n_sites <= 32 and ncls <= 4:
-        return "k_blk_lz"
+    if inst.two_s == 1 and 10 <= inst.n_sites <= 32 and ncls <= 4 and inst.n_bonds <= 64:
+        return "k_blk_lz64"
     return "k_lz_matvec"
 
 

@@ -1,7 +1,13 @@
 """GPU parity of the batched finite-temperature Lanczos driver (ftlm_run) against the CPU
-oracle: per start vector Krylov lengths and Ritz values, and the thermodynamic sums.
-The GPU keeps the Lanczos vectors in FP32 (reductions double-float/double), the oracle in
-FP64, so Ritz values agree to ~1e-5 relative and Z, E to ~1e-4."""
+oracle.  The GPU keeps the Lanczos vectors in FP32 (reductions double-float/double), the
+oracle in FP64, so Ritz values agree to ~1e-5 relative and Z, E to ~1e-4.
+
+A sector smaller than the step count exhausts its Krylov space.  In FP64 beta then falls
+below the 1e-5 threshold and the run stops; with FP32 vectors loss of orthogonality keeps
+beta near sqrt(eps_32), so the run continues to the sector dimension, adding ghost copies
+of converged Ritz values.  Both are valid Lanczos quadratures of <r|f(H)|r>: what is
+unique and compared there is the extreme Ritz values and sum_j tau_j f(theta_j); Krylov
+lengths are compared where no exhaustion can occur (dim > steps) and for dim-1 sectors."""
 import math
 
 import numpy as np
@@ -49,17 +55,30 @@ def small_case(hm):
     return inst, R, steps, seed, gpu, ora, per
 
 
+def check_vector(gpu, A, r, dim, steps, ora_run, tol_rel=2e-5):
+    th, tau, al, be = ora_run
+    m = int(gpu.mlen[A, r])
+    if dim > steps or dim == 1:
+        assert m == len(al), (A, r, m, len(al))
+    else:
+        assert len(al) <= m <= dim
+    gth = gpu.theta[A, r, :m]
+    gtau = gpu.tau[A, r, :m]
+    assert abs(gtau.sum() - 1.0) < 1e-6
+    assert abs(gth.min() - th[0]) <= tol_rel * max(1.0, abs(th[0])), (A, r)
+    assert abs(gth.max() - th[-1]) <= tol_rel * max(1.0, abs(th[-1])), (A, r)
+    for T in TEMPS:
+        qg = float(np.sum(gtau * np.exp(-(gth - th[0]) / T)))
+        qo = float(np.sum(tau * np.exp(-(th - th[0]) / T)))
+        assert abs(qg - qo) <= 1e-4 * qo, (A, r, T, qg, qo)
+
+
 def test_ftlm_krylov_lengths_and_ritz(small_case):
     inst, R, steps, seed, gpu, ora, per = small_case
     for A, res in ora.items():
+        dim = math.comb(inst.n_sites, A)
         for r in range(R):
-            th, tau, al, be = res[r]
-            m = int(gpu.mlen[A, r])
-            assert m == len(al), (A, r, m, len(al))
-            gth = np.sort(gpu.theta[A, r, :m])
-            assert abs(gth[0] - th[0]) <= 2e-5 * max(1.0, abs(th[0])), (A, r)
-            assert abs(gth[-1] - th[-1]) <= 2e-5 * max(1.0, abs(th[-1])), (A, r)
-            assert abs(gpu.tau[A, r, :m].sum() - 1.0) < 1e-6
+            check_vector(gpu, A, r, dim, steps, res[r])
     assert np.all(gpu.mlen[:, R:] == 0)
 
 
@@ -100,11 +119,9 @@ def test_ftlm_ring24_config(hm):
     assert gpu.vt in (1, 2, 4)
     ora, _ = oracle_ftlm(inst, R, steps, seed, sectors={0, 1, 2, 22, 23, 24})
     for A, res in ora.items():
+        dim = math.comb(24, A)
         for r in range(R):
-            th, tau, al, be = res[r]
-            m = int(gpu.mlen[A, r])
-            assert m == len(al)
-            assert abs(np.sort(gpu.theta[A, r, :m])[0] - th[0]) <= 2e-5 * max(1.0, abs(th[0]))
+            check_vector(gpu, A, r, dim, steps, res[r])
     # sector A = 6 (dim 134,596), first start vector
     b = oracle.Basis(24, 1, 6)
     v0 = oracle.start_pm1(oracle.stream_seed(seed, 6, 0), b.dim)
