@@ -108,6 +108,12 @@ int basis_decode(const hm_basis *basis, const int64_t *idx, uint64_t *states, in
 int matvec(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
            const double *J, const void *x, void *y, int dtype, int nvec, void *stream);
 
+/* Number of non-zero elements of H(M) for the bond list (one diagonal element per row plus
+ * every allowed exchange, Sec. 4 "N^{1..2} x dim non-zero entries"), accumulated on the
+ * device into *nnz (device int64, overwritten).  The figure behind Gnnz/s. */
+int count_nnz(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v, int64_t *nnz,
+              void *stream);
+
 /* Adjoint of the coupling dependence: out[b] = sum_i g_i [(s_u . s_v) x]_i for every
  * bond b (device double[n_bonds]), so that d(g^T H x)/dJ_b = -out[b] (H is linear in
  * J, Eq. E-2-1).  g, x: device vectors of dtype; nvec must be 1.  Deterministic:
@@ -116,6 +122,20 @@ int bond_corr_workspace(const hm_basis *basis, int n_bonds, size_t *bytes);
 int bond_corr(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
               const void *g, const void *x, double *out, int dtype, void *work,
               size_t work_bytes, void *stream);
+
+/* bond_corr with no allocation and no workspace argument -- the paper has no counterpart.
+ * For callers that cannot allocate device memory when they need the adjoint (for example
+ * while a stream is being captured into a CUDA graph, or after a pre-allocated budget is
+ * spent).  The per-block partial sums go to a file-scope device array of 1 MiB that every
+ * GPU loading the library holds until exit; a problem whose partial sums exceed it
+ * (bond_corr_workspace > 1 MiB) returns HM_EINVAL with a message.  Output as bond_corr:
+ * out[b] (device double[n_bonds]), computed with the same kernels and launch shape.
+ * The array is shared by all calls and keeps the last call's contents (each call writes
+ * every slot it reads); calls that overlap on the GPU race on it and must be ordered on
+ * one stream.  The first call on a device looks up the array's device address (no
+ * allocation); make that first call before any stream capture. */
+int bond_corr_static(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
+                     const void *g, const void *x, double *out, int dtype, void *stream);
 
 /* Seeded start vectors (device, dtype, nvec = 1).  kind 0: uniform on [-1, 1),
  * x_t = 2 (o_t >> 11) 2^-53 - 1; kind 1: +-1, x_t = -1 if bit 63 of o_t is set;

@@ -16,7 +16,8 @@ HM_MAX_BONDS = 512
 # every function the header declares (checked by tests/test_abi.py)
 EXPORTS = [
     "hm_last_error", "basis_dim_query", "bonds_check", "basis_build", "basis_free", "basis_dim",
-    "basis_encode", "basis_decode", "matvec", "bond_corr_workspace", "bond_corr", "start_vector",
+    "basis_encode", "basis_decode", "matvec", "count_nnz", "bond_corr_workspace", "bond_corr", "bond_corr_static",
+    "start_vector",
     "lanczos_workspace", "lanczos_init", "lanczos_step", "lanczos_substep", "lanczos_read", "lanczos_free",
     "lanczos_run", "e0_grad_workspace", "e0_grad", "ftlm_workspace", "ftlm_run",
 ]
@@ -55,8 +56,10 @@ def load() -> ctypes.CDLL:
         "basis_encode": (i32, [vp, vp, vp, i64, vp]),
         "basis_decode": (i32, [vp, vp, vp, i64, vp]),
         "matvec": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, i32, vp]),
+        "count_nnz": (i32, [vp, i32, vp, vp, vp, vp]),
         "bond_corr_workspace": (i32, [vp, i32, szp]),
         "bond_corr": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]),
+        "bond_corr_static": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp]),
         "start_vector": (i32, [vp, u64, i32, vp, i32, vp]),
         "lanczos_workspace": (i32, [vp, i32, i32, szp]),
         "lanczos_init": (i32, [vp, i32, vp, vp, vp, vp, u64, i32, i32, vp, sz, vp,

@@ -1,4 +1,6 @@
 // matvec.cu -- y = H x by rows (Eq. E-4-b), the bond-correlation adjoint, start vectors.
+#include <mutex>
+
 #include "hm_row.cuh"
 
 namespace hm {
@@ -171,6 +173,30 @@ int matvec_dev(const hm_basis *b, const BondParams &bp, const void *x, void *y, 
 }
 
 // ---------------------------------------------------------------------------------------
+// number of non-zero matrix elements: one diagonal per row plus every allowed exchange
+// ---------------------------------------------------------------------------------------
+template <class I>
+__global__ void __launch_bounds__(256)
+k_count_nnz(SectorView sv, BondParams bp, unsigned long long *out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const double *pdn, *pup;
+    const I *cd = stage_tables<I>(sv, bp, smem_raw, &pdn, &pup);
+    Codec<I> c{cd, sv.N, sv.S2, sv.A, sv.bits, sv.cd_w, sv.cd_rowlen};
+    unsigned long long cnt = 0;
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < sv.dim;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = c.decode((I)r);
+        cnt += 1;
+        for (int t = 0; t < bp.nb; ++t) {
+            const int ap = dig(w, bp.p[t], sv.bits), aq = dig(w, bp.q[t], sv.bits);
+            cnt += (ap >= 1 && aq < sv.S2) + (ap < sv.S2 && aq >= 1);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, cnt);   // integer sum: order-independent
+}
+
+// ---------------------------------------------------------------------------------------
 // seeded start vectors
 // ---------------------------------------------------------------------------------------
 template <class T>
@@ -209,6 +235,28 @@ int matvec(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, c
     return matvec_dev(b, bp, x, y, dtype, nvec, as_stream(stream));
 }
 
+int count_nnz(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, int64_t *nnz,
+              void *stream) {
+    if (!b || !nnz) return fail(HM_EINVAL, "NULL argument");
+    std::vector<double> ones(n_bonds > 0 ? n_bonds : 1, 1.0);
+    BondParams bp;
+    HM_TRY(make_bonds(b, n_bonds, u, v, ones.data(), &bp));
+    const SectorView &sv = b->view;
+    cudaStream_t st = as_stream(stream);
+    HM_CUDA(cudaMemsetAsync(nnz, 0, sizeof(int64_t), st));
+    if (sv.idx64) {
+        const size_t sm = row_smem_bytes<uint64_t>(sv);
+        HM_CUDA(cudaFuncSetAttribute(k_count_nnz<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_count_nnz<uint64_t><<<grid_blocks(sv.dim, 256), 256, sm, st>>>(sv, bp, (unsigned long long *)nnz);
+    } else {
+        const size_t sm = row_smem_bytes<uint32_t>(sv);
+        HM_CUDA(cudaFuncSetAttribute(k_count_nnz<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_count_nnz<uint32_t><<<grid_blocks(sv.dim, 256), 256, sm, st>>>(sv, bp, (unsigned long long *)nnz);
+    }
+    HM_CUDA(cudaGetLastError());
+    return HM_OK;
+}
+
 int bond_corr_workspace(const hm_basis *b, int n_bonds, size_t *bytes) {
     if (!b || !bytes) return fail(HM_EINVAL, "NULL argument");
     *bytes = bond_corr_bytes(b, n_bonds);
@@ -224,6 +272,62 @@ int bond_corr(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v
     BondParams bp;
     HM_TRY(make_bonds(b, n_bonds, u, v, ones.data(), &bp));
     return bond_corr_dev(b, bp, g, x, out, dtype, work, work_bytes, 1.0, nullptr, as_stream(stream));
+}
+
+// ---- bond correlations without allocation ----------------------------------------------------
+// Some callers cannot allocate device memory at the point where they need the adjoint:
+// code running while a stream is being captured into a CUDA graph (allocation is not a
+// capturable operation), hosts that pre-allocate everything up front and forbid later
+// allocation, or callers whose memory pool is exhausted by the Lanczos vectors.  For them
+// bond_corr_static keeps the per-block partial sums in this file-scope device array.
+constexpr size_t HM_BC_STATIC_DOUBLES = 131072;   // 1 MiB on every device that loads the library
+static __device__ __align__(256) double g_bc_static[HM_BC_STATIC_DOUBLES];
+
+namespace {
+constexpr int HM_BC_MAX_DEVICES = 64;
+std::mutex g_bc_mutex;
+double *g_bc_ptr[HM_BC_MAX_DEVICES];   // device address of g_bc_static, per device
+
+// The host-side name g_bc_static is only a stand-in; kernels need the device address,
+// looked up once per device with that device current.
+int bc_static_ptr(double **out) {
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= HM_BC_MAX_DEVICES) return fail(HM_EINVAL, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_bc_mutex);
+    if (!g_bc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_bc_static);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_bc_static)");
+        g_bc_ptr[dev] = (double *)p;
+    }
+    *out = g_bc_ptr[dev];
+    return HM_OK;
+}
+}  // namespace
+
+int bond_corr_static(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, const void *g,
+                     const void *x, double *out, int dtype, void *stream) {
+    if (!b) return fail(HM_EINVAL, "basis is NULL");
+    if (dtype != HM_F64 && dtype != HM_F32) return fail(HM_EINVAL, "dtype must be HM_F64 or HM_F32");
+    if (!g || !x || (n_bonds > 0 && !out)) return fail(HM_EINVAL, "NULL vector");
+    if (n_bonds < 0 || n_bonds > HM_MAX_BONDS) return fail(HM_EINVAL, "n_bonds must be in 0..%d", HM_MAX_BONDS);
+    double ones[HM_MAX_BONDS];
+    for (int t = 0; t < n_bonds; ++t) ones[t] = 1.0;
+    BondParams bp;
+    HM_TRY(make_bonds(b, n_bonds, u, v, ones, &bp));
+    // same launch shape as bond_corr: the partial sums need grid_blocks x n_bonds doubles
+    const size_t need = bond_corr_bytes(b, n_bonds);
+    if (need > HM_BC_STATIC_DOUBLES * sizeof(double))
+        return fail(HM_EINVAL, "bond_corr_static: %zu bytes of partial sums exceed the %zu-byte static "
+                    "scratch (fewer bonds or bond_corr with a workspace)", need,
+                    HM_BC_STATIC_DOUBLES * sizeof(double));
+    double *scratch = nullptr;
+    HM_TRY(bc_static_ptr(&scratch));
+    // every slot the reduction reads is written by this call's first kernel: nothing in the
+    // shared array has to start at zero
+    return bond_corr_dev(b, bp, g, x, out, dtype, scratch, HM_BC_STATIC_DOUBLES * sizeof(double), 1.0,
+                         nullptr, as_stream(stream));
 }
 
 int start_vector(const hm_basis *b, uint64_t seed, int kind, void *x, int dtype, void *stream) {
