@@ -41,8 +41,8 @@ _lib = None
 
 # breakdown threshold of the Lanczos recurrence (relative to the largest |alpha|, beta)
 LANCZOS_TOL = 1e-12
-# finite-temperature runs: exhausted sectors are detected above the FP32 noise floor, and
-# no run exceeds the sector dimension (a D-dimensional space holds at most D Lanczos vectors)
+# finite-temperature runs: breakdown threshold of the Lanczos runs (sectors small enough to
+# exhaust their Krylov space are diagonalised exactly, see ftlm_sector)
 FTLM_TOL = 1e-5
 
 
@@ -367,13 +367,23 @@ def e0_grad(basis: Basis, bonds: Bonds, v0: np.ndarray, steps: int):
 def ftlm_sector(basis: Basis, bonds: Bonds, seed: int, R: int, steps: int):
     """Per start vector r of one sector: Ritz values theta_j and weights tau_j (squared
     first components of T's eigenvectors), the start vector being the +-1 vector of
-    stream (seed, A, r).  A run stops at beta_j <= FTLM_TOL max(|alpha|, beta) or after
-    dim steps."""
+    stream (seed, A, r).  A run stops at beta_j <= FTLM_TOL max(|alpha|, beta).
+    A sector of dimension <= steps (and <= 512) would exhaust its Krylov space; it is
+    diagonalised exactly instead: theta_k = E_k, tau_k = <r/|r| | psi_k>^2, the limit of
+    the Lanczos quadrature (alpha, beta are then returned empty)."""
     from scipy.linalg import eigh_tridiagonal
     res = []
+    exact = basis.dim <= steps and basis.dim <= 512
+    if exact:
+        Hd = np.column_stack([basis.matvec(bonds, np.eye(basis.dim)[i]) for i in range(basis.dim)])
+        E, V = np.linalg.eigh(Hd)
     for r in range(R):
         v0 = start_pm1(stream_seed(seed, basis.A, r), basis.dim)
-        al, be = basis.lanczos(bonds, v0, min(steps, basis.dim), tol=FTLM_TOL)
+        if exact:
+            o = V.T @ (v0 / np.sqrt(basis.dim))
+            res.append((E.copy(), o * o, np.zeros(0), np.zeros(0)))
+            continue
+        al, be = basis.lanczos(bonds, v0, steps, tol=FTLM_TOL)
         m = len(al)
         if m == 1:
             th, c = np.array([al[0]]), np.ones((1, 1))

@@ -469,3 +469,22 @@ def test_start_vectors(orc):
     assert set(np.unique(p)) <= {-1.0, 1.0}
     assert np.array_equal(p, np.array([-1.0 if _splitmix_py(42, t) >> 63 else 1.0 for t in range(1000)]))
     assert oracle.stream_seed(1005, 12, 3) == _splitmix_py(1005, (12 << 20) + 3)
+
+
+def test_ftlm_lanczos_quadrature_large_sector(orc):
+    """A sector larger than the step count runs Lanczos: the quadrature
+    sum_j tau_j e^{-theta_j/T} of 40 steps matches <r|e^{-H/T}|r>/<r|r> (dense) for smooth
+    f; the error of a degree-40 Gauss quadrature is far below 1e-8 at these T."""
+    from scipy.linalg import expm
+    inst = W.small_ring(10, -1.0, -0.3)
+    bonds = bonds_of(inst)
+    b = Basis(10, 1, 5)
+    assert b.dim == 252
+    res = oracle.ftlm_sector(b, bonds, 21, 2, 40)
+    H = np.column_stack([b.matvec(bonds, np.eye(b.dim)[i]) for i in range(b.dim)])
+    for r, (th, tau, al, be) in enumerate(res):
+        assert len(al) == 40
+        v = oracle.start_pm1(oracle.stream_seed(21, 5, r), b.dim)
+        for T in [1.0, 3.0]:
+            ref = v @ expm(-H / T) @ v / (v @ v)
+            assert abs(np.sum(tau * np.exp(-th / T)) - ref) < 1e-8 * ref
