@@ -43,7 +43,10 @@ WORKLOADS = {
     "ring16": 122694,
     # finite-temperature Lanczos: nnz counted per sector and per executed vector-step
     "ftlm_ring24": None,
+    # s = 1 random 4-regular graph, N = 20 (FP32 vectors by default); nnz from count_nnz
+    "s1_rrg20": None,
 }
+DEFAULT_DTYPE = {"s1_rrg20": "f32"}
 
 # bytes one product must move at minimum: read x once, write y once (FP64)
 ALGO_BYTES_PER_ROW = 16
@@ -52,7 +55,8 @@ ALGO_BYTES_PER_ROW = 16
 def instance(name):
     from paper_0706_3293_gb300 import workloads as W
     return {"j1j2_ring32": W.j1j2_ring32, "j1j2_ring28": lambda: W.j1j2_ring(28),
-            "ring24_randJ": W.ring24_random_j, "ring16": W.ring16, "ftlm_ring24": W.ftlm_ring24}[name]()
+            "ring24_randJ": W.ring24_random_j, "ring16": W.ring16, "ftlm_ring24": W.ftlm_ring24,
+            "s1_rrg20": W.s1_random_graph}[name]()
 
 
 def sector_nnz_s12(n_sites: int, n_bonds: int, A: int) -> int:
@@ -67,6 +71,18 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(value: float, ws: int, device="cpu") -> float:
+    """The slowest rank's time: all_reduce(MAX) over the process group (identity for one
+    process).  device: where the reduction tensor lives (cuda for NCCL, cpu for gloo)."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def kernel_source_hash() -> str:
@@ -222,12 +238,12 @@ def run_reference(args):
     return 0
 
 
-def run_kernel_name(b, inst) -> str:
-    """Product kernel the library picks: the s = 1/2 block kernel for N = 18..32 with at
+def run_kernel_name(b, inst, dtype="f64") -> str:
+    """Product kernel the library picks: the s = 1/2 block kernel for N = 10..32 with at
     most 4 coupling classes, else the general row kernel."""
     ncls = len(set(float(j) for j in inst.J))
     if inst.two_s == 1 and 10 <= inst.n_sites <= 32 and ncls <= 4 and inst.n_bonds <= 64:
-        return "k_blk_lz64"
+        return "k_blk_lz64" if dtype == "f64" else "k_blk_lz32"
     return "k_lz_matvec"
 
 
@@ -272,15 +288,11 @@ def run_ftlm(args):
     e1.record(st)
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
+    if ws > 1 and rank != 0:
         import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        if rank != 0:
-            dist.destroy_process_group()
-            return 0
-    ms = float(t.item())
+        dist.destroy_process_group()
+        return 0
     value = work * args.steps * ws / (ms * 1e-3) / 1e9
     peak, peak_src = read_peaks()
     # algorithmic bytes of one Lanczos step on R FP32 vectors: product 8 B per vector-row
@@ -325,10 +337,12 @@ def run_ours(args):
     from paper_0706_3293_gb300 import api
 
     inst = instance(args.workload)
-    nnz = WORKLOADS[args.workload]
+    dtype = args.dtype or DEFAULT_DTYPE.get(args.workload, "f64")
+    tdt = torch.float64 if dtype == "f64" else torch.float32
     dev = torch.device("cuda", torch.cuda.current_device())
     b = api.Basis(inst.n_sites, inst.two_s, inst.two_m)
     bl = api.bonds_of(inst)
+    nnz = WORKLOADS[args.workload] or api.count_nnz(b, bl)
     total = args.warmup + args.steps
     st = torch.cuda.current_stream()
 
@@ -339,7 +353,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     # ---- device-resident timing ----
-    run = api.LanczosRun(b, bl, total, seed=inst.seed)
+    run = api.LanczosRun(b, bl, total, seed=inst.seed, dtype=tdt)
     for _ in range(args.warmup):
         run.step()
     barrier()
@@ -361,23 +375,19 @@ def run_ours(args):
     al, be, rc = run.read()
     run.close()
     del run
-    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    t_max = float(t_local.item())
+    t_max = max_over_ranks(total_ms, ws, dev)
     value = nnz * args.steps * ws / (t_max * 1e-3) / 1e9
 
     # ---- end to end through the C ABI with host buffers ----
-    x_host = torch.empty(b.dim, dtype=torch.float64, pin_memory=True)
-    x_host.copy_(api.start_vector(b, inst.seed).cpu())
+    x_host = torch.empty(b.dim, dtype=tdt, pin_memory=True)
+    x_host.copy_(api.start_vector(b, inst.seed, dtype=tdt).cpu())
     torch.cuda.synchronize()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
     v0 = x_host.to(dev, non_blocking=True)
-    run2 = api.LanczosRun(b, bl, args.steps, v0=v0)
+    run2 = api.LanczosRun(b, bl, args.steps, v0=v0, dtype=tdt)
     d2h = 0
     for k in range(args.steps):
         run2.step()
@@ -388,11 +398,7 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1)
     run2.close()
     del run2, v0
-    t_e2e = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_val = nnz * args.steps * ws / (float(t_e2e.item()) * 1e-3) / 1e9
+    e2e_val = nnz * args.steps * ws / (max_over_ranks(e2e_ms, ws, dev) * 1e-3) / 1e9
 
     if rank != 0:
         if ws > 1:
@@ -401,13 +407,14 @@ def run_ours(args):
         return 0
     peak, peak_src = read_peaks()
     mv_mean = float(np.mean(mv_ms))
-    achieved = ALGO_BYTES_PER_ROW * b.dim / (mv_mean * 1e-3) / 1e9
-    kname = run_kernel_name(b, inst)
+    algo_row = ALGO_BYTES_PER_ROW if dtype == "f64" else ALGO_BYTES_PER_ROW // 2
+    achieved = algo_row * b.dim / (mv_mean * 1e-3) / 1e9
+    kname = run_kernel_name(b, inst, dtype)
     traffic = read_traffic(kname, inst.name)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": inst.name, "n_sites": inst.n_sites, "two_s": inst.two_s,
                    "two_m": inst.two_m, "dim": b.dim, "nnz_per_product": nnz,
                    "bonds": inst.n_bonds, "start_seed": inst.seed, "parallelism": f"replicas{ws}",
@@ -415,9 +422,9 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": kname, "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": ALGO_BYTES_PER_ROW * b.dim,
+                     "algorithmic_bytes_per_launch": algo_row * b.dim,
                      "mean_launch_ms": mv_mean},
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": b.dim * 8 / args.steps,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": b.dim * (8 if dtype == "f64" else 4) / args.steps,
                 "d2h_bytes_per_step": 16},
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
@@ -441,6 +448,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="j1j2_ring32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dtype", choices=["f64", "f32"], default=None,
+                    help="Lanczos vector type (default: f64; f32 for s1_rrg20)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -115,6 +115,13 @@ def matvec(basis: Basis, bonds: BondList, x: torch.Tensor, out: torch.Tensor | N
     return y
 
 
+def count_nnz(basis: Basis, bonds: BondList, device="cuda") -> int:
+    """Non-zero elements of H(M): one diagonal per row plus every allowed exchange."""
+    out = torch.zeros(1, dtype=torch.int64, device=device)
+    check(_capi.load().count_nnz(basis.handle, *bonds.args()[:3], _vp(out), _stream()))
+    return int(out.item())
+
+
 def bond_corr(basis: Basis, bonds: BondList, g: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
     """out[b] = sum_i g_i [(s_u.s_v) x]_i (device float64[n_bonds])."""
     assert g.dtype == x.dtype and g.shape == x.shape == (basis.dim,)

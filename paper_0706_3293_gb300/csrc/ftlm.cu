@@ -63,12 +63,26 @@ struct FtDev {
     double *zsum, *esum, *eref;     // thermodynamics (n_t each), e_ref
 };
 
+// A sector whose dimension does not exceed the step count would exhaust its Krylov
+// space; it is diagonalised exactly instead (dense, FP64, one CTA): the Lanczos
+// quadrature sum_j tau_j f(theta_j) of a start vector is then the exact <r|f(H)|r>.
+struct ExactSec {
+    int A, dim;
+    uint32_t cd_off;                // its CD table inside the exact-table buffer
+    int cd_rowlen, cd_len;
+    uint64_t mat_off;               // doubles: H (dim x dim) then V (dim x dim)
+};
+constexpr int FT_MAXEXACT = 40;
+
 struct FtParams {
     BlkParams P;                    // block plan built with A = N (full binomial table)
     FtDev d;
     int nsec, R, steps, nitems;
     unsigned nctas;
     uint64_t seed;
+    uint64_t exact_mask;            // bit A set: sector A is diagonalised exactly
+    int nexact;
+    ExactSec ex[FT_MAXEXACT];
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -127,7 +141,7 @@ __global__ void k_ft_init(FtParams F) {
     const int nst = F.nsec * FT_W;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nst; t += gridDim.x * blockDim.x) {
         const int s = t / FT_W, v = t % FT_W;
-        const bool on = v < F.R && d.secdim[s] > 0;
+        const bool on = v < F.R && d.secdim[s] > 0 && !((F.exact_mask >> s) & 1ull);
         d.sig_cur[t] = on ? 1.0 / sqrt((double)d.secdim[s]) : 0.0;   // |+-1 vector| = sqrt(dim)
         d.sig_prev[t] = 0.0;
         d.beta_prev[t] = 0.0;
@@ -137,7 +151,8 @@ __global__ void k_ft_init(FtParams F) {
         d.nsteps[t] = 0;
         d.mlen[t] = 0;
     }
-    if (blockIdx.x == 0 && threadIdx.x < FT_MAXS && (int)threadIdx.x < F.nsec) d.sec_active[threadIdx.x] = 1;
+    if (blockIdx.x == 0 && threadIdx.x < FT_MAXS && (int)threadIdx.x < F.nsec)
+        d.sec_active[threadIdx.x] = ((F.exact_mask >> threadIdx.x) & 1ull) ? 0 : 1;
     if (blockIdx.x == 0 && threadIdx.x == 0) { d.bar->count = 0; d.bar->gen = 0; d.bar->abort = 0; }
 }
 
@@ -384,6 +399,7 @@ __global__ void k_ft_eig(FtParams F, double *scratch) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= F.nsec * FT_W) return;
     const int v = t % FT_W;
+    if ((F.exact_mask >> (t / FT_W)) & 1ull) return;   // filled by k_ft_exact
     const int m = (v < F.R) ? d.nsteps[t] : 0;
     d.mlen[t] = m;
     if (m == 0) return;
@@ -396,6 +412,109 @@ __global__ void k_ft_eig(FtParams F, double *scratch) {
         d.theta[(size_t)t * F.steps + i] = dg[i];
         d.tau[(size_t)t * F.steps + i] = z[i] * z[i];
     }
+}
+
+// Dense H of one small sector (rows by the paper's decode/encode, Eq. E-4-b), its
+// eigen-decomposition by parallel cyclic Jacobi (Brent-Luk round-robin ordering of the
+// rotations, each zeroing one off-diagonal pair as in Golub and Van Loan, Sec. 8.5),
+// then theta_k = E_k and tau_k = <r^|psi_k>^2 for every start vector r^ = r / |r|.
+__global__ void __launch_bounds__(256) k_ft_exact(FtParams F, BondParams bp, const uint32_t *__restrict__ cdall,
+                                                  double *__restrict__ mats) {
+    const FtDev &d = F.d;
+    const ExactSec ex = F.ex[blockIdx.x];
+    const int n = ex.dim;
+    double *H = mats + ex.mat_off, *V = H + (size_t)n * n;
+    __shared__ int sp[256], sq[256];
+    __shared__ double sc[256], ss[256], red[8];
+    __shared__ int s_stop;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        H[t] = 0.0;
+        V[t] = (t / n == t % n) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    Codec<uint32_t> c{cdall + ex.cd_off, F.P.N, 1, ex.A, 1, 3, ex.cd_rowlen};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t w = c.decode((uint32_t)i);
+        double dg = 0.0;
+        for (int t = 0; t < bp.nb; ++t) {
+            const int p = bp.p[t], q = bp.q[t];
+            const int ap = dig(w, p, 1), aq = dig(w, q, 1);
+            dg += bp.jm[t] * (0.5 - ap) * (0.5 - aq);
+            if (ap != aq) {
+                const uint32_t j = (uint32_t)i + c.delta(w, p, q, ap ? -1 : +1);
+                H[(size_t)i * n + j] += bp.jm[t] * 0.5;
+            }
+        }
+        H[(size_t)i * n + i] += dg;
+    }
+    __syncthreads();
+    const int m = n + (n & 1);            // players of the round-robin (one dummy if n is odd)
+    for (int sweep = 0; sweep < 40 && n > 1; ++sweep) {
+        // stop when the off-diagonal part is negligible
+        double off = 0.0, tot = 0.0;
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const double h = H[t];
+            tot += h * h;
+            if (t / n != t % n) off += h * h;
+        }
+        off = block_sum<256>(off, red);
+        __syncthreads();
+        tot = block_sum<256>(tot, red);
+        if (threadIdx.x == 0) s_stop = off <= 1e-30 * tot;
+        __syncthreads();
+        if (s_stop) break;
+        for (int round = 0; round < m - 1; ++round) {
+            for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
+                int p, q;
+                if (k == 0) { p = m - 1; q = round; }
+                else { p = (round + k) % (m - 1); q = (round - k + (m - 1)) % (m - 1); }
+                if (p > q) { const int tt = p; p = q; q = tt; }
+                double cc = 1.0, sn = 0.0;
+                if (q < n) {
+                    const double apq = H[(size_t)p * n + q];
+                    if (apq != 0.0) {
+                        const double tau = (H[(size_t)q * n + q] - H[(size_t)p * n + p]) / (2.0 * apq);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        cc = 1.0 / sqrt(1.0 + t * t);
+                        sn = t * cc;
+                    }
+                }
+                sp[k] = p; sq[k] = q; sc[k] = cc; ss[k] = sn;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < (m / 2) * n; t += blockDim.x) {   // rows: A <- J^T A
+                const int k = t / n, j = t % n;
+                if (sq[k] >= n) continue;
+                const double a = H[(size_t)sp[k] * n + j], b = H[(size_t)sq[k] * n + j];
+                H[(size_t)sp[k] * n + j] = sc[k] * a - ss[k] * b;
+                H[(size_t)sq[k] * n + j] = ss[k] * a + sc[k] * b;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < (m / 2) * n; t += blockDim.x) {   // columns: A <- A J, V <- V J
+                const int k = t / n, i = t % n;
+                if (sq[k] >= n) continue;
+                const double a = H[(size_t)i * n + sp[k]], b = H[(size_t)i * n + sq[k]];
+                H[(size_t)i * n + sp[k]] = sc[k] * a - ss[k] * b;
+                H[(size_t)i * n + sq[k]] = ss[k] * a + sc[k] * b;
+                const double va = V[(size_t)i * n + sp[k]], vb = V[(size_t)i * n + sq[k]];
+                V[(size_t)i * n + sp[k]] = sc[k] * va - ss[k] * vb;
+                V[(size_t)i * n + sq[k]] = ss[k] * va + sc[k] * vb;
+            }
+            __syncthreads();
+        }
+    }
+    // weights of every start vector
+    const double inv = 1.0 / sqrt((double)n);
+    for (int t = threadIdx.x; t < F.R * n; t += blockDim.x) {
+        const int r = t / n, kk = t % n;
+        const uint64_t stream = sm64(F.seed, ((uint64_t)ex.A << 20) + (uint64_t)r);
+        double o = 0.0;
+        for (int i = 0; i < n; ++i) o += V[(size_t)i * n + kk] * ((sm64(stream, (uint64_t)i) >> 63) ? -inv : inv);
+        const size_t sv = (size_t)ex.A * FT_W + r;
+        d.theta[sv * F.steps + kk] = H[(size_t)kk * n + kk];
+        d.tau[sv * F.steps + kk] = o * o;
+    }
+    for (int r = threadIdx.x; r < FT_W; r += blockDim.x) d.mlen[(size_t)ex.A * FT_W + r] = r < F.R ? n : 0;
 }
 
 // one block: e_ref = min theta, then Z and E sums for each temperature (fixed order)
@@ -442,7 +561,8 @@ __global__ void k_ft_thermo(FtParams F, const double *temps, int n_t) {
 
 // ---- host --------------------------------------------------------------------------------
 struct FtLayout {
-    size_t q0, q1, st, ab, part, sec, bar, items, rowoff, secdim, theta, tau, mlen, therm, temps, eigs, total;
+    size_t q0, q1, st, ab, part, sec, bar, items, rowoff, secdim, theta, tau, mlen, therm, temps, eigs,
+        xcd, xmat, total;
 };
 
 static int ft_choose_K(int N) {
@@ -456,7 +576,8 @@ static int ft_choose_K(int N) {
     return best;
 }
 
-static FtLayout ft_layout(int N, int nsec, int R, int steps, int nitems, int nctas, int n_t) {
+static FtLayout ft_layout(int N, int nsec, int R, int steps, int nitems, int nctas, int n_t, size_t xcd_words,
+                          size_t xmat_doubles) {
     (void)R;
     FtLayout L{};
     auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -479,6 +600,8 @@ static FtLayout ft_layout(int N, int nsec, int R, int steps, int nitems, int nct
     L.therm = o; o += a((size_t)(2 * n_t + 1) * 8);
     L.temps = o; o += a((size_t)(n_t > 0 ? n_t : 1) * 8);
     L.eigs = o; o += a(nst * 3 * (size_t)steps * 8);
+    L.xcd = o; o += a((xcd_words > 0 ? xcd_words : 1) * 4);
+    L.xmat = o; o += a((xmat_doubles > 0 ? xmat_doubles : 1) * 8);
     L.total = o;
     return L;
 }
@@ -508,9 +631,11 @@ static std::map<std::pair<int, int>, int> g_ft_tuned;
 struct FtSetup {
     hm_basis full;                   // tables with the full binomial table (A = N)
     FtParams F;
+    BondParams bp;
     FtLayout L;
     size_t smem;
     int nctas;
+    std::vector<uint32_t> xcd;       // CD tables of the exactly diagonalised sectors
 };
 
 static int ft_prepare(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_t *v,
@@ -522,7 +647,7 @@ static int ft_prepare(int n_sites, int two_s, int n_bonds, const int32_t *u, con
     const int K = ft_choose_K(n_sites);
     if (K < 0 || n_sites > 32) return fail(HM_EINVAL, "ftlm_run needs 10 <= n_sites <= 32");
     HM_TRY(build_tables(n_sites, 1, -n_sites, &S->full));      // A = N: full table
-    BondParams bp;
+    BondParams &bp = S->bp;
     HM_TRY(make_bonds(&S->full, n_bonds, u, v, J, &bp));
     memset(&S->F, 0, sizeof S->F);
     const int prc = blk_plan(&S->full, bp, K, &S->F.P);
@@ -543,6 +668,27 @@ static int ft_prepare(int n_sites, int two_s, int n_bonds, const int32_t *u, con
     S->F.nsec = nsec;
     S->F.R = R;
     S->F.steps = steps;
+    // sectors of dimension <= steps (and <= 512): exact treatment
+    S->xcd.clear();
+    uint64_t xmat = 0;
+    for (int A = 0; A <= n_sites; ++A) {
+        const int W = n_sites + 1;
+        const uint64_t dimA = S->full.D[(size_t)n_sites * W + A];
+        if (dimA > (uint64_t)steps || dimA > 512) continue;
+        if (S->F.nexact == FT_MAXEXACT) return fail(HM_EINVAL, "ftlm_run: too many small sectors");
+        hm_basis sb;
+        HM_TRY(build_tables(n_sites, 1, n_sites - 2 * A, &sb));
+        ExactSec &ex = S->F.ex[S->F.nexact++];
+        ex.A = A;
+        ex.dim = (int)dimA;
+        ex.cd_off = (uint32_t)S->xcd.size();
+        ex.cd_rowlen = sb.view.cd_rowlen;
+        ex.cd_len = sb.view.cd_len;
+        for (int k = 0; k < sb.view.cd_len; ++k) S->xcd.push_back((uint32_t)sb.cd[k]);
+        ex.mat_off = xmat;
+        xmat += 2 * dimA * dimA;
+        S->F.exact_mask |= 1ull << A;
+    }
     S->F.nitems = (int)items->size();
     S->smem = ft_smem(S->F.P, nsec);
     if (S->smem > 227 * 1024) return fail(HM_EINVAL, "ftlm_run: shared memory plan too large");
@@ -553,7 +699,7 @@ static int ft_prepare(int n_sites, int two_s, int n_bonds, const int32_t *u, con
     if (per_sm < 1) return fail(HM_EINVAL, "ftlm_run: kernel does not fit on an SM");
     S->nctas = sm_count();   // one CTA per SM (cooperative: all resident)
     S->F.nctas = (unsigned)S->nctas;
-    S->L = ft_layout(n_sites, nsec, R, steps, S->F.nitems, S->nctas, n_t);
+    S->L = ft_layout(n_sites, nsec, R, steps, S->F.nitems, S->nctas, n_t, S->xcd.size(), (size_t)xmat);
     return HM_OK;
 }
 
@@ -651,6 +797,8 @@ int ftlm_run(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_
     HM_CUDA(cudaMemcpyAsync(w + S.L.items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
     HM_CUDA(cudaMemcpyAsync(w + S.L.rowoff, rowoff.data(), rowoff.size() * 8, cudaMemcpyHostToDevice, st));
     HM_CUDA(cudaMemcpyAsync(w + S.L.secdim, dims.data(), dims.size() * 4, cudaMemcpyHostToDevice, st));
+    if (!S.xcd.empty())
+        HM_CUDA(cudaMemcpyAsync(w + S.L.xcd, S.xcd.data(), S.xcd.size() * 4, cudaMemcpyHostToDevice, st));
     double *d_temps = (double *)(w + S.L.temps);
     if (n_t > 0) HM_CUDA(cudaMemcpyAsync(d_temps, temps, n_t * 8, cudaMemcpyHostToDevice, st));
     // autotune the vectors-per-lane tiling on a short run (2 steps), once per shape
@@ -702,6 +850,11 @@ int ftlm_run(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_
             const int nst = nsec * FT_W;
             k_ft_eig<<<(nst + 127) / 128, 128, 0, cap>>>(S.F, (double *)(w + S.L.eigs));
             if ((e = cudaGetLastError()) != cudaSuccess) rc = cuda_fail(e, "k_ft_eig");
+            if (rc == HM_OK && S.F.nexact > 0) {
+                k_ft_exact<<<S.F.nexact, 256, 0, cap>>>(S.F, S.bp, (const uint32_t *)(w + S.L.xcd),
+                                                        (double *)(w + S.L.xmat));
+                if ((e = cudaGetLastError()) != cudaSuccess) rc = cuda_fail(e, "k_ft_exact");
+            }
         }
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (rc == HM_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "ftlm end capture");

@@ -385,3 +385,17 @@ def test_e0_grad_block_path(hm):
     assert abs(e0 - oe0) <= TOL_E0 * abs(oe0)
     np.testing.assert_allclose(g, og, rtol=0, atol=1e-8)
     assert abs(np.dot(inst.J, g) - e0) < 1e-8
+
+
+@pytest.mark.parametrize("inst", [SMALL[0], SMALL[1], SMALL[3], SMALL[4], SMALL[5]], ids=lambda i: i.name)
+def test_count_nnz(hm, inst):
+    b = hm.Basis(inst.n_sites, inst.two_s, inst.two_m)
+    ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
+    assert hm.count_nnz(b, hm.bonds_of(inst)) == ob.count_nnz(obonds(inst))
+
+
+def test_count_nnz_full_size_closed_form(hm):
+    """s = 1/2, M = 0: nnz = C(N, N/2) + 2 n_bonds C(N-2, N/2-1) (601M-row sector)."""
+    inst = W.j1j2_ring32()
+    b = hm.Basis(32, 1, 0)
+    assert hm.count_nnz(b, hm.bonds_of(inst)) == math.comb(32, 16) + 2 * 64 * math.comb(30, 15)
