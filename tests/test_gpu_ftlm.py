@@ -53,6 +53,18 @@ def small_case(hm):
     return inst, R, steps, seed, gpu, ora, per
 
 
+def ritz_residuals(al, be):
+    """Residual norms beta_m |s_mk| of the lowest and highest Ritz pair of the oracle's
+    m-step tridiagonal (beta_m is the coupling to the next, unused, Lanczos vector)."""
+    from scipy.linalg import eigh_tridiagonal
+    m = len(al)
+    if m == 1:
+        return abs(be[0]) if len(be) else 0.0, abs(be[0]) if len(be) else 0.0
+    _, c = eigh_tridiagonal(al, be[: m - 1])
+    bm = abs(be[m - 1]) if len(be) >= m else 0.0
+    return bm * abs(c[m - 1, 0]), bm * abs(c[m - 1, -1])
+
+
 def check_vector(gpu, A, r, dim, steps, ora_run, tol_rel=2e-5):
     th, tau, al, be = ora_run
     m = int(gpu.mlen[A, r])
@@ -60,13 +72,18 @@ def check_vector(gpu, A, r, dim, steps, ora_run, tol_rel=2e-5):
         assert m == dim
         np.testing.assert_allclose(np.sort(gpu.theta[A, r, :m]), th, rtol=0, atol=1e-10 * max(1.0, np.abs(th).max()))
         tol_rel = 1e-10
+        res_lo = res_hi = 0.0
     else:
         assert m == len(al), (A, r, m, len(al))
+        res_lo, res_hi = ritz_residuals(al, be)
     gth = gpu.theta[A, r, :m]
     gtau = gpu.tau[A, r, :m]
     assert abs(gtau.sum() - 1.0) < 1e-6
-    assert abs(gth.min() - th[0]) <= tol_rel * max(1.0, abs(th[0])), (A, r)
-    assert abs(gth.max() - th[-1]) <= tol_rel * max(1.0, abs(th[-1])), (A, r)
+    # an extreme Ritz value lies within its residual beta_m |s_mk| of an eigenvalue; one
+    # that has not converged after `steps` may differ between FP32 and FP64 runs by up to
+    # about that residual
+    assert abs(gth.min() - th[0]) <= max(tol_rel * max(1.0, abs(th[0])), 2 * res_lo), (A, r)
+    assert abs(gth.max() - th[-1]) <= max(tol_rel * max(1.0, abs(th[-1])), 2 * res_hi), (A, r)
     for T in TEMPS:
         qg = float(np.sum(gtau * np.exp(-(gth - th[0]) / T)))
         qo = float(np.sum(tau * np.exp(-(th - th[0]) / T)))
