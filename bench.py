@@ -238,15 +238,6 @@ def run_reference(args):
     return 0
 
 
-def run_kernel_name(b, inst, dtype="f64") -> str:
-    """Product kernel the library picks: the s = 1/2 block kernel for N = 10..32 with at
-    most 4 coupling classes, else the general row kernel."""
-    ncls = len(set(float(j) for j in inst.J))
-    if inst.two_s == 1 and 10 <= inst.n_sites <= 32 and ncls <= 4 and inst.n_bonds <= 64:
-        return "k_blk_lz64" if dtype == "f64" else "k_blk_lz32"
-    return "k_lz_matvec"
-
-
 def run_ftlm(args):
     """One step = one whole finite-temperature run: all 25 sectors of the N = 24 ring, 32
     +-1 vectors each, 80 Lanczos steps, in one graph launch through the C ABI.  Gnnz/s
@@ -354,6 +345,7 @@ def run_ours(args):
 
     # ---- device-resident timing ----
     run = api.LanczosRun(b, bl, total, seed=inst.seed, dtype=tdt)
+    kname = run.kernel_name()
     for _ in range(args.warmup):
         run.step()
     barrier()
@@ -409,7 +401,6 @@ def run_ours(args):
     mv_mean = float(np.mean(mv_ms))
     algo_row = ALGO_BYTES_PER_ROW if dtype == "f64" else ALGO_BYTES_PER_ROW // 2
     achieved = algo_row * b.dim / (mv_mean * 1e-3) / 1e9
-    kname = run_kernel_name(b, inst, dtype)
     traffic = read_traffic(kname, inst.name)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -172,6 +172,13 @@ int lanczos_substep(hm_lanczos *run, int phase, void *stream);
 /* Copies alpha[0..steps_done), beta[0..steps_done) (host) and steps_done; syncs. */
 int lanczos_read(hm_lanczos *run, double *alpha, double *beta, int *steps_done, void *stream);
 int lanczos_free(hm_lanczos *run);
+/* Name of the kernel that forms H q in each step of this run, NUL-terminated into
+ * name[0..cap): "k_blk_lz64_jit" / "k_blk_lz32_jit" (s = 1/2 block product compiled for
+ * this bond list at run time with NVRTC), "k_blk_lz64" / "k_blk_lz32" (the same block
+ * product reading its bonds from the parameters; used when NVRTC is unavailable or the
+ * environment sets HM_JIT=0) or "k_lz_matvec" (row kernel of Eq. E-4-b for any s).  No
+ * counterpart in the paper: it reports an implementation choice.  HM_EINVAL on NULL. */
+int lanczos_kernel_name(const hm_lanczos *run, char *name, int cap);
 
 /* A whole run: steps steps captured in one CUDA graph and launched once, then the
  * n_ritz lowest eigenvalues of T (Sturm bisection on the device).  Host outputs:

@@ -221,6 +221,12 @@ class LanczosRun:
         m = done.value
         return al[:m], be[:m], rc
 
+    def kernel_name(self) -> str:
+        """The kernel that forms H q in each step (lanczos_kernel_name)."""
+        buf = ctypes.create_string_buffer(64)
+        check(_capi.load().lanczos_kernel_name(self._h, buf, 64))
+        return buf.value.decode()
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _capi.load().lanczos_free(self._h)

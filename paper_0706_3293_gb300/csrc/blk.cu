@@ -8,12 +8,10 @@
 #include <type_traits>
 
 #include "blk.cuh"
+#include "blk_sweep.cuh"
 
 namespace hm {
 
-constexpr int BLK_NT = 512;
-
-__host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // ---------------------------------------------------------------------------------------
 // tables (cached per basis and K)
@@ -59,7 +57,8 @@ int blk_host_tables(const hm_basis *b, int K, std::vector<uint16_t> &U, std::vec
     return HM_OK;
 }
 
-static int blk_tables(hm_basis *b, int K, const void **dev, int *bytes, int *oU, int *oR0, int *oC) {
+static int blk_tables(hm_basis *b, int K, const void **dev, int *bytes, int *oU, int *oR0, int *oC,
+                      const uint16_t **lw, int *lwoff) {
     auto it = b->blk_tabs.find(K);
     if (it == b->blk_tabs.end()) {
         std::vector<uint16_t> U;
@@ -71,13 +70,30 @@ static int blk_tables(hm_basis *b, int K, const void **dev, int *bytes, int *oU,
         t.oR0 = (int)al16(U.size() * 2);
         t.oC = t.oR0 + 256;
         t.bytes = (int)al16(t.oC + C.size() * 4);
-        std::vector<unsigned char> host(t.bytes, 0);
+        // the K-bit words grouped by popcount, each group in increasing order: the low
+        // words of a block in rank order (the rank of Sec. 3.2 orders words of equal
+        // popcount numerically)
+        std::vector<uint16_t> lw((size_t)1 << K);
+        {
+            size_t w = 0;
+            for (int k = 0; k <= K; ++k) {
+                t.lwoff[k] = (int)w;
+                for (uint32_t l = 0; l < (1u << K); ++l)
+                    if (__builtin_popcount(l) == k) lw[w++] = (uint16_t)l;
+            }
+            t.lwoff[K + 1] = (int)w;
+        }
+        const size_t olw = al16(t.bytes);
+        const size_t total = olw + lw.size() * 2;
+        std::vector<unsigned char> host(total, 0);
         memcpy(host.data() + t.oU, U.data(), U.size() * 2);
         memcpy(host.data() + t.oR0, R0.data(), 256);
         memcpy(host.data() + t.oC, C.data(), C.size() * 4);
-        HM_CUDA(cudaMalloc(&t.dev, t.bytes));
-        cudaError_t e = cudaMemcpy(t.dev, host.data(), t.bytes, cudaMemcpyHostToDevice);
+        memcpy(host.data() + olw, lw.data(), lw.size() * 2);
+        HM_CUDA(cudaMalloc(&t.dev, total));
+        cudaError_t e = cudaMemcpy(t.dev, host.data(), total, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cudaFree(t.dev); return cuda_fail(e, "block tables"); }
+        t.lw = (uint16_t *)((unsigned char *)t.dev + olw);
         it = b->blk_tabs.emplace(K, t).first;
     }
     *dev = it->second.dev;
@@ -85,7 +101,49 @@ static int blk_tables(hm_basis *b, int K, const void **dev, int *bytes, int *oU,
     *oU = it->second.oU;
     *oR0 = it->second.oR0;
     *oC = it->second.oC;
+    *lw = it->second.lw;
+    memcpy(lwoff, it->second.lwoff, sizeof it->second.lwoff);
     return HM_OK;
+}
+
+// Compile-time slots of the thread-per-row kernels (BlkParams::ln ..).  Sets rows_ok = 0
+// when a class has more bonds of one kind than the slots hold.
+static void blk_plan_slots(const BondParams &bp, const std::vector<int> &bc, int K, BlkParams *P) {
+    P->rows_ok = K <= 15 ? 1 : 0;
+    P->kshift = K - 6;
+    std::map<std::pair<int, int>, uint32_t> cgroups;      // (class, d) -> mask of p
+    for (int t = 0; t < bp.nb; ++t) {
+        const int c = bc[t], p = bp.p[t], q = bp.q[t];    // p < q
+        if (q < K) {
+            const int ty = q < 8 ? 0 : (p >= 8 ? 1 : 2);
+            int &n = P->ln[c][ty];
+            if (n == HM_BLK_SL) { P->rows_ok = 0; continue; }
+            const uint32_t pat = (1u << p) | (1u << q);
+            P->ld[c][ty][n] = (uint8_t)(q - p);
+            P->lvm[c][ty][n] = 1u << p;
+            P->lxa[c][ty][n] = (uint16_t)(ty == 0 ? (pat & 255u) << 2 : ty == 2 ? (1u << p) << 2 : 0u);
+            P->lxb[c][ty][n] = (uint16_t)(ty == 1 ? (pat >> 8) << 2 : ty == 2 ? (1u << (q - 8)) << 2 : 0u);
+            ++n;
+            cgroups[{c, q - p}] |= 1u << p;
+        } else if (p < K) {
+            const int ty = p < 8 ? 0 : 1;
+            int &n = P->xn[c][ty];
+            if (n == HM_BLK_SX) { P->rows_ok = 0; continue; }
+            P->xxa[c][ty][n] = (uint16_t)(ty == 0 ? (1u << p) << 2 : (1u << (p - 8)) << 2);
+            P->xf_p[P->nxf] = (uint8_t)p;
+            P->xf_q[P->nxf] = (uint8_t)(q - K);
+            P->xf_dst[P->nxf] = (uint8_t)((2 * c + ty) * HM_BLK_SX + n);
+            ++P->nxf;
+            ++n;
+        }
+    }
+    for (auto &kv : cgroups) {
+        const int c = kv.first.first;
+        if (P->lgn[c] == HM_BLK_SG) { P->rows_ok = 0; continue; }
+        P->lgd[c][P->lgn[c]] = (uint8_t)kv.first.second;
+        P->lgm[c][P->lgn[c]] = kv.second;
+        ++P->lgn[c];
+    }
 }
 
 int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
@@ -195,97 +253,33 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
     P->max_block = mb;
     const void *dev;
     int bytes, oU, oR0, oC;
-    HM_TRY(blk_tables(b, K, &dev, &bytes, &oU, &oR0, &oC));
+    HM_TRY(blk_tables(b, K, &dev, &bytes, &oU, &oR0, &oC, &P->lw, P->lwoff));
     P->tab = dev; P->tab_bytes = bytes; P->off_U = oU; P->off_R0 = oR0; P->off_C = oC;
+    blk_plan_slots(bp, bc, K, P);
     return 0;
 }
 
-// shared memory: tables | staged rows | BlkShared
-size_t blk_smem_bytes(const BlkParams &P, int stage_bytes_per_row, int nvec) {
-    return al16(P.tab_bytes) + al16((size_t)P.max_block * stage_bytes_per_row * nvec) +
-           blk_shared_bytes(P.max_block);
-}
-
 // ---------------------------------------------------------------------------------------
-// gathers: how a row value is read from global memory
+// kernels with the generic row policy (blk_sweep.cuh); jit.cu builds the same bodies
+// with the plan's bonds written out
 // ---------------------------------------------------------------------------------------
-struct GatherF64 {          // binary64 -> fixed point on the fly (vector exponent E)
-    const unsigned long long *x;
-    int E;
-    __device__ __forceinline__ int64_t operator()(uint32_t j) const { return ef::fix_from_bits(__ldg(x + j), E); }
-};
-struct GatherFix {          // precomputed fixed-point copy
-    const long long *x;
-    __device__ __forceinline__ int64_t operator()(uint32_t j) const { return (int64_t)__ldg(x + j); }
-};
-struct GatherF32 {
-    const float *x;
-    __device__ __forceinline__ float operator()(uint32_t j) const { return __ldg(x + j); }
-};
-
-// hop sums of one row: acc[c] = sum of x over the allowed exchanges of class c, cnt[c]
-// their number
-template <class Sv, int NC, class G>
-__device__ __forceinline__ void blk_row(const BlkParams &P, const BlkTabs &tb, int k, uint32_t off, int r,
-                                        uint32_t l, const Sv *Xs, const BlkShared &sh, const G &gx, Sv *acc,
-                                        int *cnt) {
-    const uint16_t *Uk = tb.U + k * P.nb1;
-    const uint32_t i = off + (uint32_t)r;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        Sv a = Sv(0);
-        int mc = blk_low_hops(P, tb, c, l, (uint32_t)r, Uk, [&](uint32_t r2) { a += Xs[r2]; });
-        mc += blk_cross_hops(P, tb, c, l, sh, [&](uint32_t j) { a += gx(j); });
-        // exchanges among the high positions: the same low word in another block
-        const int e0 = sh.hcs[c], e1 = sh.hcs[c + 1];
-        int e = e0;
-        for (; e + 4 <= e1; e += 4) {
-            const Sv v0 = gx(i + sh.hcd[e]), v1 = gx(i + sh.hcd[e + 1]);
-            const Sv v2 = gx(i + sh.hcd[e + 2]), v3 = gx(i + sh.hcd[e + 3]);
-            a += (v0 + v1) + (v2 + v3);
-        }
-        for (; e < e1; ++e) a += gx(i + sh.hcd[e]);
-        acc[c] = a;
-        cnt[c] = mc + (e1 - e0);
-    }
+template <class T, int NC>
+__global__ void __launch_bounds__(BLK_NT, 3)
+k_blk_matvec(BlkParams P, const T *__restrict__ x, T *__restrict__ y, const int *__restrict__ Eptr) {
+    matvec_body<T, NC, RowGeneric<NC>>(P, x, y, Eptr);
 }
 
-// T_c = 2 acc_c + (ntot_c - 2 cnt_c) x_i: the class sum of Eq. (E-2-1) rows in units of
-// -J_c / 4 (s = 1/2: s^z s^z = +-1/4, exchange element 1/2)
-template <int NC>
-__device__ __forceinline__ void blk_classes(const BlkParams &P, const int64_t *acc, const int *cnt, int64_t Xo,
-                                            int64_t *T) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) T[c] = 2 * acc[c] + (int64_t)(P.ntot[c] - 2 * cnt[c]) * Xo;
-}
-
-// y (binary64 bits) of a row from its class sums; u = unit exponent of the fixed point.
-// Integer-ratio classes with a power-of-two g0 round the exact integer once.
-template <int NC>
-__device__ __forceinline__ unsigned long long blk_y_bits(const BlkParams &P, const int64_t *T, int u, int64_t *Tsum) {
-    if (P.iratio) {
-        int64_t s = 0;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) s += (int64_t)P.Kc[c] * T[c];
-        *Tsum = s;
-        if (P.g0_pow2) return ef::bits_from_int(s, u + P.g0_exp);
-        const ef::df t = ef::df_from_fix(s, u + 1022 + ef::FIX_BITS, 0, 0);
-        return ef::bits_from_df(ef::df_mul(t, ef::df{P.g0_hi, P.g0_lo}), 0);
-    }
-    *Tsum = 0;
-    ef::df y{0.0f, 0.0f};
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-        y = ef::df_add(y, ef::df_mul(ef::df_from_fix(T[c], u + 1022 + ef::FIX_BITS, 0, 0), ef::df{P.g_hi[c], P.g_lo[c]}));
-    return ef::bits_from_df(y, 0);
+template <int NC, bool IR>
+__global__ void __launch_bounds__(BLK_NT, 3)
+k_blk_lz64(BlkParams P, const long long *__restrict__ Xc, const long long *__restrict__ Xp,
+           unsigned long long *__restrict__ Y, LzScalars *S, int pc, double *__restrict__ part) {
+    lz64_body<NC, IR, RowGeneric<NC>>(P, Xc, Xp, Y, S, pc, part);
 }
 
 template <int NC>
-__device__ __forceinline__ float blk_y_f32(const BlkParams &P, const float *acc, const int *cnt, float xo) {
-    float y = 0.0f;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) y += P.gq[c] * (2.0f * acc[c] + (float)(P.ntot[c] - 2 * cnt[c]) * xo);
-    return y;
+__global__ void __launch_bounds__(BLK_NT, 3)
+k_blk_lz32(BlkParams P, const float *__restrict__ qc, float *__restrict__ qp, LzScalars *S, double *__restrict__ part) {
+    lz32_body<NC, RowGeneric<NC>>(P, qc, qp, S, part);
 }
 
 // largest exponent field of a double vector (for the fixed-point unit)
@@ -297,53 +291,9 @@ __global__ void k_max_exp(const unsigned long long *__restrict__ x, uint64_t n, 
     if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-// ---------------------------------------------------------------------------------------
-// y = H x (matvec API)
-// ---------------------------------------------------------------------------------------
-template <class T, int NC>
-__global__ void __launch_bounds__(BLK_NT)
-k_blk_matvec(BlkParams P, const T *__restrict__ x, T *__restrict__ y, const int *__restrict__ Eptr) {
-    using Sv = typename std::conditional<sizeof(T) == 8, int64_t, float>::type;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const BlkTabs tb = stage_blk_tables(P, smem);
-    Sv *Xs = (Sv *)(smem + al16(P.tab_bytes));
-    const BlkShared sh = blk_carve(smem + al16(P.tab_bytes) + al16((size_t)P.max_block * sizeof(Sv)), P.max_block);
-    const int E = Eptr ? *Eptr : 0;
-    const int u = E - 1022 - ef::FIX_BITS;
-    for (uint32_t h = blockIdx.x; h < (1u << P.H); h += gridDim.x) {
-        const int k = P.A - __popc(h);
-        if (k < 0 || k > P.K) continue;
-        __syncthreads();    // previous block done with the shared buffers
-        uint32_t off;
-        const int n = blk_setup_block(P, tb, h, k, sh, &off);
-        if constexpr (sizeof(T) == 8) {
-            const GatherF64 gx{(const unsigned long long *)x, E};
-            for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = gx(off + r);
-            __syncthreads();
-            for (int r = threadIdx.x; r < n; r += blockDim.x) {
-                int64_t acc[NC], Tc[NC], ts;
-                int cnt[NC];
-                blk_row<int64_t, NC>(P, tb, k, off, r, sh.list[r], Xs, sh, gx, acc, cnt);
-                blk_classes<NC>(P, acc, cnt, Xs[r], Tc);
-                ((unsigned long long *)y)[off + r] = blk_y_bits<NC>(P, Tc, u, &ts);
-            }
-        } else {
-            const GatherF32 gx{(const float *)x};
-            for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = gx(off + r);
-            __syncthreads();
-            for (int r = threadIdx.x; r < n; r += blockDim.x) {
-                float acc[NC];
-                int cnt[NC];
-                blk_row<float, NC>(P, tb, k, off, r, sh.list[r], Xs, sh, gx, acc, cnt);
-                y[off + r] = blk_y_f32<NC>(P, acc, cnt, Xs[r]);
-            }
-        }
-    }
-}
-
 template <class T, int NC>
 static int launch_blk_matvec(hm_basis *b, const BlkParams &P, const T *x, T *y, cudaStream_t st) {
-    const size_t sm = blk_smem_bytes(P, sizeof(T) == 8 ? 8 : 4, 1);
+    const size_t sm = blk_row_smem_bytes(P, sizeof(T) == 8 ? 8 : 4);
     HM_CUDA(cudaFuncSetAttribute(k_blk_matvec<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int *Ed = nullptr;
     if constexpr (sizeof(T) == 8) {
@@ -364,103 +314,17 @@ static int launch_blk_matvec(hm_basis *b, const BlkParams &P, const T *x, T *y, 
 // the largest K <= 15 that leaves two high sites
 static int blk_K(const hm_basis *b) { return std::min(15, b->view.N - 2); }
 
-// ---------------------------------------------------------------------------------------
-// Lanczos, FP64: y = H q_cur from the fixed-point copy Xc of q_cur (every gather an
-// integer load), written as binary64 to Y; the exact integer dots q.y and q.q_prev
-// (Xp: fixed-point copy of q_prev) give alpha without re-reading y.
-// part[blk] = (q . H q) and part[gridDim + blk] = (q . q_prev), both in true units.
-// ---------------------------------------------------------------------------------------
-__device__ __forceinline__ double i128_to_double(__int128 v) {
-    const long long hi = (long long)(v >> 64);
-    const unsigned long long lo = (unsigned long long)v;
-    return (double)hi * 18446744073709551616.0 + (double)lo;
-}
-
-template <int NC>
-__global__ void __launch_bounds__(BLK_NT)
-k_blk_lz64(BlkParams P, const long long *__restrict__ Xc, const long long *__restrict__ Xp,
-           unsigned long long *__restrict__ Y, LzScalars *S, int pc, double *__restrict__ part) {
-    if (S->done) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[BLK_NT / 32];
-    const BlkTabs tb = stage_blk_tables(P, smem);
-    int64_t *Xs = (int64_t *)(smem + al16(P.tab_bytes));
-    const BlkShared sh = blk_carve(smem + al16(P.tab_bytes) + al16((size_t)P.max_block * 8), P.max_block);
-    const int E = S->emax[pc], Ep = S->emax[pc ^ 1];
-    const int u = E - 1022 - ef::FIX_BITS, up = Ep - 1022 - ef::FIX_BITS;
-    const GatherFix gx{Xc};
-    __int128 d1 = 0, d2 = 0;
-    ef::df d1f{0.0f, 0.0f};
-    for (uint32_t h = blockIdx.x; h < (1u << P.H); h += gridDim.x) {
-        const int k = P.A - __popc(h);
-        if (k < 0 || k > P.K) continue;
-        __syncthreads();
-        uint32_t off;
-        const int n = blk_setup_block(P, tb, h, k, sh, &off);
-        for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = gx(off + r);
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += blockDim.x) {
-            int64_t acc[NC], Tc[NC], ts;
-            int cnt[NC];
-            blk_row<int64_t, NC>(P, tb, k, off, r, sh.list[r], Xs, sh, gx, acc, cnt);
-            const int64_t xo = Xs[r];
-            blk_classes<NC>(P, acc, cnt, xo, Tc);
-            const unsigned long long yb = blk_y_bits<NC>(P, Tc, u, &ts);
-            Y[off + r] = yb;
-            if (P.iratio) d1 += (__int128)xo * ts;
-            else d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
-            d2 += (__int128)xo * (int64_t)__ldg(Xp + off + r);
-        }
+// f(kernel) for the FP64 block-product instance of the plan (class count, integer ratios)
+template <class F>
+static int lz64_dispatch(const BlkParams &P, F &&f) {
+    if (P.iratio) {
+        if (P.nc == 1) return f(k_blk_lz64<1, true>);
+        if (P.nc == 2) return f(k_blk_lz64<2, true>);
+        return f(k_blk_lz64<4, true>);
     }
-    // true units: q.y = g0 2^(2u) sum X Tsum (integer ratios) or the double-float sum
-    // scaled back by 2^(2(E-1023)); q.q_prev = 2^(u+up) sum X Xp
-    const double q_y = P.iratio ? ldexp(i128_to_double(d1) * P.g0, 2 * u)
-                                : ldexp((double)d1f.hi + (double)d1f.lo, 2 * (E - 1023));
-    const double q_qp = ldexp(i128_to_double(d2), u + up);
-    const double s1 = block_sum<BLK_NT>(q_y, red);
-    __syncthreads();
-    const double s2 = block_sum<BLK_NT>(q_qp, red);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = s1;
-        part[gridDim.x + blockIdx.x] = s2;
-    }
-}
-
-// ---------------------------------------------------------------------------------------
-// Lanczos, FP32: u = sigma H q - gamma q_prev over q_prev, dot in double-float
-// ---------------------------------------------------------------------------------------
-template <int NC>
-__global__ void __launch_bounds__(BLK_NT)
-k_blk_lz32(BlkParams P, const float *__restrict__ qc, float *__restrict__ qp, LzScalars *S, double *__restrict__ part) {
-    if (S->done) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[BLK_NT / 32];
-    const BlkTabs tb = stage_blk_tables(P, smem);
-    float *Xs = (float *)(smem + al16(P.tab_bytes));
-    const BlkShared sh = blk_carve(smem + al16(P.tab_bytes) + al16((size_t)P.max_block * 4), P.max_block);
-    const float sig = (float)S->sigma_cur, gam = (float)(S->beta_prev * S->sigma_prev);
-    const GatherF32 gx{qc};
-    ef::df dot{0.0f, 0.0f};
-    for (uint32_t h = blockIdx.x; h < (1u << P.H); h += gridDim.x) {
-        const int k = P.A - __popc(h);
-        if (k < 0 || k > P.K) continue;
-        __syncthreads();
-        uint32_t off;
-        const int n = blk_setup_block(P, tb, h, k, sh, &off);
-        for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = gx(off + r);
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += blockDim.x) {
-            float acc[NC];
-            int cnt[NC];
-            blk_row<float, NC>(P, tb, k, off, r, sh.list[r], Xs, sh, gx, acc, cnt);
-            const float hv = blk_y_f32<NC>(P, acc, cnt, Xs[r]);
-            const float uu = sig * hv - gam * qp[off + r];
-            qp[off + r] = uu;
-            dot = ef::df_add(dot, ef::two_prod(sig * Xs[r], uu));
-        }
-    }
-    const double d = block_sum<BLK_NT>((double)dot.hi + (double)dot.lo, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = d;
+    if (P.nc == 1) return f(k_blk_lz64<1, false>);
+    if (P.nc == 2) return f(k_blk_lz64<2, false>);
+    return f(k_blk_lz64<4, false>);
 }
 
 template <class K_t>
@@ -473,13 +337,15 @@ static int set_smem(K_t kern, size_t sm) {
 int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int *blocks) {
     int rc = blk_plan(b, bp, blk_K(b), P);
     if (rc != 0) return rc;
-    const size_t sm = blk_smem_bytes(*P, dtype == HM_F64 ? 8 : 4, 1);
-    if (sm > 227 * 1024) return 1;
+    const size_t sm = blk_row_smem_bytes(*P, dtype == HM_F64 ? 8 : 4);
+    if (!P->rows_ok || sm > 200 * 1024) return 1;
     int per = 1;
     if (dtype == HM_F64) {
-        if (P->nc == 1) { HM_TRY(set_smem(k_blk_lz64<1>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz64<1>, BLK_NT, sm)); }
-        else if (P->nc == 2) { HM_TRY(set_smem(k_blk_lz64<2>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz64<2>, BLK_NT, sm)); }
-        else { HM_TRY(set_smem(k_blk_lz64<4>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz64<4>, BLK_NT, sm)); }
+        HM_TRY(lz64_dispatch(*P, [&](auto kern) -> int {
+            HM_TRY(set_smem(kern, sm));
+            HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BLK_NT, sm));
+            return HM_OK;
+        }));
     } else {
         if (P->nc == 1) { HM_TRY(set_smem(k_blk_lz32<1>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz32<1>, BLK_NT, sm)); }
         else if (P->nc == 2) { HM_TRY(set_smem(k_blk_lz32<2>, sm)); HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blk_lz32<2>, BLK_NT, sm)); }
@@ -489,19 +355,53 @@ int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int 
     return 0;
 }
 
+// kernel specialised to the plan (jit.cu), with its launch attributes; 1 = not available
+int jit_lz_kernel(const BlkParams &P, int dtype, const void **kern);
+
+int blk_lz_jit(const BlkParams &P, int dtype, const void **kern, int *blocks) {
+    *kern = nullptr;
+    const void *k = nullptr;
+    if (jit_lz_kernel(P, dtype, &k) != 0) return 1;
+    const size_t sm = blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BLK_NT, sm) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    *blocks = std::min<int>(sm_count() * per, 1 << P.H);
+    *kern = k;
+    return 0;
+}
+
+// jit: the specialised kernel, or nullptr for the generic one
 int blk_lz64_launch(const BlkParams &P, const long long *Xc, const long long *Xp, unsigned long long *Y,
-                    LzScalars *S, int pc, double *part, int blocks, cudaStream_t st) {
-    const size_t sm = blk_smem_bytes(P, 8, 1);
-    if (P.nc == 1) k_blk_lz64<1><<<blocks, BLK_NT, sm, st>>>(P, Xc, Xp, Y, S, pc, part);
-    else if (P.nc == 2) k_blk_lz64<2><<<blocks, BLK_NT, sm, st>>>(P, Xc, Xp, Y, S, pc, part);
-    else k_blk_lz64<4><<<blocks, BLK_NT, sm, st>>>(P, Xc, Xp, Y, S, pc, part);
+                    LzScalars *S, int pc, double *part, int blocks, cudaStream_t st, const void *jit) {
+    const size_t sm = blk_row_smem_bytes(P, 8);
+    if (jit) {
+        void *args[] = {(void *)&P, (void *)&Xc, (void *)&Xp, (void *)&Y, (void *)&S, (void *)&pc, (void *)&part};
+        HM_CUDA(cudaLaunchKernel(jit, dim3(blocks), dim3(BLK_NT), args, sm, st));
+        return HM_OK;
+    }
+    HM_TRY(lz64_dispatch(P, [&](auto kern) -> int {
+        kern<<<blocks, BLK_NT, sm, st>>>(P, Xc, Xp, Y, S, pc, part);
+        return HM_OK;
+    }));
     HM_CUDA(cudaGetLastError());
     return HM_OK;
 }
 
 int blk_lz32_launch(const BlkParams &P, const float *qc, float *qp, LzScalars *S, double *part, int blocks,
-                    cudaStream_t st) {
-    const size_t sm = blk_smem_bytes(P, 4, 1);
+                    cudaStream_t st, const void *jit) {
+    const size_t sm = blk_row_smem_bytes(P, 4);
+    if (jit) {
+        void *args[] = {(void *)&P, (void *)&qc, (void *)&qp, (void *)&S, (void *)&part};
+        HM_CUDA(cudaLaunchKernel(jit, dim3(blocks), dim3(BLK_NT), args, sm, st));
+        return HM_OK;
+    }
     if (P.nc == 1) k_blk_lz32<1><<<blocks, BLK_NT, sm, st>>>(P, qc, qp, S, part);
     else if (P.nc == 2) k_blk_lz32<2><<<blocks, BLK_NT, sm, st>>>(P, qc, qp, S, part);
     else k_blk_lz32<4><<<blocks, BLK_NT, sm, st>>>(P, qc, qp, S, part);
@@ -516,7 +416,7 @@ int blk_matvec(hm_basis *b, const BondParams &bp, const void *x, void *y, int dt
     BlkParams P;
     int rc = blk_plan(b, bp, blk_K(b), &P);
     if (rc != 0) return rc;
-    if (blk_smem_bytes(P, dtype == HM_F64 ? 8 : 4, 1) > 227 * 1024) return 1;
+    if (!P.rows_ok || blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4) > 200 * 1024) return 1;
     if (dtype == HM_F64) {
         switch (P.nc) {
             case 1: return launch_blk_matvec<double, 1>(b, P, (const double *)x, (double *)y, st);

@@ -24,56 +24,16 @@
 
 #include <climits>
 
+#include "blk_params.cuh"
 #include "ef64.cuh"
 #include "hm_internal.cuh"
 
 namespace hm {
 
-constexpr int HM_BLK_MAXC = 4;      // coupling classes on the fast path
-constexpr int HM_BLK_MAXG = 48;     // low bond groups
-constexpr int HM_BLK_MAXB = 64;     // high / cross bonds
-
-struct BlkParams {
-    int N, K, H, A, nb1;            // nb1 = 2^(K-8)
-    uint32_t dim;
-    int max_block;
-    int nc;
-    float g_hi[HM_BLK_MAXC], g_lo[HM_BLK_MAXC];   // FP64 mode: -J_c / 4 as double-float
-    float gq[HM_BLK_MAXC];                        // FP32 mode: -J_c / 4
-    int ntot[HM_BLK_MAXC];                        // bonds in class c
-    // integer-ratio classes: -J_c / 4 = Kc[c] * g0 exactly (small integers), so the row
-    // value is g0 * sum_c Kc T_c, one exact integer; g0 = +-2^g0_exp when g0_pow2
-    int iratio, g0_pow2, g0_exp;
-    int Kc[HM_BLK_MAXC];
-    double g0;
-    float g0_hi, g0_lo;
-    // low bonds grouped by (class, byte type, distance d): mask of start positions p;
-    // type 0: both ends in byte 0, 1: both in byte 1, 2: across the bytes.  Groups of
-    // class c and type t are [lg_cs[3c+t], lg_cs[3c+t+1]).
-    int nlg, lg_cs[3 * HM_BLK_MAXC + 1];
-    uint32_t lg_mask[HM_BLK_MAXG];
-    uint8_t lg_d[HM_BLK_MAXG];
-    // high bonds (positions relative to K) and cross bonds (p < K <= q), by class
-    int nhb, hb_start[HM_BLK_MAXC + 1];
-    uint8_t hb_p[HM_BLK_MAXB], hb_q[HM_BLK_MAXB];
-    int ncb, cb_start[HM_BLK_MAXC + 1];
-    uint8_t cb_p[HM_BLK_MAXB], cb_q[HM_BLK_MAXB];
-    // device tables: U[(K+1) x nb1] (uint16), R0[256] (uint8), Cb[(N+1) x (A+1)] (uint32)
-    const void *tab;
-    int tab_bytes, off_U, off_R0, off_C;
-};
-
 // host: builds the plan; returns 0 if the bond list and sector take the fast path
 int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *out);
-size_t blk_smem_bytes(const BlkParams &P, int stage_bytes_per_row, int nvec);
 
 // ---- device helpers ----------------------------------------------------------------------
-struct BlkTabs {
-    const uint16_t *U;
-    const uint8_t *R0;
-    const uint32_t *C;   // C[p * (A+1) + c] = D(p, c) = binomial(p, c), c <= A
-};
-
 __device__ __forceinline__ BlkTabs stage_blk_tables(const BlkParams &P, unsigned char *smem) {
     const uint32_t *src = (const uint32_t *)P.tab;
     uint32_t *dst = (uint32_t *)smem;
@@ -83,21 +43,6 @@ __device__ __forceinline__ BlkTabs stage_blk_tables(const BlkParams &P, unsigned
     t.R0 = (const uint8_t *)(smem + P.off_R0);
     t.C = (const uint32_t *)(smem + P.off_C);
     return t;
-}
-
-// off(h): rank contribution of the high positions (Sec. 3.2) for a block whose low part
-// holds k ones
-__device__ __forceinline__ uint32_t blk_off(const BlkParams &P, const BlkTabs &T, uint32_t h, int k) {
-    uint32_t off = 0;
-    int cnt = k;
-    uint32_t m = h;
-    while (m) {
-        const int t = __ffs(m) - 1;
-        m &= m - 1;
-        ++cnt;
-        off += T.C[(P.K + t) * (P.A + 1) + cnt];
-    }
-    return off;
 }
 
 __device__ __forceinline__ uint32_t rank_low(const BlkParams &P, const BlkTabs &T, uint32_t l, int k) {

@@ -1,0 +1,435 @@
+// blk_sweep.cuh -- thread-per-row kernels of the s = 1/2 block path (layout in blk.cuh):
+// the sweep over the blocks of a sector and the bodies of the matvec and Lanczos
+// products.  Compiles under nvcc (blk.cu, generic row policy) and under NVRTC (jit.cu,
+// bond slots written out per plan).
+#pragma once
+
+#include "blk_params.cuh"
+#include "ef64.cuh"
+#include "hm_dev.cuh"
+
+namespace hm {
+
+constexpr int BLK_NT = 512;
+
+__host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// ---------------------------------------------------------------------------------------
+// Thread-per-row sweep over the blocks (matvec API and the Lanczos products)
+//
+// One thread per row of a block.  Every bond is a slot whose constants sit in the kernel
+// parameters at a compile-time offset, so a low-bond exchange costs a handful of integer
+// instructions and no branch: test the two spins, xor the byte offsets, read the rank
+// table, read x from shared memory, add under the test's predicate.  The rank tables are
+// kept pre-multiplied by the element size, so table values are byte offsets.
+// ---------------------------------------------------------------------------------------
+constexpr int BLK_XPAD = 128;        // a failed exchange may index up to 70 rows past a block
+
+__shared__ uint32_t s_US[16 * 128];  // sizeof(element) * U[k][b1]   (K <= 15)
+__shared__ uint32_t s_R0S[256];      // sizeof(element) * R0[b0]
+__shared__ uint32_t s_hnext[2];      // dynamic schedule: blocks handed to this CTA
+
+struct XSlot {                       // a cross bond in the current block
+    const unsigned char *base;       // first row of the target block
+    uint16_t wm, vm;                 // allowed iff (l ^ wm) & vm: bit p differs from bit q of h
+    uint32_t kofs2;                  // byte offset of row k2 of s_US (k2 = k -+ 1)
+};
+
+struct BlkMeta {                     // per-block data, double-buffered
+    XSlot xs[HM_BLK_MAXC * 2 * HM_BLK_SX];
+    const unsigned char *hb[HM_BLK_MAXB];   // first rows of the high-exchange targets, by class
+    int hs[HM_BLK_MAXC + 1];
+    uint32_t hv[2];
+    uint32_t off, n, kofs, lwo;
+};
+
+__device__ __forceinline__ uint32_t us_at(uint32_t byte_off) {
+    return *(const uint32_t *)((const unsigned char *)s_US + byte_off);
+}
+__device__ __forceinline__ uint32_t r0s_at(uint32_t byte_off) {
+    return *(const uint32_t *)((const unsigned char *)s_R0S + byte_off);
+}
+
+// dynamic shared memory of the sweep: staged rows (padded) | C table | 2 BlkMeta
+__host__ __device__ __forceinline__ size_t blk_row_xs_bytes(const BlkParams &P, int esize) {
+    return al16(((size_t)P.max_block + BLK_XPAD) * esize);
+}
+__host__ __device__ __forceinline__ size_t blk_row_c_bytes(const BlkParams &P) {
+    return al16((size_t)(P.N + 1) * (P.A + 1) * 4);
+}
+__host__ __device__ __forceinline__ size_t blk_row_smem_bytes(const BlkParams &P, int esize) {
+    return blk_row_xs_bytes(P, esize) + blk_row_c_bytes(P) + 2 * al16(sizeof(BlkMeta));
+}
+
+__device__ __forceinline__ bool blk_h_valid(const BlkParams &P, uint32_t h) {
+    const int k = P.A - __popc(h);
+    return k >= 0 && k <= P.K;
+}
+
+// next block of the dynamic schedule (in increasing h, i.e. increasing row index)
+__device__ __forceinline__ uint32_t blk_fetch(const BlkParams &P, unsigned *sched, uint32_t nH) {
+    uint32_t h;
+    do { h = atomicAdd(&sched[0], 1u); } while (h < nH && !blk_h_valid(P, h));
+    return h;
+}
+
+// gathers: element at a byte address of the vector
+struct GFix {                        // fixed-point copy
+    __device__ __forceinline__ int64_t operator()(const unsigned char *p) const {
+        return (int64_t)__ldg((const long long *)p);
+    }
+};
+struct GF64 {                        // binary64, converted to fixed point (exponent E)
+    int E;
+    __device__ __forceinline__ int64_t operator()(const unsigned char *p) const {
+        return ef::fix_from_bits(__ldg((const unsigned long long *)p), E);
+    }
+};
+struct GF32 {
+    __device__ __forceinline__ float operator()(const unsigned char *p) const { return __ldg((const float *)p); }
+};
+
+#define HM_XS(off_) (*(const Sv *)(Xsb + (off_)))
+#define HM_L0(s) { const uint32_t z_ = l ^ (l >> P.ld[c][0][s]);                                  \
+        const uint32_t v_ = r0s_at((l4 ^ P.lxa[c][0][s]) & 0x3FCu);                               \
+        if (z_ & P.lvm[c][0][s]) a += HM_XS(R1own + v_); }
+#define HM_L1(s) { const uint32_t z_ = l ^ (l >> P.ld[c][1][s]);                                  \
+        const uint32_t v_ = us_at(lh4k ^ P.lxb[c][1][s]);                                          \
+        if (z_ & P.lvm[c][1][s]) a += HM_XS(R0own + v_); }
+#define HM_L2(s) { const uint32_t z_ = l ^ (l >> P.ld[c][2][s]);                                  \
+        const uint32_t v_ = us_at(lh4k ^ P.lxb[c][2][s]) + r0s_at((l4 ^ P.lxa[c][2][s]) & 0x3FCu); \
+        if (z_ & P.lvm[c][2][s]) a += HM_XS(v_); }
+#define HM_LG(g) m += __popc((l ^ (l >> P.lgd[c][g])) & P.lgm[c][g]);
+#define HM_X0(s) { const XSlot x_ = B.xs[(2 * c) * HM_BLK_SX + (s)];                              \
+        const uint32_t v_ = us_at(lh4 | x_.kofs2) + r0s_at((l4 ^ P.xxa[c][0][s]) & 0x3FCu);        \
+        if ((l ^ x_.wm) & x_.vm) { a += gx(x_.base + v_); ++m; } }
+#define HM_X1(s) { const XSlot x_ = B.xs[(2 * c + 1) * HM_BLK_SX + (s)];                          \
+        const uint32_t v_ = us_at((lh4 ^ P.xxa[c][1][s]) | x_.kofs2) + R0own;                      \
+        if ((l ^ x_.wm) & x_.vm) { a += gx(x_.base + v_); ++m; } }
+// a switch entering an unrolled run of slots n-1, ..., 0
+#define HM_RUN16(M) case 16: M(15) [[fallthrough]]; case 15: M(14) [[fallthrough]]; case 14: M(13) [[fallthrough]]; \
+    case 13: M(12) [[fallthrough]]; case 12: M(11) [[fallthrough]]; case 11: M(10) [[fallthrough]];                \
+    case 10: M(9) [[fallthrough]]; case 9: M(8) [[fallthrough]]; HM_RUN8(M)
+#define HM_RUN8(M) case 8: M(7) [[fallthrough]]; case 7: M(6) [[fallthrough]]; HM_RUN6(M)
+#define HM_RUN6(M) case 6: M(5) [[fallthrough]]; case 5: M(4) [[fallthrough]]; case 4: M(3) [[fallthrough]]; \
+    case 3: M(2) [[fallthrough]]; case 2: M(1) [[fallthrough]]; case 1: M(0) [[fallthrough]]; default: break;
+
+// Row policy: Row::sums(P, B, Xsb, l, r, gx, acc, cnt) sets, for row r (low word l) of
+// the current block, acc[c] = sum of x over the allowed exchanges of class c and cnt[c]
+// = their number.  RowGeneric reads the bond slots from the parameters; the kernels
+// specialised at run time (jit.cu) bring a policy with the slots written out.
+template <int NC>
+struct RowGeneric {
+template <class Sv, class G>
+static __device__ __forceinline__ void sums(const BlkParams &P, const BlkMeta &B, const unsigned char *Xsb,
+                                            uint32_t l, uint32_t r, const G &gx, Sv *acc, int *cnt) {
+    const uint32_t l4 = l << 2, lh4 = (l >> 8) << 2, lh4k = lh4 | B.kofs;
+    const uint32_t R0own = r0s_at(l4 & 0x3FCu), R1own = us_at(lh4k);
+    const uint32_t rb = r * (uint32_t)sizeof(Sv);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        Sv a = Sv(0);
+        int m = 0;
+        switch (P.ln[c][0]) { HM_RUN16(HM_L0) }
+        switch (P.ln[c][1]) { HM_RUN16(HM_L1) }
+        switch (P.ln[c][2]) { HM_RUN16(HM_L2) }
+        switch (P.lgn[c]) { HM_RUN6(HM_LG) }
+        switch (P.xn[c][0]) { HM_RUN8(HM_X0) }
+        switch (P.xn[c][1]) { HM_RUN8(HM_X1) }
+        // exchanges among the high positions: the same low word in another block
+        const int e0 = B.hs[c], e1 = B.hs[c + 1];
+        int e = e0;
+        for (; e + 4 <= e1; e += 4) {
+            const Sv v0 = gx(B.hb[e] + rb), v1 = gx(B.hb[e + 1] + rb);
+            const Sv v2 = gx(B.hb[e + 2] + rb), v3 = gx(B.hb[e + 3] + rb);
+            a += (v0 + v1) + (v2 + v3);
+        }
+        for (; e < e1; ++e) a += gx(B.hb[e] + rb);
+        acc[c] = a;
+        cnt[c] = m + (e1 - e0);
+    }
+}
+};
+#undef HM_XS
+#undef HM_L0
+#undef HM_L1
+#undef HM_L2
+#undef HM_LG
+#undef HM_X0
+#undef HM_X1
+
+// Every block of the sector through rowf(off, r, x_r, acc, cnt) once.  X: the vector as
+// gx reads it (element size sizeof(Sv)).  DYN: blocks handed out in increasing order by
+// the counter pair sched (zero on entry, zero again on exit), so the CTAs sweep the
+// vector together and the targets of nearby exchanges are still in L2; otherwise a
+// static round robin.  After the rows of a block every thread calls endf(it); one thread
+// then calls flushf(h, it) once the whole CTA is past endf(it), so per-block reductions
+// come out the same whichever CTA ran the block.  All threads of the CTA must call it.
+template <class Sv, int NC, bool DYN, class Row, class G, class RowF, class EndF, class FlushF>
+__device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned char *X, const G &gx, unsigned *sched,
+                                          RowF &&rowf, EndF &&endf, FlushF &&flushf) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const unsigned char *Xsb = smem;
+    Sv *Xs = (Sv *)smem;
+    uint32_t *Ct = (uint32_t *)(smem + blk_row_xs_bytes(P, sizeof(Sv)));
+    BlkMeta *meta = (BlkMeta *)((unsigned char *)Ct + blk_row_c_bytes(P));
+    const int tid = threadIdx.x;
+    {
+        const unsigned char *tab = (const unsigned char *)P.tab;
+        const uint16_t *Ug = (const uint16_t *)(tab + P.off_U);
+        const uint8_t *R0g = tab + P.off_R0;
+        const uint32_t *Cg = (const uint32_t *)(tab + P.off_C);
+        const int nU = (P.K + 1) * P.nb1, nC = (P.N + 1) * (P.A + 1);
+        for (int i = tid; i < nU; i += BLK_NT) s_US[i] = (uint32_t)Ug[i] * (uint32_t)sizeof(Sv);
+        for (int i = tid; i < 256; i += BLK_NT) s_R0S[i] = (uint32_t)R0g[i] * (uint32_t)sizeof(Sv);
+        for (int i = tid; i < nC; i += BLK_NT) Ct[i] = Cg[i];
+    }
+    BlkTabs tb;
+    tb.U = nullptr; tb.R0 = nullptr; tb.C = Ct;
+    const uint32_t nH = 1u << P.H;
+    if (DYN && tid == 0) s_hnext[0] = blk_fetch(P, sched, nH);
+    __syncthreads();
+    uint32_t hs = blockIdx.x, h_prev = 0u;
+    int it_prev = -1;
+    for (int it = 0;; ++it) {
+        uint32_t h;
+        if (DYN) {
+            h = s_hnext[it & 1];
+        } else {
+            h = hs;
+            while (h < nH && !blk_h_valid(P, h)) h += gridDim.x;
+            hs = h + gridDim.x;
+        }
+        if (h >= nH) break;
+        BlkMeta &B = meta[it & 1];
+        const int k = P.A - __popc(h);
+        // setup 1: targets of the high and cross exchanges, own offset, next block
+        if (DYN && tid == 0) s_hnext[(it + 1) & 1] = blk_fetch(P, sched, nH);
+        const unsigned char *hptr = X;
+        bool hval = false;
+        if (tid < P.nhb) {
+            const int p = P.hb_p[tid], q = P.hb_q[tid];
+            hval = (((h >> p) ^ (h >> q)) & 1u) != 0u;
+            if (hval) hptr = X + (size_t)blk_off(P, tb, h ^ ((1u << p) | (1u << q)), k) * sizeof(Sv);
+        }
+        if (tid < 64) {
+            const unsigned bal = __ballot_sync(0xffffffffu, hval);
+            if ((tid & 31) == 0) B.hv[tid >> 5] = bal;
+        }
+        if (tid >= 64 && tid < 64 + P.nxf) {
+            const int e = tid - 64, p = P.xf_p[e], q = P.xf_q[e];
+            const uint32_t bq = (h >> q) & 1u;
+            const int k2 = k + (bq ? 1 : -1);
+            const bool ok = k2 >= 0 && k2 <= P.K;
+            XSlot xs;
+            xs.base = ok ? X + (size_t)blk_off(P, tb, h ^ (1u << q), k2) * sizeof(Sv) : X;
+            xs.wm = (uint16_t)(bq << p);
+            xs.vm = (uint16_t)(ok ? 1u << p : 0u);
+            xs.kofs2 = ok ? (uint32_t)k2 << P.kshift : 0u;
+            B.xs[P.xf_dst[e]] = xs;
+        }
+        if (tid == 128) {
+            B.off = blk_off(P, tb, h, k);
+            B.n = Ct[P.K * (P.A + 1) + k];
+            B.kofs = (uint32_t)k << P.kshift;
+            B.lwo = (uint32_t)P.lwoff[k];
+        }
+        __syncthreads();
+        if (tid == BLK_NT - 1 && it_prev >= 0) flushf(h_prev, it_prev);
+        // setup 2: compact the allowed high exchanges by class; stage the block's x
+        {
+            const uint32_t h0 = B.hv[0], h1 = B.hv[1];
+            if (hval) {
+                const int pos = tid < 32 ? __popc(h0 & ((1u << tid) - 1u))
+                                         : __popc(h0) + __popc(h1 & ((1u << (tid - 32)) - 1u));
+                B.hb[pos] = hptr;
+            }
+            if (tid <= HM_BLK_MAXC) {
+                const int e = P.hb_start[tid];
+                B.hs[tid] = e >= 32 ? __popc(h0) + __popc(e >= 64 ? h1 : h1 & ((1u << (e - 32)) - 1u))
+                                    : __popc(h0 & ((1u << e) - 1u));
+            }
+        }
+        const uint32_t off = B.off, n = B.n;
+        for (uint32_t r = tid; r < n; r += BLK_NT) Xs[r] = gx(X + (size_t)(off + r) * sizeof(Sv));
+        __syncthreads();
+        const uint16_t *lw = P.lw + B.lwo;
+        for (uint32_t r = tid; r < n; r += BLK_NT) {
+            Sv acc[NC];
+            int cnt[NC];
+            Row::template sums<Sv>(P, B, Xsb, (uint32_t)__ldg(lw + r), r, gx, acc, cnt);
+            rowf(off, r, Xs[r], acc, cnt);
+        }
+        endf(it);
+        h_prev = h;
+        it_prev = it;
+    }
+    __syncthreads();
+    if (tid == BLK_NT - 1 && it_prev >= 0) flushf(h_prev, it_prev);
+    if (DYN && tid == 0) {
+        if (atomicAdd(&sched[1], 1u) == gridDim.x - 1) {   // every CTA is past its last fetch
+            sched[0] = 0u;
+            sched[1] = 0u;
+        }
+    }
+}
+
+// T_c = 2 acc_c + (ntot_c - 2 cnt_c) x_i: the class sum of Eq. (E-2-1) rows in units of
+// -J_c / 4 (s = 1/2: s^z s^z = +-1/4, exchange element 1/2)
+template <int NC>
+__device__ __forceinline__ void blk_classes(const BlkParams &P, const int64_t *acc, const int *cnt, int64_t Xo,
+                                            int64_t *T) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) T[c] = 2 * acc[c] + (int64_t)(P.ntot[c] - 2 * cnt[c]) * Xo;
+}
+
+// y (binary64 bits) of a row from its class sums; u = unit exponent of the fixed point.
+// Integer-ratio classes with a power-of-two g0 round the exact integer once.
+template <int NC, int IRM = -1>       // IRM: integer ratios known at compile time (1 / 0), or -1
+__device__ __forceinline__ unsigned long long blk_y_bits(const BlkParams &P, const int64_t *T, int u, int64_t *Tsum) {
+    if (IRM == 1 || (IRM < 0 && P.iratio)) {
+        int64_t s = 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s += (int64_t)P.Kc[c] * T[c];
+        *Tsum = s;
+        if (P.g0_pow2) return ef::bits_from_int(s, u + P.g0_exp);
+        const ef::df t = ef::df_from_fix(s, u + 1022 + ef::FIX_BITS, 0, 0);
+        return ef::bits_from_df(ef::df_mul(t, ef::df{P.g0_hi, P.g0_lo}), 0);
+    }
+    *Tsum = 0;
+    ef::df y{0.0f, 0.0f};
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+        y = ef::df_add(y, ef::df_mul(ef::df_from_fix(T[c], u + 1022 + ef::FIX_BITS, 0, 0), ef::df{P.g_hi[c], P.g_lo[c]}));
+    return ef::bits_from_df(y, 0);
+}
+
+template <int NC>
+__device__ __forceinline__ float blk_y_f32(const BlkParams &P, const float *acc, const int *cnt, float xo) {
+    float y = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) y += P.gq[c] * (2.0f * acc[c] + (float)(P.ntot[c] - 2 * cnt[c]) * xo);
+    return y;
+}
+
+// ---------------------------------------------------------------------------------------
+// y = H x (matvec API)
+// ---------------------------------------------------------------------------------------
+template <class T, int NC, class Row>
+__device__ __forceinline__ void matvec_body(const BlkParams &P, const T *__restrict__ x, T *__restrict__ y,
+                                            const int *__restrict__ Eptr) {
+    if constexpr (sizeof(T) == 8) {
+        const int E = Eptr ? *Eptr : 0;
+        const int u = E - 1022 - ef::FIX_BITS;
+        unsigned long long *yb = (unsigned long long *)y;
+        blk_sweep<int64_t, NC, false, Row>(P, (const unsigned char *)x, GF64{E}, nullptr,
+                                      [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt) {
+                                          int64_t Tc[NC], ts;
+                                          blk_classes<NC>(P, acc, cnt, xo, Tc);
+                                          yb[off + r] = blk_y_bits<NC>(P, Tc, u, &ts);
+                                      },
+                                      [](int) {}, [](uint32_t, int) {});
+    } else {
+        blk_sweep<float, NC, false, Row>(P, (const unsigned char *)x, GF32{}, nullptr,
+                                    [&](uint32_t off, uint32_t r, float xo, const float *acc, const int *cnt) {
+                                        y[off + r] = blk_y_f32<NC>(P, acc, cnt, xo);
+                                    },
+                                    [](int) {}, [](uint32_t, int) {});
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Lanczos, FP64: y = H q_cur from the fixed-point copy Xc of q_cur (every gather an
+// integer load), written as binary64 to Y; the exact integer dots q.y and q.q_prev
+// (Xp: fixed-point copy of q_prev) give alpha without re-reading y.
+// part[blk] = (q . H q) and part[gridDim + blk] = (q . q_prev), both in true units.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo = (unsigned long long)v;
+    return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+// per-warp partial sums of the current and previous block (blk_sweep's endf / flushf)
+__shared__ double s_wpart[2][BLK_NT / 32][2];
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// part[h] = (q . H q) and part[2^H + h] = (q . q_prev) over the rows of block h, in true
+// units; entries of blocks that do not exist stay as they are
+template <int NC, bool IR, class Row>
+__device__ __forceinline__ void lz64_body(const BlkParams &P, const long long *__restrict__ Xc,
+                                          const long long *__restrict__ Xp, unsigned long long *__restrict__ Y,
+                                          LzScalars *S, int pc, double *__restrict__ part) {
+    if (S->done) return;
+    const int E = S->emax[pc], Ep = S->emax[pc ^ 1];
+    const int u = E - 1022 - ef::FIX_BITS, up = Ep - 1022 - ef::FIX_BITS;
+    const uint32_t nH = 1u << P.H;
+    __int128 d1 = 0, d2 = 0;
+    ef::df d1f{0.0f, 0.0f};
+    blk_sweep<int64_t, NC, true, Row>(
+        P, (const unsigned char *)Xc, GFix{}, S->sched,
+        [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt) {
+            int64_t Tc[NC], ts;
+            blk_classes<NC>(P, acc, cnt, xo, Tc);
+            const unsigned long long yb = blk_y_bits<NC, IR ? 1 : 0>(P, Tc, u, &ts);
+            __stcs(Y + off + r, yb);
+            if constexpr (IR) d1 += (__int128)xo * ts;
+            else d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
+            d2 += (__int128)xo * (int64_t)__ldcs(Xp + off + r);
+        },
+        [&](int it) {
+            // true units: q.y = g0 2^(2u) sum X Tsum (integer ratios) or the double-float
+            // sum scaled back by 2^(2(E-1023)); q.q_prev = 2^(u+up) sum X Xp
+            const double q_y = IR ? ldexp(i128_to_double(d1) * P.g0, 2 * u)
+                                  : ldexp((double)d1f.hi + (double)d1f.lo, 2 * (E - 1023));
+            const double q_qp = ldexp(i128_to_double(d2), u + up);
+            d1 = 0; d2 = 0; d1f = ef::df{0.0f, 0.0f};
+            const double a = warp_sum(q_y), b = warp_sum(q_qp);
+            if ((threadIdx.x & 31) == 0) {
+                s_wpart[it & 1][threadIdx.x >> 5][0] = a;
+                s_wpart[it & 1][threadIdx.x >> 5][1] = b;
+            }
+        },
+        [&](uint32_t h, int it) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < BLK_NT / 32; ++w) { a += s_wpart[it & 1][w][0]; b += s_wpart[it & 1][w][1]; }
+            part[h] = a;
+            part[nH + h] = b;
+        });
+}
+
+// ---------------------------------------------------------------------------------------
+// Lanczos, FP32: u = sigma H q - gamma q_prev over q_prev, dot in double-float
+// ---------------------------------------------------------------------------------------
+// part[h] = (sigma q . u) over the rows of block h
+template <int NC, class Row>
+__device__ __forceinline__ void lz32_body(const BlkParams &P, const float *__restrict__ qc, float *__restrict__ qp,
+                                          LzScalars *S, double *__restrict__ part) {
+    if (S->done) return;
+    const float sig = (float)S->sigma_cur, gam = (float)(S->beta_prev * S->sigma_prev);
+    ef::df dot{0.0f, 0.0f};
+    blk_sweep<float, NC, true, Row>(
+        P, (const unsigned char *)qc, GF32{}, S->sched,
+        [&](uint32_t off, uint32_t r, float xo, const float *acc, const int *cnt) {
+            const float hv = blk_y_f32<NC>(P, acc, cnt, xo);
+            const float uu = sig * hv - gam * qp[off + r];
+            qp[off + r] = uu;
+            dot = ef::df_add(dot, ef::two_prod(sig * xo, uu));
+        },
+        [&](int it) {
+            const double a = warp_sum((double)dot.hi + (double)dot.lo);
+            dot = ef::df{0.0f, 0.0f};
+            if ((threadIdx.x & 31) == 0) s_wpart[it & 1][threadIdx.x >> 5][0] = a;
+        },
+        [&](uint32_t h, int it) {
+            double a = 0.0;
+            for (int w = 0; w < BLK_NT / 32; ++w) a += s_wpart[it & 1][w][0];
+            part[h] = a;
+        });
+}
+
+}  // namespace hm

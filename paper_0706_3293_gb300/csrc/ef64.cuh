@@ -10,9 +10,11 @@
 // Every function is __host__ __device__ so the host tests can check it against doubles.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <stdint.h>
 #include <string.h>
 #include <math.h>
+#endif
 
 #ifdef __CUDA_ARCH__
 #define EF_HD __host__ __device__ __forceinline__

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/hm.h"
+#include "hm_dev.cuh"
 
 // ---------------------------------------------------------------------------------------
 // error reporting (thread-local message, see hm_last_error)
@@ -58,6 +59,8 @@ namespace hm {
 struct BlkTab {                     // byte-chunk rank tables of the s = 1/2 block path
     void *dev = nullptr;
     int bytes = 0, oU = 0, oR0 = 0, oC = 0;
+    uint16_t *lw = nullptr;         // K-bit words by popcount, each run in increasing order
+    int lwoff[18] = {};             // run of popcount k starts at lw + lwoff[k]
 };
 }  // namespace hm
 
@@ -72,21 +75,6 @@ struct hm_basis {
 };
 
 namespace hm {
-
-// device state of a Lanczos run (see lanczos.cu)
-struct LzScalars {
-    double sigma_cur;    // v_j = sigma_cur * q_cur (stored vectors are unnormalised)
-    double sigma_prev;
-    double beta_prev;
-    double scale;        // max(|alpha_1..alpha_j|, beta_1..beta_{j-1})
-    double nrm2;         // scratch for norms
-    int j;               // steps done
-    int done;
-    int status;
-    int mconv;           // e0_grad: Krylov length used
-    int emax[2];         // largest exponent field of the vector held in buffer 0 / 1
-    int emax_old;        // exponent of q_prev while its buffer receives w
-};
 
 int digit_bits(int two_s);
 // host helpers shared by the translation units
@@ -202,22 +190,6 @@ __host__ __device__ __forceinline__ uint64_t sm64(uint64_t seed, uint64_t t) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
-}
-
-// ---------------------------------------------------------------------------------------
-// deterministic block reduction of doubles (fixed shuffle tree + fixed warp order)
-// ---------------------------------------------------------------------------------------
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double *sh /* >= NT/32 */) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < NT / 32; ++k) t += sh[k];
-    return t;  // valid in thread 0
 }
 
 // number of blocks used by grid-stride kernels: fixed per device so reductions are

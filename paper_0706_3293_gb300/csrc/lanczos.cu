@@ -2,6 +2,7 @@
 // eigensolvers on the device, lanczos_run (one CUDA graph) and e0_grad.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 
@@ -12,10 +13,11 @@
 namespace hm {
 
 int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int *blocks);
+int blk_lz_jit(const BlkParams &P, int dtype, const void **kern, int *blocks);
 int blk_lz64_launch(const BlkParams &P, const long long *Xc, const long long *Xp, unsigned long long *Y,
-                    LzScalars *S, int pc, double *part, int blocks, cudaStream_t st);
+                    LzScalars *S, int pc, double *part, int blocks, cudaStream_t st, const void *jit);
 int blk_lz32_launch(const BlkParams &P, const float *qc, float *qp, LzScalars *S, double *part, int blocks,
-                    cudaStream_t st);
+                    cudaStream_t st, const void *jit);
 
 int matvec_dev(const hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype,
                int nvec, cudaStream_t st);
@@ -33,6 +35,7 @@ constexpr int NT = 256;
 struct LzLayout {
     size_t buf[2], part, sc, alpha, beta, ritz, psi, coef, res, gout, tri, bpart, total;
     size_t ybuf, xs[2];     // FP64 block path: y = H q and the fixed-point copies of q
+    size_t hpart;           // s = 1/2 block path: per-block partial sums, 2 x 2^H doubles
     bool shadow;
 };
 
@@ -54,6 +57,11 @@ static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad
         L.ybuf = o; o += al256(dim * 8);
         L.xs[0] = o; o += al256(dim * 8);
         L.xs[1] = o; o += al256(dim * 8);
+    }
+    // per-block partials of the s = 1/2 block path (split K = min(15, N - 2): H <= 17)
+    if (b->view.S2 == 1 && b->view.N >= 10 && b->view.N <= 32 && !b->view.idx64) {
+        const int H = b->view.N - std::min(15, b->view.N - 2);
+        L.hpart = o; o += al256(((size_t)2 << H) * sizeof(double));
     }
     L.sc = o; o += al256(sizeof(LzScalars));
     L.alpha = o; o += al256((size_t)max_steps * 8);
@@ -79,11 +87,13 @@ struct hm_lanczos {
     hm::BondParams bp;
     hm::BlkParams blk;      // s = 1/2 block path (use_blk)
     int use_blk, blk_blocks;
+    const void *jit;        // block product specialised to the bonds (jit.cu), or nullptr
     int dtype, max_steps, host_j, next_phase;
     unsigned char *work;
     hm::LzLayout L;
     hm::LzScalars *sc;
     double *alpha, *beta, *part, *psi, *coef;
+    double *hpart;          // per-block partials of the block path (entries of absent blocks stay 0)
 };
 
 namespace hm {
@@ -461,11 +471,11 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
     unsigned long long *Y = R->L.shadow ? (unsigned long long *)(R->work + R->L.ybuf) : nullptr;
     if (phase == 0) {
         if (b64) {
-            HM_TRY(blk_lz64_launch(R->blk, xs[parity], xs[pprev], Y, R->sc, parity, R->part, R->blk_blocks, st));
-            k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, R->part, R->blk_blocks, R->alpha, pprev);
+            HM_TRY(blk_lz64_launch(R->blk, xs[parity], xs[pprev], Y, R->sc, parity, R->hpart, R->blk_blocks, st, R->jit));
+            k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->alpha, pprev);
         } else if (R->use_blk) {
-            HM_TRY(blk_lz32_launch(R->blk, (const float *)qc, (float *)qp, R->sc, R->part, R->blk_blocks, st));
-            k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, R->blk_blocks, R->alpha, pprev);
+            HM_TRY(blk_lz32_launch(R->blk, (const float *)qc, (float *)qp, R->sc, R->hpart, R->blk_blocks, st, R->jit));
+            k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->alpha, pprev);
         } else {
             const size_t sm = row_smem_bytes<I>(sv);
             k_lz_matvec<I, T, Acc><<<nblk, NT, sm, st>>>(sv, R->bp, qc, qp, R->sc, R->part);
@@ -527,6 +537,7 @@ static int enqueue_start(hm_lanczos *R, const void *v0, uint64_t seed, cudaStrea
     else HM_TRY(start_vector_dev(sv.dim, seed, 0, b0, R->dtype, st));
     HM_CUDA(cudaMemsetAsync(b1, 0, sv.dim * es, st));
     HM_CUDA(cudaMemsetAsync(R->sc, 0, sizeof(LzScalars), st));
+    if (R->use_blk) HM_CUDA(cudaMemsetAsync(R->hpart, 0, ((size_t)2 << R->blk.H) * sizeof(double), st));
     const int nblk = grid_blocks(sv.dim, NT);
     if (R->dtype == HM_F64) k_sumsq<double><<<nblk, NT, 0, st>>>((const double *)b0, sv.dim, R->part, &R->sc->emax[0]);
     else k_sumsq<float><<<nblk, NT, 0, st>>>((const float *)b0, sv.dim, R->part, nullptr);
@@ -565,12 +576,19 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
     R->use_blk = 0;
     rc = blk_lz_plan(const_cast<hm_basis *>(b), R->bp, dtype, &R->blk, &R->blk_blocks);
     if (rc < 0) { delete R; return rc; }
-    R->use_blk = rc == 0 && (dtype == HM_F32 || R->L.shadow);
+    R->use_blk = rc == 0 && (dtype == HM_F32 || R->L.shadow) && R->L.hpart != 0 && R->blk.H <= 17;
+    R->jit = nullptr;
+    if (R->use_blk) {
+        int jb = 0;
+        const void *jk = nullptr;
+        if (blk_lz_jit(R->blk, dtype, &jk, &jb) == 0) { R->jit = jk; R->blk_blocks = jb; }
+    }
     R->work = (unsigned char *)work;
     R->sc = (LzScalars *)(R->work + R->L.sc);
     R->alpha = (double *)(R->work + R->L.alpha);
     R->beta = (double *)(R->work + R->L.beta);
     R->part = (double *)(R->work + R->L.part);
+    R->hpart = R->L.hpart ? (double *)(R->work + R->L.hpart) : nullptr;
     R->psi = nullptr;
     R->coef = grad ? (double *)(R->work + R->L.coef) : nullptr;
     *out = R;
@@ -672,6 +690,16 @@ int lanczos_read(hm_lanczos *R, double *alpha, double *beta, int *steps_done, vo
 
 int lanczos_free(hm_lanczos *R) {
     delete R;
+    return HM_OK;
+}
+
+int lanczos_kernel_name(const hm_lanczos *R, char *name, int cap) {
+    if (!R || !name || cap < 1) return fail(HM_EINVAL, "NULL argument");
+    const bool f64 = R->dtype == HM_F64;
+    const char *n = !R->use_blk ? "k_lz_matvec"
+                    : R->jit    ? (f64 ? "k_blk_lz64_jit" : "k_blk_lz32_jit")
+                                : (f64 ? "k_blk_lz64" : "k_blk_lz32");
+    snprintf(name, (size_t)cap, "%s", n);
     return HM_OK;
 }
 

@@ -399,3 +399,34 @@ def test_count_nnz_full_size_closed_form(hm):
     inst = W.j1j2_ring32()
     b = hm.Basis(32, 1, 0)
     assert hm.count_nnz(b, hm.bonds_of(inst)) == math.comb(32, 16) + 2 * 64 * math.comb(30, 15)
+
+
+@pytest.mark.parametrize("case", ["j1j2_n20_f64", "three_class_n18_f64", "j1j2_n20_f32"])
+def test_block_product_specialised_equals_generic(hm, case, monkeypatch):
+    """The block product compiled for the bond list at run time (NVRTC) and the generic
+    block kernel form the same exact integer sums (FP64) or the same float operations
+    (FP32), so 60 Lanczos steps agree bit for bit."""
+    if case == "three_class_n18_f64":
+        n, J = 18, [-1.0 if i % 3 == 0 else (0.5 if i % 3 == 1 else -0.25) for i in range(18)]
+        u = list(range(18)) + [0, 3, 2]
+        v = [(i + 1) % 18 for i in range(18)] + [9, 12, 17]
+        J = J + [-1.0, 0.5, -0.25]
+        bonds = hm.BondList.make(u, v, J)
+        two_m, dt = 2, torch.float64
+    else:
+        n = 20
+        bonds = hm.bonds_of(W.small_ring(n, -1.0, -0.3))
+        two_m, dt = 0, (torch.float32 if case.endswith("f32") else torch.float64)
+    b = hm.Basis(n, 1, two_m)
+    runs = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("HM_JIT", mode)
+        r = hm.LanczosRun(b, bonds, 60, seed=11, dtype=dt)
+        name = r.kernel_name()
+        r.step(60)
+        runs[mode] = (name, r.read())
+        r.close()
+    assert runs["1"][0].endswith("_jit"), runs["1"][0]
+    assert runs["0"][0].startswith("k_blk_lz") and not runs["0"][0].endswith("_jit")
+    (a1, b1, _), (a0, b0, _) = runs["1"][1], runs["0"][1]
+    assert np.array_equal(a1, a0) and np.array_equal(b1, b0)
