@@ -271,9 +271,9 @@ k_blk_matvec(BlkParams P, const T *__restrict__ x, T *__restrict__ y, const int 
 
 template <int NC, bool IR>
 __global__ void __launch_bounds__(BLK_NT, 3)
-k_blk_lz64(BlkParams P, const long long *__restrict__ Xc, const long long *__restrict__ Xp,
-           unsigned long long *__restrict__ Y, LzScalars *S, int pc, double *__restrict__ part) {
-    lz64_body<NC, IR, RowGeneric<NC>>(P, Xc, Xp, Y, S, pc, part);
+k_blk_lz64(BlkParams P, const long long *__restrict__ Xc, unsigned long long *__restrict__ Y, LzScalars *S, int pc,
+           double *__restrict__ part) {
+    lz64_body<NC, IR, RowGeneric<NC>>(P, Xc, Y, S, pc, part);
 }
 
 template <int NC>
@@ -293,7 +293,7 @@ __global__ void k_max_exp(const unsigned long long *__restrict__ x, uint64_t n, 
 
 template <class T, int NC>
 static int launch_blk_matvec(hm_basis *b, const BlkParams &P, const T *x, T *y, cudaStream_t st) {
-    const size_t sm = blk_row_smem_bytes(P, sizeof(T) == 8 ? 8 : 4);
+    const size_t sm = blk_row_smem_bytes(P, sizeof(T) == 8 ? 8 : 4, BLK_XPAD);
     HM_CUDA(cudaFuncSetAttribute(k_blk_matvec<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int *Ed = nullptr;
     if constexpr (sizeof(T) == 8) {
@@ -337,7 +337,7 @@ static int set_smem(K_t kern, size_t sm) {
 int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int *blocks) {
     int rc = blk_plan(b, bp, blk_K(b), P);
     if (rc != 0) return rc;
-    const size_t sm = blk_row_smem_bytes(*P, dtype == HM_F64 ? 8 : 4);
+    const size_t sm = blk_row_smem_bytes(*P, dtype == HM_F64 ? 8 : 4, BLK_XPAD);
     if (!P->rows_ok || sm > 200 * 1024) return 1;
     int per = 1;
     if (dtype == HM_F64) {
@@ -357,12 +357,14 @@ int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int 
 
 // kernel specialised to the plan (jit.cu), with its launch attributes; 1 = not available
 int jit_lz_kernel(const BlkParams &P, int dtype, const void **kern);
+// pad elements after the staged rows of a specialised kernel (jit.cu)
+int jit_pad(const void *kern);
 
 int blk_lz_jit(const BlkParams &P, int dtype, const void **kern, int *blocks) {
     *kern = nullptr;
     const void *k = nullptr;
     if (jit_lz_kernel(P, dtype, &k) != 0) return 1;
-    const size_t sm = blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4);
+    const size_t sm = blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4, jit_pad(k));
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -378,16 +380,16 @@ int blk_lz_jit(const BlkParams &P, int dtype, const void **kern, int *blocks) {
 }
 
 // jit: the specialised kernel, or nullptr for the generic one
-int blk_lz64_launch(const BlkParams &P, const long long *Xc, const long long *Xp, unsigned long long *Y,
-                    LzScalars *S, int pc, double *part, int blocks, cudaStream_t st, const void *jit) {
-    const size_t sm = blk_row_smem_bytes(P, 8);
+int blk_lz64_launch(const BlkParams &P, const long long *Xc, unsigned long long *Y, LzScalars *S, int pc,
+                    double *part, int blocks, cudaStream_t st, const void *jit) {
+    const size_t sm = blk_row_smem_bytes(P, 8, jit_pad(jit));
     if (jit) {
-        void *args[] = {(void *)&P, (void *)&Xc, (void *)&Xp, (void *)&Y, (void *)&S, (void *)&pc, (void *)&part};
+        void *args[] = {(void *)&P, (void *)&Xc, (void *)&Y, (void *)&S, (void *)&pc, (void *)&part};
         HM_CUDA(cudaLaunchKernel(jit, dim3(blocks), dim3(BLK_NT), args, sm, st));
         return HM_OK;
     }
     HM_TRY(lz64_dispatch(P, [&](auto kern) -> int {
-        kern<<<blocks, BLK_NT, sm, st>>>(P, Xc, Xp, Y, S, pc, part);
+        kern<<<blocks, BLK_NT, sm, st>>>(P, Xc, Y, S, pc, part);
         return HM_OK;
     }));
     HM_CUDA(cudaGetLastError());
@@ -396,7 +398,7 @@ int blk_lz64_launch(const BlkParams &P, const long long *Xc, const long long *Xp
 
 int blk_lz32_launch(const BlkParams &P, const float *qc, float *qp, LzScalars *S, double *part, int blocks,
                     cudaStream_t st, const void *jit) {
-    const size_t sm = blk_row_smem_bytes(P, 4);
+    const size_t sm = blk_row_smem_bytes(P, 4, jit_pad(jit));
     if (jit) {
         void *args[] = {(void *)&P, (void *)&qc, (void *)&qp, (void *)&S, (void *)&part};
         HM_CUDA(cudaLaunchKernel(jit, dim3(blocks), dim3(BLK_NT), args, sm, st));
@@ -416,7 +418,7 @@ int blk_matvec(hm_basis *b, const BondParams &bp, const void *x, void *y, int dt
     BlkParams P;
     int rc = blk_plan(b, bp, blk_K(b), &P);
     if (rc != 0) return rc;
-    if (!P.rows_ok || blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4) > 200 * 1024) return 1;
+    if (!P.rows_ok || blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4, BLK_XPAD) > 200 * 1024) return 1;
     if (dtype == HM_F64) {
         switch (P.nc) {
             case 1: return launch_blk_matvec<double, 1>(b, P, (const double *)x, (double *)y, st);

@@ -50,15 +50,12 @@ __device__ __forceinline__ uint32_t r0s_at(uint32_t byte_off) {
     return *(const uint32_t *)((const unsigned char *)s_R0S + byte_off);
 }
 
-// dynamic shared memory of the sweep: staged rows (padded) | C table | 2 BlkMeta
-__host__ __device__ __forceinline__ size_t blk_row_xs_bytes(const BlkParams &P, int esize) {
-    return al16(((size_t)P.max_block + BLK_XPAD) * esize);
+// dynamic shared memory of the sweep: staged rows (+ pad elements) | 2 BlkMeta
+__host__ __device__ __forceinline__ size_t blk_row_xs_bytes(const BlkParams &P, int esize, int pad) {
+    return al16(((size_t)P.max_block + pad) * esize);
 }
-__host__ __device__ __forceinline__ size_t blk_row_c_bytes(const BlkParams &P) {
-    return al16((size_t)(P.N + 1) * (P.A + 1) * 4);
-}
-__host__ __device__ __forceinline__ size_t blk_row_smem_bytes(const BlkParams &P, int esize) {
-    return blk_row_xs_bytes(P, esize) + blk_row_c_bytes(P) + 2 * al16(sizeof(BlkMeta));
+__host__ __device__ __forceinline__ size_t blk_row_smem_bytes(const BlkParams &P, int esize, int pad) {
+    return blk_row_xs_bytes(P, esize, pad) + 2 * al16(sizeof(BlkMeta));
 }
 
 __device__ __forceinline__ bool blk_h_valid(const BlkParams &P, uint32_t h) {
@@ -118,11 +115,28 @@ struct GF32 {
 // the current block, acc[c] = sum of x over the allowed exchanges of class c and cnt[c]
 // = their number.  RowGeneric reads the bond slots from the parameters; the kernels
 // specialised at run time (jit.cu) bring a policy with the slots written out.
+//
+// A policy also says how many pad elements follow the staged rows (kPad), whether the
+// cross slots index rows k-1, k, k+1 of a per-block copy of US (kRelUS) or US itself,
+// and has two hooks: stage<Sv>(P) at kernel start (all threads, before the first
+// barrier; s_R0S is being written in the same phase and may not be read) and
+// block<Sv>(P, k) once per block between the block setup and the rows (all threads).
 template <int NC>
 struct RowGeneric {
+static constexpr int kPad = BLK_XPAD;
+static constexpr bool kRelUS = false;
+template <class Sv>
+static __device__ __forceinline__ void stage(const BlkParams &P) {
+    const uint16_t *Ug = (const uint16_t *)((const unsigned char *)P.tab + P.off_U);
+    const int nU = (P.K + 1) * P.nb1;
+    for (int i = threadIdx.x; i < nU; i += BLK_NT) s_US[i] = (uint32_t)Ug[i] * (uint32_t)sizeof(Sv);
+}
+template <class Sv>
+static __device__ __forceinline__ void block(const BlkParams &, uint32_t) {}
 template <class Sv, class G>
 static __device__ __forceinline__ void sums(const BlkParams &P, const BlkMeta &B, const unsigned char *Xsb,
-                                            uint32_t l, uint32_t r, const G &gx, Sv *acc, int *cnt) {
+                                            uint32_t l, uint32_t r, const G &gx, Sv xo, Sv *acc, int *cnt) {
+    (void)xo;
     const uint32_t l4 = l << 2, lh4 = (l >> 8) << 2, lh4k = lh4 | B.kofs;
     const uint32_t R0own = r0s_at(l4 & 0x3FCu), R1own = us_at(lh4k);
     const uint32_t rb = r * (uint32_t)sizeof(Sv);
@@ -158,34 +172,30 @@ static __device__ __forceinline__ void sums(const BlkParams &P, const BlkMeta &B
 #undef HM_X0
 #undef HM_X1
 
-// Every block of the sector through rowf(off, r, x_r, acc, cnt) once.  X: the vector as
+// Every block of the sector through rowf(off, r, x_r, acc, cnt, pref(off + r)) once
+// (pref loads what the row needs besides x, issued before the hop sums).  X: the vector as
 // gx reads it (element size sizeof(Sv)).  DYN: blocks handed out in increasing order by
 // the counter pair sched (zero on entry, zero again on exit), so the CTAs sweep the
 // vector together and the targets of nearby exchanges are still in L2; otherwise a
 // static round robin.  After the rows of a block every thread calls endf(it); one thread
 // then calls flushf(h, it) once the whole CTA is past endf(it), so per-block reductions
 // come out the same whichever CTA ran the block.  All threads of the CTA must call it.
-template <class Sv, int NC, bool DYN, class Row, class G, class RowF, class EndF, class FlushF>
+template <class Sv, int NC, bool DYN, class Row, class G, class PrefF, class RowF, class EndF, class FlushF>
 __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned char *X, const G &gx, unsigned *sched,
-                                          RowF &&rowf, EndF &&endf, FlushF &&flushf) {
+                                          PrefF &&pref, RowF &&rowf, EndF &&endf, FlushF &&flushf) {
     extern __shared__ __align__(16) unsigned char smem[];
     const unsigned char *Xsb = smem;
     Sv *Xs = (Sv *)smem;
-    uint32_t *Ct = (uint32_t *)(smem + blk_row_xs_bytes(P, sizeof(Sv)));
-    BlkMeta *meta = (BlkMeta *)((unsigned char *)Ct + blk_row_c_bytes(P));
+    BlkMeta *meta = (BlkMeta *)(smem + blk_row_xs_bytes(P, sizeof(Sv), Row::kPad));
     const int tid = threadIdx.x;
+    const uint32_t *Cg = (const uint32_t *)((const unsigned char *)P.tab + P.off_C);
     {
-        const unsigned char *tab = (const unsigned char *)P.tab;
-        const uint16_t *Ug = (const uint16_t *)(tab + P.off_U);
-        const uint8_t *R0g = tab + P.off_R0;
-        const uint32_t *Cg = (const uint32_t *)(tab + P.off_C);
-        const int nU = (P.K + 1) * P.nb1, nC = (P.N + 1) * (P.A + 1);
-        for (int i = tid; i < nU; i += BLK_NT) s_US[i] = (uint32_t)Ug[i] * (uint32_t)sizeof(Sv);
+        const uint8_t *R0g = (const uint8_t *)P.tab + P.off_R0;
         for (int i = tid; i < 256; i += BLK_NT) s_R0S[i] = (uint32_t)R0g[i] * (uint32_t)sizeof(Sv);
-        for (int i = tid; i < nC; i += BLK_NT) Ct[i] = Cg[i];
+        Row::template stage<Sv>(P);
     }
     BlkTabs tb;
-    tb.U = nullptr; tb.R0 = nullptr; tb.C = Ct;
+    tb.U = nullptr; tb.R0 = nullptr; tb.C = Cg;
     const uint32_t nH = 1u << P.H;
     if (DYN && tid == 0) s_hnext[0] = blk_fetch(P, sched, nH);
     __syncthreads();
@@ -225,12 +235,12 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
             xs.base = ok ? X + (size_t)blk_off(P, tb, h ^ (1u << q), k2) * sizeof(Sv) : X;
             xs.wm = (uint16_t)(bq << p);
             xs.vm = (uint16_t)(ok ? 1u << p : 0u);
-            xs.kofs2 = ok ? (uint32_t)k2 << P.kshift : 0u;
+            xs.kofs2 = ok ? (uint32_t)(Row::kRelUS ? k2 - k + 1 : k2) << P.kshift : 0u;
             B.xs[P.xf_dst[e]] = xs;
         }
         if (tid == 128) {
             B.off = blk_off(P, tb, h, k);
-            B.n = Ct[P.K * (P.A + 1) + k];
+            B.n = Cg[P.K * (P.A + 1) + k];
             B.kofs = (uint32_t)k << P.kshift;
             B.lwo = (uint32_t)P.lwoff[k];
         }
@@ -252,13 +262,19 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
         }
         const uint32_t off = B.off, n = B.n;
         for (uint32_t r = tid; r < n; r += BLK_NT) Xs[r] = gx(X + (size_t)(off + r) * sizeof(Sv));
+        Row::template block<Sv>(P, (uint32_t)k);
         __syncthreads();
         const uint16_t *lw = P.lw + B.lwo;
+        uint32_t l_next = tid < n ? (uint32_t)__ldg(lw + tid) : 0u;
         for (uint32_t r = tid; r < n; r += BLK_NT) {
+            const uint32_t l = l_next;                     // the list word one row ahead
+            if (r + BLK_NT < n) l_next = (uint32_t)__ldg(lw + r + BLK_NT);
+            const auto pv = pref(off + r);                 // the row's other operand, ahead of the sums
+            const Sv xo = Xs[r];
             Sv acc[NC];
             int cnt[NC];
-            Row::template sums<Sv>(P, B, Xsb, (uint32_t)__ldg(lw + r), r, gx, acc, cnt);
-            rowf(off, r, Xs[r], acc, cnt);
+            Row::template sums<Sv>(P, B, Xsb, l, r, gx, xo, acc, cnt);
+            rowf(off, r, xo, acc, cnt, pv);
         }
         endf(it);
         h_prev = h;
@@ -322,16 +338,16 @@ __device__ __forceinline__ void matvec_body(const BlkParams &P, const T *__restr
         const int E = Eptr ? *Eptr : 0;
         const int u = E - 1022 - ef::FIX_BITS;
         unsigned long long *yb = (unsigned long long *)y;
-        blk_sweep<int64_t, NC, false, Row>(P, (const unsigned char *)x, GF64{E}, nullptr,
-                                      [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt) {
+        blk_sweep<int64_t, NC, false, Row>(P, (const unsigned char *)x, GF64{E}, nullptr, [](uint32_t) { return 0; },
+                                      [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt, int) {
                                           int64_t Tc[NC], ts;
                                           blk_classes<NC>(P, acc, cnt, xo, Tc);
                                           yb[off + r] = blk_y_bits<NC>(P, Tc, u, &ts);
                                       },
                                       [](int) {}, [](uint32_t, int) {});
     } else {
-        blk_sweep<float, NC, false, Row>(P, (const unsigned char *)x, GF32{}, nullptr,
-                                    [&](uint32_t off, uint32_t r, float xo, const float *acc, const int *cnt) {
+        blk_sweep<float, NC, false, Row>(P, (const unsigned char *)x, GF32{}, nullptr, [](uint32_t) { return 0; },
+                                    [&](uint32_t off, uint32_t r, float xo, const float *acc, const int *cnt, int) {
                                         y[off + r] = blk_y_f32<NC>(P, acc, cnt, xo);
                                     },
                                     [](int) {}, [](uint32_t, int) {});
@@ -340,9 +356,8 @@ __device__ __forceinline__ void matvec_body(const BlkParams &P, const T *__restr
 
 // ---------------------------------------------------------------------------------------
 // Lanczos, FP64: y = H q_cur from the fixed-point copy Xc of q_cur (every gather an
-// integer load), written as binary64 to Y; the exact integer dots q.y and q.q_prev
-// (Xp: fixed-point copy of q_prev) give alpha without re-reading y.
-// part[blk] = (q . H q) and part[gridDim + blk] = (q . q_prev), both in true units.
+// integer load), written as binary64 to Y; the exact integer dot q.y gives alpha
+// (with q.q_prev from the fixed-point copy kernel) without re-reading y.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ double i128_to_double(__int128 v) {
     const long long hi = (long long)(v >> 64);
@@ -351,54 +366,47 @@ __device__ __forceinline__ double i128_to_double(__int128 v) {
 }
 
 // per-warp partial sums of the current and previous block (blk_sweep's endf / flushf)
-__shared__ double s_wpart[2][BLK_NT / 32][2];
+__shared__ double s_wpart[2][BLK_NT / 32][1];
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
 
-// part[h] = (q . H q) and part[2^H + h] = (q . q_prev) over the rows of block h, in true
-// units; entries of blocks that do not exist stay as they are
+// part[h] = (q . H q) over the rows of block h, in true units; entries of blocks that do
+// not exist stay as they are
 template <int NC, bool IR, class Row>
 __device__ __forceinline__ void lz64_body(const BlkParams &P, const long long *__restrict__ Xc,
-                                          const long long *__restrict__ Xp, unsigned long long *__restrict__ Y,
-                                          LzScalars *S, int pc, double *__restrict__ part) {
+                                          unsigned long long *__restrict__ Y, LzScalars *S, int pc,
+                                          double *__restrict__ part) {
     if (S->done) return;
-    const int E = S->emax[pc], Ep = S->emax[pc ^ 1];
-    const int u = E - 1022 - ef::FIX_BITS, up = Ep - 1022 - ef::FIX_BITS;
-    const uint32_t nH = 1u << P.H;
-    __int128 d1 = 0, d2 = 0;
+    const int E = S->emax[pc];
+    const int u = E - 1022 - ef::FIX_BITS;
+    __int128 d1 = 0;
     ef::df d1f{0.0f, 0.0f};
     blk_sweep<int64_t, NC, true, Row>(
-        P, (const unsigned char *)Xc, GFix{}, S->sched,
-        [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt) {
+        P, (const unsigned char *)Xc, GFix{}, S->sched, [](uint32_t) { return 0; },
+        [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt, int) {
             int64_t Tc[NC], ts;
             blk_classes<NC>(P, acc, cnt, xo, Tc);
             const unsigned long long yb = blk_y_bits<NC, IR ? 1 : 0>(P, Tc, u, &ts);
             __stcs(Y + off + r, yb);
             if constexpr (IR) d1 += (__int128)xo * ts;
             else d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
-            d2 += (__int128)xo * (int64_t)__ldcs(Xp + off + r);
         },
         [&](int it) {
             // true units: q.y = g0 2^(2u) sum X Tsum (integer ratios) or the double-float
-            // sum scaled back by 2^(2(E-1023)); q.q_prev = 2^(u+up) sum X Xp
+            // sum scaled back by 2^(2(E-1023))
             const double q_y = IR ? ldexp(i128_to_double(d1) * P.g0, 2 * u)
                                   : ldexp((double)d1f.hi + (double)d1f.lo, 2 * (E - 1023));
-            const double q_qp = ldexp(i128_to_double(d2), u + up);
-            d1 = 0; d2 = 0; d1f = ef::df{0.0f, 0.0f};
-            const double a = warp_sum(q_y), b = warp_sum(q_qp);
-            if ((threadIdx.x & 31) == 0) {
-                s_wpart[it & 1][threadIdx.x >> 5][0] = a;
-                s_wpart[it & 1][threadIdx.x >> 5][1] = b;
-            }
+            d1 = 0; d1f = ef::df{0.0f, 0.0f};
+            const double a = warp_sum(q_y);
+            if ((threadIdx.x & 31) == 0) s_wpart[it & 1][threadIdx.x >> 5][0] = a;
         },
         [&](uint32_t h, int it) {
-            double a = 0.0, b = 0.0;
-            for (int w = 0; w < BLK_NT / 32; ++w) { a += s_wpart[it & 1][w][0]; b += s_wpart[it & 1][w][1]; }
+            double a = 0.0;
+            for (int w = 0; w < BLK_NT / 32; ++w) a += s_wpart[it & 1][w][0];
             part[h] = a;
-            part[nH + h] = b;
         });
 }
 
@@ -414,9 +422,10 @@ __device__ __forceinline__ void lz32_body(const BlkParams &P, const float *__res
     ef::df dot{0.0f, 0.0f};
     blk_sweep<float, NC, true, Row>(
         P, (const unsigned char *)qc, GF32{}, S->sched,
-        [&](uint32_t off, uint32_t r, float xo, const float *acc, const int *cnt) {
+        [&](uint32_t i) { return qp[i]; },
+        [&](uint32_t off, uint32_t r, float xo, const float *acc, const int *cnt, float qpr) {
             const float hv = blk_y_f32<NC>(P, acc, cnt, xo);
-            const float uu = sig * hv - gam * qp[off + r];
+            const float uu = sig * hv - gam * qpr;
             qp[off + r] = uu;
             dot = ef::df_add(dot, ef::two_prod(sig * xo, uu));
         },

@@ -2,17 +2,22 @@
 //
 // The generic block kernels (blk.cu) read every bond slot from the kernel parameters and
 // enter the runs of slots through switches.  Here the slots of a plan are written out as
-// straight-line code with their positions and masks as literals, the result is compiled
-// for sm_103a with NVRTC and loaded with cudaLibraryLoadData.  Both variants run the
-// same bodies (blk_sweep.cuh) and form the same exact integer sums, so their outputs
-// agree bit for bit; the generic kernel stays the fallback when NVRTC is not available
-// (HM_JIT=0 selects it on purpose).
+// straight-line code with their positions and masks as literals, the in-byte exchanges
+// go through delta tables (gen_row), the result is compiled for sm_103a with NVRTC and
+// loaded with cudaLibraryLoadData.  Both variants run the same bodies (blk_sweep.cuh);
+// in FP64 both form the same exact integer sums, so their outputs agree bit for bit.
+// The generic kernel stays the fallback when NVRTC is not available (HM_JIT=0 selects
+// it on purpose).  Two row policies: the slots written out (default), or per-byte delta
+// tables (HM_JIT_ROW=delta: fewer instructions and shared-memory wavefronts, faster where
+// the hop gathers hit L2, as for N = 28; slower at N = 32).  HM_JIT_CTAS=2 trades the
+// third resident CTA per SM for 64 registers a thread.
 #include <dlfcn.h>
 #include <nvrtc.h>
 
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -47,6 +52,7 @@ struct Nvrtc {
 std::mutex g_mu;
 Nvrtc g_nv;
 std::map<std::string, const void *> g_cache;   // (device, source) -> kernel handle
+std::map<const void *, int> g_pad;              // kernel handle -> pad elements after the staged rows
 std::set<std::string> g_failed;
 
 bool load_nvrtc() {
@@ -79,28 +85,38 @@ bool verbose() {
 
 void put(std::string &s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 void put(std::string &s, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
+    va_list ap, ap2;
     va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_copy(ap2, ap);
+    const int n = vsnprintf(nullptr, 0, fmt, ap);
     va_end(ap);
-    s += buf;
+    if (n > 0) {
+        std::vector<char> buf((size_t)n + 1);
+        vsnprintf(buf.data(), buf.size(), fmt, ap2);
+        s.append(buf.data(), (size_t)n);
+    }
+    va_end(ap2);
 }
 
-// The row policy of a plan: the slots of RowGeneric (blk_sweep.cuh) with every count,
-// shift and mask a literal, in RowGeneric's order (each run from its last slot down, so
-// FP32 sums round the same way).  Failed exchanges read x too (the staged rows are padded, so
-// the address stays inside the buffer) and add under the test's predicate.
-std::string gen_row(const BlkParams &P) {
+// The row policy of a plan written out slot by slot: RowGeneric (blk_sweep.cuh) with
+// every count, shift and mask a literal, in RowGeneric's order (each run from its last
+// slot down, so FP32 sums round the same way).
+std::string gen_row_slots(const BlkParams &P) {
     std::string s;
     s += "struct RowJit {\n"
+         "static constexpr int kPad = hm::BLK_XPAD;\n"
+         "static constexpr bool kRelUS = false;\n"
+         "template <class Sv>\n"
+         "static __device__ __forceinline__ void stage(const hm::BlkParams &P) { hm::RowGeneric<1>::stage<Sv>(P); }\n"
+         "template <class Sv>\n"
+         "static __device__ __forceinline__ void block(const hm::BlkParams &, uint32_t) {}\n"
          "template <class Sv, class G>\n"
          "static __device__ __forceinline__ void sums(const hm::BlkParams &P, const hm::BlkMeta &B,\n"
-         "        const unsigned char *Xsb, uint32_t l, uint32_t r, const G &gx, Sv *acc, int *cnt) {\n"
+         "        const unsigned char *Xsb, uint32_t l, uint32_t r, const G &gx, Sv xo, Sv *acc, int *cnt) {\n"
          "    const uint32_t l4 = l << 2, lh4 = (l >> 8) << 2, lh4k = lh4 | B.kofs;\n"
          "    const uint32_t R0own = hm::r0s_at(l4 & 0x3FCu), R1own = hm::us_at(lh4k);\n"
          "    const uint32_t rb = r * (uint32_t)sizeof(Sv);\n"
-         "    (void)R0own; (void)R1own; (void)lh4; (void)gx;\n";
+         "    (void)R0own; (void)R1own; (void)lh4; (void)gx; (void)xo;\n";
     // the distances that occur among the low bonds and count groups
     std::set<int> ds;
     for (int c = 0; c < P.nc; ++c) {
@@ -143,6 +159,141 @@ std::string gen_row(const BlkParams &P) {
         put(s, "        acc[%d] = a;\n        cnt[%d] = m + (e1 - e0);\n    }\n", c, c);
     }
     s += "}\n};\n";
+    return s;
+}
+
+// The row policy of a plan (interface in blk_sweep.cuh), every count, shift and mask a
+// literal.  The low bonds with both ends in one byte of the low word take their target
+// from per-byte delta tables: the target row of slot s is r + D[b][s], with D = 0 when
+// the two spins are parallel (no exchange).  Such a slot then adds the row's own x, and
+// every low or cross slot is reported in cnt whether its exchange is allowed or not:
+// T_c = 2 acc_c + (ntot_c - 2 cnt_c) x_r turns a reported slot with target r into +x_r,
+// the diagonal term of a parallel bond, and one with another target into
+// 2 x_target - x_r, as the two terms of Eq. (E-2-1) require.  Bonds across the bytes
+// and cross bonds take the own x when not allowed; high bonds are reported only when
+// allowed.
+//   D0[c][b0][s]: byte offset R0[b0 ^ pat] - R0[b0] (fixed per kernel), 16 bits
+//   D1[c][b1][s]: byte offset U[k][b1 ^ pat] - U[k][b1] (rebuilt per block), 32 bits
+//   US3[j][b1]: U[k - 1 + j][b1] (per block), for the bonds across bytes and the cross bonds
+std::string gen_row(const BlkParams &P, bool &ok) {
+    ok = true;
+    std::string s;
+    const int NC = P.nc;
+    int w0 = 1, w1 = 1;
+    for (int c = 0; c < NC; ++c) {
+        w0 = std::max(w0, (P.ln[c][0] + 7) / 8);
+        w1 = std::max(w1, (P.ln[c][1] + 3) / 4);
+    }
+    if (w0 > 2 || w1 > 4) { ok = false; return s; }
+    put(s, "__shared__ uint4 s_D0[%d];\n__shared__ int4 s_D1[%d];\n__shared__ uint32_t s_US3[%d];\n",
+        NC * 256 * w0, NC * P.nb1 * w1, 3 * P.nb1);
+    s += "__device__ __forceinline__ uint32_t us3_at(uint32_t o) {\n"
+         "    return *(const uint32_t *)((const unsigned char *)s_US3 + o);\n}\n";
+    s += "struct RowJit {\nstatic constexpr int kPad = 0;\nstatic constexpr bool kRelUS = true;\n";
+    // stage: D0
+    s += "template <class Sv>\nstatic __device__ __forceinline__ void stage(const hm::BlkParams &P) {\n"
+         "    const uint8_t *R0g = (const uint8_t *)P.tab + P.off_R0;\n"
+         "    const int es = (int)sizeof(Sv);\n"
+         "    for (int b0 = threadIdx.x; b0 < 256; b0 += hm::BLK_NT) {\n"
+         "        const int r0 = R0g[b0];\n";
+    for (int c = 0; c < NC; ++c) {
+        put(s, "        {   // class %d\n            int d[%d] = {0};\n", c, 8 * w0);
+        for (int k = 0; k < P.ln[c][0]; ++k) {
+            const unsigned pat = ((unsigned)P.lxa[c][0][k] >> 2) & 255u;
+            put(s, "            d[%d] = __popc(b0 & 0x%xu) == 1 ? (R0g[b0 ^ 0x%x] - r0) * es : 0;\n", k, pat, pat);
+        }
+        for (int w = 0; w < w0; ++w)
+            put(s, "            s_D0[(%d * 256 + b0) * %d + %d] = make_uint4("
+                   "(uint32_t)(d[%d] & 0xFFFF) | ((uint32_t)d[%d] << 16), (uint32_t)(d[%d] & 0xFFFF) | ((uint32_t)d[%d] << 16), "
+                   "(uint32_t)(d[%d] & 0xFFFF) | ((uint32_t)d[%d] << 16), (uint32_t)(d[%d] & 0xFFFF) | ((uint32_t)d[%d] << 16));\n",
+                c, w0, w, 8 * w, 8 * w + 1, 8 * w + 2, 8 * w + 3, 8 * w + 4, 8 * w + 5, 8 * w + 6, 8 * w + 7);
+        s += "        }\n";
+    }
+    s += "    }\n}\n";
+    // block: US3 and D1
+    put(s, "template <class Sv>\nstatic __device__ __forceinline__ void block(const hm::BlkParams &P, uint32_t k) {\n"
+           "    const uint16_t *Ug = (const uint16_t *)((const unsigned char *)P.tab + P.off_U);\n"
+           "    const int es = (int)sizeof(Sv);\n"
+           "    for (int i = threadIdx.x; i < %d; i += hm::BLK_NT) {\n"
+           "        const int j = i / %d, b1 = i %% %d, kk = (int)k - 1 + j;\n"
+           "        s_US3[i] = (kk >= 0 && kk <= %d) ? (uint32_t)Ug[kk * %d + b1] * (uint32_t)es : 0u;\n"
+           "    }\n"
+           "    for (int b1 = threadIdx.x; b1 < %d; b1 += hm::BLK_NT) {\n"
+           "        const uint16_t *Uk = Ug + k * %d;\n"
+           "        const int u0 = Uk[b1];\n",
+        3 * P.nb1, P.nb1, P.nb1, P.K, P.nb1, P.nb1, P.nb1);
+    for (int c = 0; c < NC; ++c) {
+        put(s, "        {   // class %d\n            int d[%d] = {0};\n", c, 4 * w1);
+        for (int k = 0; k < P.ln[c][1]; ++k) {
+            const unsigned pat = ((unsigned)P.lxb[c][1][k] >> 2);
+            put(s, "            d[%d] = __popc(b1 & 0x%xu) == 1 ? (Uk[b1 ^ 0x%x] - u0) * es : 0;\n", k, pat, pat);
+        }
+        for (int w = 0; w < w1; ++w)
+            put(s, "            s_D1[(%d * %d + b1) * %d + %d] = make_int4(d[%d], d[%d], d[%d], d[%d]);\n", c, P.nb1, w1, w,
+                4 * w, 4 * w + 1, 4 * w + 2, 4 * w + 3);
+        s += "        }\n";
+    }
+    s += "    }\n}\n";
+    // sums
+    s += "template <class Sv, class G>\n"
+         "static __device__ __forceinline__ void sums(const hm::BlkParams &P, const hm::BlkMeta &B,\n"
+         "        const unsigned char *Xsb, uint32_t l, uint32_t r, const G &gx, Sv xo, Sv *acc, int *cnt) {\n"
+         "    const uint32_t b0 = l & 255u, b1 = l >> 8, rb = r * (uint32_t)sizeof(Sv);\n"
+         "    const uint32_t l4 = l << 2, lh4 = b1 << 2;\n"
+         "    (void)b0; (void)b1; (void)l4; (void)lh4; (void)xo; (void)gx;\n";
+    std::set<int> ds;
+    bool need_r0own = false;
+    for (int c = 0; c < NC; ++c) {
+        for (int k = 0; k < P.ln[c][2]; ++k) ds.insert(P.ld[c][2][k]);
+        if (P.xn[c][1] > 0) need_r0own = true;
+    }
+    for (int d : ds) put(s, "    const uint32_t z%d = l ^ (l >> %d);\n", d, d);
+    if (need_r0own) s += "    const uint32_t R0own = hm::r0s_at(l4 & 0x3FCu);\n";
+    s += "#define XS(o) (*(const Sv *)(Xsb + (o)))\n";
+    for (int c = 0; c < NC; ++c) {
+        put(s, "    {   // class %d\n        Sv a = Sv(0);\n", c);
+        for (int w = 0; w < w0 && w * 8 < P.ln[c][0]; ++w) {
+            put(s, "        { const uint4 q = s_D0[(%d * 256 + b0) * %d + %d];\n", c, w0, w);
+            const char *fld[4] = {"x", "y", "z", "w"};
+            for (int k = 8 * w; k < std::min(P.ln[c][0], 8 * w + 8); ++k) {
+                const int j = k - 8 * w;
+                if (j % 2 == 0) put(s, "          a += XS(rb + (int)(short)(q.%s & 0xFFFFu));\n", fld[j / 2]);
+                else put(s, "          a += XS(rb + ((int)q.%s >> 16));\n", fld[j / 2]);
+            }
+            s += "        }\n";
+        }
+        for (int w = 0; w < w1 && w * 4 < P.ln[c][1]; ++w) {
+            put(s, "        { const int4 q = s_D1[(%d * %d + b1) * %d + %d];\n", c, P.nb1, w1, w);
+            const char *fld[4] = {"x", "y", "z", "w"};
+            for (int k = 4 * w; k < std::min(P.ln[c][1], 4 * w + 4); ++k)
+                put(s, "          a += XS(rb + q.%s);\n", fld[k - 4 * w]);
+            s += "        }\n";
+        }
+        for (int k = 0; k < P.ln[c][2]; ++k)
+            put(s, "        { const uint32_t t = z%d & 0x%xu; const uint32_t v = us3_at(%uu | (lh4 ^ 0x%xu)) + "
+                   "hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu); a += XS(t ? v : rb); }\n",
+                P.ld[c][2][k], P.lvm[c][2][k], 1u << P.kshift, (unsigned)P.lxb[c][2][k], (unsigned)P.lxa[c][2][k]);
+        for (int k = 0; k < P.xn[c][0]; ++k)
+            put(s, "        { const hm::XSlot x_ = B.xs[%d]; const uint32_t t = (l ^ x_.wm) & x_.vm; "
+                   "const uint32_t v = us3_at(x_.kofs2 | lh4) + hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu); "
+                   "a += t ? gx(x_.base + v) : xo; }\n",
+                (2 * c) * HM_BLK_SX + k, (unsigned)P.xxa[c][0][k]);
+        for (int k = 0; k < P.xn[c][1]; ++k)
+            put(s, "        { const hm::XSlot x_ = B.xs[%d]; const uint32_t t = (l ^ x_.wm) & x_.vm; "
+                   "const uint32_t v = us3_at(x_.kofs2 | (lh4 ^ 0x%xu)) + R0own; a += t ? gx(x_.base + v) : xo; }\n",
+                (2 * c + 1) * HM_BLK_SX + k, (unsigned)P.xxa[c][1][k]);
+        put(s, "        const int e0 = B.hs[%d], e1 = B.hs[%d];\n", c, c + 1);
+        s += "        int e = e0;\n"
+             "        for (; e + 4 <= e1; e += 4) {\n"
+             "            const Sv v0 = gx(B.hb[e] + rb), v1 = gx(B.hb[e + 1] + rb);\n"
+             "            const Sv v2_ = gx(B.hb[e + 2] + rb), v3 = gx(B.hb[e + 3] + rb);\n"
+             "            a += (v0 + v1) + (v2_ + v3);\n"
+             "        }\n"
+             "        for (; e < e1; ++e) a += gx(B.hb[e] + rb);\n";
+        put(s, "        acc[%d] = a;\n        cnt[%d] = %d + (e1 - e0);\n    }\n", c, c,
+            P.ln[c][0] + P.ln[c][1] + P.ln[c][2] + P.xn[c][0] + P.xn[c][1]);
+    }
+    s += "#undef XS\n}\n};\n";
     return s;
 }
 
@@ -191,23 +342,31 @@ int jit_lz_kernel(const BlkParams &P, int dtype, const void **kern) {
     if (!P.rows_ok) return 1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
-    std::string src = "#include \"blk_sweep.cuh\"\n" + gen_row(P);
+    bool gen_ok = true;
+    const char *rowk = getenv("HM_JIT_ROW");
+    const bool delta = rowk && strcmp(rowk, "delta") == 0;
+    std::string src = "#include \"blk_sweep.cuh\"\n" + (delta ? gen_row(P, gen_ok) : gen_row_slots(P));
+    if (!gen_ok) return 1;
     const bool f64 = dtype == HM_F64;
     const int nc = P.nc == 1 ? 1 : (P.nc == 2 ? 2 : 4);
     const char *name = f64 ? "k_blk_lz64_jit" : "k_blk_lz32_jit";
+    // resident CTAs per SM the register budget is cut for (3: 40 registers a thread, 2: 64);
+    // HM_JIT_CTAS overrides the default
+    int ctas = 3;
+    if (const char *e = getenv("HM_JIT_CTAS")) ctas = atoi(e) == 2 ? 2 : 3;
     if (f64)
         put(src,
-            "extern \"C\" __global__ void __launch_bounds__(512, 3) k_blk_lz64_jit(hm::BlkParams P,\n"
-            "        const long long *__restrict__ Xc, const long long *__restrict__ Xp,\n"
-            "        unsigned long long *__restrict__ Y, hm::LzScalars *S, int pc, double *__restrict__ part) {\n"
-            "    hm::lz64_body<%d, %s, RowJit>(P, Xc, Xp, Y, S, pc, part);\n}\n",
-            nc, P.iratio ? "true" : "false");
+            "extern \"C\" __global__ void __launch_bounds__(512, %d) k_blk_lz64_jit(hm::BlkParams P,\n"
+            "        const long long *__restrict__ Xc, unsigned long long *__restrict__ Y, hm::LzScalars *S, int pc,\n"
+            "        double *__restrict__ part) {\n"
+            "    hm::lz64_body<%d, %s, RowJit>(P, Xc, Y, S, pc, part);\n}\n",
+            ctas, nc, P.iratio ? "true" : "false");
     else
         put(src,
-            "extern \"C\" __global__ void __launch_bounds__(512, 3) k_blk_lz32_jit(hm::BlkParams P,\n"
+            "extern \"C\" __global__ void __launch_bounds__(512, %d) k_blk_lz32_jit(hm::BlkParams P,\n"
             "        const float *__restrict__ qc, float *__restrict__ qp, hm::LzScalars *S, double *__restrict__ part) {\n"
             "    hm::lz32_body<%d, RowJit>(P, qc, qp, S, part);\n}\n",
-            nc);
+            ctas, nc);
     const std::string key = std::to_string(dev) + "\n" + src;
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
@@ -220,8 +379,16 @@ int jit_lz_kernel(const BlkParams &P, int dtype, const void **kern) {
     const void *k = nullptr;
     if (compile(src, name, dev, &k) != 0) { g_failed.insert(key); return 1; }
     g_cache.emplace(key, k);
+    g_pad[k] = delta ? 0 : BLK_XPAD;
     *kern = k;
     return 0;
+}
+
+int jit_pad(const void *kern) {
+    if (!kern) return BLK_XPAD;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_pad.find(kern);
+    return it == g_pad.end() ? BLK_XPAD : it->second;
 }
 
 }  // namespace hm

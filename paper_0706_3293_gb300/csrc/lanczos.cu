@@ -14,8 +14,8 @@ namespace hm {
 
 int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int *blocks);
 int blk_lz_jit(const BlkParams &P, int dtype, const void **kern, int *blocks);
-int blk_lz64_launch(const BlkParams &P, const long long *Xc, const long long *Xp, unsigned long long *Y,
-                    LzScalars *S, int pc, double *part, int blocks, cudaStream_t st, const void *jit);
+int blk_lz64_launch(const BlkParams &P, const long long *Xc, unsigned long long *Y, LzScalars *S, int pc,
+                    double *part, int blocks, cudaStream_t st, const void *jit);
 int blk_lz32_launch(const BlkParams &P, const float *qc, float *qp, LzScalars *S, double *part, int blocks,
                     cudaStream_t st, const void *jit);
 
@@ -35,6 +35,7 @@ constexpr int NT = 256;
 struct LzLayout {
     size_t buf[2], part, sc, alpha, beta, ritz, psi, coef, res, gout, tri, bpart, total;
     size_t ybuf, xs[2];     // FP64 block path: y = H q and the fixed-point copies of q
+    size_t qqp;             // FP64 block path: partials of q_cur . q_prev (k_fix)
     size_t hpart;           // s = 1/2 block path: per-block partial sums, 2 x 2^H doubles
     bool shadow;
 };
@@ -57,6 +58,7 @@ static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad
         L.ybuf = o; o += al256(dim * 8);
         L.xs[0] = o; o += al256(dim * 8);
         L.xs[1] = o; o += al256(dim * 8);
+        L.qqp = o; o += al256(npart * sizeof(double));
     }
     // per-block partials of the s = 1/2 block path (split K = min(15, N - 2): H <= 17)
     if (b->view.S2 == 1 && b->view.N >= 10 && b->view.N <= 32 && !b->view.idx64) {
@@ -94,6 +96,7 @@ struct hm_lanczos {
     hm::LzScalars *sc;
     double *alpha, *beta, *part, *psi, *coef;
     double *hpart;          // per-block partials of the block path (entries of absent blocks stay 0)
+    double *qqp;            // partials of q_cur . q_prev (FP64 block path)
 };
 
 namespace hm {
@@ -232,22 +235,37 @@ k_lz_update(const T *__restrict__ qc, T *__restrict__ qp, uint64_t n, LzScalars 
     }
 }
 
-// fixed-point copy of q (FP64 block path), unit from the vector's largest exponent
+// fixed-point copy X of the new vector w (FP64 block path), unit from its largest
+// exponent, and the exact dot X . Xo with the fixed-point copy Xo of the vector before
+// it: qqp[blk] = (q_new . q_cur) in true units, for the next alpha
 __global__ void __launch_bounds__(NT)
-k_fix(const unsigned long long *__restrict__ w, long long *__restrict__ X, uint64_t n, const LzScalars *S, int slot) {
+k_fix(const unsigned long long *__restrict__ w, long long *__restrict__ X, const long long *__restrict__ Xo,
+      uint64_t n, const LzScalars *S, int slot, double *__restrict__ qqp) {
     if (S->done) return;
-    const int E = S->emax[slot];
-    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT)
-        X[r] = (long long)ef::fix_from_bits(w[r], E);
+    __shared__ double red[NT / 32];
+    const int E = S->emax[slot], Eo = S->emax[slot ^ 1];
+    __int128 d = 0;
+    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
+        const long long x = (long long)ef::fix_from_bits(__ldcs(w + r), E);
+        __stcs(X + r, x);
+        d += (__int128)x * __ldcs(Xo + r);
+    }
+    const long long hi = (long long)(d >> 64);
+    const double dd = (double)hi * 18446744073709551616.0 + (double)(unsigned long long)d;
+    const double t = block_sum<NT>(ldexp(dd, (E - 1022 - ef::FIX_BITS) + (Eo - 1022 - ef::FIX_BITS)), red);
+    if (threadIdx.x == 0) qqp[blockIdx.x] = t;
 }
 
-// alpha_j = sigma^2 (q.Hq) - sigma gamma (q.q_prev) from the two partial sums of the
-// FP64 block product (the Paige form v.(Hv - beta v_prev))
-__global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int nblk, double *alpha, int pprev) {
+// alpha_j = sigma^2 (q.Hq) - sigma gamma (q.q_prev): q.Hq from the per-block partials of
+// the FP64 block product, q.q_prev from those of the fixed-point copy (k_fix) of q (the
+// Paige form v.(Hv - beta v_prev))
+__global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int nblk, const double *__restrict__ qqp,
+                            int nq, double *alpha, int pprev) {
     if (S->done) return;
     __shared__ double red[NT / 32];
     double s1 = 0.0, s2 = 0.0;
-    for (int k = threadIdx.x; k < nblk; k += NT) { s1 += part[k]; s2 += part[nblk + k]; }
+    for (int k = threadIdx.x; k < nblk; k += NT) s1 += part[k];
+    for (int k = threadIdx.x; k < nq; k += NT) s2 += qqp[k];
     s1 = block_sum<NT>(s1, red);
     __syncthreads();
     s2 = block_sum<NT>(s2, red);
@@ -471,8 +489,8 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
     unsigned long long *Y = R->L.shadow ? (unsigned long long *)(R->work + R->L.ybuf) : nullptr;
     if (phase == 0) {
         if (b64) {
-            HM_TRY(blk_lz64_launch(R->blk, xs[parity], xs[pprev], Y, R->sc, parity, R->hpart, R->blk_blocks, st, R->jit));
-            k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->alpha, pprev);
+            HM_TRY(blk_lz64_launch(R->blk, xs[parity], Y, R->sc, parity, R->hpart, R->blk_blocks, st, R->jit));
+            k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->qqp, nblk, R->alpha, pprev);
         } else if (R->use_blk) {
             HM_TRY(blk_lz32_launch(R->blk, (const float *)qc, (float *)qp, R->sc, R->hpart, R->blk_blocks, st, R->jit));
             k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->alpha, pprev);
@@ -485,7 +503,7 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
         k_lz_update_y<<<nblk, NT, 0, st>>>(Y, (const unsigned long long *)qc, (unsigned long long *)qp, sv.dim,
                                            R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
         k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
-        k_fix<<<nblk, NT, 0, st>>>((const unsigned long long *)qp, xs[pprev], sv.dim, R->sc, pprev);
+        k_fix<<<nblk, NT, 0, st>>>((const unsigned long long *)qp, xs[pprev], xs[parity], sv.dim, R->sc, pprev, R->qqp);
     } else {
         k_lz_update<T><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
         k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
@@ -543,8 +561,9 @@ static int enqueue_start(hm_lanczos *R, const void *v0, uint64_t seed, cudaStrea
     else k_sumsq<float><<<nblk, NT, 0, st>>>((const float *)b0, sv.dim, R->part, nullptr);
     k_lz_start<<<1, NT, 0, st>>>(R->sc, R->part, nblk);
     if (R->use_blk && R->dtype == HM_F64) {
-        k_fix<<<nblk, NT, 0, st>>>((const unsigned long long *)b0, (long long *)(R->work + R->L.xs[0]), sv.dim, R->sc, 0);
         HM_CUDA(cudaMemsetAsync(R->work + R->L.xs[1], 0, sv.dim * 8, st));
+        k_fix<<<nblk, NT, 0, st>>>((const unsigned long long *)b0, (long long *)(R->work + R->L.xs[0]),
+                                   (const long long *)(R->work + R->L.xs[1]), sv.dim, R->sc, 0, R->qqp);
     }
     HM_CUDA(cudaGetLastError());
     R->host_j = 0;
@@ -589,6 +608,7 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
     R->beta = (double *)(R->work + R->L.beta);
     R->part = (double *)(R->work + R->L.part);
     R->hpart = R->L.hpart ? (double *)(R->work + R->L.hpart) : nullptr;
+    R->qqp = R->L.shadow ? (double *)(R->work + R->L.qqp) : nullptr;
     R->psi = nullptr;
     R->coef = grad ? (double *)(R->work + R->L.coef) : nullptr;
     *out = R;

@@ -401,11 +401,15 @@ def test_count_nnz_full_size_closed_form(hm):
     assert hm.count_nnz(b, hm.bonds_of(inst)) == math.comb(32, 16) + 2 * 64 * math.comb(30, 15)
 
 
-@pytest.mark.parametrize("case", ["j1j2_n20_f64", "three_class_n18_f64", "j1j2_n20_f32"])
-def test_block_product_specialised_equals_generic(hm, case, monkeypatch):
-    """The block product compiled for the bond list at run time (NVRTC) and the generic
-    block kernel form the same exact integer sums (FP64) or the same float operations
-    (FP32), so 60 Lanczos steps agree bit for bit."""
+@pytest.mark.parametrize("case,row", [("j1j2_n20_f64", "slots"), ("three_class_n18_f64", "slots"),
+                                      ("j1j2_n20_f32", "slots"), ("j1j2_n20_f64", "delta"),
+                                      ("three_class_n18_f64", "delta"), ("j1j2_n20_f32", "delta")])
+def test_block_product_specialised_equals_generic(hm, case, row, monkeypatch):
+    """The block product compiled for the bond list at run time (NVRTC; both row policies:
+    slots written out, or per-byte delta tables) and the generic block kernel form the same
+    exact integer sums in FP64, so 60 Lanczos steps agree bit for bit.  In FP32 the sums
+    round in another order (the delta policy adds x_r for parallel bonds and takes it back
+    in the diagonal term): the recurrences agree to FP32 accuracy."""
     if case == "three_class_n18_f64":
         n, J = 18, [-1.0 if i % 3 == 0 else (0.5 if i % 3 == 1 else -0.25) for i in range(18)]
         u = list(range(18)) + [0, 3, 2]
@@ -418,6 +422,7 @@ def test_block_product_specialised_equals_generic(hm, case, monkeypatch):
         bonds = hm.bonds_of(W.small_ring(n, -1.0, -0.3))
         two_m, dt = 0, (torch.float32 if case.endswith("f32") else torch.float64)
     b = hm.Basis(n, 1, two_m)
+    monkeypatch.setenv("HM_JIT_ROW", row)
     runs = {}
     for mode in ("1", "0"):
         monkeypatch.setenv("HM_JIT", mode)
@@ -429,4 +434,11 @@ def test_block_product_specialised_equals_generic(hm, case, monkeypatch):
     assert runs["1"][0].endswith("_jit"), runs["1"][0]
     assert runs["0"][0].startswith("k_blk_lz") and not runs["0"][0].endswith("_jit")
     (a1, b1, _), (a0, b0, _) = runs["1"][1], runs["0"][1]
-    assert np.array_equal(a1, a0) and np.array_equal(b1, b0)
+    if dt == torch.float64:
+        assert np.array_equal(a1, a0) and np.array_equal(b1, b0)
+    else:
+        np.testing.assert_allclose(a1[:10], a0[:10], rtol=0, atol=2e-5)
+        np.testing.assert_allclose(b1[:10], b0[:10], rtol=0, atol=2e-5)
+        e1 = oracle.tridiag_lowest(a1, b1, 1)[0]
+        e0 = oracle.tridiag_lowest(a0, b0, 1)[0]
+        assert abs(e1 - e0) <= 1e-5 * abs(e0)
