@@ -119,14 +119,15 @@ struct GF32 {
 // A policy also says how many pad elements follow the staged rows (kPad), whether the
 // cross slots index rows k-1, k, k+1 of a per-block copy of US (kRelUS) or US itself,
 // and has two hooks: stage<Sv>(P) at kernel start (all threads, before the first
-// barrier; s_R0S is being written in the same phase and may not be read) and
+// barrier, with the dynamic shared base; s_R0S is being written in the same phase and
+// may not be read) and
 // block<Sv>(P, k) once per block between the block setup and the rows (all threads).
 template <int NC>
 struct RowGeneric {
 static constexpr int kPad = BLK_XPAD;
 static constexpr bool kRelUS = false;
 template <class Sv>
-static __device__ __forceinline__ void stage(const BlkParams &P) {
+static __device__ __forceinline__ void stage(const BlkParams &P, unsigned char *) {
     const uint16_t *Ug = (const uint16_t *)((const unsigned char *)P.tab + P.off_U);
     const int nU = (P.K + 1) * P.nb1;
     for (int i = threadIdx.x; i < nU; i += BLK_NT) s_US[i] = (uint32_t)Ug[i] * (uint32_t)sizeof(Sv);
@@ -192,7 +193,7 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
     {
         const uint8_t *R0g = (const uint8_t *)P.tab + P.off_R0;
         for (int i = tid; i < 256; i += BLK_NT) s_R0S[i] = (uint32_t)R0g[i] * (uint32_t)sizeof(Sv);
-        Row::template stage<Sv>(P);
+        Row::template stage<Sv>(P, smem);
     }
     BlkTabs tb;
     tb.U = nullptr; tb.R0 = nullptr; tb.C = Cg;

@@ -248,6 +248,29 @@ EF_HD uint64_t bits_from_int(int64_t T, int k) {
     return sign | ((uint64_t)be << 52) | (mant & 0xFFFFFFFFFFFFFull);
 }
 
+// double-float (true value (hi + lo) 2^scale) -> fixed point with unit
+// 2^(E - 1022 - FIX_BITS): each float is its 24-bit significand shifted into place with
+// 8 guard bits (bits of lo below them dropped), the sum rounded half up, so the result
+// is within 1/2 + 2^-8 units of the value.  With |value| < 2^(E - 1022) + one unit the
+// result stays within 2^FIX_BITS + 1.
+EF_HD int64_t fix_from_df(df v, int E, int scale) {
+    constexpr int G = 8;
+    const int u = E - 1022 - FIX_BITS - scale;            // unit exponent relative to v
+    int64_t s = 0;
+    const float f2[2] = {v.hi, v.lo};
+    for (int i = 0; i < 2; ++i) {
+        const uint32_t b = f2u(f2[i]);
+        const int ef = (int)((b >> 23) & 0xFF);
+        if (ef == 0) continue;                             // zero (or subnormal: far below the unit)
+        const int64_t M = (int64_t)((b & 0x7FFFFFu) | 0x800000u);
+        const int sh = ef - 150 - u + G;                   // f = M 2^(ef - 150); in units 2^(u - G)
+        int64_t t = sh >= 0 ? (sh > 38 ? (M << 38) : (M << sh)) : (sh < -62 ? 0 : (M >> -sh));
+        if (b & 0x80000000u) t = -t;
+        s += t;
+    }
+    return (s + (1ll << (G - 1))) >> G;                   // arithmetic shift: floor(x + 1/2)
+}
+
 // fixed point (unit 2^(E - 1022 - FIX_BITS)) times 2^extra -> double-float, scaled by
 // 2^-scale.  Exact splitting into 21-bit pieces, then two TwoSums.
 EF_HD df df_from_fix(int64_t T, int E, int extra, int scale) {

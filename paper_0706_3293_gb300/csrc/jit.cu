@@ -100,14 +100,19 @@ void put(std::string &s, const char *fmt, ...) {
 
 // The row policy of a plan written out slot by slot: RowGeneric (blk_sweep.cuh) with
 // every count, shift and mask a literal, in RowGeneric's order (each run from its last
-// slot down, so FP32 sums round the same way).
+// slot down, so FP32 sums round the same way).  A failed exchange reads byte-0 table
+// entry 0 and a zero element past the staged rows instead of its own lookups: all such
+// lanes hit the same words (broadcasts), and the add needs no select.
 std::string gen_row_slots(const BlkParams &P) {
     std::string s;
     s += "struct RowJit {\n"
          "static constexpr int kPad = hm::BLK_XPAD;\n"
          "static constexpr bool kRelUS = false;\n"
          "template <class Sv>\n"
-         "static __device__ __forceinline__ void stage(const hm::BlkParams &P) { hm::RowGeneric<1>::stage<Sv>(P); }\n"
+         "static __device__ __forceinline__ void stage(const hm::BlkParams &P, unsigned char *dyn) {\n"
+         "    hm::RowGeneric<1>::stage<Sv>(P, dyn);\n"
+         "    if (threadIdx.x == 0) *(Sv *)(dyn + (P.max_block + hm::BLK_XPAD - 1) * sizeof(Sv)) = Sv(0);\n"
+         "}\n"
          "template <class Sv>\n"
          "static __device__ __forceinline__ void block(const hm::BlkParams &, uint32_t) {}\n"
          "template <class Sv, class G>\n"
@@ -116,7 +121,8 @@ std::string gen_row_slots(const BlkParams &P) {
          "    const uint32_t l4 = l << 2, lh4 = (l >> 8) << 2, lh4k = lh4 | B.kofs;\n"
          "    const uint32_t R0own = hm::r0s_at(l4 & 0x3FCu), R1own = hm::us_at(lh4k);\n"
          "    const uint32_t rb = r * (uint32_t)sizeof(Sv);\n"
-         "    (void)R0own; (void)R1own; (void)lh4; (void)gx; (void)xo;\n";
+         "    const uint32_t zo = (uint32_t)((P.max_block + hm::BLK_XPAD - 1) * sizeof(Sv));   // zero slot\n"
+         "    (void)R0own; (void)R1own; (void)lh4; (void)gx; (void)xo; (void)zo;\n";
     // the distances that occur among the low bonds and count groups
     std::set<int> ds;
     for (int c = 0; c < P.nc; ++c) {
@@ -128,17 +134,17 @@ std::string gen_row_slots(const BlkParams &P) {
     for (int c = 0; c < P.nc; ++c) {
         put(s, "    {   // class %d\n        Sv a = Sv(0);\n        int m = 0;\n", c);
         for (int k = P.ln[c][0] - 1; k >= 0; --k)
-            put(s, "        { const Sv v = *(const Sv *)(Xsb + R1own + hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu)); "
-                   "if (z%d & 0x%xu) a += v; }\n",
-                (unsigned)P.lxa[c][0][k], P.ld[c][0][k], P.lvm[c][0][k]);
+            put(s, "        { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = R1own + hm::r0s_at(t ? (l4 ^ 0x%xu) & 0x3FCu : 0u); "
+                   "a += *(const Sv *)(Xsb + (t ? o : zo)); }\n",
+                P.ld[c][0][k], P.lvm[c][0][k], (unsigned)P.lxa[c][0][k]);
         for (int k = P.ln[c][1] - 1; k >= 0; --k)
-            put(s, "        { const Sv v = *(const Sv *)(Xsb + R0own + hm::us_at(lh4k ^ 0x%xu)); "
-                   "if (z%d & 0x%xu) a += v; }\n",
-                (unsigned)P.lxb[c][1][k], P.ld[c][1][k], P.lvm[c][1][k]);
+            put(s, "        { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = R0own + hm::us_at(lh4k ^ 0x%xu); "
+                   "a += *(const Sv *)(Xsb + (t ? o : zo)); }\n",
+                P.ld[c][1][k], P.lvm[c][1][k], (unsigned)P.lxb[c][1][k]);
         for (int k = P.ln[c][2] - 1; k >= 0; --k)
-            put(s, "        { const Sv v = *(const Sv *)(Xsb + hm::us_at(lh4k ^ 0x%xu) + "
-                   "hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu)); if (z%d & 0x%xu) a += v; }\n",
-                (unsigned)P.lxb[c][2][k], (unsigned)P.lxa[c][2][k], P.ld[c][2][k], P.lvm[c][2][k]);
+            put(s, "        { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = hm::us_at(lh4k ^ 0x%xu) + "
+                   "hm::r0s_at(t ? (l4 ^ 0x%xu) & 0x3FCu : 0u); a += *(const Sv *)(Xsb + (t ? o : zo)); }\n",
+                P.ld[c][2][k], P.lvm[c][2][k], (unsigned)P.lxb[c][2][k], (unsigned)P.lxa[c][2][k]);
         for (int g = P.lgn[c] - 1; g >= 0; --g) put(s, "        m += __popc(z%d & 0x%xu);\n", P.lgd[c][g], P.lgm[c][g]);
         for (int k = P.xn[c][0] - 1; k >= 0; --k)
             put(s, "        { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at(lh4 | x_.kofs2) + "
@@ -191,7 +197,7 @@ std::string gen_row(const BlkParams &P, bool &ok) {
          "    return *(const uint32_t *)((const unsigned char *)s_US3 + o);\n}\n";
     s += "struct RowJit {\nstatic constexpr int kPad = 0;\nstatic constexpr bool kRelUS = true;\n";
     // stage: D0
-    s += "template <class Sv>\nstatic __device__ __forceinline__ void stage(const hm::BlkParams &P) {\n"
+    s += "template <class Sv>\nstatic __device__ __forceinline__ void stage(const hm::BlkParams &P, unsigned char *) {\n"
          "    const uint8_t *R0g = (const uint8_t *)P.tab + P.off_R0;\n"
          "    const int es = (int)sizeof(Sv);\n"
          "    for (int b0 = threadIdx.x; b0 < 256; b0 += hm::BLK_NT) {\n"

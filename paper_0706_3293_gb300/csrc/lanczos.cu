@@ -279,37 +279,71 @@ __global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int n
     }
 }
 
-// FP64 block path: w = sigma y - alpha sigma q - gamma q_prev over q_prev, in
-// double-float on the bit patterns; part = |w|^2; exponent of w to S->emax[pprev]
+// FP64 block path.  The Lanczos vectors are kept as double-float pairs (hi, lo floats,
+// 8 bytes): the update computes in double-float, so a pair holds all it produces and
+// needs no conversion to or from binary64.
+// w = sigma y - alpha sigma q - gamma q_prev over q_prev (y: binary64 bits of H q);
+// part = |w|^2; largest exponent of w, as a binary64 exponent field, to S->emax[pprev]
 __global__ void __launch_bounds__(NT)
-k_lz_update_y(const unsigned long long *__restrict__ Y, const unsigned long long *__restrict__ qc,
-              unsigned long long *__restrict__ qp, uint64_t n, LzScalars *S, const double *__restrict__ alpha,
-              double *__restrict__ part, double *__restrict__ psi, const double *__restrict__ coef, int pprev) {
+k_lz_update_y(const unsigned long long *__restrict__ Y, const float2 *__restrict__ qc, float2 *__restrict__ qp,
+              uint64_t n, LzScalars *S, const double *__restrict__ alpha, double *__restrict__ part,
+              double *__restrict__ psi, const double *__restrict__ coef, int pprev) {
     if (S->done) return;
     __shared__ double red[NT / 32];
     const double sg = S->sigma_cur, gm = S->beta_prev * S->sigma_prev, as = alpha[S->j] * sg;
     const double cj = psi ? coef[S->j] * sg : 0.0;
-    const int scale_q = S->emax[pprev ^ 1] - 1023, scale_p = S->emax_old - 1023;
     auto todf = [](double v) { const float h = (float)v; return ef::df{h, (float)(v - (double)h)}; };
-    const ef::df sg_d = todf(sg), as_s = todf(ldexp(as, scale_q)), gm_s = todf(ldexp(gm, scale_p));
+    const ef::df sg_d = todf(sg), as_d = todf(as), gm_d = todf(gm);
     ef::df s{0.0f, 0.0f};
-    int em = 0;
+    uint32_t eh = 0;
     for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
-        const unsigned long long qb = qc[r];
-        const ef::df t1 = ef::df_mul(sg_d, ef::df_from_bits(Y[r], 0));
-        const ef::df t2 = ef::df_mul(as_s, ef::df_from_bits(qb, scale_q));
-        const ef::df t3 = ef::df_mul(gm_s, ef::df_from_bits(qp[r], scale_p));
+        const float2 q2 = __ldcs(qc + r), p2 = qp[r];
+        const ef::df t1 = ef::df_mul(sg_d, ef::df_from_bits(__ldcs(Y + r), 0));
+        const ef::df t2 = ef::df_mul(as_d, ef::df{q2.x, q2.y});
+        const ef::df t3 = ef::df_mul(gm_d, ef::df{p2.x, p2.y});
         const ef::df w = ef::df_add(t1, ef::df_neg(ef::df_add(t2, t3)));
-        const unsigned long long wb = ef::bits_from_df(w, 0);
-        qp[r] = wb;
-        em = max(em, (int)((wb >> 52) & 0x7FF));
+        qp[r] = make_float2(w.hi, w.lo);
+        eh = max(eh, (ef::f2u(w.hi) >> 23) & 0xFFu);
         s = ef::df_add(s, ef::df_mul(w, w));
-        if (psi) psi[r] += cj * ef::u2d(qb);
+        if (psi) psi[r] += cj * ((double)q2.x + (double)q2.y);
     }
     const double tot = block_sum<NT>((double)s.hi + (double)s.lo, red);
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
-    for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_down_sync(0xffffffffu, em, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&S->emax[pprev], em);
+    for (int o = 16; o > 0; o >>= 1) eh = max(eh, __shfl_down_sync(0xffffffffu, eh, o));
+    // |hi| < 2^(eh - 126): the binary64 field eh - 127 + 1023 bounds hi, and hi + lo up
+    // to a factor 1 + 2^-24 (the fixed-point copy then stays within 2^53 + 2^29 units)
+    if ((threadIdx.x & 31) == 0 && eh) atomicMax(&S->emax[pprev], (int)eh - 127 + 1023);
+}
+
+// start vector, binary64 -> double-float pairs in place (FP64 block path; integer
+// conversion, no FP64 instruction)
+__global__ void __launch_bounds__(NT) k_to_df(unsigned long long *__restrict__ b, uint64_t n) {
+    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
+        const ef::df v = ef::df_from_bits(b[r], 0);
+        ((float2 *)b)[r] = make_float2(v.hi, v.lo);
+    }
+}
+
+// fixed-point copy X of the new vector w (double-float pairs), unit from its largest
+// exponent, and the exact dot X . Xo with the copy Xo of the vector before it:
+// qqp[blk] = (q_new . q_cur) in true units, for the next alpha
+__global__ void __launch_bounds__(NT)
+k_fixd(const float2 *__restrict__ w, long long *__restrict__ X, const long long *__restrict__ Xo, uint64_t n,
+       const LzScalars *S, int slot, double *__restrict__ qqp) {
+    if (S->done) return;
+    __shared__ double red[NT / 32];
+    const int E = S->emax[slot], Eo = S->emax[slot ^ 1];
+    __int128 d = 0;
+    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
+        const float2 v = __ldcs(w + r);
+        const long long x = (long long)ef::fix_from_df(ef::df{v.x, v.y}, E, 0);
+        __stcs(X + r, x);
+        d += (__int128)x * __ldcs(Xo + r);
+    }
+    const long long hi = (long long)(d >> 64);
+    const double dd = (double)hi * 18446744073709551616.0 + (double)(unsigned long long)d;
+    const double t = block_sum<NT>(ldexp(dd, (E - 1022 - ef::FIX_BITS) + (Eo - 1022 - ef::FIX_BITS)), red);
+    if (threadIdx.x == 0) qqp[blockIdx.x] = t;
 }
 
 __global__ void k_lz_beta(LzScalars *S, const double *__restrict__ part, int nblk, double *beta, double tol) {
@@ -500,10 +534,10 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
             k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->alpha, pprev);
         }
     } else if (b64) {
-        k_lz_update_y<<<nblk, NT, 0, st>>>(Y, (const unsigned long long *)qc, (unsigned long long *)qp, sv.dim,
-                                           R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
+        k_lz_update_y<<<nblk, NT, 0, st>>>(Y, (const float2 *)qc, (float2 *)qp, sv.dim, R->sc, R->alpha, R->part,
+                                           R->psi, R->coef, pprev);
         k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
-        k_fix<<<nblk, NT, 0, st>>>((const unsigned long long *)qp, xs[pprev], xs[parity], sv.dim, R->sc, pprev, R->qqp);
+        k_fixd<<<nblk, NT, 0, st>>>((const float2 *)qp, xs[pprev], xs[parity], sv.dim, R->sc, pprev, R->qqp);
     } else {
         k_lz_update<T><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
         k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
@@ -564,6 +598,7 @@ static int enqueue_start(hm_lanczos *R, const void *v0, uint64_t seed, cudaStrea
         HM_CUDA(cudaMemsetAsync(R->work + R->L.xs[1], 0, sv.dim * 8, st));
         k_fix<<<nblk, NT, 0, st>>>((const unsigned long long *)b0, (long long *)(R->work + R->L.xs[0]),
                                    (const long long *)(R->work + R->L.xs[1]), sv.dim, R->sc, 0, R->qqp);
+        k_to_df<<<nblk, NT, 0, st>>>((unsigned long long *)b0, sv.dim);
     }
     HM_CUDA(cudaGetLastError());
     R->host_j = 0;
