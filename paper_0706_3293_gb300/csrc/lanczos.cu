@@ -284,7 +284,7 @@ __global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int n
 // needs no conversion to or from binary64.
 // w = sigma y - alpha sigma q - gamma q_prev over q_prev (y: binary64 bits of H q);
 // part = |w|^2; largest exponent of w, as a binary64 exponent field, to S->emax[pprev]
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 2048 / NT)
 k_lz_update_y(const unsigned long long *__restrict__ Y, const float2 *__restrict__ qc, float2 *__restrict__ qp,
               uint64_t n, LzScalars *S, const double *__restrict__ alpha, double *__restrict__ part,
               double *__restrict__ psi, const double *__restrict__ coef, int pprev) {
@@ -296,9 +296,17 @@ k_lz_update_y(const unsigned long long *__restrict__ Y, const float2 *__restrict
     const ef::df sg_d = todf(sg), as_d = todf(as), gm_d = todf(gm);
     ef::df s{0.0f, 0.0f};
     uint32_t eh = 0;
-    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
-        const float2 q2 = __ldcs(qc + r), p2 = qp[r];
-        const ef::df t1 = ef::df_mul(sg_d, ef::df_from_bits(__ldcs(Y + r), 0));
+    const uint64_t stride = (uint64_t)gridDim.x * NT;
+    uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x;
+    // operands of the next row are loaded before the current row is computed
+    unsigned long long yn = 0;
+    float2 qn = make_float2(0.0f, 0.0f), pn = qn;
+    if (r < n) { yn = __ldcs(Y + r); qn = __ldcs(qc + r); pn = qp[r]; }
+    for (; r < n; r += stride) {
+        const unsigned long long yb = yn;
+        const float2 q2 = qn, p2 = pn;
+        if (r + stride < n) { yn = __ldcs(Y + r + stride); qn = __ldcs(qc + r + stride); pn = qp[r + stride]; }
+        const ef::df t1 = ef::df_mul(sg_d, ef::df_from_bits(yb, 0));
         const ef::df t2 = ef::df_mul(as_d, ef::df{q2.x, q2.y});
         const ef::df t3 = ef::df_mul(gm_d, ef::df{p2.x, p2.y});
         const ef::df w = ef::df_add(t1, ef::df_neg(ef::df_add(t2, t3)));
@@ -327,18 +335,25 @@ __global__ void __launch_bounds__(NT) k_to_df(unsigned long long *__restrict__ b
 // fixed-point copy X of the new vector w (double-float pairs), unit from its largest
 // exponent, and the exact dot X . Xo with the copy Xo of the vector before it:
 // qqp[blk] = (q_new . q_cur) in true units, for the next alpha
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 2048 / NT)
 k_fixd(const float2 *__restrict__ w, long long *__restrict__ X, const long long *__restrict__ Xo, uint64_t n,
        const LzScalars *S, int slot, double *__restrict__ qqp) {
     if (S->done) return;
     __shared__ double red[NT / 32];
     const int E = S->emax[slot], Eo = S->emax[slot ^ 1];
     __int128 d = 0;
-    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
-        const float2 v = __ldcs(w + r);
+    const uint64_t stride = (uint64_t)gridDim.x * NT;
+    uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x;
+    float2 vn = make_float2(0.0f, 0.0f);
+    long long on = 0;
+    if (r < n) { vn = __ldcs(w + r); on = __ldcs(Xo + r); }
+    for (; r < n; r += stride) {                       // next row's operands loaded first
+        const float2 v = vn;
+        const long long o = on;
+        if (r + stride < n) { vn = __ldcs(w + r + stride); on = __ldcs(Xo + r + stride); }
         const long long x = (long long)ef::fix_from_df(ef::df{v.x, v.y}, E, 0);
         __stcs(X + r, x);
-        d += (__int128)x * __ldcs(Xo + r);
+        d += (__int128)x * o;
     }
     const long long hi = (long long)(d >> 64);
     const double dd = (double)hi * 18446744073709551616.0 + (double)(unsigned long long)d;
