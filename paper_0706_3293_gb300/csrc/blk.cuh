@@ -54,10 +54,9 @@ __device__ __forceinline__ uint32_t rank_low(const BlkParams &P, const BlkTabs &
 namespace hm {
 
 // ---- per-block setup shared by the block kernels -------------------------------------------
-// Shared scratch of one block: low words, compacted high-exchange offsets per class,
-// cross-exchange targets.
+// Shared scratch of one block: compacted high-exchange offsets per class, cross-exchange
+// targets.
 struct BlkShared {
-    uint16_t *list;       // [max_block] low words in rank order
     int *hcd;             // [HM_BLK_MAXB] offsets (target row - own row) of the valid high exchanges
     int *hcs;             // [HM_BLK_MAXC + 1] class c owns hcd[hcs[c] .. hcs[c+1])
     int *tmp;             // [HM_BLK_MAXB]
@@ -70,13 +69,14 @@ __host__ __device__ __forceinline__ size_t blk_al16(size_t x) { return (x + 15) 
 
 // bytes of BlkShared after the staged rows
 __host__ __device__ __forceinline__ size_t blk_shared_bytes(int max_block) {
-    return blk_al16((size_t)max_block * 2) + blk_al16(HM_BLK_MAXB * 4) + blk_al16((HM_BLK_MAXC + 1) * 4) +
+    (void)max_block;
+    return blk_al16(HM_BLK_MAXB * 4) + blk_al16((HM_BLK_MAXC + 1) * 4) +
            blk_al16(HM_BLK_MAXB * 4) + blk_al16(HM_BLK_MAXB * 4) + blk_al16(HM_BLK_MAXB) * 2;
 }
 
 __device__ __forceinline__ BlkShared blk_carve(unsigned char *p, int max_block) {
     BlkShared s;
-    s.list = (uint16_t *)p; p += blk_al16((size_t)max_block * 2);
+    (void)max_block;
     s.hcd = (int *)p; p += blk_al16(HM_BLK_MAXB * 4);
     s.hcs = (int *)p; p += blk_al16((HM_BLK_MAXC + 1) * 4);
     s.tmp = (int *)p; p += blk_al16(HM_BLK_MAXB * 4);
@@ -86,9 +86,10 @@ __device__ __forceinline__ BlkShared blk_carve(unsigned char *p, int max_block) 
     return s;
 }
 
-// Offsets of the block one exchange away (high and cross bonds) and the low words of the
-// block, for the block of high word h whose low part holds k ones.  Contains barriers:
-// every thread of the CTA must call it.  Returns the block's row count; *off_out = off(h).
+// Offsets of the block one exchange away (high and cross bonds), for the block of high
+// word h whose low part holds k ones (its low words, in rank order, are the run of
+// popcount k of BlkParams::lw).  Contains barriers: every thread of the CTA must call it.
+// Returns the block's row count; *off_out = off(h).
 __device__ __forceinline__ int blk_setup_block(const BlkParams &P, const BlkTabs &tb, uint32_t h, int k,
                                                const BlkShared &sh, uint32_t *off_out) {
     const uint32_t off = blk_off(P, tb, h, k);
@@ -106,19 +107,6 @@ __device__ __forceinline__ int blk_setup_block(const BlkParams &P, const BlkTabs
         sh.cbq[e] = (uint8_t)bq;
         sh.ck[e] = (int8_t)(ok ? k2 : -1);
         sh.coff[e] = ok ? blk_off(P, tb, h ^ (1u << q), k2) : 0u;
-    }
-    for (int b1 = threadIdx.x; b1 < P.nb1; b1 += blockDim.x) {
-        const int c0 = k - __popc(b1);
-        if (c0 < 0 || c0 > 8) continue;
-        int bs = tb.U[k * P.nb1 + b1];
-        const uint32_t hib = (uint32_t)b1 << 8;
-        if (c0 == 0) { sh.list[bs] = (uint16_t)hib; continue; }
-        uint32_t b0 = (1u << c0) - 1u;
-        while (b0 < 256u) {                        // bytes of popcount c0 in increasing order
-            sh.list[bs++] = (uint16_t)(hib | b0);
-            const uint32_t t = b0 | (b0 - 1);
-            b0 = (t + 1) | (((~t & (t + 1)) - 1) >> (__ffs(b0)));
-        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {                        // compact the valid high exchanges by class

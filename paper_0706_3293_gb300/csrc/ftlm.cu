@@ -35,6 +35,7 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *out);
 __host__ __device__ __forceinline__ size_t al16f(size_t x) { return (x + 15) & ~(size_t)15; }
 
 constexpr int FT_NT = 512;          // threads per CTA of the persistent kernel
+constexpr int FT_CTAS = 2;          // CTAs per SM the register budget is cut for
 constexpr int FT_W = 32;            // row stride in floats (vectors per row, padded)
 constexpr int FT_MAXS = 65;         // sectors (N + 1 for s = 1/2, N <= 64)
 constexpr double FT_TOL = 1e-5;     // breakdown threshold (above the FP32 noise floor)
@@ -156,11 +157,32 @@ __global__ void k_ft_init(FtParams F) {
     if (blockIdx.x == 0 && threadIdx.x == 0) { d.bar->count = 0; d.bar->gen = 0; d.bar->abort = 0; }
 }
 
+// adds the per-thread partials p (vectors v0..v0+VT-1 of row group grp in this warp) to
+// the CTA's accumulator of sector A in a fixed order, and clears them.  All threads of
+// the CTA call it; it contains barriers.
+template <int VT>
+__device__ __forceinline__ void ft_flush(ef::df *p, float *red, ef::df *cacc, int A, int warp, int grp, int v0) {
+#pragma unroll
+    for (int q = 0; q < VT; ++q) {
+        red[((warp * VT + grp) * FT_W + v0 + q) * 2] = p[q].hi;
+        red[((warp * VT + grp) * FT_W + v0 + q) * 2 + 1] = p[q].lo;
+        p[q] = ef::df{0.0f, 0.0f};
+    }
+    __syncthreads();
+    if (threadIdx.x < FT_W) {
+        ef::df s = cacc[A * FT_W + threadIdx.x];
+        for (int w = 0; w < (FT_NT / 32) * VT; ++w)
+            s = ef::df_add(s, ef::df{red[(w * FT_W + threadIdx.x) * 2], red[(w * FT_W + threadIdx.x) * 2 + 1]});
+        cacc[A * FT_W + threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
 // ---- the persistent kernel ---------------------------------------------------------------
 // shared layout: block tables | low words | staged rows [max_block][FT_W] floats |
 // hop lists | sigma/gamma of the item's sector | per-CTA accumulators [nsec][FT_W] (df)
 template <int NC, int VT>
-__global__ void __launch_bounds__(FT_NT, 1) k_ftlm(FtParams F) {
+__global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
     const BlkParams &P = F.P;
     const FtDev &d = F.d;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -182,11 +204,21 @@ __global__ void __launch_bounds__(FT_NT, 1) k_ftlm(FtParams F) {
 
     for (int j = 0; j < F.steps; ++j) {
         // ---------------- phase A: products ----------------
+        // dot partials stay in registers over consecutive items of one sector (items are
+        // sorted by sector) and are reduced into the CTA's accumulator when it changes
+        ef::df dot[VT];
+#pragma unroll
+        for (int q = 0; q < VT; ++q) dot[q] = ef::df{0.0f, 0.0f};
+        int curA = -1;
         for (int it = blockIdx.x; it < F.nitems; it += gridDim.x) {
             const uint32_t item = d.items[it];
             const int A = (int)(item >> 16);
             const uint32_t h = item & 0xFFFFu;
             if (!d.sec_active[A]) continue;
+            if (A != curA) {
+                if (curA >= 0) ft_flush<VT>(dot, red, cacc, curA, warp, grp, v0);
+                curA = A;
+            }
             const int k = A - __popc(h);
             const uint64_t base = d.rowoff[A];
             __syncthreads();
@@ -204,11 +236,9 @@ __global__ void __launch_bounds__(FT_NT, 1) k_ftlm(FtParams F) {
             const float *qc = (j & 1) ? d.q1 : d.q0;
             float *qp = (j & 1) ? d.q0 : d.q1;
             const uint16_t *Uk = tb.U + k * P.nb1;
-            ef::df dot[VT];
-#pragma unroll
-            for (int q = 0; q < VT; ++q) dot[q] = ef::df{0.0f, 0.0f};
+            const uint16_t *lw = P.lw + P.lwoff[k];
             for (int r = warp * VT + grp; r < n; r += nwarps * VT) {
-                const uint32_t l = sh.list[r];
+                const uint32_t l = __ldg(lw + r);
                 float acc[NC][VT];
                 int cnt[NC];
 #pragma unroll
@@ -246,20 +276,8 @@ __global__ void __launch_bounds__(FT_NT, 1) k_ftlm(FtParams F) {
                     dot[q] = ef::df_add(dot[q], ef::two_prod(sg[v0 + q] * xo, u));
                 }
             }
-            // item reduction: per vector over warps and row groups, fixed order
-#pragma unroll
-            for (int q = 0; q < VT; ++q) {
-                red[((warp * VT + grp) * FT_W + v0 + q) * 2] = dot[q].hi;
-                red[((warp * VT + grp) * FT_W + v0 + q) * 2 + 1] = dot[q].lo;
-            }
-            __syncthreads();
-            if (threadIdx.x < FT_W) {
-                ef::df s = cacc[A * FT_W + threadIdx.x];
-                for (int w = 0; w < nwarps * VT; ++w)
-                    s = ef::df_add(s, ef::df{red[(w * FT_W + threadIdx.x) * 2], red[(w * FT_W + threadIdx.x) * 2 + 1]});
-                cacc[A * FT_W + threadIdx.x] = s;
-            }
         }
+        if (curA >= 0) ft_flush<VT>(dot, red, cacc, curA, warp, grp, v0);
         __syncthreads();
         for (int t = threadIdx.x; t < F.nsec * FT_W; t += FT_NT) {
             d.part[(size_t)blockIdx.x * F.nsec * FT_W + t] = (double)cacc[t].hi + (double)cacc[t].lo;
@@ -277,11 +295,19 @@ __global__ void __launch_bounds__(FT_NT, 1) k_ftlm(FtParams F) {
         }
         if (!grid_sync(d.bar, F.nctas, LIMIT)) return;
         // ---------------- phase C: update ----------------
+        ef::df nn[VT];
+#pragma unroll
+        for (int q = 0; q < VT; ++q) nn[q] = ef::df{0.0f, 0.0f};
+        curA = -1;
         for (int it = blockIdx.x; it < F.nitems; it += gridDim.x) {
             const uint32_t item = d.items[it];
             const int A = (int)(item >> 16);
             const uint32_t h = item & 0xFFFFu;
             if (!d.sec_active[A]) continue;
+            if (A != curA) {
+                if (curA >= 0) ft_flush<VT>(nn, red, cacc, curA, warp, grp, v0);
+                curA = A;
+            }
             const int k = A - __popc(h);
             const uint32_t off = blk_off(P, tb, h, k);
             const int n = (int)tb.C[P.K * (P.A + 1) + k];
@@ -291,9 +317,6 @@ __global__ void __launch_bounds__(FT_NT, 1) k_ftlm(FtParams F) {
             __syncthreads();
             const float *qc = (j & 1) ? d.q1 : d.q0;
             float *qp = (j & 1) ? d.q0 : d.q1;
-            ef::df nn[VT];
-#pragma unroll
-            for (int q = 0; q < VT; ++q) nn[q] = ef::df{0.0f, 0.0f};
             for (int r = warp * VT + grp; r < n; r += nwarps * VT) {
                 const uint64_t row = base + (uint32_t)r;
 #pragma unroll
@@ -304,19 +327,8 @@ __global__ void __launch_bounds__(FT_NT, 1) k_ftlm(FtParams F) {
                     nn[q] = ef::df_add(nn[q], ef::two_prod(w, w));
                 }
             }
-#pragma unroll
-            for (int q = 0; q < VT; ++q) {
-                red[((warp * VT + grp) * FT_W + v0 + q) * 2] = nn[q].hi;
-                red[((warp * VT + grp) * FT_W + v0 + q) * 2 + 1] = nn[q].lo;
-            }
-            __syncthreads();
-            if (threadIdx.x < FT_W) {
-                ef::df s = cacc[A * FT_W + threadIdx.x];
-                for (int w = 0; w < nwarps * VT; ++w)
-                    s = ef::df_add(s, ef::df{red[(w * FT_W + threadIdx.x) * 2], red[(w * FT_W + threadIdx.x) * 2 + 1]});
-                cacc[A * FT_W + threadIdx.x] = s;
-            }
         }
+        if (curA >= 0) ft_flush<VT>(nn, red, cacc, curA, warp, grp, v0);
         __syncthreads();
         for (int t = threadIdx.x; t < F.nsec * FT_W; t += FT_NT) {
             d.part[(size_t)blockIdx.x * F.nsec * FT_W + t] = (double)cacc[t].hi + (double)cacc[t].lo;
@@ -566,12 +578,13 @@ struct FtLayout {
 };
 
 static int ft_choose_K(int N) {
-    // largest K (8..16, K <= N-2) whose biggest block of 32-float rows fits ~150 KB
+    // largest K (8..16, K <= N-2) whose biggest block of 32-float rows fits ~75 KB, so
+    // two CTAs fit on an SM (K = 11: 462 rows, 59 KB)
     int best = -1;
     for (int K = 8; K <= 16 && K <= N - 2; ++K) {
         uint64_t c = 1;
         for (int i = 0; i < K / 2; ++i) c = c * (K - i) / (i + 1);
-        if (c * FT_W * 4 <= 150 * 1024) best = K;
+        if (c * FT_W * 4 <= 75 * 1024) best = K;
     }
     return best;
 }
@@ -692,12 +705,17 @@ static int ft_prepare(int n_sites, int two_s, int n_bonds, const int32_t *u, con
     S->F.nitems = (int)items->size();
     S->smem = ft_smem(S->F.P, nsec);
     if (S->smem > 227 * 1024) return fail(HM_EINVAL, "ftlm_run: shared memory plan too large");
-    int per_sm = 0;
-    const void *kfn = pick_kernel(S->F.P.nc, 1);
-    HM_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem));
-    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, FT_NT, S->smem));
+    // co-resident CTAs per SM: the fewest any tiling allows (at most FT_CTAS)
+    int per_sm = FT_CTAS;
+    for (int vt : {1, 2, 4}) {
+        const void *kfn = pick_kernel(S->F.P.nc, vt);
+        int p = 0;
+        HM_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem));
+        HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kfn, FT_NT, S->smem));
+        per_sm = std::min(per_sm, p);
+    }
     if (per_sm < 1) return fail(HM_EINVAL, "ftlm_run: kernel does not fit on an SM");
-    S->nctas = sm_count();   // one CTA per SM (cooperative: all resident)
+    S->nctas = sm_count() * per_sm;   // cooperative: all resident
     S->F.nctas = (unsigned)S->nctas;
     S->L = ft_layout(n_sites, nsec, R, steps, S->F.nitems, S->nctas, n_t, S->xcd.size(), (size_t)xmat);
     return HM_OK;
