@@ -59,7 +59,6 @@ namespace hm {
 struct BlkShared {
     int *hcd;             // [HM_BLK_MAXB] offsets (target row - own row) of the valid high exchanges
     int *hcs;             // [HM_BLK_MAXC + 1] class c owns hcd[hcs[c] .. hcs[c+1])
-    int *tmp;             // [HM_BLK_MAXB]
     uint32_t *coff;       // [HM_BLK_MAXB] sector offset of the cross target block
     int8_t *ck;           // [HM_BLK_MAXB] low popcount of the cross target (-1: none)
     uint8_t *cbq;         // [HM_BLK_MAXB] bit q of h for the cross bond
@@ -70,8 +69,8 @@ __host__ __device__ __forceinline__ size_t blk_al16(size_t x) { return (x + 15) 
 // bytes of BlkShared after the staged rows
 __host__ __device__ __forceinline__ size_t blk_shared_bytes(int max_block) {
     (void)max_block;
-    return blk_al16(HM_BLK_MAXB * 4) + blk_al16((HM_BLK_MAXC + 1) * 4) +
-           blk_al16(HM_BLK_MAXB * 4) + blk_al16(HM_BLK_MAXB * 4) + blk_al16(HM_BLK_MAXB) * 2;
+    return blk_al16(HM_BLK_MAXB * 4) + blk_al16((HM_BLK_MAXC + 1) * 4) + blk_al16(HM_BLK_MAXB * 4) +
+           blk_al16(HM_BLK_MAXB) * 2;
 }
 
 __device__ __forceinline__ BlkShared blk_carve(unsigned char *p, int max_block) {
@@ -79,7 +78,6 @@ __device__ __forceinline__ BlkShared blk_carve(unsigned char *p, int max_block) 
     (void)max_block;
     s.hcd = (int *)p; p += blk_al16(HM_BLK_MAXB * 4);
     s.hcs = (int *)p; p += blk_al16((HM_BLK_MAXC + 1) * 4);
-    s.tmp = (int *)p; p += blk_al16(HM_BLK_MAXB * 4);
     s.coff = (uint32_t *)p; p += blk_al16(HM_BLK_MAXB * 4);
     s.ck = (int8_t *)p; p += blk_al16(HM_BLK_MAXB);
     s.cbq = (uint8_t *)p;
@@ -88,35 +86,44 @@ __device__ __forceinline__ BlkShared blk_carve(unsigned char *p, int max_block) 
 
 // Offsets of the block one exchange away (high and cross bonds), for the block of high
 // word h whose low part holds k ones (its low words, in rank order, are the run of
-// popcount k of BlkParams::lw).  Contains barriers: every thread of the CTA must call it.
-// Returns the block's row count; *off_out = off(h).
+// popcount k of BlkParams::lw).  Warp 0 lists the valid high exchanges (two bonds a lane,
+// compacted by class through its ballots), warp 1 the cross exchanges; no barrier here:
+// the caller syncs before reading sh.  Returns the block's row count; *off_out = off(h).
 __device__ __forceinline__ int blk_setup_block(const BlkParams &P, const BlkTabs &tb, uint32_t h, int k,
                                                const BlkShared &sh, uint32_t *off_out) {
     const uint32_t off = blk_off(P, tb, h, k);
     const int n = (int)tb.C[P.K * (P.A + 1) + k];
-    for (int e = threadIdx.x; e < P.nhb; e += blockDim.x) {
-        const int p = P.hb_p[e], q = P.hb_q[e];
-        const bool valid = ((h >> p) ^ (h >> q)) & 1u;
-        sh.tmp[e] = valid ? (int)(blk_off(P, tb, h ^ ((1u << p) | (1u << q)), k) - off) : INT_MIN;
-    }
-    for (int e = threadIdx.x; e < P.ncb; e += blockDim.x) {
-        const int q = P.cb_q[e];
-        const uint32_t bq = (h >> q) & 1u;
-        const int k2 = k + (bq ? 1 : -1);
-        const bool ok = k2 >= 0 && k2 <= P.K;
-        sh.cbq[e] = (uint8_t)bq;
-        sh.ck[e] = (int8_t)(ok ? k2 : -1);
-        sh.coff[e] = ok ? blk_off(P, tb, h ^ (1u << q), k2) : 0u;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {                        // compact the valid high exchanges by class
-        int cnt = 0;
-        for (int c = 0; c < HM_BLK_MAXC; ++c) {
-            sh.hcs[c] = cnt;
-            for (int e = P.hb_start[c]; e < P.hb_start[c + 1]; ++e)
-                if (sh.tmp[e] != INT_MIN) sh.hcd[cnt++] = sh.tmp[e];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        int val[2] = {0, 0}, hoff[2] = {0, 0};
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int e = lane + 32 * half;
+            if (e < P.nhb) {
+                const int p = P.hb_p[e], q = P.hb_q[e];
+                val[half] = (((h >> p) ^ (h >> q)) & 1u) ? 1 : 0;
+                if (val[half]) hoff[half] = (int)(blk_off(P, tb, h ^ ((1u << p) | (1u << q)), k) - off);
+            }
         }
-        sh.hcs[HM_BLK_MAXC] = cnt;
+        const uint32_t b0 = __ballot_sync(0xffffffffu, val[0]), b1 = __ballot_sync(0xffffffffu, val[1]);
+        const uint32_t below = (1u << lane) - 1u;
+        if (val[0]) sh.hcd[__popc(b0 & below)] = hoff[0];
+        if (val[1]) sh.hcd[__popc(b0) + __popc(b1 & below)] = hoff[1];
+        if (lane <= HM_BLK_MAXC) {                 // class c starts at the valid ones before hb_start[c]
+            const int e = P.hb_start[lane];
+            sh.hcs[lane] = e >= 32 ? __popc(b0) + __popc(e >= 64 ? b1 : b1 & ((1u << (e - 32)) - 1u))
+                                   : __popc(b0 & ((1u << e) - 1u));
+        }
+    } else if (warp == 1) {
+        for (int e = lane; e < P.ncb; e += 32) {
+            const int q = P.cb_q[e];
+            const uint32_t bq = (h >> q) & 1u;
+            const int k2 = k + (bq ? 1 : -1);
+            const bool ok = k2 >= 0 && k2 <= P.K;
+            sh.cbq[e] = (uint8_t)bq;
+            sh.ck[e] = (int8_t)(ok ? k2 : -1);
+            sh.coff[e] = ok ? blk_off(P, tb, h ^ (1u << q), k2) : 0u;
+        }
     }
     *off_out = off;
     return n;

@@ -178,9 +178,25 @@ __device__ __forceinline__ void ft_flush(ef::df *p, float *red, ef::df *cacc, in
     __syncthreads();
 }
 
+// VT consecutive floats of one row (16- or 8-byte aligned for VT = 4, 2), read-only path
+template <int VT>
+__device__ __forceinline__ void ft_ld(const float *p, float *v) {
+    if constexpr (VT == 4) {
+        const float4 t = __ldg((const float4 *)p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (VT == 2) {
+        const float2 t = __ldg((const float2 *)p);
+        v[0] = t.x; v[1] = t.y;
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+
 // ---- the persistent kernel ---------------------------------------------------------------
-// shared layout: block tables | low words | staged rows [max_block][FT_W] floats |
-// hop lists | sigma/gamma of the item's sector | per-CTA accumulators [nsec][FT_W] (df)
+// shared layout: block tables | two copies of the block metadata (hop lists) | two copies
+// of sigma/gamma of the item's sector | alpha*sigma | per-warp partials | per-CTA
+// accumulators [nsec][FT_W] (df).  The block's own rows are read through L1 (a block of
+// K = 11 is at most 59 KB).
 template <int NC, int VT>
 __global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
     const BlkParams &P = F.P;
@@ -188,9 +204,13 @@ __global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
     extern __shared__ __align__(16) unsigned char smem[];
     const BlkTabs tb = stage_blk_tables(P, smem);
     size_t o = al16f(P.tab_bytes);
-    float *Xs = (float *)(smem + o); o += al16f((size_t)P.max_block * FT_W * 4);
-    const BlkShared sh = blk_carve(smem + o, P.max_block); o += blk_shared_bytes(P.max_block);
-    float *sg = (float *)(smem + o); o += al16f(FT_W * 4 * 3);   // sigma, gamma, alpha*sigma
+    // per-block metadata and sigma/gamma, double-buffered: the setup of a block writes one
+    // copy while slower warps still read the other (one barrier per block)
+    unsigned char *shb = smem + o;
+    const size_t shs = blk_shared_bytes(P.max_block);
+    o += 2 * shs;
+    float *sgb = (float *)(smem + o); o += al16f(FT_W * 4 * 2 * 2);   // [2][sigma, gamma]
+    float *sg = (float *)(smem + o); o += al16f(FT_W * 4 * 3);   // phase C: alpha*sigma at [2 FT_W]
     float *red = (float *)(smem + o); o += al16f((size_t)(FT_NT / 32) * 4 * 2 * FT_W * 4);   // [warp*VT+grp][v] df
     ef::df *cacc = (ef::df *)(smem + o);                          // [nsec][FT_W]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -209,7 +229,7 @@ __global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
         ef::df dot[VT];
 #pragma unroll
         for (int q = 0; q < VT; ++q) dot[q] = ef::df{0.0f, 0.0f};
-        int curA = -1;
+        int curA = -1, ib = 0;
         for (int it = blockIdx.x; it < F.nitems; it += gridDim.x) {
             const uint32_t item = d.items[it];
             const int A = (int)(item >> 16);
@@ -221,20 +241,21 @@ __global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
             }
             const int k = A - __popc(h);
             const uint64_t base = d.rowoff[A];
-            __syncthreads();
             // block setup (offsets inside the sector; rows of the sector start at base)
+            const BlkShared sh = blk_carve(shb + ib * shs, P.max_block);
+            float *sgi = sgb + ib * 2 * FT_W;
+            ib ^= 1;
             uint32_t off;
             const int n = blk_setup_block(P, tb, h, k, sh, &off);
-            const float4 *src = (const float4 *)((j & 1) ? d.q1 : d.q0) + (base + off) * (FT_W / 4);
-            for (int t = threadIdx.x; t < n * (FT_W / 4); t += FT_NT) ((float4 *)Xs)[t] = src[t];
-            if (threadIdx.x < FT_W) {
-                const int sv = A * FT_W + threadIdx.x;
-                sg[threadIdx.x] = (float)d.sig_cur[sv];
-                sg[FT_W + threadIdx.x] = (float)(d.beta_prev[sv] * d.sig_prev[sv]);
+            if (threadIdx.x >= 64 && threadIdx.x < 64 + FT_W) {
+                const int sv = A * FT_W + threadIdx.x - 64;
+                sgi[threadIdx.x - 64] = (float)d.sig_cur[sv];
+                sgi[FT_W + threadIdx.x - 64] = (float)(d.beta_prev[sv] * d.sig_prev[sv]);
             }
             __syncthreads();
             const float *qc = (j & 1) ? d.q1 : d.q0;
             float *qp = (j & 1) ? d.q0 : d.q1;
+            const float *Xb = qc + (base + off) * FT_W + v0;   // the block's rows, this lane's vectors
             const uint16_t *Uk = tb.U + k * P.nb1;
             const uint16_t *lw = P.lw + P.lwoff[k];
             for (int r = warp * VT + grp; r < n; r += nwarps * VT) {
@@ -247,9 +268,10 @@ __global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
 #pragma unroll
                     for (int q = 0; q < VT; ++q) ac[q] = 0.0f;
                     int mc = blk_low_hops(P, tb, c, l, (uint32_t)r, Uk, [&](uint32_t r2) {
-                        const float *xr = Xs + (size_t)r2 * FT_W + v0;
+                        float xv[VT];
+                        ft_ld<VT>(Xb + (size_t)r2 * FT_W, xv);
 #pragma unroll
-                        for (int q = 0; q < VT; ++q) ac[q] += xr[q];
+                        for (int q = 0; q < VT; ++q) ac[q] += xv[q];
                     });
                     mc += blk_cross_hops(P, tb, c, l, sh, [&](uint32_t jj) {
                         const float *xr = qc + (base + jj) * FT_W + v0;
@@ -265,15 +287,17 @@ __global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
                     cnt[c] = mc + (sh.hcs[c + 1] - sh.hcs[c]);
                 }
                 const uint64_t row = base + off + (uint32_t)r;
+                float xov[VT];
+                ft_ld<VT>(Xb + (size_t)r * FT_W, xov);
 #pragma unroll
                 for (int q = 0; q < VT; ++q) {
-                    const float xo = Xs[(size_t)r * FT_W + v0 + q];
+                    const float xo = xov[q];
                     float y = 0.0f;
 #pragma unroll
                     for (int c = 0; c < NC; ++c) y += P.gq[c] * (2.0f * acc[c][q] + (float)(P.ntot[c] - 2 * cnt[c]) * xo);
-                    const float u = sg[v0 + q] * y - sg[FT_W + v0 + q] * qp[row * FT_W + v0 + q];
+                    const float u = sgi[v0 + q] * y - sgi[FT_W + v0 + q] * qp[row * FT_W + v0 + q];
                     qp[row * FT_W + v0 + q] = u;
-                    dot[q] = ef::df_add(dot[q], ef::two_prod(sg[v0 + q] * xo, u));
+                    dot[q] = ef::df_add(dot[q], ef::two_prod(sgi[v0 + q] * xo, u));
                 }
             }
         }
@@ -630,8 +654,8 @@ static const void *pick_kernel(int nc, int vt) {
 
 static size_t ft_smem(const BlkParams &P, int nsec) {
     size_t o = al16f(P.tab_bytes);
-    o += al16f((size_t)P.max_block * FT_W * 4);
-    o += blk_shared_bytes(P.max_block);
+    o += 2 * blk_shared_bytes(P.max_block);
+    o += al16f(FT_W * 4 * 2 * 2);
     o += al16f(FT_W * 4 * 3);
     o += al16f((size_t)(FT_NT / 32) * 4 * 2 * FT_W * 4);
     o += al16f((size_t)nsec * FT_W * sizeof(ef::df));
