@@ -442,3 +442,40 @@ def test_block_product_specialised_equals_generic(hm, case, row, monkeypatch):
         e1 = oracle.tridiag_lowest(a1, b1, 1)[0]
         e0 = oracle.tridiag_lowest(a0, b0, 1)[0]
         assert abs(e1 - e0) <= 1e-5 * abs(e0)
+
+
+@pytest.mark.slow
+def test_lanczos_full_size_majumdar_ghosh(hm):
+    """The bench workload at full size (N = 32, J2 = J1/2, M = 0, 601,080,390 rows) through
+    the same run type bench.py times: J2 = J1/2 on an even periodic ring is the
+    Majumdar-Ghosh point, whose ground energy is exactly -3N/8 = -12 (two dimer
+    singlets), independent of this code and of the oracle."""
+    inst = W.j1j2_ring32()
+    b = hm.Basis(32, 1, 0)
+    run = hm.LanczosRun(b, hm.bonds_of(inst), 150, seed=inst.seed)
+    assert run.kernel_name().startswith("k_blk_lz64")
+    run.step(150)
+    al, be, rc = run.read()
+    run.close()
+    e0 = oracle.tridiag_lowest(al, be, 1)[0]
+    assert abs(e0 - (-12.0)) <= 1e-9 * 12.0, e0
+
+
+@pytest.mark.slow
+def test_block_product_specialised_equals_generic_full_size(hm, monkeypatch):
+    """At N = 32 (the bench's launch configuration: dynamic block schedule over 131,070
+    blocks, 456 CTAs) the specialised and the generic FP64 block products give the same
+    Lanczos coefficients bit for bit over 4 steps."""
+    inst = W.j1j2_ring32()
+    b = hm.Basis(32, 1, 0)
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("HM_JIT", mode)
+        run = hm.LanczosRun(b, hm.bonds_of(inst), 4, seed=inst.seed)
+        name = run.kernel_name()
+        run.step(4)
+        out[mode] = (name, run.read())
+        run.close()
+    assert out["1"][0] == "k_blk_lz64_jit" and out["0"][0] == "k_blk_lz64"
+    (a1, b1, _), (a0, b0, _) = out["1"][1], out["0"][1]
+    assert np.array_equal(a1, a0) and np.array_equal(b1, b0)
