@@ -189,6 +189,21 @@ int lanczos_run(const hm_basis *basis, int n_bonds, const int32_t *u, const int3
                 void *work, size_t work_bytes, double *alpha, double *beta,
                 int *steps_done, double *ritz, int n_ritz, void *stream);
 
+/* The lowest energy of every magnetisation sector: for A = 0 .. 2sN (sector 2M =
+ * 2sN - 2A, i.e. M = Ns - A) one Lanczos run (lanczos_run) of up to `steps` steps from
+ * the uniform start vector of seed sm64(seed, A * 2^20) (output #(A * 2^20) of SplitMix64;
+ * the key the finite-temperature driver uses for the first vector of sector A), on the
+ * sector coding of Sec. 3 and the products of Eq. (E-4-b).  e0[A] = the lowest Ritz value
+ * of T (host, 2sN + 1 entries); steps_done[A] (host, may be NULL) = the run's length, less
+ * than `steps` when the sector's Krylov space is exhausted (then e0[A] is exact).  The
+ * paper has no routine of this name: its applications (Sec. 1) use this curve E0(M).
+ * work: device memory of sector_ground_energies_workspace bytes, reused by every sector.
+ * Synchronises the stream once per sector.  Errors as lanczos_run. */
+int sector_ground_energies_workspace(int n_sites, int two_s, int steps, int dtype, size_t *bytes);
+int sector_ground_energies(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_t *v,
+                           const double *J, int steps, uint64_t seed, int dtype, void *work,
+                           size_t work_bytes, double *e0, int *steps_done, void *stream);
+
 /* Ground energy and its coupling gradient dE0/dJ_b = -<psi0| s_u.s_v |psi0>
  * (Hellmann-Feynman on Eq. E-2-1).  A first Lanczos pass gives T, its lowest
  * eigenvector c is found on the device (bisection + inverse iteration), a second pass

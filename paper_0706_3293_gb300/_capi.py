@@ -20,7 +20,8 @@ EXPORTS = [
     "start_vector",
     "lanczos_workspace", "lanczos_init", "lanczos_step", "lanczos_substep", "lanczos_read", "lanczos_free",
     "lanczos_kernel_name",
-    "lanczos_run", "e0_grad_workspace", "e0_grad", "ftlm_workspace", "ftlm_run",
+    "lanczos_run", "sector_ground_energies_workspace", "sector_ground_energies", "e0_grad_workspace", "e0_grad",
+    "ftlm_workspace", "ftlm_run",
 ]
 
 _lib = None
@@ -72,6 +73,8 @@ def load() -> ctypes.CDLL:
         "lanczos_kernel_name": (i32, [vp, ctypes.c_char_p, i32]),
         "lanczos_run": (i32, [vp, i32, vp, vp, vp, vp, u64, i32, i32, vp, sz, dp, dp, ip, dp,
                               i32, vp]),
+        "sector_ground_energies_workspace": (i32, [i32, i32, i32, i32, szp]),
+        "sector_ground_energies": (i32, [i32, i32, i32, vp, vp, vp, i32, u64, i32, vp, sz, dp, ip, vp]),
         "e0_grad_workspace": (i32, [vp, i32, i32, szp]),
         "e0_grad": (i32, [vp, i32, vp, vp, vp, vp, u64, i32, vp, sz, dp, dp, vp, vp]),
         "ftlm_workspace": (i32, [i32, i32, i32, vp, vp, vp, i32, i32, i32, szp]),

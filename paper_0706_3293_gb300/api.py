@@ -239,6 +239,37 @@ class LanczosRun:
             pass
 
 
+@dataclass
+class SectorEnergies:
+    """Lowest energy of every magnetisation sector (sector_ground_energies)."""
+    two_m: np.ndarray           # 2M of each sector, 2sN down to -2sN
+    e0: np.ndarray
+    steps_done: np.ndarray
+
+    def magnetisation(self, h: float) -> float:
+        """M minimising E0(M) - h M: the ground-state magnetisation in a field h along z
+        (the Zeeman term -h sum s^z commutes with H(J) and shifts sector M by -h M)."""
+        k = int(np.argmin(self.e0 - h * self.two_m / 2.0))
+        return float(self.two_m[k]) / 2.0
+
+
+def sector_ground_energies(n_sites: int, two_s: int, bonds: BondList, steps: int, seed: int = 0,
+                           dtype=torch.float64, work: torch.Tensor | None = None,
+                           device="cuda") -> SectorEnergies:
+    L = _capi.load()
+    nb = ctypes.c_size_t()
+    check(L.sector_ground_energies_workspace(n_sites, two_s, steps, _DT[dtype], ctypes.byref(nb)))
+    work = work if work is not None and work.numel() >= nb.value else _workspace(nb.value, device)
+    nsec = two_s * n_sites + 1
+    e0 = np.zeros(nsec)
+    done = np.zeros(nsec, dtype=np.int32)
+    check(L.sector_ground_energies(n_sites, two_s, *bonds.args(), steps, seed & (2**64 - 1), _DT[dtype],
+                                   _vp(work), work.numel(), e0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   done.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _stream()))
+    two_m = two_s * n_sites - 2 * np.arange(nsec)
+    return SectorEnergies(two_m, e0, done)
+
+
 def e0_grad(basis: Basis, bonds: BondList, steps: int, v0: torch.Tensor | None = None,
             seed: int = 0, want_psi: bool = False, device="cuda"):
     """Returns (E0, dE0/dJ as numpy, psi0 or None, status)."""
