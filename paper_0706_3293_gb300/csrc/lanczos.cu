@@ -153,6 +153,7 @@ k_lz_matvec(SectorView sv, BondParams bp, const T *__restrict__ qc, T *__restric
     __shared__ double red[NT / 32];
     const double *pdn, *pup;
     const I *cd = stage_tables<I>(sv, bp, smem_raw, &pdn, &pup);
+    I *const px = row_px_base<I>(sv, smem_raw);
     Codec<I> c{cd, sv.N, sv.S2, sv.A, sv.bits, sv.cd_w, sv.cd_rowlen};
     const double sc = S->sigma_cur, bp_ = S->beta_prev * S->sigma_prev;
     const float scf = (float)sc, bpf = (float)bp_;
@@ -162,7 +163,7 @@ k_lz_matvec(SectorView sv, BondParams bp, const T *__restrict__ qc, T *__restric
         const I i = (I)r;
         const uint64_t w = c.decode(i);
         Acc acc[1], dg;
-        row_apply<I, T, Acc, 1>(c, bp, pdn, pup, i, w, qc, 1, 0, acc, &dg);
+        row_apply<I, T, Acc, 1>(c, bp, pdn, pup, i, w, qc, 1, 0, acc, &dg, px);
         const Acc hv = dg * (Acc)qc[r] + acc[0];
         if constexpr (sizeof(T) == 8) {
             const T u = (T)(sc * (double)hv - bp_ * (double)qp[r]);

@@ -14,13 +14,14 @@ k_matvec(SectorView sv, BondParams bp, const T *__restrict__ x, T *__restrict__ 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const double *pdn, *pup;
     const I *cd = stage_tables<I>(sv, bp, smem_raw, &pdn, &pup);
+    I *const px = row_px_base<I>(sv, smem_raw);
     Codec<I> c{cd, sv.N, sv.S2, sv.A, sv.bits, sv.cd_w, sv.cd_rowlen};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < sv.dim; r += stride) {
         const I i = (I)r;
         const uint64_t w = c.decode(i);
         Acc acc[NV], dg;
-        row_apply<I, T, Acc, NV>(c, bp, pdn, pup, i, w, x, ld, c0, acc, &dg);
+        row_apply<I, T, Acc, NV>(c, bp, pdn, pup, i, w, x, ld, c0, acc, &dg, px);
         const T *xi = x + r * ld + c0;
         T *yi = y + r * ld + c0;
 #pragma unroll
