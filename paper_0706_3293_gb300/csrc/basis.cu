@@ -1,5 +1,6 @@
 // basis.cu -- sector tables (Sec. 3, Eq. E-3-c), the codec test hooks (Sec. 3.1, 3.2),
 // bond preparation, seeded start vectors and error reporting.
+#include <stdlib.h>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -106,6 +107,12 @@ int grid_blocks(uint64_t rows, int threads) {
     uint64_t cap = (uint64_t)sm_count() * 8;
     if (need < 1) need = 1;
     return (int)(need < cap ? need : cap);
+}
+
+int row_run_len() {
+    const char *e = getenv("HM_ROW_RUN");
+    const int v = e ? atoi(e) : 1;
+    return v < 1 ? 1 : v > 64 ? 64 : v;
 }
 
 int make_bonds(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v,

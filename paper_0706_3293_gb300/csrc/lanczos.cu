@@ -27,7 +27,10 @@ int bond_corr_dev(const hm_basis *b, const BondParams &bp, const void *g, const 
 size_t bond_corr_bytes(const hm_basis *b, int n_bonds);
 int start_vector_dev(uint64_t n, uint64_t seed, int kind, void *x, int dtype, cudaStream_t st);
 
-constexpr double LZ_TOL = 1e-12;     // breakdown: beta_j <= LZ_TOL * max(|alpha|, beta), FP64
+// breakdown: beta_j <= LZ_TOL * max(|alpha|, beta).  FP64 vectors are updated in double-float
+// arithmetic (about 2^-48 unit roundoff, not binary64's 2^-53), so a beta that vanishes in
+// exact arithmetic comes out near 1e-12 of the scale; the threshold sits well above that floor.
+constexpr double LZ_TOL = 1e-10;
 constexpr double LZ_TOL32 = 1e-5;    // FP32 vectors: above their rounding floor
 constexpr int NT = 256;
 
@@ -90,6 +93,7 @@ struct hm_lanczos {
     hm::BlkParams blk;      // s = 1/2 block path (use_blk)
     int use_blk, blk_blocks;
     const void *jit;        // block product specialised to the bonds (jit.cu), or nullptr
+    int run;                // rows per thread run of the general product (row_runs)
     int dtype, max_steps, host_j, next_phase;
     unsigned char *work;
     hm::LzLayout L;
@@ -147,7 +151,7 @@ __global__ void k_lz_start(LzScalars *S, const double *__restrict__ part, int nb
 template <class I, class T, class Acc>
 __global__ void __launch_bounds__(NT)
 k_lz_matvec(SectorView sv, BondParams bp, const T *__restrict__ qc, T *__restrict__ qp,
-            const LzScalars *__restrict__ S, double *__restrict__ part) {
+            const LzScalars *__restrict__ S, double *__restrict__ part, int run) {
     if (S->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[NT / 32];
@@ -159,9 +163,8 @@ k_lz_matvec(SectorView sv, BondParams bp, const T *__restrict__ qc, T *__restric
     const float scf = (float)sc, bpf = (float)bp_;
     double dot = 0.0;
     ef::df dotf{0.0f, 0.0f};
-    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < sv.dim; r += (uint64_t)gridDim.x * NT) {
+    row_runs(c, sv.dim, px, run, [&](uint64_t r, uint64_t w) {
         const I i = (I)r;
-        const uint64_t w = c.decode(i);
         Acc acc[1], dg;
         row_apply<I, T, Acc, 1>(c, bp, pdn, pup, i, w, qc, 1, 0, acc, &dg, px);
         const Acc hv = dg * (Acc)qc[r] + acc[0];
@@ -174,7 +177,7 @@ k_lz_matvec(SectorView sv, BondParams bp, const T *__restrict__ qc, T *__restric
             qp[r] = (T)u;
             dotf = ef::df_add(dotf, ef::two_prod(scf * (float)qc[r], u));
         }
-    }
+    });
     dot = block_sum<NT>(dot + (double)dotf.hi + (double)dotf.lo, red);
     if (threadIdx.x == 0) part[blockIdx.x] = dot;
 }
@@ -546,7 +549,7 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
             k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->alpha, pprev);
         } else {
             const size_t sm = row_smem_bytes<I>(sv);
-            k_lz_matvec<I, T, Acc><<<nblk, NT, sm, st>>>(sv, R->bp, qc, qp, R->sc, R->part);
+            k_lz_matvec<I, T, Acc><<<nblk, NT, sm, st>>>(sv, R->bp, qc, qp, R->sc, R->part, R->run);
             k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->alpha, pprev);
         }
     } else if (b64) {
@@ -648,6 +651,7 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
     if (rc < 0) { delete R; return rc; }
     R->use_blk = rc == 0 && (dtype == HM_F32 || R->L.shadow) && R->L.hpart != 0 && R->blk.H <= 17;
     R->jit = nullptr;
+    R->run = row_run_len();
     if (R->use_blk) {
         int jb = 0;
         const void *jk = nullptr;

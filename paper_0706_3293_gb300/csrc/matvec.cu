@@ -10,23 +10,21 @@ namespace hm {
 // ---------------------------------------------------------------------------------------
 template <class I, class T, class Acc, int NV>
 __global__ void __launch_bounds__(256)
-k_matvec(SectorView sv, BondParams bp, const T *__restrict__ x, T *__restrict__ y, int ld, int c0) {
+k_matvec(SectorView sv, BondParams bp, const T *__restrict__ x, T *__restrict__ y, int ld, int c0, int run) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const double *pdn, *pup;
     const I *cd = stage_tables<I>(sv, bp, smem_raw, &pdn, &pup);
     I *const px = row_px_base<I>(sv, smem_raw);
     Codec<I> c{cd, sv.N, sv.S2, sv.A, sv.bits, sv.cd_w, sv.cd_rowlen};
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < sv.dim; r += stride) {
+    row_runs(c, sv.dim, px, run, [&](uint64_t r, uint64_t w) {
         const I i = (I)r;
-        const uint64_t w = c.decode(i);
         Acc acc[NV], dg;
         row_apply<I, T, Acc, NV>(c, bp, pdn, pup, i, w, x, ld, c0, acc, &dg, px);
         const T *xi = x + r * ld + c0;
         T *yi = y + r * ld + c0;
 #pragma unroll
         for (int k = 0; k < NV; ++k) yi[k] = (T)(dg * (Acc)xi[k] + acc[k]);
-    }
+    });
 }
 
 template <class I, class T, class Acc, int NV>
@@ -35,7 +33,7 @@ static int launch_matvec(const SectorView &sv, const BondParams &bp, const T *x,
     size_t sm = row_smem_bytes<I>(sv);
     HM_CUDA(cudaFuncSetAttribute(k_matvec<I, T, Acc, NV>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_matvec<I, T, Acc, NV><<<grid_blocks(sv.dim, 256), 256, sm, st>>>(sv, bp, x, y, ld, c0);
+    k_matvec<I, T, Acc, NV><<<grid_blocks(sv.dim, 256), 256, sm, st>>>(sv, bp, x, y, ld, c0, row_run_len());
     HM_CUDA(cudaGetLastError());
     return HM_OK;
 }

@@ -159,6 +159,30 @@ def test_matvec_batched(hm, nvec, dtype):
         assert rel(Y[:, r], ref) <= (TOL_F64 if dtype == "f64" else TOL_F32)
 
 
+@pytest.mark.parametrize("run", [3, 8])
+@pytest.mark.parametrize("inst", SMALL[2:], ids=lambda i: i.name)
+def test_general_rows_successor_runs(hm, inst, run, monkeypatch):
+    """The general row kernels walking runs of consecutive rows by the successor rule
+    (Sec. 3.1) instead of one decode per row: the same products as the oracle, single and
+    batched, and the same Lanczos coefficients.  Run lengths 3 and 8 leave ragged last runs."""
+    monkeypatch.setenv("HM_ROW_RUN", str(run))
+    b = hm.Basis(inst.n_sites, inst.two_s, inst.two_m)
+    ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
+    x = oracle.start_uniform(5, b.dim)
+    ref = ob.matvec(obonds(inst), x)
+    y = hm.matvec(b, hm.bonds_of(inst), torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, ref) <= TOL_F64
+    X = np.stack([oracle.start_pm1(40 + r, b.dim) for r in range(5)], axis=1)
+    Y = hm.matvec(b, hm.bonds_of(inst), torch.from_numpy(X).cuda()).cpu().numpy()
+    for r in range(5):
+        assert rel(Y[:, r], ob.matvec(obonds(inst), X[:, r].copy())) <= TOL_F64
+    steps = min(20, b.dim)
+    res = hm.lanczos_run(b, hm.bonds_of(inst), steps, seed=9, n_ritz=1)
+    al, be = ob.lanczos(obonds(inst), oracle.start_uniform(9, b.dim), steps)
+    k = min(len(al), res.steps_done, 12)
+    np.testing.assert_allclose(res.alpha[:k], al[:k], rtol=0, atol=1e-12 * np.abs(al).max())
+
+
 def test_matvec_empty_bonds_and_tiny_sectors(hm):
     """No bonds: y = 0.  A dim-1 sector: y = E x with E = -s^2 sum J."""
     b = hm.Basis(6, 1, 6)
