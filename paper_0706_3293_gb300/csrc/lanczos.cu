@@ -196,10 +196,12 @@ __global__ void k_lz_alpha(LzScalars *S, const double *__restrict__ part, int nb
     }
 }
 
-// w = u - alpha_j sigma_cur q_cur over q_prev; part = sum w^2; psi += coef_j v_j if psi.
-// FP64 in double-float arithmetic on the bit patterns (no FP64 instruction per row);
+// w = u - alpha_j sigma_cur q_cur over q_prev; part = sum w^2; psi += coef_j v_j if PSI.
+// FP64 in double-float arithmetic on the bit patterns (no FP64 instruction per row
+// unless PSI: a run-time test of psi inside the loop would be predicated, not branched
+// around, and the psi terms would cost binary64 instructions on every row);
 // the largest exponent field of w goes to S->emax[pprev].
-template <class T>
+template <class T, bool PSI>
 __global__ void __launch_bounds__(NT)
 k_lz_update(const T *__restrict__ qc, T *__restrict__ qp, uint64_t n, LzScalars *S,
             const double *__restrict__ alpha, double *__restrict__ part, double *__restrict__ psi,
@@ -223,12 +225,12 @@ k_lz_update(const T *__restrict__ qc, T *__restrict__ qp, uint64_t n, LzScalars 
             ((unsigned long long *)qp)[r] = wb;
             em = max(em, (int)((wb >> 52) & 0x7FF));
             s = ef::df_add(s, ef::df_mul(w, w));
-            if (psi) psi[r] += cj * ef::u2d(qb);
+            if constexpr (PSI) psi[r] += cj * ef::u2d(qb);
         } else {
             const float w = qp[r] - asf * qc[r];
             qp[r] = w;
             s = ef::df_add(s, ef::two_prod(w, w));
-            if (psi) psi[r] += cj * (double)qc[r];
+            if constexpr (PSI) psi[r] += cj * (double)qc[r];
         }
     }
     const double tot = block_sum<NT>((double)s.hi + (double)s.lo, red);
@@ -287,7 +289,9 @@ __global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int n
 // 8 bytes): the update computes in double-float, so a pair holds all it produces and
 // needs no conversion to or from binary64.
 // w = sigma y - alpha sigma q - gamma q_prev over q_prev (y: binary64 bits of H q);
-// part = |w|^2; largest exponent of w, as a binary64 exponent field, to S->emax[pprev]
+// part = |w|^2; largest exponent of w, as a binary64 exponent field, to S->emax[pprev];
+// psi += coef_j q if PSI
+template <bool PSI>
 __global__ void __launch_bounds__(NT, 2048 / NT)
 k_lz_update_y(const unsigned long long *__restrict__ Y, const float2 *__restrict__ qc, float2 *__restrict__ qp,
               uint64_t n, LzScalars *S, const double *__restrict__ alpha, double *__restrict__ part,
@@ -317,7 +321,7 @@ k_lz_update_y(const unsigned long long *__restrict__ Y, const float2 *__restrict
         qp[r] = make_float2(w.hi, w.lo);
         eh = max(eh, (ef::f2u(w.hi) >> 23) & 0xFFu);
         s = ef::df_add(s, ef::df_mul(w, w));
-        if (psi) psi[r] += cj * ((double)q2.x + (double)q2.y);
+        if constexpr (PSI) psi[r] += cj * ((double)q2.x + (double)q2.y);
     }
     const double tot = block_sum<NT>((double)s.hi + (double)s.lo, red);
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
@@ -553,12 +557,19 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
             k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->alpha, pprev);
         }
     } else if (b64) {
-        k_lz_update_y<<<nblk, NT, 0, st>>>(Y, (const float2 *)qc, (float2 *)qp, sv.dim, R->sc, R->alpha, R->part,
-                                           R->psi, R->coef, pprev);
+        if (R->psi)
+            k_lz_update_y<true><<<nblk, NT, 0, st>>>(Y, (const float2 *)qc, (float2 *)qp, sv.dim, R->sc, R->alpha,
+                                                     R->part, R->psi, R->coef, pprev);
+        else
+            k_lz_update_y<false><<<nblk, NT, 0, st>>>(Y, (const float2 *)qc, (float2 *)qp, sv.dim, R->sc, R->alpha,
+                                                      R->part, nullptr, R->coef, pprev);
         k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
         k_fixd<<<nblk, NT, 0, st>>>((const float2 *)qp, xs[pprev], xs[parity], sv.dim, R->sc, pprev, R->qqp);
     } else {
-        k_lz_update<T><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
+        if (R->psi)
+            k_lz_update<T, true><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
+        else
+            k_lz_update<T, false><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, nullptr, R->coef, pprev);
         k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
     }
     HM_CUDA(cudaGetLastError());
