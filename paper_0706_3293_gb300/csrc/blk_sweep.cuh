@@ -35,13 +35,46 @@ struct XSlot {                       // a cross bond in the current block
     uint32_t kofs2;                  // byte offset of row k2 of s_US (k2 = k -+ 1)
 };
 
+constexpr int BLK_HBI = HM_BLK_MAXB + 4 * HM_BLK_MAXC;   // high-exchange list with its padding
+
 struct BlkMeta {                     // per-block data, double-buffered
     XSlot xs[HM_BLK_MAXC * 2 * HM_BLK_SX];
-    const unsigned char *hb[HM_BLK_MAXB];   // first rows of the high-exchange targets, by class
-    int hs[HM_BLK_MAXC + 1];
+    // element index of the first row of each allowed high-exchange target block; class c
+    // occupies [hs[c], he[c]) with hs[c] a multiple of 4, so four entries are one 16-byte load
+    __align__(16) uint32_t hbi[BLK_HBI];
+    int hs[HM_BLK_MAXC], he[HM_BLK_MAXC];
     uint32_t hv[2];
     uint32_t off, n, kofs, lwo;
 };
+
+// bits below position e of the 64-bit mask m
+__device__ __forceinline__ int popc_below(uint64_t m, int e) {
+    return e >= 64 ? __popcll(m) : __popcll(m & ((1ull << e) - 1ull));
+}
+
+// sum of the high-exchange gathers of class c for row r (the same low word in each target
+// block): four target offsets per 16-byte shared load
+template <class Sv, class G>
+__device__ __forceinline__ Sv blk_high_sum(const BlkMeta &B, int c, const unsigned char *Xg, uint32_t r,
+                                           const G &gx) {
+    const int e0 = B.hs[c], e1 = B.he[c];
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(B.hbi);
+    Sv a = Sv(0);
+    int e = e0;
+    for (; e + 4 <= e1; e += 4) {
+        const uint4 t = h4[e >> 2];
+        const Sv v0 = gx(Xg + (size_t)(t.x + r) * sizeof(Sv)), v1 = gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
+        const Sv v2 = gx(Xg + (size_t)(t.z + r) * sizeof(Sv)), v3 = gx(Xg + (size_t)(t.w + r) * sizeof(Sv));
+        a += (v0 + v1) + (v2 + v3);
+    }
+    if (e < e1) {                    // 1..3 left, the same count for every row of the block
+        const uint4 t = h4[e >> 2];
+        a += gx(Xg + (size_t)(t.x + r) * sizeof(Sv));
+        if (e + 1 < e1) a += gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
+        if (e + 2 < e1) a += gx(Xg + (size_t)(t.z + r) * sizeof(Sv));
+    }
+    return a;
+}
 
 __device__ __forceinline__ uint32_t us_at(uint32_t byte_off) {
     return *(const uint32_t *)((const unsigned char *)s_US + byte_off);
@@ -111,7 +144,7 @@ struct GF32 {
 #define HM_RUN6(M) case 6: M(5) [[fallthrough]]; case 5: M(4) [[fallthrough]]; case 4: M(3) [[fallthrough]]; \
     case 3: M(2) [[fallthrough]]; case 2: M(1) [[fallthrough]]; case 1: M(0) [[fallthrough]]; default: break;
 
-// Row policy: Row::sums(P, B, Xsb, l, r, gx, acc, cnt) sets, for row r (low word l) of
+// Row policy: Row::sums(P, B, Xsb, Xg, l, r, gx, acc, cnt) sets, for row r (low word l) of
 // the current block, acc[c] = sum of x over the allowed exchanges of class c and cnt[c]
 // = their number.  RowGeneric reads the bond slots from the parameters; the kernels
 // specialised at run time (jit.cu) bring a policy with the slots written out.
@@ -136,11 +169,11 @@ template <class Sv>
 static __device__ __forceinline__ void block(const BlkParams &, uint32_t) {}
 template <class Sv, class G>
 static __device__ __forceinline__ void sums(const BlkParams &P, const BlkMeta &B, const unsigned char *Xsb,
-                                            uint32_t l, uint32_t r, const G &gx, Sv xo, Sv *acc, int *cnt) {
+                                            const unsigned char *Xg, uint32_t l, uint32_t r, const G &gx, Sv xo,
+                                            Sv *acc, int *cnt) {
     (void)xo;
     const uint32_t l4 = l << 2, lh4 = (l >> 8) << 2, lh4k = lh4 | B.kofs;
     const uint32_t R0own = r0s_at(l4 & 0x3FCu), R1own = us_at(lh4k);
-    const uint32_t rb = r * (uint32_t)sizeof(Sv);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         Sv a = Sv(0);
@@ -152,16 +185,9 @@ static __device__ __forceinline__ void sums(const BlkParams &P, const BlkMeta &B
         switch (P.xn[c][0]) { HM_RUN8(HM_X0) }
         switch (P.xn[c][1]) { HM_RUN8(HM_X1) }
         // exchanges among the high positions: the same low word in another block
-        const int e0 = B.hs[c], e1 = B.hs[c + 1];
-        int e = e0;
-        for (; e + 4 <= e1; e += 4) {
-            const Sv v0 = gx(B.hb[e] + rb), v1 = gx(B.hb[e + 1] + rb);
-            const Sv v2 = gx(B.hb[e + 2] + rb), v3 = gx(B.hb[e + 3] + rb);
-            a += (v0 + v1) + (v2 + v3);
-        }
-        for (; e < e1; ++e) a += gx(B.hb[e] + rb);
+        a += blk_high_sum<Sv>(B, c, Xg, r, gx);
         acc[c] = a;
-        cnt[c] = m + (e1 - e0);
+        cnt[c] = m + (B.he[c] - B.hs[c]);
     }
 }
 };
@@ -216,12 +242,12 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
         const int k = P.A - __popc(h);
         // setup 1: targets of the high and cross exchanges, own offset, next block
         if (DYN && tid == 0) s_hnext[(it + 1) & 1] = blk_fetch(P, sched, nH);
-        const unsigned char *hptr = X;
+        uint32_t hidx = 0u;
         bool hval = false;
         if (tid < P.nhb) {
             const int p = P.hb_p[tid], q = P.hb_q[tid];
             hval = (((h >> p) ^ (h >> q)) & 1u) != 0u;
-            if (hval) hptr = X + (size_t)blk_off(P, tb, h ^ ((1u << p) | (1u << q)), k) * sizeof(Sv);
+            if (hval) hidx = blk_off(P, tb, h ^ ((1u << p) | (1u << q)), k);
         }
         if (tid < 64) {
             const unsigned bal = __ballot_sync(0xffffffffu, hval);
@@ -247,18 +273,17 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
         }
         __syncthreads();
         if (tid == BLK_NT - 1 && it_prev >= 0) flushf(h_prev, it_prev);
-        // setup 2: compact the allowed high exchanges by class; stage the block's x
-        {
-            const uint32_t h0 = B.hv[0], h1 = B.hv[1];
-            if (hval) {
-                const int pos = tid < 32 ? __popc(h0 & ((1u << tid) - 1u))
-                                         : __popc(h0) + __popc(h1 & ((1u << (tid - 32)) - 1u));
-                B.hb[pos] = hptr;
-            }
-            if (tid <= HM_BLK_MAXC) {
-                const int e = P.hb_start[tid];
-                B.hs[tid] = e >= 32 ? __popc(h0) + __popc(e >= 64 ? h1 : h1 & ((1u << (e - 32)) - 1u))
-                                    : __popc(h0 & ((1u << e) - 1u));
+        // setup 2: compact the allowed high exchanges by class, each class's run padded to a
+        // multiple of 4 entries; stage the block's x
+        if (hval || tid < HM_BLK_MAXC) {
+            const uint64_t hm = ((uint64_t)B.hv[1] << 32) | B.hv[0];
+            int start = 0;                           // padded start of the class
+            for (int c = 0; c < HM_BLK_MAXC; ++c) {
+                const int b0 = popc_below(hm, P.hb_start[c]), b1 = popc_below(hm, P.hb_start[c + 1]);
+                if (hval && tid >= P.hb_start[c] && tid < P.hb_start[c + 1])
+                    B.hbi[start + popc_below(hm, tid) - b0] = hidx;
+                if (tid == c) { B.hs[c] = start; B.he[c] = start + (b1 - b0); }
+                start += (b1 - b0 + 3) & ~3;
             }
         }
         const uint32_t off = B.off, n = B.n;
@@ -274,7 +299,7 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
             const Sv xo = Xs[r];
             Sv acc[NC];
             int cnt[NC];
-            Row::template sums<Sv>(P, B, Xsb, l, r, gx, xo, acc, cnt);
+            Row::template sums<Sv>(P, B, Xsb, X, l, r, gx, xo, acc, cnt);
             rowf(off, r, xo, acc, cnt, pv);
         }
         endf(it);

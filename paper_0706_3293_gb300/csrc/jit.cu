@@ -117,10 +117,10 @@ std::string gen_row_slots(const BlkParams &P) {
          "static __device__ __forceinline__ void block(const hm::BlkParams &, uint32_t) {}\n"
          "template <class Sv, class G>\n"
          "static __device__ __forceinline__ void sums(const hm::BlkParams &P, const hm::BlkMeta &B,\n"
-         "        const unsigned char *Xsb, uint32_t l, uint32_t r, const G &gx, Sv xo, Sv *acc, int *cnt) {\n"
+         "        const unsigned char *Xsb, const unsigned char *Xg, uint32_t l, uint32_t r, const G &gx, Sv xo,\n"
+         "        Sv *acc, int *cnt) {\n"
          "    const uint32_t l4 = l << 2, lh4 = (l >> 8) << 2, lh4k = lh4 | B.kofs;\n"
          "    const uint32_t R0own = hm::r0s_at(l4 & 0x3FCu), R1own = hm::us_at(lh4k);\n"
-         "    const uint32_t rb = r * (uint32_t)sizeof(Sv);\n"
          "    const uint32_t zo = (uint32_t)((P.max_block + hm::BLK_XPAD - 1) * sizeof(Sv));   // zero slot\n"
          "    (void)R0own; (void)R1own; (void)lh4; (void)gx; (void)xo; (void)zo;\n";
     // the distances that occur among the low bonds and count groups
@@ -154,15 +154,8 @@ std::string gen_row_slots(const BlkParams &P) {
             put(s, "        { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at((lh4 ^ 0x%xu) | x_.kofs2) + "
                    "R0own; if ((l ^ x_.wm) & x_.vm) { a += gx(x_.base + v_); ++m; } }\n",
                 (2 * c + 1) * HM_BLK_SX + k, (unsigned)P.xxa[c][1][k]);
-        put(s, "        const int e0 = B.hs[%d], e1 = B.hs[%d];\n", c, c + 1);
-        s += "        int e = e0;\n"
-             "        for (; e + 4 <= e1; e += 4) {\n"
-             "            const Sv v0 = gx(B.hb[e] + rb), v1 = gx(B.hb[e + 1] + rb);\n"
-             "            const Sv v2 = gx(B.hb[e + 2] + rb), v3 = gx(B.hb[e + 3] + rb);\n"
-             "            a += (v0 + v1) + (v2 + v3);\n"
-             "        }\n"
-             "        for (; e < e1; ++e) a += gx(B.hb[e] + rb);\n";
-        put(s, "        acc[%d] = a;\n        cnt[%d] = m + (e1 - e0);\n    }\n", c, c);
+        put(s, "        a += hm::blk_high_sum<Sv>(B, %d, Xg, r, gx);\n", c);
+        put(s, "        acc[%d] = a;\n        cnt[%d] = m + (B.he[%d] - B.hs[%d]);\n    }\n", c, c, c, c);
     }
     s += "}\n};\n";
     return s;
@@ -243,7 +236,8 @@ std::string gen_row(const BlkParams &P, bool &ok) {
     // sums
     s += "template <class Sv, class G>\n"
          "static __device__ __forceinline__ void sums(const hm::BlkParams &P, const hm::BlkMeta &B,\n"
-         "        const unsigned char *Xsb, uint32_t l, uint32_t r, const G &gx, Sv xo, Sv *acc, int *cnt) {\n"
+         "        const unsigned char *Xsb, const unsigned char *Xg, uint32_t l, uint32_t r, const G &gx, Sv xo,\n"
+         "        Sv *acc, int *cnt) {\n"
          "    const uint32_t b0 = l & 255u, b1 = l >> 8, rb = r * (uint32_t)sizeof(Sv);\n"
          "    const uint32_t l4 = l << 2, lh4 = b1 << 2;\n"
          "    (void)b0; (void)b1; (void)l4; (void)lh4; (void)xo; (void)gx;\n";
@@ -288,16 +282,9 @@ std::string gen_row(const BlkParams &P, bool &ok) {
             put(s, "        { const hm::XSlot x_ = B.xs[%d]; const uint32_t t = (l ^ x_.wm) & x_.vm; "
                    "const uint32_t v = us3_at(x_.kofs2 | (lh4 ^ 0x%xu)) + R0own; a += t ? gx(x_.base + v) : xo; }\n",
                 (2 * c + 1) * HM_BLK_SX + k, (unsigned)P.xxa[c][1][k]);
-        put(s, "        const int e0 = B.hs[%d], e1 = B.hs[%d];\n", c, c + 1);
-        s += "        int e = e0;\n"
-             "        for (; e + 4 <= e1; e += 4) {\n"
-             "            const Sv v0 = gx(B.hb[e] + rb), v1 = gx(B.hb[e + 1] + rb);\n"
-             "            const Sv v2_ = gx(B.hb[e + 2] + rb), v3 = gx(B.hb[e + 3] + rb);\n"
-             "            a += (v0 + v1) + (v2_ + v3);\n"
-             "        }\n"
-             "        for (; e < e1; ++e) a += gx(B.hb[e] + rb);\n";
-        put(s, "        acc[%d] = a;\n        cnt[%d] = %d + (e1 - e0);\n    }\n", c, c,
-            P.ln[c][0] + P.ln[c][1] + P.ln[c][2] + P.xn[c][0] + P.xn[c][1]);
+        put(s, "        a += hm::blk_high_sum<Sv>(B, %d, Xg, r, gx);\n", c);
+        put(s, "        acc[%d] = a;\n        cnt[%d] = %d + (B.he[%d] - B.hs[%d]);\n    }\n", c, c,
+            P.ln[c][0] + P.ln[c][1] + P.ln[c][2] + P.xn[c][0] + P.xn[c][1], c, c);
     }
     s += "#undef XS\n}\n};\n";
     return s;
