@@ -8,10 +8,13 @@
 // 128-byte line (row-major [dim][32]), a warp serves VT rows with 32/VT lanes each, lane
 // l of a row holding vectors l*VT .. l*VT+VT-1, so the codec of a row runs once per
 // warp instruction for all of its vectors.  The rows of all sectors are cut into the
-// blocks of blk.cuh (one high word, all low words); a step is four phases separated by
-// grid barriers with bounded waits:
+// blocks of blk.cuh (one high word, all low words).  Every warp owns an equal share of
+// the rows (a fixed interval of the row order, cut on the host): it walks the blocks its
+// rows fall in, builds their exchange lists itself and writes one partial sum per sector
+// it touches, so no CTA barrier separates blocks and the sums come out in a fixed order.
+// A step is four phases separated by grid barriers with bounded waits:
 //   A  u = sigma H q - beta_prev sigma_prev q_prev over q_prev, alpha partials
-//   B  alpha per (sector, vector)
+//   B  alpha per (sector, vector): the sector's warp partials in order
 //   C  w = u - alpha sigma q over q_prev, |w|^2 partials
 //   D  beta, breakdown, sigma
 // Then per (sector, vector) the tridiagonal T is diagonalised on the device (implicit
@@ -21,6 +24,7 @@
 //   Z(T) = sum_A (D_A / R) sum_r sum_j tau e^{-(theta - e_ref)/T},
 //   E(T) = [same with theta inside] / Z(T)     (Z returned relative to e^{-e_ref/T}).
 #include <algorithm>
+#include <cstdlib>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -47,12 +51,26 @@ struct GridBar {
     int pad;
 };
 
+// A warp's share of the row phases: global rows [g0, g1) (all sectors' rows in order, which
+// is also the order of the blocks in `items`), the first of them in item it0; its partial
+// sums go to slots slot0, slot0 + 1, ... one per sector the rows touch, so the slots of a
+// sector are consecutive over the warps.
+struct FtRange {
+    uint64_t g0, g1;
+    uint32_t it0, slot0;
+};
+
 struct FtDev {
     // per (sector, vector) state, index s * FT_W + v
     double *sig_cur, *sig_prev, *beta_prev, *scale, *as;
     int *done, *nsteps;
     double *alpha, *beta;           // [(s * FT_W + v) * steps + j]
-    double *part;                   // [cta][s][v]
+    double *part;                   // [slot][v]: warp partials of the update phase (FtRange)
+    double *parta;                  // [sector][warp][v]: warp partials of the product phase
+    const uint32_t *ck_it0;         // [chunk]: the block holding the chunk's first row
+    const uint32_t *ck_cs;          // [nsec + 1]: sector s owns chunks ck_cs[s] .. ck_cs[s + 1] - 1
+    const FtRange *wr;              // [warp]
+    const uint32_t *slo;            // [nsec + 1]: sector s owns slots slo[s] .. slo[s + 1] - 1
     int *sec_active;                // [s]
     GridBar *bar;
     const uint32_t *items;          // (A << 16) | h, sorted by A
@@ -79,6 +97,7 @@ struct FtParams {
     BlkParams P;                    // block plan built with A = N (full binomial table)
     FtDev d;
     int nsec, R, steps, nitems;
+    uint32_t nchunks, ck_rows;      // product phase: chunks of ck_rows rows (a sector's last is shorter)
     unsigned nctas;
     uint64_t seed;
     uint64_t exact_mask;            // bit A set: sector A is diagonalised exactly
@@ -139,6 +158,10 @@ __global__ void k_ft_init(FtParams F) {
         d.q0[t] = val;
         d.q1[t] = 0.0f;
     }
+    // product-phase partials: the (sector, warp) pairs no chunk visits stay zero
+    const uint64_t npa = (uint64_t)F.nsec * F.nctas * (FT_NT / 32) * FT_W;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < npa; t += (uint64_t)gridDim.x * blockDim.x)
+        d.parta[t] = 0.0;
     const int nst = F.nsec * FT_W;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nst; t += gridDim.x * blockDim.x) {
         const int s = t / FT_W, v = t % FT_W;
@@ -157,25 +180,104 @@ __global__ void k_ft_init(FtParams F) {
     if (blockIdx.x == 0 && threadIdx.x == 0) { d.bar->count = 0; d.bar->gen = 0; d.bar->abort = 0; }
 }
 
-// adds the per-thread partials p (vectors v0..v0+VT-1 of row group grp in this warp) to
-// the CTA's accumulator of sector A in a fixed order, and clears them.  All threads of
-// the CTA call it; it contains barriers.
+// The warp's partials p[q] (vectors v0 + q of row group grp) summed over its VT row groups
+// in a fixed order and written to slot `slot` of part, then cleared.  All 32 lanes call it.
 template <int VT>
-__device__ __forceinline__ void ft_flush(ef::df *p, float *red, ef::df *cacc, int A, int warp, int grp, int v0) {
+__device__ __forceinline__ void ft_warp_flush(ef::df *p, double *part, uint32_t slot, int lane, int grp, int v0) {
+    constexpr int LPR = 32 / VT;                  // lanes per row group
 #pragma unroll
     for (int q = 0; q < VT; ++q) {
-        red[((warp * VT + grp) * FT_W + v0 + q) * 2] = p[q].hi;
-        red[((warp * VT + grp) * FT_W + v0 + q) * 2 + 1] = p[q].lo;
+        ef::df s = p[q];
+#pragma unroll
+        for (int g = 1; g < VT; ++g) {
+            const float hi = __shfl_sync(0xffffffffu, p[q].hi, lane + g * LPR);
+            const float lo = __shfl_sync(0xffffffffu, p[q].lo, lane + g * LPR);
+            s = ef::df_add(s, ef::df{hi, lo});
+        }
+        if (grp == 0) part[(size_t)slot * FT_W + v0 + q] = (double)s.hi + (double)s.lo;
         p[q] = ef::df{0.0f, 0.0f};
     }
-    __syncthreads();
-    if (threadIdx.x < FT_W) {
-        ef::df s = cacc[A * FT_W + threadIdx.x];
-        for (int w = 0; w < (FT_NT / 32) * VT; ++w)
-            s = ef::df_add(s, ef::df{red[(w * FT_W + threadIdx.x) * 2], red[(w * FT_W + threadIdx.x) * 2 + 1]});
-        cacc[A * FT_W + threadIdx.x] = s;
+}
+
+// Hop lists of block (h, k) for one warp: the valid high exchanges as row offsets,
+// compacted by class (lane e tests bonds e and e + 32, ballots give the positions), and
+// the targets of the cross exchanges.  The caller syncs the warp before and after.
+__device__ __forceinline__ void ft_warp_setup(const BlkParams &P, const BlkTabs &tb, uint32_t h, int k, uint32_t off,
+                                              const BlkShared &sh, int lane) {
+    int val[2] = {0, 0}, hoff[2] = {0, 0};
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int e = lane + 32 * half;
+        if (e < P.nhb) {
+            const int p = P.hb_p[e], q = P.hb_q[e];
+            val[half] = (((h >> p) ^ (h >> q)) & 1u) ? 1 : 0;
+            if (val[half]) hoff[half] = (int)(blk_off(P, tb, h ^ ((1u << p) | (1u << q)), k) - off);
+        }
     }
-    __syncthreads();
+    const uint32_t b0 = __ballot_sync(0xffffffffu, val[0]), b1 = __ballot_sync(0xffffffffu, val[1]);
+    const uint32_t below = (1u << lane) - 1u;
+    if (val[0]) sh.hcd[__popc(b0 & below)] = hoff[0];
+    if (val[1]) sh.hcd[__popc(b0) + __popc(b1 & below)] = hoff[1];
+    if (lane <= HM_BLK_MAXC) {                    // class c starts at the valid ones before hb_start[c]
+        const int e = P.hb_start[lane];
+        sh.hcs[lane] = e >= 32 ? __popc(b0) + __popc(e >= 64 ? b1 : b1 & ((1u << (e - 32)) - 1u))
+                               : __popc(b0 & ((1u << e) - 1u));
+    }
+    for (int e = lane; e < P.ncb; e += 32) {
+        const int q = P.cb_q[e];
+        const uint32_t bq = (h >> q) & 1u;
+        const int k2 = k + (bq ? 1 : -1);
+        const bool ok = k2 >= 0 && k2 <= P.K;
+        sh.cbq[e] = (uint8_t)bq;
+        sh.ck[e] = (int8_t)(ok ? k2 : -1);
+        sh.coff[e] = ok ? blk_off(P, tb, h ^ (1u << q), k2) : 0u;
+    }
+}
+
+// Per (sector, vector) sums of the warp partials: the slots of sector s, slo[s] ..
+// slo[s + 1] - 1, in a fixed order (16 strided chunks, then the chunks in order);
+// f(s, v, sum) runs on warp 0 of the CTA that owns sector s.  All threads call it.
+template <class F>
+__device__ __forceinline__ void ft_sector_sums(const FtParams &Fp, double *red, F &&f) {
+    const FtDev &d = Fp.d;
+    constexpr int NCH = FT_NT / FT_W;
+    const int v = threadIdx.x % FT_W, c = threadIdx.x / FT_W;
+    for (int s = blockIdx.x; s < Fp.nsec; s += gridDim.x) {
+        const uint32_t s0 = d.slo[s], s1 = d.slo[s + 1];
+        double a = 0.0;
+        for (uint32_t sl = s0 + c; sl < s1; sl += NCH) a += d.part[(size_t)sl * FT_W + v];
+        red[c * FT_W + v] = a;
+        __syncthreads();
+        if (c == 0) {
+            double t = 0.0;
+            for (int i = 0; i < NCH; ++i) t += red[i * FT_W + v];
+            f(s, v, t);
+        }
+        __syncthreads();
+    }
+}
+
+// Per (sector, vector) sums of the product-phase partials parta[s][w][v] over all warps w
+// in order (16 strided chunks, then the chunks in order); f(s, v, sum) runs on warp 0 of
+// the CTA that owns sector s.  All threads call it.
+template <class F>
+__device__ __forceinline__ void ft_sector_sums_a(const FtParams &Fp, double *red, unsigned nw, F &&f) {
+    const FtDev &d = Fp.d;
+    constexpr int NCH = FT_NT / FT_W;
+    const int v = threadIdx.x % FT_W, c = threadIdx.x / FT_W;
+    for (int s = blockIdx.x; s < Fp.nsec; s += gridDim.x) {
+        const double *ps = d.parta + (size_t)s * nw * FT_W;
+        double a = 0.0;
+        for (unsigned w = c; w < nw; w += NCH) a += ps[(size_t)w * FT_W + v];
+        red[c * FT_W + v] = a;
+        __syncthreads();
+        if (c == 0) {
+            double t = 0.0;
+            for (int i = 0; i < NCH; ++i) t += red[i * FT_W + v];
+            f(s, v, t);
+        }
+        __syncthreads();
+    }
 }
 
 // VT consecutive floats of one row (16- or 8-byte aligned for VT = 4, 2), read-only path
@@ -192,184 +294,211 @@ __device__ __forceinline__ void ft_ld(const float *p, float *v) {
     }
 }
 
+// sector of a global row (few sectors: linear search)
+__device__ __forceinline__ int ft_sector_of(const FtDev &d, int nsec, uint64_t g) {
+    int A = 0;
+    while (A + 1 < nsec && d.rowoff[A + 1] <= g) ++A;
+    return A;
+}
+
+// per-warp shared slice: hop lists | sigma, gamma of the current sector | alpha sigma
+__host__ __device__ __forceinline__ size_t ft_warp_bytes(int max_block) {
+    return al16f(blk_shared_bytes(max_block)) + al16f(FT_W * 4 * 3);
+}
+
 // ---- the persistent kernel ---------------------------------------------------------------
-// shared layout: block tables | two copies of the block metadata (hop lists) | two copies
-// of sigma/gamma of the item's sector | alpha*sigma | per-warp partials | per-CTA
-// accumulators [nsec][FT_W] (df).  The block's own rows are read through L1 (a block of
-// K = 11 is at most 59 KB).
+// Every warp owns the global rows [g0, g1) of its FtRange (rows of all sectors in order,
+// balanced over the warps) in both row phases, so no CTA barrier separates blocks: a
+// warp walks the blocks its rows fall in, builds their hop lists itself, and writes one
+// partial per sector it touches.  Shared layout: block tables | per-warp slices | the
+// sector-sum scratch.  A block's own rows are read through L1.
 template <int NC, int VT>
 __global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
     const BlkParams &P = F.P;
     const FtDev &d = F.d;
     extern __shared__ __align__(16) unsigned char smem[];
     const BlkTabs tb = stage_blk_tables(P, smem);
-    size_t o = al16f(P.tab_bytes);
-    // per-block metadata and sigma/gamma, double-buffered: the setup of a block writes one
-    // copy while slower warps still read the other (one barrier per block)
-    unsigned char *shb = smem + o;
-    const size_t shs = blk_shared_bytes(P.max_block);
-    o += 2 * shs;
-    float *sgb = (float *)(smem + o); o += al16f(FT_W * 4 * 2 * 2);   // [2][sigma, gamma]
-    float *sg = (float *)(smem + o); o += al16f(FT_W * 4 * 3);   // phase C: alpha*sigma at [2 FT_W]
-    float *red = (float *)(smem + o); o += al16f((size_t)(FT_NT / 32) * 4 * 2 * FT_W * 4);   // [warp*VT+grp][v] df
-    ef::df *cacc = (ef::df *)(smem + o);                          // [nsec][FT_W]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int lpr = 32 / VT;                       // lanes per row
-    const int grp = lane / lpr, li = lane % lpr;   // row group in the warp, lane in row
+    const size_t wbytes = ft_warp_bytes(P.max_block);
+    unsigned char *ws = smem + al16f(P.tab_bytes) + warp * wbytes;
+    const BlkShared sh = blk_carve(ws, P.max_block);
+    float *sgw = (float *)(ws + al16f(blk_shared_bytes(P.max_block)));   // [sigma | gamma | alpha sigma][FT_W]
+    double *red = (double *)(smem + al16f(P.tab_bytes) + (FT_NT / 32) * wbytes);
+    constexpr int LPR = 32 / VT;                   // lanes per row
+    const int grp = lane / LPR, li = lane % LPR;   // row group in the warp, lane in row
     const int v0 = li * VT;                        // first vector of this lane
-    const int nwarps = FT_NT / 32;
+    const unsigned nw = gridDim.x * (FT_NT / 32), gw = blockIdx.x * (FT_NT / 32) + warp;
+    const FtRange rg = d.wr[gw];
     const unsigned long long LIMIT = 5000000000ull;   // 5 s per barrier
-    for (int t = threadIdx.x; t < F.nsec * FT_W; t += FT_NT) cacc[t] = ef::df{0.0f, 0.0f};
     __syncthreads();
 
     for (int j = 0; j < F.steps; ++j) {
+        const float *qc = (j & 1) ? d.q1 : d.q0;
+        float *qp = (j & 1) ? d.q0 : d.q1;
         // ---------------- phase A: products ----------------
-        // dot partials stay in registers over consecutive items of one sector (items are
-        // sorted by sector) and are reduced into the CTA's accumulator when it changes
-        ef::df dot[VT];
+        // chunk c of ck_rows rows goes to warp c mod W, so all warps sweep the rows together
+        // and the targets of nearby exchanges are still in L2; a warp's partial for sector s
+        // sums its chunks of s and goes to parta[s][warp]
+        {
+            ef::df dot[VT];
 #pragma unroll
-        for (int q = 0; q < VT; ++q) dot[q] = ef::df{0.0f, 0.0f};
-        int curA = -1, ib = 0;
-        for (int it = blockIdx.x; it < F.nitems; it += gridDim.x) {
-            const uint32_t item = d.items[it];
-            const int A = (int)(item >> 16);
-            const uint32_t h = item & 0xFFFFu;
-            if (!d.sec_active[A]) continue;
-            if (A != curA) {
-                if (curA >= 0) ft_flush<VT>(dot, red, cacc, curA, warp, grp, v0);
-                curA = A;
-            }
-            const int k = A - __popc(h);
-            const uint64_t base = d.rowoff[A];
-            // block setup (offsets inside the sector; rows of the sector start at base)
-            const BlkShared sh = blk_carve(shb + ib * shs, P.max_block);
-            float *sgi = sgb + ib * 2 * FT_W;
-            ib ^= 1;
-            uint32_t off;
-            const int n = blk_setup_block(P, tb, h, k, sh, &off);
-            if (threadIdx.x >= 64 && threadIdx.x < 64 + FT_W) {
-                const int sv = A * FT_W + threadIdx.x - 64;
-                sgi[threadIdx.x - 64] = (float)d.sig_cur[sv];
-                sgi[FT_W + threadIdx.x - 64] = (float)(d.beta_prev[sv] * d.sig_prev[sv]);
-            }
-            __syncthreads();
-            const float *qc = (j & 1) ? d.q1 : d.q0;
-            float *qp = (j & 1) ? d.q0 : d.q1;
-            const float *Xb = qc + (base + off) * FT_W + v0;   // the block's rows, this lane's vectors
-            const uint16_t *Uk = tb.U + k * P.nb1;
-            const uint16_t *lw = P.lw + P.lwoff[k];
-            for (int r = warp * VT + grp; r < n; r += nwarps * VT) {
-                const uint32_t l = __ldg(lw + r);
-                float acc[NC][VT];
-                int cnt[NC];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    float *ac = acc[c];
-#pragma unroll
-                    for (int q = 0; q < VT; ++q) ac[q] = 0.0f;
-                    int mc = blk_low_hops(P, tb, c, l, (uint32_t)r, Uk, [&](uint32_t r2) {
-                        float xv[VT];
-                        ft_ld<VT>(Xb + (size_t)r2 * FT_W, xv);
-#pragma unroll
-                        for (int q = 0; q < VT; ++q) ac[q] += xv[q];
-                    });
-                    mc += blk_cross_hops(P, tb, c, l, sh, [&](uint32_t jj) {
-                        const float *xr = qc + (base + jj) * FT_W + v0;
-#pragma unroll
-                        for (int q = 0; q < VT; ++q) ac[q] += __ldg(xr + q);
-                    });
-                    for (int e = sh.hcs[c]; e < sh.hcs[c + 1]; ++e) {
-                        const uint64_t jr = base + (uint64_t)((int64_t)(off + (uint32_t)r) + sh.hcd[e]);
-                        const float *xr = qc + jr * FT_W + v0;
-#pragma unroll
-                        for (int q = 0; q < VT; ++q) ac[q] += __ldg(xr + q);
+            for (int q = 0; q < VT; ++q) dot[q] = ef::df{0.0f, 0.0f};
+            int curA = -1;
+            bool act = false;
+            for (uint32_t c = gw; c < F.nchunks; c += nw) {
+                int A = curA < 0 ? 0 : curA;
+                while (d.ck_cs[A + 1] <= c) ++A;
+                const uint64_t g0 = d.rowoff[A] + (uint64_t)(c - d.ck_cs[A]) * F.ck_rows;
+                const uint64_t g1 = g0 + F.ck_rows < d.rowoff[A + 1] ? g0 + F.ck_rows : d.rowoff[A + 1];
+                if (A != curA) {
+                    if (curA >= 0) ft_warp_flush<VT>(dot, d.parta, (uint32_t)curA * nw + gw, lane, grp, v0);
+                    curA = A;
+                    act = d.sec_active[A] != 0;
+                    __syncwarp();
+                    if (act) {
+                        const int sv = A * FT_W + lane;
+                        sgw[lane] = (float)d.sig_cur[sv];
+                        sgw[FT_W + lane] = (float)(d.beta_prev[sv] * d.sig_prev[sv]);
                     }
-                    cnt[c] = mc + (sh.hcs[c + 1] - sh.hcs[c]);
                 }
-                const uint64_t row = base + off + (uint32_t)r;
-                float xov[VT];
-                ft_ld<VT>(Xb + (size_t)r * FT_W, xov);
+                if (!act) continue;
+                const uint64_t base = d.rowoff[A];
+                for (uint32_t it = d.ck_it0[c]; it < (uint32_t)F.nitems; ++it) {
+                    const uint32_t item = d.items[it];
+                    if ((int)(item >> 16) != A) break;     // the chunk ends at the sector's end
+                    const uint32_t h = item & 0xFFFFu;
+                    const int k = A - __popc(h);
+                    const uint32_t off = blk_off(P, tb, h, k);
+                    const uint32_t n = tb.C[P.K * (P.A + 1) + k];
+                    const uint64_t ig0 = base + off;
+                    if (ig0 >= g1) break;
+                    const uint32_t ra = ig0 < g0 ? (uint32_t)(g0 - ig0) : 0u;
+                    const uint32_t rb = ig0 + n > g1 ? (uint32_t)(g1 - ig0) : n;
+                    __syncwarp();                  // the previous block's lists are read no more
+                    ft_warp_setup(P, tb, h, k, off, sh, lane);
+                    __syncwarp();
+                    const float *Xb = qc + ig0 * FT_W + v0;   // the block's rows, this lane's vectors
+                    const uint16_t *Uk = tb.U + k * P.nb1;
+                    const uint16_t *lw = P.lw + P.lwoff[k];
+                    for (uint32_t r = ra + grp; r < rb; r += VT) {
+                        const uint32_t l = __ldg(lw + r);
+                        float acc[NC][VT];
+                        int cnt[NC];
 #pragma unroll
-                for (int q = 0; q < VT; ++q) {
-                    const float xo = xov[q];
-                    float y = 0.0f;
+                        for (int cl = 0; cl < NC; ++cl) {
+                            float *ac = acc[cl];
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) y += P.gq[c] * (2.0f * acc[c][q] + (float)(P.ntot[c] - 2 * cnt[c]) * xo);
-                    const float u = sgi[v0 + q] * y - sgi[FT_W + v0 + q] * qp[row * FT_W + v0 + q];
-                    qp[row * FT_W + v0 + q] = u;
-                    dot[q] = ef::df_add(dot[q], ef::two_prod(sgi[v0 + q] * xo, u));
+                            for (int q = 0; q < VT; ++q) ac[q] = 0.0f;
+                            int mc = blk_low_hops(P, tb, cl, l, r, Uk, [&](uint32_t r2) {
+                                float xv[VT];
+                                ft_ld<VT>(Xb + (size_t)r2 * FT_W, xv);
+#pragma unroll
+                                for (int q = 0; q < VT; ++q) ac[q] += xv[q];
+                            });
+                            mc += blk_cross_hops(P, tb, cl, l, sh, [&](uint32_t jj) {
+                                float xv[VT];
+                                ft_ld<VT>(qc + (base + jj) * FT_W + v0, xv);
+#pragma unroll
+                                for (int q = 0; q < VT; ++q) ac[q] += xv[q];
+                            });
+                            // high exchanges: four independent gathers in flight (the far ones miss L2)
+                            const int e1 = sh.hcs[cl + 1];
+                            int e = sh.hcs[cl];
+                            for (; e + 4 <= e1; e += 4) {
+                                float x0[VT], x1[VT], x2[VT], x3[VT];
+                                ft_ld<VT>(Xb + (int64_t)((int64_t)r + sh.hcd[e]) * FT_W, x0);
+                                ft_ld<VT>(Xb + (int64_t)((int64_t)r + sh.hcd[e + 1]) * FT_W, x1);
+                                ft_ld<VT>(Xb + (int64_t)((int64_t)r + sh.hcd[e + 2]) * FT_W, x2);
+                                ft_ld<VT>(Xb + (int64_t)((int64_t)r + sh.hcd[e + 3]) * FT_W, x3);
+#pragma unroll
+                                for (int q = 0; q < VT; ++q) ac[q] += (x0[q] + x1[q]) + (x2[q] + x3[q]);
+                            }
+                            for (; e < e1; ++e) {
+                                float xv[VT];
+                                ft_ld<VT>(Xb + (int64_t)((int64_t)r + sh.hcd[e]) * FT_W, xv);
+#pragma unroll
+                                for (int q = 0; q < VT; ++q) ac[q] += xv[q];
+                            }
+                            cnt[cl] = mc + (sh.hcs[cl + 1] - sh.hcs[cl]);
+                        }
+                        const uint64_t row = ig0 + r;
+                        float xov[VT];
+                        ft_ld<VT>(Xb + (size_t)r * FT_W, xov);
+#pragma unroll
+                        for (int q = 0; q < VT; ++q) {
+                            const float xo = xov[q];
+                            float y = 0.0f;
+#pragma unroll
+                            for (int cl = 0; cl < NC; ++cl)
+                                y += P.gq[cl] * (2.0f * acc[cl][q] + (float)(P.ntot[cl] - 2 * cnt[cl]) * xo);
+                            const float u = sgw[v0 + q] * y - sgw[FT_W + v0 + q] * qp[row * FT_W + v0 + q];
+                            qp[row * FT_W + v0 + q] = u;
+                            dot[q] = ef::df_add(dot[q], ef::two_prod(sgw[v0 + q] * xo, u));
+                        }
+                    }
                 }
             }
-        }
-        if (curA >= 0) ft_flush<VT>(dot, red, cacc, curA, warp, grp, v0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < F.nsec * FT_W; t += FT_NT) {
-            d.part[(size_t)blockIdx.x * F.nsec * FT_W + t] = (double)cacc[t].hi + (double)cacc[t].lo;
-            cacc[t] = ef::df{0.0f, 0.0f};
+            if (curA >= 0) ft_warp_flush<VT>(dot, d.parta, (uint32_t)curA * nw + gw, lane, grp, v0);
         }
         if (!grid_sync(d.bar, F.nctas, LIMIT)) return;
         // ---------------- phase B: alpha ----------------
-        for (int t = blockIdx.x * FT_NT + threadIdx.x; t < F.nsec * FT_W; t += gridDim.x * FT_NT) {
-            if (d.done[t]) continue;
-            double a = 0.0;
-            for (unsigned c = 0; c < F.nctas; ++c) a += d.part[(size_t)c * F.nsec * FT_W + t];
+        ft_sector_sums_a(F, red, nw, [&](int s, int v, double a) {
+            const int t = s * FT_W + v;
+            if (d.done[t]) return;
             d.alpha[(size_t)t * F.steps + j] = a;
             d.scale[t] = fmax(d.scale[t], fabs(a));
             d.as[t] = a * d.sig_cur[t];
-        }
+        });
         if (!grid_sync(d.bar, F.nctas, LIMIT)) return;
-        // ---------------- phase C: update ----------------
-        ef::df nn[VT];
+        // ---------------- phase C: update (a stream over the warp's rows) ----------------
+        // lane: float4 number lane % 8 of a row, i.e. vectors 4 (lane % 8) .. + 3; the four
+        // lanes of one float4 position are row groups 0..3 (ft_warp_flush<4> layout)
+        if (rg.g0 < rg.g1) {
+            ef::df nn[4];
 #pragma unroll
-        for (int q = 0; q < VT; ++q) nn[q] = ef::df{0.0f, 0.0f};
-        curA = -1;
-        for (int it = blockIdx.x; it < F.nitems; it += gridDim.x) {
-            const uint32_t item = d.items[it];
-            const int A = (int)(item >> 16);
-            const uint32_t h = item & 0xFFFFu;
-            if (!d.sec_active[A]) continue;
-            if (A != curA) {
-                if (curA >= 0) ft_flush<VT>(nn, red, cacc, curA, warp, grp, v0);
-                curA = A;
-            }
-            const int k = A - __popc(h);
-            const uint32_t off = blk_off(P, tb, h, k);
-            const int n = (int)tb.C[P.K * (P.A + 1) + k];
-            const uint64_t base = d.rowoff[A] + off;
-            __syncthreads();
-            if (threadIdx.x < FT_W) sg[2 * FT_W + threadIdx.x] = (float)d.as[A * FT_W + threadIdx.x];
-            __syncthreads();
-            const float *qc = (j & 1) ? d.q1 : d.q0;
-            float *qp = (j & 1) ? d.q0 : d.q1;
-            for (int r = warp * VT + grp; r < n; r += nwarps * VT) {
-                const uint64_t row = base + (uint32_t)r;
+            for (int q = 0; q < 4; ++q) nn[q] = ef::df{0.0f, 0.0f};
+            const int c4 = lane & 7, g4 = lane >> 3;
+            int A = ft_sector_of(d, F.nsec, rg.g0);
+            uint32_t slot = rg.slot0;
+            for (;; ++A, ++slot) {
+                const uint64_t a0 = rg.g0 > d.rowoff[A] ? rg.g0 : d.rowoff[A];
+                const uint64_t a1 = rg.g1 < d.rowoff[A + 1] ? rg.g1 : d.rowoff[A + 1];
+                if (d.sec_active[A]) {
+                    __syncwarp();
+                    sgw[2 * FT_W + lane] = (float)d.as[A * FT_W + lane];
+                    __syncwarp();
+                    float as4[4];
 #pragma unroll
-                for (int q = 0; q < VT; ++q) {
-                    const uint64_t ix = row * FT_W + v0 + q;
-                    const float w = qp[ix] - sg[2 * FT_W + v0 + q] * qc[ix];
-                    qp[ix] = w;
-                    nn[q] = ef::df_add(nn[q], ef::two_prod(w, w));
+                    for (int q = 0; q < 4; ++q) as4[q] = sgw[2 * FT_W + 4 * c4 + q];
+                    for (uint64_t row = a0 + g4; row < a1; row += 4) {
+                        const size_t ix = row * FT_W + 4 * c4;
+                        const float4 u = *(const float4 *)(qp + ix);
+                        const float4 x = __ldcs((const float4 *)(qc + ix));
+                        float4 w;
+                        w.x = u.x - as4[0] * x.x; w.y = u.y - as4[1] * x.y;
+                        w.z = u.z - as4[2] * x.z; w.w = u.w - as4[3] * x.w;
+                        *(float4 *)(qp + ix) = w;
+                        nn[0] = ef::df_add(nn[0], ef::two_prod(w.x, w.x));
+                        nn[1] = ef::df_add(nn[1], ef::two_prod(w.y, w.y));
+                        nn[2] = ef::df_add(nn[2], ef::two_prod(w.z, w.z));
+                        nn[3] = ef::df_add(nn[3], ef::two_prod(w.w, w.w));
+                    }
                 }
+                ft_warp_flush<4>(nn, d.part, slot, lane, g4, 4 * c4);
+                if (a1 >= rg.g1) break;
             }
-        }
-        if (curA >= 0) ft_flush<VT>(nn, red, cacc, curA, warp, grp, v0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < F.nsec * FT_W; t += FT_NT) {
-            d.part[(size_t)blockIdx.x * F.nsec * FT_W + t] = (double)cacc[t].hi + (double)cacc[t].lo;
-            cacc[t] = ef::df{0.0f, 0.0f};
         }
         if (!grid_sync(d.bar, F.nctas, LIMIT)) return;
         // ---------------- phase D: beta ----------------
-        for (int t = blockIdx.x * FT_NT + threadIdx.x; t < F.nsec * FT_W; t += gridDim.x * FT_NT) {
+        ft_sector_sums(F, red, [&](int s, int v, double sum) {
+            const int t = s * FT_W + v;
             bool act = false;
             if (!d.done[t]) {
-                double s = 0.0;
-                for (unsigned c = 0; c < F.nctas; ++c) s += d.part[(size_t)c * F.nsec * FT_W + t];
-                const double b = sqrt(s);
+                const double b = sqrt(sum);
                 d.beta[(size_t)t * F.steps + j] = b;
                 d.nsteps[t] = j + 1;
                 // stop when beta is at the noise floor or the sector is exhausted
-                if (b <= FT_TOL * d.scale[t] || (uint32_t)(j + 1) >= d.secdim[t / FT_W]) {
+                if (b <= FT_TOL * d.scale[t] || (uint32_t)(j + 1) >= d.secdim[s]) {
                     d.done[t] = 1;
                     d.sig_cur[t] = 0.0;
                     d.sig_prev[t] = 0.0;
@@ -383,10 +512,10 @@ __global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
                     act = true;
                 }
             }
-            // a sector stays active while any of its vectors runs (a warp holds one sector)
+            // a sector stays active while any of its vectors runs (warp 0 holds one sector)
             const unsigned any = __ballot_sync(0xffffffffu, act);
-            if ((t & 31) == 0) d.sec_active[t / FT_W] = any != 0u;
-        }
+            if (v == 0) d.sec_active[s] = any != 0u;
+        });
         if (!grid_sync(d.bar, F.nctas, LIMIT)) return;
     }
 }
@@ -597,7 +726,7 @@ __global__ void k_ft_thermo(FtParams F, const double *temps, int n_t) {
 
 // ---- host --------------------------------------------------------------------------------
 struct FtLayout {
-    size_t q0, q1, st, ab, part, sec, bar, items, rowoff, secdim, theta, tau, mlen, therm, temps, eigs,
+    size_t q0, q1, st, ab, part, wr, slo, parta, ckit, ckcs, sec, bar, items, rowoff, secdim, theta, tau, mlen, therm, temps, eigs,
         xcd, xmat, total;
 };
 
@@ -614,7 +743,7 @@ static int ft_choose_K(int N) {
 }
 
 static FtLayout ft_layout(int N, int nsec, int R, int steps, int nitems, int nctas, int n_t, size_t xcd_words,
-                          size_t xmat_doubles) {
+                          size_t xmat_doubles, size_t nchunks) {
     (void)R;
     FtLayout L{};
     auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -625,7 +754,13 @@ static FtLayout ft_layout(int N, int nsec, int R, int steps, int nitems, int nct
     L.q1 = o; o += a(rows * FT_W * 4);
     L.st = o; o += a(nst * 8 * 5 + nst * 4 * 2);
     L.ab = o; o += a(nst * (size_t)steps * 8 * 2);
-    L.part = o; o += a((size_t)nctas * nst * 8);
+    const size_t nslots = (size_t)nctas * (FT_NT / 32) + nsec + 1;   // bound on the warp-sector pairs
+    L.part = o; o += a(nslots * FT_W * 8);
+    L.wr = o; o += a((size_t)nctas * (FT_NT / 32) * sizeof(FtRange));
+    L.slo = o; o += a((size_t)(nsec + 1) * 4);
+    L.parta = o; o += a((size_t)nsec * nctas * (FT_NT / 32) * FT_W * 8);
+    L.ckit = o; o += a((nchunks > 0 ? nchunks : 1) * 4);
+    L.ckcs = o; o += a((size_t)(nsec + 1) * 4);
     L.sec = o; o += a(FT_MAXS * 4);
     L.bar = o; o += a(sizeof(GridBar));
     L.items = o; o += a((size_t)nitems * 4);
@@ -653,13 +788,62 @@ static const void *pick_kernel(int nc, int vt) {
 }
 
 static size_t ft_smem(const BlkParams &P, int nsec) {
+    (void)nsec;
     size_t o = al16f(P.tab_bytes);
-    o += 2 * blk_shared_bytes(P.max_block);
-    o += al16f(FT_W * 4 * 2 * 2);
-    o += al16f(FT_W * 4 * 3);
-    o += al16f((size_t)(FT_NT / 32) * 4 * 2 * FT_W * 4);
-    o += al16f((size_t)nsec * FT_W * sizeof(ef::df));
+    o += (FT_NT / 32) * ft_warp_bytes(P.max_block);
+    o += al16f((size_t)(FT_NT / FT_W) * FT_W * 8);    // sector-sum scratch
     return o;
+}
+
+// The warps' row ranges (equal shares of all 2^N rows) and their partial-sum slots.
+// items: the blocks (A << 16 | h) in row order; C(K, k) rows each.
+static void ft_ranges(int n_sites, int K, const hm_basis &full, const std::vector<uint32_t> &items, int W,
+                      uint32_t ck_rows, std::vector<FtRange> *wr, std::vector<uint32_t> *slo,
+                      std::vector<uint32_t> *ck_it0, std::vector<uint32_t> *ck_cs) {
+    const int N = n_sites, nsec = N + 1, Wd = N + 1;
+    std::vector<uint64_t> r0(items.size() + 1, 0);
+    for (size_t i = 0; i < items.size(); ++i) {
+        const int A = (int)(items[i] >> 16);
+        const int k = A - __builtin_popcount(items[i] & 0xFFFFu);
+        r0[i + 1] = r0[i] + full.D[(size_t)K * Wd + k];
+    }
+    std::vector<uint64_t> rowoff(nsec + 1, 0);
+    for (int A = 0; A < nsec; ++A) rowoff[A + 1] = rowoff[A] + full.D[(size_t)N * Wd + A];
+    const uint64_t T = r0.back();
+    auto sector_of = [&](uint64_t g) { return (int)(std::upper_bound(rowoff.begin(), rowoff.end(), g) - rowoff.begin()) - 1; };
+    wr->assign(W, FtRange{});
+    std::vector<int> slot_sec;
+    for (int w = 0; w < W; ++w) {
+        FtRange &g = (*wr)[w];
+        g.g0 = T * (uint64_t)w / (uint64_t)W;
+        g.g1 = T * (uint64_t)(w + 1) / (uint64_t)W;
+        g.slot0 = (uint32_t)slot_sec.size();
+        if (g.g0 >= g.g1) { g.it0 = (uint32_t)items.size(); continue; }
+        g.it0 = (uint32_t)(std::upper_bound(r0.begin(), r0.end(), g.g0) - r0.begin() - 1);
+        for (int A = sector_of(g.g0); A <= sector_of(g.g1 - 1); ++A) slot_sec.push_back(A);
+    }
+    slo->assign(nsec + 1, 0);
+    size_t i = 0;
+    for (int s = 0; s <= nsec; ++s) {
+        while (i < slot_sec.size() && slot_sec[i] < s) ++i;
+        (*slo)[s] = (uint32_t)i;
+    }
+    // product-phase chunks: each sector cut into runs of ck_rows rows
+    ck_it0->clear();
+    ck_cs->assign(nsec + 1, 0);
+    for (int A = 0; A < nsec; ++A) {
+        (*ck_cs)[A] = (uint32_t)ck_it0->size();
+        for (uint64_t g = rowoff[A]; g < rowoff[A + 1]; g += ck_rows)
+            ck_it0->push_back((uint32_t)(std::upper_bound(r0.begin(), r0.end(), g) - r0.begin() - 1));
+    }
+    (*ck_cs)[nsec] = (uint32_t)ck_it0->size();
+}
+
+// rows per product-phase chunk: HM_FT_CHUNK (16..1024), default 64
+static uint32_t ft_chunk_rows() {
+    const char *e = getenv("HM_FT_CHUNK");
+    const int v = e ? atoi(e) : 64;
+    return (uint32_t)(v < 16 ? 16 : v > 1024 ? 1024 : v);
 }
 
 // vectors-per-lane tiling chosen by timing each candidate once per (N, bonds) shape
@@ -673,6 +857,10 @@ struct FtSetup {
     size_t smem;
     int nctas;
     std::vector<uint32_t> xcd;       // CD tables of the exactly diagonalised sectors
+    std::vector<FtRange> wr;         // per warp
+    std::vector<uint32_t> slo;       // per sector, + 1
+    std::vector<uint32_t> ck_it0;    // per product-phase chunk
+    std::vector<uint32_t> ck_cs;     // per sector, + 1
 };
 
 static int ft_prepare(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_t *v,
@@ -741,7 +929,12 @@ static int ft_prepare(int n_sites, int two_s, int n_bonds, const int32_t *u, con
     if (per_sm < 1) return fail(HM_EINVAL, "ftlm_run: kernel does not fit on an SM");
     S->nctas = sm_count() * per_sm;   // cooperative: all resident
     S->F.nctas = (unsigned)S->nctas;
-    S->L = ft_layout(n_sites, nsec, R, steps, S->F.nitems, S->nctas, n_t, S->xcd.size(), (size_t)xmat);
+    S->F.ck_rows = ft_chunk_rows();
+    ft_ranges(n_sites, K, S->full, *items, S->nctas * (FT_NT / 32), S->F.ck_rows, &S->wr, &S->slo, &S->ck_it0,
+              &S->ck_cs);
+    S->F.nchunks = (uint32_t)S->ck_it0.size();
+    S->L = ft_layout(n_sites, nsec, R, steps, S->F.nitems, S->nctas, n_t, S->xcd.size(), (size_t)xmat,
+                     S->F.nchunks);
     return HM_OK;
 }
 
@@ -758,6 +951,11 @@ static void ft_bind(FtSetup *S, unsigned char *w) {
     d.alpha = (double *)(w + L.ab);
     d.beta = d.alpha + nst * S->F.steps;
     d.part = (double *)(w + L.part);
+    d.wr = (const FtRange *)(w + L.wr);
+    d.slo = (const uint32_t *)(w + L.slo);
+    d.parta = (double *)(w + L.parta);
+    d.ck_it0 = (const uint32_t *)(w + L.ckit);
+    d.ck_cs = (const uint32_t *)(w + L.ckcs);
     d.sec_active = (int *)(w + L.sec);
     d.bar = (GridBar *)(w + L.bar);
     d.items = (const uint32_t *)(w + L.items);
@@ -839,6 +1037,11 @@ int ftlm_run(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_
     HM_CUDA(cudaMemcpyAsync(w + S.L.items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
     HM_CUDA(cudaMemcpyAsync(w + S.L.rowoff, rowoff.data(), rowoff.size() * 8, cudaMemcpyHostToDevice, st));
     HM_CUDA(cudaMemcpyAsync(w + S.L.secdim, dims.data(), dims.size() * 4, cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(w + S.L.wr, S.wr.data(), S.wr.size() * sizeof(FtRange), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(w + S.L.slo, S.slo.data(), S.slo.size() * 4, cudaMemcpyHostToDevice, st));
+    if (!S.ck_it0.empty())
+        HM_CUDA(cudaMemcpyAsync(w + S.L.ckit, S.ck_it0.data(), S.ck_it0.size() * 4, cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(w + S.L.ckcs, S.ck_cs.data(), S.ck_cs.size() * 4, cudaMemcpyHostToDevice, st));
     if (!S.xcd.empty())
         HM_CUDA(cudaMemcpyAsync(w + S.L.xcd, S.xcd.data(), S.xcd.size() * 4, cudaMemcpyHostToDevice, st));
     double *d_temps = (double *)(w + S.L.temps);
