@@ -67,6 +67,7 @@ struct FtDev {
     double *alpha, *beta;           // [(s * FT_W + v) * steps + j]
     double *part;                   // [slot][v]: warp partials of the update phase (FtRange)
     double *parta;                  // [sector][warp][v]: warp partials of the product phase
+    double *partc;                  // [sector][cta][v]: the same summed over each CTA's warps
     const uint32_t *ck_it0;         // [chunk]: the block holding the chunk's first row
     const uint32_t *ck_cs;          // [nsec + 1]: sector s owns chunks ck_cs[s] .. ck_cs[s + 1] - 1
     const FtRange *wr;              // [warp]
@@ -244,8 +245,16 @@ __device__ __forceinline__ void ft_sector_sums(const FtParams &Fp, double *red, 
     const int v = threadIdx.x % FT_W, c = threadIdx.x / FT_W;
     for (int s = blockIdx.x; s < Fp.nsec; s += gridDim.x) {
         const uint32_t s0 = d.slo[s], s1 = d.slo[s + 1];
-        double a = 0.0;
-        for (uint32_t sl = s0 + c; sl < s1; sl += NCH) a += d.part[(size_t)sl * FT_W + v];
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        uint32_t sl = s0 + c;
+        for (; sl + 3 * NCH < s1; sl += 4 * NCH) {
+            a0 += d.part[(size_t)sl * FT_W + v];
+            a1 += d.part[(size_t)(sl + NCH) * FT_W + v];
+            a2 += d.part[(size_t)(sl + 2 * NCH) * FT_W + v];
+            a3 += d.part[(size_t)(sl + 3 * NCH) * FT_W + v];
+        }
+        for (; sl < s1; sl += NCH) a0 += d.part[(size_t)sl * FT_W + v];
+        const double a = (a0 + a1) + (a2 + a3);
         red[c * FT_W + v] = a;
         __syncthreads();
         if (c == 0) {
@@ -257,18 +266,27 @@ __device__ __forceinline__ void ft_sector_sums(const FtParams &Fp, double *red, 
     }
 }
 
-// Per (sector, vector) sums of the product-phase partials parta[s][w][v] over all warps w
-// in order (16 strided chunks, then the chunks in order); f(s, v, sum) runs on warp 0 of
-// the CTA that owns sector s.  All threads call it.
+// Per (sector, vector) sums of the product-phase partials partc[s][b][v] over all CTAs b
+// in a fixed order (16 strided chunks of four running sums, then the chunks in order);
+// f(s, v, sum) runs on warp 0 of the CTA that owns sector s.  All threads call it.
 template <class F>
-__device__ __forceinline__ void ft_sector_sums_a(const FtParams &Fp, double *red, unsigned nw, F &&f) {
+__device__ __forceinline__ void ft_sector_sums_a(const FtParams &Fp, double *red, F &&f) {
     const FtDev &d = Fp.d;
     constexpr int NCH = FT_NT / FT_W;
     const int v = threadIdx.x % FT_W, c = threadIdx.x / FT_W;
+    const unsigned nb = Fp.nctas;
     for (int s = blockIdx.x; s < Fp.nsec; s += gridDim.x) {
-        const double *ps = d.parta + (size_t)s * nw * FT_W;
-        double a = 0.0;
-        for (unsigned w = c; w < nw; w += NCH) a += ps[(size_t)w * FT_W + v];
+        const double *ps = d.partc + (size_t)s * nb * FT_W;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        unsigned b = c;
+        for (; b + 3 * NCH < nb; b += 4 * NCH) {
+            a0 += ps[(size_t)b * FT_W + v];
+            a1 += ps[(size_t)(b + NCH) * FT_W + v];
+            a2 += ps[(size_t)(b + 2 * NCH) * FT_W + v];
+            a3 += ps[(size_t)(b + 3 * NCH) * FT_W + v];
+        }
+        for (; b < nb; b += NCH) a0 += ps[(size_t)b * FT_W + v];
+        const double a = (a0 + a1) + (a2 + a3);
         red[c * FT_W + v] = a;
         __syncthreads();
         if (c == 0) {
@@ -439,10 +457,21 @@ __global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
                 }
             }
             if (curA >= 0) ft_warp_flush<VT>(dot, d.parta, (uint32_t)curA * nw + gw, lane, grp, v0);
+            // the CTA's warp partials, summed in warp order (written by this CTA just now)
+            __syncthreads();
+            const unsigned w0 = blockIdx.x * (FT_NT / 32);
+            for (int t = threadIdx.x; t < F.nsec * FT_W; t += FT_NT) {
+                const int s = t / FT_W, v = t % FT_W;
+                const double *ps = d.parta + ((size_t)s * nw + w0) * FT_W + v;
+                double a = 0.0;
+#pragma unroll
+                for (int i = 0; i < FT_NT / 32; ++i) a += ps[(size_t)i * FT_W];
+                d.partc[((size_t)s * F.nctas + blockIdx.x) * FT_W + v] = a;
+            }
         }
         if (!grid_sync(d.bar, F.nctas, LIMIT)) return;
         // ---------------- phase B: alpha ----------------
-        ft_sector_sums_a(F, red, nw, [&](int s, int v, double a) {
+        ft_sector_sums_a(F, red, [&](int s, int v, double a) {
             const int t = s * FT_W + v;
             if (d.done[t]) return;
             d.alpha[(size_t)t * F.steps + j] = a;
@@ -726,7 +755,7 @@ __global__ void k_ft_thermo(FtParams F, const double *temps, int n_t) {
 
 // ---- host --------------------------------------------------------------------------------
 struct FtLayout {
-    size_t q0, q1, st, ab, part, wr, slo, parta, ckit, ckcs, sec, bar, items, rowoff, secdim, theta, tau, mlen, therm, temps, eigs,
+    size_t q0, q1, st, ab, part, wr, slo, parta, partc, ckit, ckcs, sec, bar, items, rowoff, secdim, theta, tau, mlen, therm, temps, eigs,
         xcd, xmat, total;
 };
 
@@ -759,6 +788,7 @@ static FtLayout ft_layout(int N, int nsec, int R, int steps, int nitems, int nct
     L.wr = o; o += a((size_t)nctas * (FT_NT / 32) * sizeof(FtRange));
     L.slo = o; o += a((size_t)(nsec + 1) * 4);
     L.parta = o; o += a((size_t)nsec * nctas * (FT_NT / 32) * FT_W * 8);
+    L.partc = o; o += a((size_t)nsec * nctas * FT_W * 8);
     L.ckit = o; o += a((nchunks > 0 ? nchunks : 1) * 4);
     L.ckcs = o; o += a((size_t)(nsec + 1) * 4);
     L.sec = o; o += a(FT_MAXS * 4);
@@ -954,6 +984,7 @@ static void ft_bind(FtSetup *S, unsigned char *w) {
     d.wr = (const FtRange *)(w + L.wr);
     d.slo = (const uint32_t *)(w + L.slo);
     d.parta = (double *)(w + L.parta);
+    d.partc = (double *)(w + L.partc);
     d.ck_it0 = (const uint32_t *)(w + L.ckit);
     d.ck_cs = (const uint32_t *)(w + L.ckcs);
     d.sec_active = (int *)(w + L.sec);
