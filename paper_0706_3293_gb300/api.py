@@ -290,6 +290,18 @@ def e0_grad(basis: Basis, bonds: BondList, steps: int, v0: torch.Tensor | None =
     return e0.value, g[: len(bonds)], psi, rc
 
 
+def ground_state_correlations(basis: Basis, bonds: BondList, pairs_u, pairs_v, steps: int,
+                              v0: torch.Tensor | None = None, seed: int = 0, device="cuda"):
+    """Ground energy and the correlations <psi0| s_u.s_v |psi0> of any site pairs (u, v) in the
+    ground state of H(bonds) on the basis sector: psi0 (normalised) from e0_grad, then the
+    bond-correlation kernel on (psi0, psi0).  Returns (E0, correlations as numpy, status)."""
+    e0, _, psi, rc = e0_grad(basis, bonds, steps, v0=v0, seed=seed, want_psi=True, device=device)
+    pairs = BondList.make(pairs_u, pairs_v, np.zeros(len(pairs_u)))
+    check(_capi.load().bonds_check(basis.n_sites, *pairs.args()))
+    corr = bond_corr(basis, pairs, psi, psi).cpu().numpy()
+    return e0, corr, rc
+
+
 @dataclass
 class FTLMResult:
     Z: np.ndarray          # partition function / e^{-e_ref / T}

@@ -486,6 +486,21 @@ def test_lanczos_full_size_majumdar_ghosh(hm):
 
 
 @pytest.mark.slow
+def test_lanczos_full_size_majumdar_ghosh_f32(hm):
+    """The same full-size run with FP32 Lanczos vectors (FP64 reductions): the ground energy
+    -12 of the Majumdar-Ghosh point within |dE0/E0| <= 1e-6."""
+    inst = W.j1j2_ring32()
+    b = hm.Basis(32, 1, 0)
+    run = hm.LanczosRun(b, hm.bonds_of(inst), 150, seed=inst.seed, dtype=torch.float32)
+    assert run.kernel_name().startswith("k_blk_lz32")
+    run.step(150)
+    al, be, rc = run.read()
+    run.close()
+    e0 = oracle.tridiag_lowest(al, be, 1)[0]
+    assert abs(e0 - (-12.0)) <= 1e-6 * 12.0, e0
+
+
+@pytest.mark.slow
 def test_block_product_specialised_equals_generic_full_size(hm, monkeypatch):
     """At N = 32 (the bench's launch configuration: dynamic block schedule over 131,070
     blocks, 456 CTAs) the specialised and the generic FP64 block products give the same
