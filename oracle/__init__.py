@@ -341,6 +341,22 @@ def converged_length(al: np.ndarray, be: np.ndarray, tol: float = 1e-10) -> int:
     return m
 
 
+def flip_matvec(basis: Basis, bonds: Bonds, x: np.ndarray, parity: int) -> np.ndarray:
+    """H on the spin-flip parity subspace of an s = 1/2 sector with M = 0 (N even).
+
+    The flip a_p -> 1 - a_p of every digit maps the sector onto itself and commutes with
+    Eq. E-2-1.  Representatives of the pairs {w, flip(w)} are the states whose digit at
+    position N - 1 is 0, i.e. the first half of the indices; flip reverses the order of the
+    sector, index(flip(w)) = dim - 1 - index(w).  A parity-p vector x on the representatives
+    is the full vector [x, p reversed(x)], and its image is the first half of H applied to it."""
+    n = basis.dim
+    assert basis.S2 == 1 and 2 * basis.A == basis.N and n % 2 == 0 and parity in (1, -1)
+    x = np.asarray(x, dtype=np.float64)
+    assert x.shape == (n // 2,)
+    full = np.concatenate([x, parity * x[::-1]])
+    return basis.matvec(bonds, full)[: n // 2]
+
+
 def ground_state(basis: Basis, bonds: Bonds, v0: np.ndarray, steps: int):
     """Lanczos E0 and psi0: a first pass gives T, cut at the converged length (see
     converged_length); a library eigensolver gives its lowest eigenvector c, a second pass

@@ -488,3 +488,50 @@ def test_ftlm_lanczos_quadrature_large_sector(orc):
         for T in [1.0, 3.0]:
             ref = v @ expm(-H / T) @ v / (v @ v)
             assert abs(np.sum(tau * np.exp(-th / T)) - ref) < 1e-8 * ref
+
+
+# ---- spin-flip parity sectors (M = 0) ------------------------------------------------------
+
+@pytest.mark.parametrize("N", [6, 8, 10])
+def test_flip_reverses_the_index(orc, N):
+    """Brute force: complementing every digit of a sector state at M = 0 maps index i to
+    dim - 1 - i (the flip reverses the numerical order of words of weight N/2)."""
+    b = Basis(N, 1, N // 2)
+    for i in range(b.dim):
+        d = b.decode(i)
+        assert b.encode(1 - d) == b.dim - 1 - i
+        assert (d[N - 1] == 0) == (i < b.dim // 2)     # representatives: first half
+
+
+def _flip_dense(b, bonds, parity):
+    n = b.dim // 2
+    return np.stack([oracle.flip_matvec(b, bonds, np.eye(n)[:, j], parity) for j in range(n)], axis=1)
+
+
+@pytest.mark.parametrize("N,j2,seed", [(8, -0.3, 1), (10, -0.5, 2), (10, 0.7, 3)])
+def test_flip_sectors_split_the_spectrum(orc, N, j2, seed):
+    """The two parity blocks are symmetric and their spectra together are the sector's
+    spectrum (dense diagonalisation of the full M = 0 sector)."""
+    inst = W.small_ring(N, -1.0, j2)
+    J = np.random.default_rng(seed).uniform(-1.3, 0.6, inst.n_bonds)
+    bonds = Bonds(inst.u, inst.v, J)
+    b = Basis(N, 1, N // 2)
+    Hp, Hm = _flip_dense(b, bonds, 1), _flip_dense(b, bonds, -1)
+    np.testing.assert_allclose(Hp, Hp.T, atol=1e-13)
+    np.testing.assert_allclose(Hm, Hm.T, atol=1e-13)
+    full = np.linalg.eigvalsh(oracle.dense_hamiltonian_sector(N, 1, N // 2, bonds))
+    both = np.sort(np.concatenate([np.linalg.eigvalsh(Hp), np.linalg.eigvalsh(Hm)]))
+    np.testing.assert_allclose(both, full, rtol=0, atol=1e-10)
+
+
+def test_flip_majumdar_ghosh_parity(orc):
+    """N = 8 ring at J2 = J1/2 (J1 = -1): the ground states are the two dimer coverings by
+    singlets, each singlet odd under the flip, so a product of N/2 = 4 singlets is even:
+    E0 = -3N/8 = -3 lies in the parity +1 block, and the -1 block lies above it."""
+    inst = W.small_ring(8, -1.0, -0.5)
+    bonds = Bonds(inst.u, inst.v, inst.J)
+    b = Basis(8, 1, 4)
+    ep = np.linalg.eigvalsh(_flip_dense(b, bonds, 1))
+    em = np.linalg.eigvalsh(_flip_dense(b, bonds, -1))
+    assert abs(ep[0] + 3.0) < 1e-12
+    assert em[0] > -3.0 + 1e-6
