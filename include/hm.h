@@ -87,6 +87,18 @@ int bonds_check(int n_sites, int n_bonds, const int32_t *u, const int32_t *v, co
  * host, and uploads them to the current device.  *out is library-owned; free it with
  * basis_free. */
 int basis_build(int n_sites, int two_s, int two_m, hm_basis **out);
+
+/* Spin-flip parity block of the s = 1/2 sector M = 0 (n_sites even, 10..32), a symmetry
+ * reduction beyond the paper's sectors (its Sec. 1 names symmetries as the next way to
+ * shrink a sector).  Flipping every spin (digit a -> 1 - a) maps the sector onto itself,
+ * commutes with Eq. (E-2-1) and reverses the Sec. 3 order: index(flip w) = D - 1 -
+ * index(w).  The basis keeps the representatives, the states with site N-1 up (digit
+ * a_{N-1} = 0), which are indices 0 .. D/2 - 1 of the sector; a vector x on them stands for
+ * the sector vector [x, parity * reversed(x)].  basis_dim gives D/2; basis_encode gives -1
+ * for the other half.  matvec (one vector) and the Lanczos calls act as H restricted to
+ * the block, through the s = 1/2 block kernels only (a bond list they cannot take fails
+ * with HM_EINVAL); count_nnz, bond_corr and e0_grad return HM_EINVAL.  parity: +1 or -1. */
+int basis_build_flip(int n_sites, int parity, hm_basis **out);
 int basis_free(hm_basis *basis);
 int basis_dim(const hm_basis *basis, int64_t *dim);
 

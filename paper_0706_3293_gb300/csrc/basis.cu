@@ -177,7 +177,8 @@ __global__ void k_encode(SectorView sv, const uint64_t *__restrict__ st,
             S += a;
         }
         ok = ok && S == sv.A;
-        out[t] = ok ? (int64_t)c.encode(w) : -1;
+        const int64_t ix = ok ? (int64_t)c.encode(w) : -1;
+        out[t] = ix >= 0 && (uint64_t)ix < sv.dim ? ix : -1;   // spin-flip basis: representatives only
     }
 }
 
@@ -241,6 +242,18 @@ int basis_build(int n_sites, int two_s, int two_m, hm_basis **out) {
     }
     v.cd = b->d_cd;
     *out = b;
+    return HM_OK;
+}
+
+int basis_build_flip(int n_sites, int parity, hm_basis **out) {
+    if (!out) return fail(HM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (parity != 1 && parity != -1) return fail(HM_EINVAL, "parity must be +1 or -1 (got %d)", parity);
+    if (n_sites < 10 || n_sites > 32 || (n_sites & 1))
+        return fail(HM_EINVAL, "spin-flip basis needs an even n_sites in 10..32 (got %d)", n_sites);
+    HM_TRY(basis_build(n_sites, 1, 0, out));
+    (*out)->parity = parity;
+    (*out)->view.dim /= 2;          // the representatives: the first half of the sector
     return HM_OK;
 }
 

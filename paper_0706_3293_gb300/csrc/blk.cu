@@ -154,6 +154,7 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
     memset(P, 0, sizeof *P);
     P->N = sv.N; P->K = K; P->H = sv.N - K; P->A = sv.A; P->nb1 = 1 << (K - 8);
     P->dim = (uint32_t)sv.dim;
+    P->par = b->parity;
     // coupling classes: distinct J values
     std::vector<double> cls;
     std::vector<int> bc(bp.nb);

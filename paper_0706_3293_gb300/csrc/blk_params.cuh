@@ -65,6 +65,9 @@ struct BlkParams {
     uint8_t xf_p[HM_BLK_MAXB], xf_q[HM_BLK_MAXB], xf_dst[HM_BLK_MAXB];
     const uint16_t *lw;                           // low words by popcount (BlkTab::lw)
     int lwoff[18];
+    // spin-flip basis (M = 0): parity +1 / -1 of the representatives' vectors, 0 otherwise;
+    // the blocks swept are those whose site N-1 (high bit H - 1) is up
+    int par;
 };
 
 

@@ -30,10 +30,13 @@ __shared__ uint32_t s_R0S[256];      // sizeof(element) * R0[b0]
 __shared__ uint32_t s_hnext[2];      // dynamic schedule: blocks handed to this CTA
 
 struct XSlot {                       // a cross bond in the current block
-    const unsigned char *base;       // first row of the target block
-    uint16_t wm, vm;                 // allowed iff (l ^ wm) & vm: bit p differs from bit q of h
+    const unsigned char *base;       // first row of the target block (flipped: its last row,
+                                     // in the complement block; the target is base - offset)
+    uint16_t wm, vm;                 // allowed iff (l ^ wm) & vm: bit p differs from bit q of h;
+                                     // vm bit 15 (above every low position) marks a flipped target
     uint32_t kofs2;                  // byte offset of row k2 of s_US (k2 = k -+ 1)
 };
+constexpr uint16_t BLK_XFLIP = 0x8000u;
 
 constexpr int BLK_HBI = HM_BLK_MAXB + 4 * HM_BLK_MAXC;   // high-exchange list with its padding
 
@@ -43,7 +46,11 @@ struct BlkMeta {                     // per-block data, double-buffered
     // occupies [hs[c], he[c]) with hs[c] a multiple of 4, so four entries are one 16-byte load
     __align__(16) uint32_t hbi[BLK_HBI];
     int hs[HM_BLK_MAXC], he[HM_BLK_MAXC];
-    uint32_t hv[2];
+    // spin-flip basis: exchanges that move site N-1 lead out of the representatives; their
+    // target is row n - 1 - r of the complement block, hbf[e] its last row, by class
+    uint32_t hbf[HM_BLK_MAXB];
+    int fs[HM_BLK_MAXC], fe[HM_BLK_MAXC];
+    uint32_t hv[2], hf[2];
     uint32_t off, n, kofs, lwo;
 };
 
@@ -73,6 +80,16 @@ __device__ __forceinline__ Sv blk_high_sum(const BlkMeta &B, int c, const unsign
         if (e + 1 < e1) a += gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
         if (e + 2 < e1) a += gx(Xg + (size_t)(t.z + r) * sizeof(Sv));
     }
+    return a;
+}
+
+// spin-flip basis: sum of the flipped high-exchange gathers of class c for row r (row
+// n - 1 - r of each complement block), before the parity sign
+template <class Sv, class G>
+__device__ __forceinline__ Sv blk_flip_sum(const BlkMeta &B, int c, const unsigned char *Xg, uint32_t r,
+                                           const G &gx) {
+    Sv a = Sv(0);
+    for (int e = B.fs[c]; e < B.fe[c]; ++e) a += gx(Xg + (size_t)(B.hbf[e] - r) * sizeof(Sv));
     return a;
 }
 
@@ -130,12 +147,14 @@ struct GF32 {
         const uint32_t v_ = us_at(lh4k ^ P.lxb[c][2][s]) + r0s_at((l4 ^ P.lxa[c][2][s]) & 0x3FCu); \
         if (z_ & P.lvm[c][2][s]) a += HM_XS(v_); }
 #define HM_LG(g) m += __popc((l ^ (l >> P.lgd[c][g])) & P.lgm[c][g]);
+#define HM_XADD(v_) { if (x_.vm & BLK_XFLIP) { const Sv t_ = gx(x_.base - (v_)); a += P.par < 0 ? -t_ : t_; } \
+        else a += gx(x_.base + (v_)); ++m; }
 #define HM_X0(s) { const XSlot x_ = B.xs[(2 * c) * HM_BLK_SX + (s)];                              \
         const uint32_t v_ = us_at(lh4 | x_.kofs2) + r0s_at((l4 ^ P.xxa[c][0][s]) & 0x3FCu);        \
-        if ((l ^ x_.wm) & x_.vm) { a += gx(x_.base + v_); ++m; } }
+        if ((l ^ x_.wm) & x_.vm) HM_XADD(v_) }
 #define HM_X1(s) { const XSlot x_ = B.xs[(2 * c + 1) * HM_BLK_SX + (s)];                          \
         const uint32_t v_ = us_at((lh4 ^ P.xxa[c][1][s]) | x_.kofs2) + R0own;                      \
-        if ((l ^ x_.wm) & x_.vm) { a += gx(x_.base + v_); ++m; } }
+        if ((l ^ x_.wm) & x_.vm) HM_XADD(v_) }
 // a switch entering an unrolled run of slots n-1, ..., 0
 #define HM_RUN16(M) case 16: M(15) [[fallthrough]]; case 15: M(14) [[fallthrough]]; case 14: M(13) [[fallthrough]]; \
     case 13: M(12) [[fallthrough]]; case 12: M(11) [[fallthrough]]; case 11: M(10) [[fallthrough]];                \
@@ -186,8 +205,12 @@ static __device__ __forceinline__ void sums(const BlkParams &P, const BlkMeta &B
         switch (P.xn[c][1]) { HM_RUN8(HM_X1) }
         // exchanges among the high positions: the same low word in another block
         a += blk_high_sum<Sv>(B, c, Xg, r, gx);
+        if (P.par) {
+            const Sv f = blk_flip_sum<Sv>(B, c, Xg, r, gx);
+            a += P.par < 0 ? -f : f;
+        }
         acc[c] = a;
-        cnt[c] = m + (B.he[c] - B.hs[c]);
+        cnt[c] = m + (B.he[c] - B.hs[c]) + (B.fe[c] - B.fs[c]);
     }
 }
 };
@@ -198,6 +221,7 @@ static __device__ __forceinline__ void sums(const BlkParams &P, const BlkMeta &B
 #undef HM_LG
 #undef HM_X0
 #undef HM_X1
+#undef HM_XADD
 
 // Every block of the sector through rowf(off, r, x_r, acc, cnt, pref(off + r)) once
 // (pref loads what the row needs besides x, issued before the hop sums).  X: the vector as
@@ -223,7 +247,8 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
     }
     BlkTabs tb;
     tb.U = nullptr; tb.R0 = nullptr; tb.C = Cg;
-    const uint32_t nH = 1u << P.H;
+    // spin-flip basis: only the representatives, the blocks whose site N-1 is up
+    const uint32_t nH = 1u << (P.H - (P.par ? 1 : 0));
     if (DYN && tid == 0) s_hnext[0] = blk_fetch(P, sched, nH);
     __syncthreads();
     uint32_t hs = blockIdx.x, h_prev = 0u;
@@ -243,25 +268,36 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
         // setup 1: targets of the high and cross exchanges, own offset, next block
         if (DYN && tid == 0) s_hnext[(it + 1) & 1] = blk_fetch(P, sched, nH);
         uint32_t hidx = 0u;
-        bool hval = false;
+        bool hval = false, hflip = false;
         if (tid < P.nhb) {
             const int p = P.hb_p[tid], q = P.hb_q[tid];
-            hval = (((h >> p) ^ (h >> q)) & 1u) != 0u;
-            if (hval) hidx = blk_off(P, tb, h ^ ((1u << p) | (1u << q)), k);
+            const bool ok = (((h >> p) ^ (h >> q)) & 1u) != 0u;
+            const uint32_t h2 = h ^ ((1u << p) | (1u << q));
+            if (ok && P.par && q == P.H - 1) {     // site N-1 flips up: the complement block
+                hflip = true;
+                hidx = blk_off(P, tb, ~h2 & ((1u << P.H) - 1u), P.K - k) + Cg[P.K * (P.A + 1) + k] - 1u;
+            } else if (ok) {
+                hval = true;
+                hidx = blk_off(P, tb, h2, k);
+            }
         }
         if (tid < 64) {
-            const unsigned bal = __ballot_sync(0xffffffffu, hval);
-            if ((tid & 31) == 0) B.hv[tid >> 5] = bal;
+            const unsigned bal = __ballot_sync(0xffffffffu, hval), balf = __ballot_sync(0xffffffffu, hflip);
+            if ((tid & 31) == 0) { B.hv[tid >> 5] = bal; B.hf[tid >> 5] = balf; }
         }
         if (tid >= 64 && tid < 64 + P.nxf) {
             const int e = tid - 64, p = P.xf_p[e], q = P.xf_q[e];
             const uint32_t bq = (h >> q) & 1u;
             const int k2 = k + (bq ? 1 : -1);
             const bool ok = k2 >= 0 && k2 <= P.K;
+            const bool fl = ok && P.par && q == P.H - 1;   // site N-1 flips up: complement block
             XSlot xs;
-            xs.base = ok ? X + (size_t)blk_off(P, tb, h ^ (1u << q), k2) * sizeof(Sv) : X;
+            xs.base = !ok ? X
+                      : fl ? X + (size_t)(blk_off(P, tb, ~(h ^ (1u << q)) & ((1u << P.H) - 1u), P.K - k2) +
+                                          Cg[P.K * (P.A + 1) + k2] - 1u) * sizeof(Sv)
+                           : X + (size_t)blk_off(P, tb, h ^ (1u << q), k2) * sizeof(Sv);
             xs.wm = (uint16_t)(bq << p);
-            xs.vm = (uint16_t)(ok ? 1u << p : 0u);
+            xs.vm = (uint16_t)(ok ? (1u << p) | (fl ? BLK_XFLIP : 0u) : 0u);
             xs.kofs2 = ok ? (uint32_t)(Row::kRelUS ? k2 - k + 1 : k2) << P.kshift : 0u;
             B.xs[P.xf_dst[e]] = xs;
         }
@@ -275,14 +311,18 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
         if (tid == BLK_NT - 1 && it_prev >= 0) flushf(h_prev, it_prev);
         // setup 2: compact the allowed high exchanges by class, each class's run padded to a
         // multiple of 4 entries; stage the block's x
-        if (hval || tid < HM_BLK_MAXC) {
+        if (hval || hflip || tid < HM_BLK_MAXC) {
             const uint64_t hm = ((uint64_t)B.hv[1] << 32) | B.hv[0];
+            const uint64_t fm = ((uint64_t)B.hf[1] << 32) | B.hf[0];
             int start = 0;                           // padded start of the class
             for (int c = 0; c < HM_BLK_MAXC; ++c) {
                 const int b0 = popc_below(hm, P.hb_start[c]), b1 = popc_below(hm, P.hb_start[c + 1]);
-                if (hval && tid >= P.hb_start[c] && tid < P.hb_start[c + 1])
-                    B.hbi[start + popc_below(hm, tid) - b0] = hidx;
-                if (tid == c) { B.hs[c] = start; B.he[c] = start + (b1 - b0); }
+                const int f0 = popc_below(fm, P.hb_start[c]), f1 = popc_below(fm, P.hb_start[c + 1]);
+                if (tid >= P.hb_start[c] && tid < P.hb_start[c + 1]) {
+                    if (hval) B.hbi[start + popc_below(hm, tid) - b0] = hidx;
+                    if (hflip) B.hbf[popc_below(fm, tid)] = hidx;
+                }
+                if (tid == c) { B.hs[c] = start; B.he[c] = start + (b1 - b0); B.fs[c] = f0; B.fe[c] = f1; }
                 start += (b1 - b0 + 3) & ~3;
             }
         }

@@ -71,6 +71,7 @@ struct hm_basis {
     void *d_cd = nullptr;           // device copy (owned)
     void *d_scratch = nullptr;      // 256 bytes of device scratch (owned), e.g. exponents
     std::map<int, hm::BlkTab> blk_tabs;   // per split position K (owned device memory)
+    int parity = 0;                 // spin-flip basis (basis_build_flip): +1 / -1, view.dim halved
     int device = 0;
 };
 

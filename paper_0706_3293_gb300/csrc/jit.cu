@@ -103,6 +103,15 @@ void put(std::string &s, const char *fmt, ...) {
 // slot down, so FP32 sums round the same way).  A failed exchange reads byte-0 table
 // entry 0 and a zero element past the staged rows instead of its own lookups: all such
 // lanes hit the same words (broadcasts), and the add needs no select.
+// the add of cross slot `dst`: a target in the complement block (spin-flip basis, bond
+// on site N-1) lies below its base and carries the parity sign
+const char *xadd(const BlkParams &P, int dst) {
+    for (int e = 0; e < P.nxf; ++e)
+        if (P.xf_dst[e] == dst && P.par && P.xf_q[e] == P.H - 1)
+            return P.par < 0 ? "a -= gx(x_.base - v_)" : "a += gx(x_.base - v_)";
+    return "a += gx(x_.base + v_)";
+}
+
 std::string gen_row_slots(const BlkParams &P) {
     std::string s;
     s += "struct RowJit {\n"
@@ -148,14 +157,20 @@ std::string gen_row_slots(const BlkParams &P) {
         for (int g = P.lgn[c] - 1; g >= 0; --g) put(s, "        m += __popc(z%d & 0x%xu);\n", P.lgd[c][g], P.lgm[c][g]);
         for (int k = P.xn[c][0] - 1; k >= 0; --k)
             put(s, "        { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at(lh4 | x_.kofs2) + "
-                   "hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu); if ((l ^ x_.wm) & x_.vm) { a += gx(x_.base + v_); ++m; } }\n",
-                (2 * c) * HM_BLK_SX + k, (unsigned)P.xxa[c][0][k]);
+                   "hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu); if ((l ^ x_.wm) & x_.vm) { %s; ++m; } }\n",
+                (2 * c) * HM_BLK_SX + k, (unsigned)P.xxa[c][0][k], xadd(P, (2 * c) * HM_BLK_SX + k));
         for (int k = P.xn[c][1] - 1; k >= 0; --k)
             put(s, "        { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at((lh4 ^ 0x%xu) | x_.kofs2) + "
-                   "R0own; if ((l ^ x_.wm) & x_.vm) { a += gx(x_.base + v_); ++m; } }\n",
-                (2 * c + 1) * HM_BLK_SX + k, (unsigned)P.xxa[c][1][k]);
+                   "R0own; if ((l ^ x_.wm) & x_.vm) { %s; ++m; } }\n",
+                (2 * c + 1) * HM_BLK_SX + k, (unsigned)P.xxa[c][1][k], xadd(P, (2 * c + 1) * HM_BLK_SX + k));
         put(s, "        a += hm::blk_high_sum<Sv>(B, %d, Xg, r, gx);\n", c);
-        put(s, "        acc[%d] = a;\n        cnt[%d] = m + (B.he[%d] - B.hs[%d]);\n    }\n", c, c, c, c);
+        if (P.par) {
+            put(s, "        a %s= hm::blk_flip_sum<Sv>(B, %d, Xg, r, gx);\n", P.par < 0 ? "-" : "+", c);
+            put(s, "        acc[%d] = a;\n        cnt[%d] = m + (B.he[%d] - B.hs[%d]) + (B.fe[%d] - B.fs[%d]);\n    }\n",
+                c, c, c, c, c, c);
+        } else {
+            put(s, "        acc[%d] = a;\n        cnt[%d] = m + (B.he[%d] - B.hs[%d]);\n    }\n", c, c, c, c);
+        }
     }
     s += "}\n};\n";
     return s;
@@ -337,7 +352,7 @@ int jit_lz_kernel(const BlkParams &P, int dtype, const void **kern) {
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
     bool gen_ok = true;
     const char *rowk = getenv("HM_JIT_ROW");
-    const bool delta = rowk && strcmp(rowk, "delta") == 0;
+    const bool delta = rowk && strcmp(rowk, "delta") == 0 && !P.par;   // no spin-flip form
     std::string src = "#include \"blk_sweep.cuh\"\n" + (delta ? gen_row(P, gen_ok) : gen_row_slots(P));
     if (!gen_ok) return 1;
     const bool f64 = dtype == HM_F64;

@@ -661,6 +661,10 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
     rc = blk_lz_plan(const_cast<hm_basis *>(b), R->bp, dtype, &R->blk, &R->blk_blocks);
     if (rc < 0) { delete R; return rc; }
     R->use_blk = rc == 0 && (dtype == HM_F32 || R->L.shadow) && R->L.hpart != 0 && R->blk.H <= 17;
+    if (b->parity && !R->use_blk) {
+        delete R;
+        return fail(HM_EINVAL, "spin-flip basis: this bond list does not take the s = 1/2 block path");
+    }
     R->jit = nullptr;
     R->run = row_run_len();
     if (R->use_blk) {
@@ -816,6 +820,7 @@ int lanczos_run(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t 
 int e0_grad(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, const double *J,
             const void *v0, uint64_t seed, int steps, void *work, size_t work_bytes, double *e0,
             double *dE0_dJ, double *psi_out, void *stream) {
+    if (b && b->parity) return fail(HM_EINVAL, "e0_grad: not available on a spin-flip basis");
     if (!e0 || (n_bonds > 0 && !dE0_dJ)) return fail(HM_EINVAL, "NULL output");
     hm_lanczos *R = nullptr;
     HM_TRY(lz_create(b, n_bonds, u, v, J, HM_F64, steps, work, work_bytes, true, &R));

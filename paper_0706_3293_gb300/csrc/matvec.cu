@@ -163,6 +163,8 @@ int matvec_dev(const hm_basis *b, const BondParams &bp, const void *x, void *y, 
     // s = 1/2 sectors with few coupling classes take the block path (blk.cu)
     const int brc = blk_matvec(const_cast<hm_basis *>(b), bp, x, y, dtype, nvec, st);
     if (brc <= 0) return brc;
+    if (b->parity)
+        return fail(HM_EINVAL, "spin-flip basis: this bond list or vector count does not take the s = 1/2 block path");
     if (dtype == HM_F64) {
         if (sv.idx64) return matvec_cols<uint64_t, double, double>(sv, bp, (const double *)x, (double *)y, nvec, st);
         return matvec_cols<uint32_t, double, double>(sv, bp, (const double *)x, (double *)y, nvec, st);
@@ -236,6 +238,7 @@ int matvec(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, c
 
 int count_nnz(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, int64_t *nnz,
               void *stream) {
+    if (b && b->parity) return fail(HM_EINVAL, "count_nnz: not available on a spin-flip basis");
     if (!b || !nnz) return fail(HM_EINVAL, "NULL argument");
     std::vector<double> ones(n_bonds > 0 ? n_bonds : 1, 1.0);
     BondParams bp;
@@ -264,6 +267,7 @@ int bond_corr_workspace(const hm_basis *b, int n_bonds, size_t *bytes) {
 
 int bond_corr(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, const void *g,
               const void *x, double *out, int dtype, void *work, size_t work_bytes, void *stream) {
+    if (b && b->parity) return fail(HM_EINVAL, "bond_corr: not available on a spin-flip basis");
     if (!b) return fail(HM_EINVAL, "basis is NULL");
     if (dtype != HM_F64 && dtype != HM_F32) return fail(HM_EINVAL, "dtype must be HM_F64 or HM_F32");
     if (!g || !x || (n_bonds > 0 && !out)) return fail(HM_EINVAL, "NULL vector");
@@ -307,6 +311,7 @@ int bc_static_ptr(double **out) {
 
 int bond_corr_static(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, const void *g,
                      const void *x, double *out, int dtype, void *stream) {
+    if (b && b->parity) return fail(HM_EINVAL, "bond_corr: not available on a spin-flip basis");
     if (!b) return fail(HM_EINVAL, "basis is NULL");
     if (dtype != HM_F64 && dtype != HM_F32) return fail(HM_EINVAL, "dtype must be HM_F64 or HM_F32");
     if (!g || !x || (n_bonds > 0 && !out)) return fail(HM_EINVAL, "NULL vector");
