@@ -38,6 +38,9 @@ WORKLOADS = {
     # M = 0 every bond connects C(N-2, N/2-1) states in each direction, so
     # nnz = C(N, N/2) + 2 n_bonds C(N-2, N/2-1).
     "j1j2_ring32": 20456122950,
+    # the spin-flip +1 block of the same sector: the representatives are the first half of
+    # the rows, and no two exchanges of a row fold onto one column (N >= 6), so half the nnz
+    "j1j2_ring32_flip": 10228061475,
     "j1j2_ring28": 1204983800,
     "ring24_randJ": 70425628,
     "ring16": 122694,
@@ -47,6 +50,7 @@ WORKLOADS = {
     "s1_rrg20": None,
 }
 DEFAULT_DTYPE = {"s1_rrg20": "f32"}
+PARITY = {"j1j2_ring32_flip": 1}     # spin-flip block (basis_build_flip) of the workload's sector
 
 # bytes one product must move at minimum: read x once, write y once (FP64)
 ALGO_BYTES_PER_ROW = 16
@@ -54,9 +58,13 @@ ALGO_BYTES_PER_ROW = 16
 
 def instance(name):
     from paper_0706_3293_gb300 import workloads as W
-    return {"j1j2_ring32": W.j1j2_ring32, "j1j2_ring28": lambda: W.j1j2_ring(28),
+    return {"j1j2_ring32": W.j1j2_ring32, "j1j2_ring32_flip": W.j1j2_ring32, "j1j2_ring28": lambda: W.j1j2_ring(28),
             "ring24_randJ": W.ring24_random_j, "ring16": W.ring16, "ftlm_ring24": W.ftlm_ring24,
             "s1_rrg20": W.s1_random_graph}[name]()
+
+
+def workload_name(inst, parity):
+    return inst.name + (f"_flip{parity:+d}" if parity else "")
 
 
 def sector_nnz_s12(n_sites: int, n_bonds: int, A: int) -> int:
@@ -175,27 +183,39 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(inst, nnz_total, target_s=15.0):
+def oracle_vector(ob, inst, parity):
+    """The oracle's start vector for the workload's product: the sector vector, or for a
+    spin-flip block the sector vector [x, parity reversed(x)] its representatives stand for
+    (the block's rows are the first half of the sector's).  Returns (vector, rows)."""
+    import numpy as np
+    import oracle
+    if not parity:
+        return oracle.start_uniform(inst.seed, ob.dim), ob.dim
+    xr = oracle.start_uniform(inst.seed, ob.dim // 2)
+    return np.concatenate([xr, parity * xr[::-1]]), ob.dim // 2
+
+
+def cpu_baseline(inst, nnz_total, target_s=15.0, parity=0):
     """The oracle's row matvec on a bounded contiguous sample of rows, all host cores."""
     import numpy as np
     import oracle
     ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
     bonds = oracle.Bonds(inst.u, inst.v, inst.J)
-    x = oracle.start_uniform(inst.seed, ob.dim)
-    mid = ob.dim // 3
-    pilot = min(ob.dim, 200000)
+    x, rows = oracle_vector(ob, inst, parity)
+    mid = rows // 3
+    pilot = min(rows, 200000)
     t0 = time.perf_counter()
-    ob.matvec_rows(bonds, x, mid if mid + pilot <= ob.dim else 0, (mid if mid + pilot <= ob.dim else 0) + pilot)
+    ob.matvec_rows(bonds, x, mid if mid + pilot <= rows else 0, (mid if mid + pilot <= rows else 0) + pilot)
     rate = pilot / max(time.perf_counter() - t0, 1e-6)
-    n = int(min(ob.dim, max(pilot, rate * target_s)))
-    r0 = min(mid, ob.dim - n)
+    n = int(min(rows, max(pilot, rate * target_s)))
+    r0 = min(mid, rows - n)
     t0 = time.perf_counter()
     ob.matvec_rows(bonds, x, r0, r0 + n)
     dt = time.perf_counter() - t0
     nnz = ob.count_nnz(bonds, r0, r0 + n)
     del x
     return {"value": nnz / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"rows [{r0}, {r0 + n}) of one FP64 product ({n} of {ob.dim} rows, "
+            "sample": f"rows [{r0}, {r0 + n}) of one FP64 product ({n} of {rows} rows, "
                       f"{nnz} nnz, {dt:.1f} s)"}
 
 
@@ -208,15 +228,16 @@ def run_reference(args):
     inst = instance(args.workload)
     ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
     bonds = oracle.Bonds(inst.u, inst.v, inst.J)
-    x = oracle.start_uniform(inst.seed, ob.dim)
+    parity = PARITY.get(args.workload, 0)
+    x, rows = oracle_vector(ob, inst, parity)
     # one step = one oracle product over a bounded row sample sized to ~3 s
-    pilot = min(ob.dim, 100000)
-    r0 = ob.dim // 3 if ob.dim // 3 + pilot <= ob.dim else 0
+    pilot = min(rows, 100000)
+    r0 = rows // 3 if rows // 3 + pilot <= rows else 0
     t0 = time.perf_counter()
     ob.matvec_rows(bonds, x, r0, r0 + pilot)
     rate = pilot / max(time.perf_counter() - t0, 1e-6)
-    n = int(min(ob.dim, max(pilot, rate * 3.0)))
-    r0 = min(r0, ob.dim - n)
+    n = int(min(rows, max(pilot, rate * 3.0)))
+    r0 = min(r0, rows - n)
     nnz = ob.count_nnz(bonds, r0, r0 + n)
     for _ in range(args.warmup):
         ob.matvec_rows(bonds, x, r0, r0 + n)
@@ -225,11 +246,11 @@ def run_reference(args):
         ob.matvec_rows(bonds, x, r0, r0 + n)
     dt = time.perf_counter() - t0
     val = nnz * args.steps / dt / 1e9
-    sample = f"rows [{r0}, {r0 + n}) of {ob.dim} per step ({nnz} nnz), FP64"
+    sample = f"rows [{r0}, {r0 + n}) of {rows} per step ({nnz} nnz), FP64"
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": inst.name, "dim": ob.dim, "n_sites": inst.n_sites,
+           "data": "synthetic", "config": {"workload": workload_name(inst, parity), "dim": rows, "n_sites": inst.n_sites,
                                           "two_s": inst.two_s, "two_m": inst.two_m, "l2": "inputs larger than L2"},
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                             "sample": sample},
@@ -331,7 +352,8 @@ def run_ours(args):
     dtype = args.dtype or DEFAULT_DTYPE.get(args.workload, "f64")
     tdt = torch.float64 if dtype == "f64" else torch.float32
     dev = torch.device("cuda", torch.cuda.current_device())
-    b = api.Basis(inst.n_sites, inst.two_s, inst.two_m)
+    parity = PARITY.get(args.workload, 0)
+    b = api.Basis(inst.n_sites, inst.two_s, inst.two_m, parity=parity)
     bl = api.bonds_of(inst)
     nnz = WORKLOADS[args.workload] or api.count_nnz(b, bl)
     total = args.warmup + args.steps
@@ -401,12 +423,12 @@ def run_ours(args):
     mv_mean = float(np.mean(mv_ms))
     algo_row = ALGO_BYTES_PER_ROW if dtype == "f64" else ALGO_BYTES_PER_ROW // 2
     achieved = algo_row * b.dim / (mv_mean * 1e-3) / 1e9
-    traffic = read_traffic(kname, inst.name)
+    traffic = read_traffic(kname, workload_name(inst, parity))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": inst.name, "n_sites": inst.n_sites, "two_s": inst.two_s,
+        "config": {"workload": workload_name(inst, parity), "n_sites": inst.n_sites, "two_s": inst.two_s,
                    "two_m": inst.two_m, "dim": b.dim, "nnz_per_product": nnz,
                    "bonds": inst.n_bonds, "start_seed": inst.seed, "parallelism": f"replicas{ws}",
                    "l2": "inputs larger than L2 (2 x %.1f GB vectors)" % (b.dim * 8 / 1e9)},
@@ -423,7 +445,7 @@ def run_ours(args):
                     "steps_done": int(len(al)), "status": int(rc)},
     }
     if ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(inst, nnz)
+        out["cpu_baseline"] = cpu_baseline(inst, nnz, parity=parity)
     print(json.dumps(out))
     if ws > 1:
         import torch.distributed as dist
