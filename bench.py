@@ -9,7 +9,7 @@ non-zero matrix elements one product applies (20,456,122,950 here) per step, ove
 timed steps.  The vectors (2 x 4.8 GB) are far larger than L2, so no L2 flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload j1j2_ring32|ring24_randJ|ring16]
+                  [--workload j1j2_ring32|j1j2_ring32_flip|ring24_randJ|ring24_grad|ring16 ...]
 
 --impl reference times the CPU oracle (test infrastructure, the only baseline: the paper
 ships no code) on the host cores, on bounded row samples of the same workload.
@@ -46,6 +46,9 @@ WORKLOADS = {
     "ring16": 122694,
     # finite-temperature Lanczos: nnz counted per sector and per executed vector-step
     "ftlm_ring24": None,
+    # differentiation (config 4): one step = y = H x through the autograd function and its
+    # backward (dL/dx = H g, dL/dJ by the bond-correlation kernel): 3 x nnz of the sector
+    "ring24_grad": 70425628,
     # s = 1 random 4-regular graph, N = 20 (FP32 vectors by default); nnz from count_nnz
     "s1_rrg20": None,
 }
@@ -59,7 +62,8 @@ ALGO_BYTES_PER_ROW = 16
 def instance(name):
     from paper_0706_3293_gb300 import workloads as W
     return {"j1j2_ring32": W.j1j2_ring32, "j1j2_ring32_flip": W.j1j2_ring32, "j1j2_ring28": lambda: W.j1j2_ring(28),
-            "ring24_randJ": W.ring24_random_j, "ring16": W.ring16, "ftlm_ring24": W.ftlm_ring24,
+            "ring24_randJ": W.ring24_random_j, "ring24_grad": W.ring24_random_j, "ring16": W.ring16,
+            "ftlm_ring24": W.ftlm_ring24,
             "s1_rrg20": W.s1_random_graph}[name]()
 
 
@@ -226,6 +230,21 @@ def run_reference(args):
     import numpy as np
     import oracle
     inst = instance(args.workload)
+    if args.workload == "ring24_grad":
+        nnz = WORKLOADS[args.workload]
+        for _ in range(args.warmup):
+            grad_oracle_rate(inst, nnz, 1)
+        cb = grad_oracle_rate(inst, nnz, args.steps)
+        val = cb["value"]
+        out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 3 * nnz / (val * 1e9) * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": {"workload": inst.name + "_grad", "n_sites": inst.n_sites,
+                                              "products_per_step": 3},
+               "cpu_baseline": cb,
+               "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return 0
     ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
     bonds = oracle.Bonds(inst.u, inst.v, inst.J)
     parity = PARITY.get(args.workload, 0)
@@ -257,6 +276,145 @@ def run_reference(args):
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
+
+
+def oracle_free_uniform(seed, n):
+    import numpy as np
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, n)
+
+
+def run_grad(args):
+    """Config 4: one step = y = H(J) x through the autograd function (HeisenbergMatvec), the
+    loss L = g.y and its backward: dL/dx = H g and dL/dJ_b = -g^T (s_u.s_v) x.  Gnnz/s counts
+    the three passes over the sector's nonzeros (forward product, backward product, bond
+    correlations)."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0706_3293_gb300 import api
+    from paper_0706_3293_gb300.autograd import HeisenbergMatvec
+    inst = instance(args.workload)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.cuda.current_stream()
+    b = api.Basis(inst.n_sites, inst.two_s, inst.two_m)
+    nnz = WORKLOADS[args.workload]
+    xs, gs = oracle_free_uniform(inst.seed, b.dim), oracle_free_uniform(inst.seed + 1, b.dim)
+    x0 = torch.from_numpy(xs).to(dev)
+    g = torch.from_numpy(gs).to(dev)
+    Jd = torch.from_numpy(inst.J.copy()).to(dev)
+
+    def step(x, J):
+        y = HeisenbergMatvec.apply(x, J, b, inst.u, inst.v)
+        (g * y).sum().backward()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    x = x0.clone().requires_grad_(True)
+    J = Jd.clone().requires_grad_(True)
+    for _ in range(args.warmup):
+        step(x, J)
+        x.grad = None; J.grad = None
+    barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    ev[0].record(st)
+    for k in range(args.steps):
+        y = HeisenbergMatvec.apply(x, J, b, inst.u, inst.v)
+        ev[2 * k + 1].record(st)
+        (g * y).sum().backward()
+        ev[2 * k + 2].record(st)
+        x.grad = None; J.grad = None
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    total_ms = ev[0].elapsed_time(ev[-1])
+    fwd_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
+    t_max = max_over_ranks(total_ms, ws, dev)
+    value = 3 * nnz * args.steps * ws / (t_max * 1e-3) / 1e9
+    # end to end: x and g from pinned host memory, both gradients back to the host, per step
+    xh = torch.from_numpy(xs).pin_memory()
+    gh = torch.from_numpy(gs).pin_memory()
+    gxh = torch.empty(b.dim, dtype=torch.float64).pin_memory()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for k in range(args.steps):
+        xd = xh.to(dev, non_blocking=True).requires_grad_(True)
+        gd = gh.to(dev, non_blocking=True)
+        Jk = Jd.clone().requires_grad_(True)
+        y = HeisenbergMatvec.apply(xd, Jk, b, inst.u, inst.v)
+        (gd * y).sum().backward()
+        gxh.copy_(xd.grad, non_blocking=True)
+        gJ = Jk.grad.cpu()
+    e1.record(st)
+    barrier()
+    e2e_val = 3 * nnz * args.steps * ws / (max_over_ranks(e0.elapsed_time(e1), ws, dev) * 1e-3) / 1e9
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    peak, peak_src = read_peaks()
+    fwd_mean = float(np.mean(fwd_ms))
+    achieved = ALGO_BYTES_PER_ROW * b.dim / (fwd_mean * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": inst.name + "_grad", "n_sites": inst.n_sites, "dim": b.dim,
+                   "nnz_per_product": nnz, "products_per_step": 3, "bonds": inst.n_bonds,
+                   "step": "autograd forward y = H x, backward dL/dx = H g and dL/dJ",
+                   "parallelism": f"replicas{ws}", "l2": "inputs smaller than L2 (21.6 MB vectors)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_matvec (forward)",
+                     "peak_source": peak_src, "algorithmic_bytes_per_launch": ALGO_BYTES_PER_ROW * b.dim,
+                     "mean_launch_ms": fwd_mean},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * b.dim,
+                "d2h_bytes_per_step": 8 * b.dim + 8 * inst.n_bonds},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "grad_check": {"dL_dJ_first": float(gJ[0])},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = grad_oracle_rate(inst, nnz, 1)
+    print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def grad_oracle_rate(inst, nnz, reps):
+    """The oracle's forward product, backward product and bond correlations on the whole
+    sector, all host cores: (value, seconds per step, sample)."""
+    import oracle
+    ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
+    bonds = oracle.Bonds(inst.u, inst.v, inst.J)
+    xs, gs = oracle_free_uniform(inst.seed, ob.dim), oracle_free_uniform(inst.seed + 1, ob.dim)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ob.matvec(bonds, xs)
+        ob.matvec(bonds, gs)
+        ob.bond_corr(bonds, gs, xs)
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": 3 * nnz / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"the whole sector ({ob.dim} rows): forward and backward products and the "
+                      f"bond correlations, {dt:.2f} s per step"}
 
 
 def run_ftlm(args):
@@ -333,6 +491,8 @@ def run_ftlm(args):
 
 
 def run_ours(args):
+    if args.workload == "ring24_grad":
+        return run_grad(args)
     if args.workload == "ftlm_ring24":
         return run_ftlm(args)
     import numpy as np
