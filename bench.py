@@ -381,7 +381,8 @@ def run_grad(args):
                    "step": "autograd forward y = H x, backward dL/dx = H g and dL/dJ",
                    "parallelism": f"replicas{ws}", "l2": "inputs smaller than L2 (21.6 MB vectors)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_matvec (forward)",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": api.matvec_kernel_name(b, api.bonds_of(inst)) + " (forward)",
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": ALGO_BYTES_PER_ROW * b.dim,
                      "mean_launch_ms": fwd_mean},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * b.dim,

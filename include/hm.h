@@ -192,6 +192,13 @@ int lanczos_free(hm_lanczos *run);
  * counterpart in the paper: it reports an implementation choice.  HM_EINVAL on NULL. */
 int lanczos_kernel_name(const hm_lanczos *run, char *name, int cap);
 
+/* Name of the kernel `matvec` launches for these arguments (the same dispatch, nothing
+ * launched): "k_blk_matvec" (s = 1/2 block kernel, up to 4 distinct couplings),
+ * "k_blk_matvec_jit" (block kernel compiled at run time for a bond list with more distinct
+ * couplings) or "k_matvec" (general row kernel).  name: host buffer of cap bytes. */
+int matvec_kernel_name(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
+                       const double *J, int dtype, int nvec, char *name, int cap);
+
 /* A whole run: steps steps captured in one CUDA graph and launched once, then the
  * n_ritz lowest eigenvalues of T (Sturm bisection on the device).  Host outputs:
  * alpha[steps], beta[steps], *steps_done, ritz[n_ritz].  Returns HM_OK or

@@ -19,7 +19,7 @@ EXPORTS = [
     "basis_encode", "basis_decode", "matvec", "count_nnz", "bond_corr_workspace", "bond_corr", "bond_corr_static",
     "start_vector",
     "lanczos_workspace", "lanczos_init", "lanczos_step", "lanczos_substep", "lanczos_read", "lanczos_free",
-    "lanczos_kernel_name",
+    "lanczos_kernel_name", "matvec_kernel_name",
     "lanczos_run", "sector_ground_energies_workspace", "sector_ground_energies", "e0_grad_workspace", "e0_grad",
     "ftlm_workspace", "ftlm_run",
 ]
@@ -72,6 +72,7 @@ def load() -> ctypes.CDLL:
         "lanczos_read": (i32, [vp, dp, dp, ip, vp]),
         "lanczos_free": (i32, [vp]),
         "lanczos_kernel_name": (i32, [vp, ctypes.c_char_p, i32]),
+        "matvec_kernel_name": (i32, [vp, i32, vp, vp, vp, i32, i32, ctypes.c_char_p, i32]),
         "lanczos_run": (i32, [vp, i32, vp, vp, vp, vp, u64, i32, i32, vp, sz, dp, dp, ip, dp,
                               i32, vp]),
         "sector_ground_energies_workspace": (i32, [i32, i32, i32, i32, szp]),

@@ -120,6 +120,13 @@ def matvec(basis: Basis, bonds: BondList, x: torch.Tensor, out: torch.Tensor | N
     return y
 
 
+def matvec_kernel_name(basis: Basis, bonds: BondList, dtype=torch.float64, nvec: int = 1) -> str:
+    """The kernel matvec launches for these arguments (matvec_kernel_name)."""
+    buf = ctypes.create_string_buffer(64)
+    check(_capi.load().matvec_kernel_name(basis.handle, *bonds.args(), _DT[dtype], nvec, buf, 64))
+    return buf.value.decode()
+
+
 def count_nnz(basis: Basis, bonds: BondList, device="cuda") -> int:
     """Non-zero elements of H(M): one diagonal per row plus every allowed exchange."""
     out = torch.zeros(1, dtype=torch.int64, device=device)

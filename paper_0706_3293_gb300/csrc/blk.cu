@@ -120,6 +120,7 @@ static void blk_plan_slots(const BondParams &bp, const std::vector<int> &bc, int
             if (n == HM_BLK_SL) { P->rows_ok = 0; continue; }
             const uint32_t pat = (1u << p) | (1u << q);
             P->ld[c][ty][n] = (uint8_t)(q - p);
+            if (P->perbond) P->pb_lb[ty][n] = (uint8_t)t;
             P->lvm[c][ty][n] = 1u << p;
             P->lxa[c][ty][n] = (uint16_t)(ty == 0 ? (pat & 255u) << 2 : ty == 2 ? (1u << p) << 2 : 0u);
             P->lxb[c][ty][n] = (uint16_t)(ty == 1 ? (pat >> 8) << 2 : ty == 2 ? (1u << (q - 8)) << 2 : 0u);
@@ -130,6 +131,7 @@ static void blk_plan_slots(const BondParams &bp, const std::vector<int> &bc, int
             int &n = P->xn[c][ty];
             if (n == HM_BLK_SX) { P->rows_ok = 0; continue; }
             P->xxa[c][ty][n] = (uint16_t)(ty == 0 ? (1u << p) << 2 : (1u << (p - 8)) << 2);
+            if (P->perbond) P->pb_xb[ty][n] = (uint8_t)t;
             P->xf_p[P->nxf] = (uint8_t)p;
             P->xf_q[P->nxf] = (uint8_t)(q - K);
             P->xf_dst[P->nxf] = (uint8_t)((2 * c + ty) * HM_BLK_SX + n);
@@ -155,19 +157,26 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
     P->N = sv.N; P->K = K; P->H = sv.N - K; P->A = sv.A; P->nb1 = 1 << (K - 8);
     P->dim = (uint32_t)sv.dim;
     P->par = b->parity;
-    // coupling classes: distinct J values
+    // coupling classes: distinct J values; with more than HM_BLK_MAXC of them every bond
+    // keeps its own coefficient (per-bond rows, class 0 slots)
     std::vector<double> cls;
     std::vector<int> bc(bp.nb);
     for (int t = 0; t < bp.nb; ++t) {
         const double J = -bp.jm[t];
         int c = (int)(std::find(cls.begin(), cls.end(), J) - cls.begin());
-        if (c == (int)cls.size()) {
-            if ((int)cls.size() == HM_BLK_MAXC) return 1;
-            cls.push_back(J);
-        }
+        if (c == (int)cls.size()) cls.push_back(J);
         bc[t] = c;
     }
+    if ((int)cls.size() > HM_BLK_MAXC) {
+        P->perbond = 1;
+        cls.clear();
+        std::fill(bc.begin(), bc.end(), 0);
+        double g0 = 0.0;
+        for (int t = 0; t < bp.nb; ++t) g0 += bp.jm[t] / 4.0;      // -J_b / 4
+        P->pb_g0 = g0;
+    }
     P->nc = (int)cls.size() > 0 ? (int)cls.size() : 1;
+    if (P->perbond) P->ntot[0] = 0;
     for (int c = 0; c < (int)cls.size(); ++c) {
         const double g = -cls[c] / 4.0;
         P->g_hi[c] = (float)g;
@@ -207,16 +216,16 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
     }
     // low groups keyed by (class, type, d); high and cross bonds by class
     std::map<std::tuple<int, int, int>, uint32_t> groups;
-    std::vector<std::pair<int, int>> hi[HM_BLK_MAXC], cr[HM_BLK_MAXC];
+    std::vector<std::tuple<int, int, int>> hi[HM_BLK_MAXC], cr[HM_BLK_MAXC];   // (p, q, bond)
     for (int t = 0; t < bp.nb; ++t) {
         const int p = bp.p[t], q = bp.q[t];  // p < q
         if (q < K) {
             const int type = q < 8 ? 0 : (p >= 8 ? 1 : 2);
             groups[std::make_tuple(bc[t], type, q - p)] |= 1u << p;
         } else if (p >= K) {
-            hi[bc[t]].push_back({p - K, q - K});
+            hi[bc[t]].push_back({p - K, q - K, t});
         } else {
-            cr[bc[t]].push_back({p, q - K});
+            cr[bc[t]].push_back({p, q - K, t});
         }
     }
     if ((int)groups.size() > HM_BLK_MAXG) return 1;
@@ -236,9 +245,14 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
     int nh = 0, ncr = 0;
     for (int c = 0; c < HM_BLK_MAXC; ++c) {
         P->hb_start[c] = nh;
-        for (auto &e : hi[c]) { P->hb_p[nh] = (uint8_t)e.first; P->hb_q[nh] = (uint8_t)e.second; ++nh; }
+        for (auto &e : hi[c]) {
+            P->hb_p[nh] = (uint8_t)std::get<0>(e);
+            P->hb_q[nh] = (uint8_t)std::get<1>(e);
+            P->pb_hh[nh] = -bp.jm[std::get<2>(e)] / 2.0;                 // J_b / 2
+            ++nh;
+        }
         P->cb_start[c] = ncr;
-        for (auto &e : cr[c]) { P->cb_p[ncr] = (uint8_t)e.first; P->cb_q[ncr] = (uint8_t)e.second; ++ncr; }
+        for (auto &e : cr[c]) { P->cb_p[ncr] = (uint8_t)std::get<0>(e); P->cb_q[ncr] = (uint8_t)std::get<1>(e); ++ncr; }
     }
     P->hb_start[HM_BLK_MAXC] = nh;
     P->cb_start[HM_BLK_MAXC] = ncr;
@@ -357,14 +371,15 @@ int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int 
 }
 
 // kernel specialised to the plan (jit.cu), with its launch attributes; 1 = not available
-int jit_lz_kernel(const BlkParams &P, int dtype, const void **kern);
+int jit_lz_kernel(const BlkParams &P, int dtype, const BondParams &bp, const void **kern);
+int jit_mv_kernel(const BlkParams &P, int dtype, const BondParams &bp, const void **kern);
 // pad elements after the staged rows of a specialised kernel (jit.cu)
 int jit_pad(const void *kern);
 
-int blk_lz_jit(const BlkParams &P, int dtype, const void **kern, int *blocks) {
+int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void **kern, int *blocks) {
     *kern = nullptr;
     const void *k = nullptr;
-    if (jit_lz_kernel(P, dtype, &k) != 0) return 1;
+    if (jit_lz_kernel(P, dtype, bp, &k) != 0) return 1;
     const size_t sm = blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4, jit_pad(k));
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
         cudaGetLastError();
@@ -412,6 +427,40 @@ int blk_lz32_launch(const BlkParams &P, const float *qc, float *qp, LzScalars *S
     return HM_OK;
 }
 
+// per-bond plan: the specialised y = H x kernel (jit.cu); 1 when it is not available
+static int launch_blk_matvec_pb(hm_basis *b, const BlkParams &P, const BondParams &bp, const void *x, void *y,
+                                int dtype, cudaStream_t st) {
+    const void *k = nullptr;
+    if (jit_mv_kernel(P, dtype, bp, &k) != 0) return 1;
+    const size_t sm = blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4, BLK_XPAD);
+    HM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int *Ed = nullptr;
+    if (dtype == HM_F64) {
+        Ed = (int *)b->d_scratch;
+        HM_CUDA(cudaMemsetAsync(Ed, 0, sizeof(int), st));
+        k_max_exp<<<grid_blocks(P.dim, 256), 256, 0, st>>>((const unsigned long long *)x, P.dim, Ed);
+        HM_CUDA(cudaGetLastError());
+    }
+    int per = 0;
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BLK_NT, sm));
+    const int blocks = std::min<int>(sm_count() * std::max(per, 1), 1 << P.H);
+    void *args[] = {(void *)&P, (void *)&x, (void *)&y, (void *)&Ed};
+    HM_CUDA(cudaLaunchKernel(k, dim3(blocks), dim3(BLK_NT), args, sm, st));
+    return HM_OK;
+}
+
+// name of the kernel blk_matvec launches for these arguments, or nullptr when the block
+// path does not apply
+const char *blk_matvec_kernel(hm_basis *b, const BondParams &bp, int dtype, int nvec) {
+    if (nvec != 1) return nullptr;
+    BlkParams P;
+    if (blk_plan(b, bp, blk_K(b), &P) != 0) return nullptr;
+    if (!P.rows_ok || blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4, BLK_XPAD) > 200 * 1024) return nullptr;
+    if (!P.perbond) return "k_blk_matvec";
+    const void *k = nullptr;
+    return jit_mv_kernel(P, dtype, bp, &k) == 0 ? "k_blk_matvec_jit" : nullptr;
+}
+
 // returns 1 when the block path does not apply (caller falls back to the row kernel)
 int blk_matvec(hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype, int nvec,
                cudaStream_t st) {
@@ -420,6 +469,7 @@ int blk_matvec(hm_basis *b, const BondParams &bp, const void *x, void *y, int dt
     int rc = blk_plan(b, bp, blk_K(b), &P);
     if (rc != 0) return rc;
     if (!P.rows_ok || blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4, BLK_XPAD) > 200 * 1024) return 1;
+    if (P.perbond) return launch_blk_matvec_pb(b, P, bp, x, y, dtype, st);
     if (dtype == HM_F64) {
         switch (P.nc) {
             case 1: return launch_blk_matvec<double, 1>(b, P, (const double *)x, (double *)y, st);

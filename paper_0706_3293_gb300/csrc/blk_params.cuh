@@ -68,6 +68,13 @@ struct BlkParams {
     // spin-flip basis (M = 0): parity +1 / -1 of the representatives' vectors, 0 otherwise;
     // the blocks swept are those whose site N-1 (high bit H - 1) is up
     int par;
+    // per-bond couplings (more than HM_BLK_MAXC distinct J): every bond sits in the slots of
+    // class 0 and a row is y_i = pb_g0 x_i + sum over its allowed exchanges of
+    // h_b (x_i - x_target), h_b = J_b / 2, pb_g0 = -sum_b J_b / 4 (Eq. E-2-1)
+    int perbond;
+    double pb_g0;
+    uint8_t pb_lb[3][HM_BLK_SL], pb_xb[2][HM_BLK_SX];   // bond index of each low / cross slot
+    double pb_hh[HM_BLK_MAXB];                        // h_b of each high bond (hb_p / hb_q order)
 };
 
 

@@ -50,6 +50,8 @@ struct BlkMeta {                     // per-block data, double-buffered
     // target is row n - 1 - r of the complement block, hbf[e] its last row, by class
     uint32_t hbf[HM_BLK_MAXB];
     int fs[HM_BLK_MAXC], fe[HM_BLK_MAXC];
+    // per-bond plan: h_b of each entry of hbi and of hbf
+    double hbc[BLK_HBI], hbfc[HM_BLK_MAXB];
     uint32_t hv[2], hf[2];
     uint32_t off, n, kofs, lwo;
 };
@@ -90,6 +92,40 @@ __device__ __forceinline__ Sv blk_flip_sum(const BlkMeta &B, int c, const unsign
                                            const G &gx) {
     Sv a = Sv(0);
     for (int e = B.fs[c]; e < B.fe[c]; ++e) a += gx(Xg + (size_t)(B.hbf[e] - r) * sizeof(Sv));
+    return a;
+}
+
+// ---- per-bond rows: y_i = pb_g0 x_i + sum over allowed exchanges of h_b (x_i - x_t) ----------
+// accumulator: binary64 for the fixed-point rows (the difference of two fixed-point values
+// is exact; one rounding per term), float for FP32 rows
+template <class Sv> struct PbAcc { using T = double; };
+template <> struct PbAcc<float> { using T = float; };
+__device__ __forceinline__ double pb_fma(double h, int64_t d, double a) { return fma(h, (double)d, a); }
+__device__ __forceinline__ float pb_fma(double h, float d, float a) { return fmaf((float)h, d, a); }
+
+// high exchanges of a per-bond plan (class 0 lists), four gathers at a time; flipped
+// targets carry the parity
+template <class Sv, class G>
+__device__ __forceinline__ typename PbAcc<Sv>::T blk_high_pb(const BlkParams &P, const BlkMeta &B,
+                                                             const unsigned char *Xg, uint32_t r, const G &gx,
+                                                             Sv xo, typename PbAcc<Sv>::T a) {
+    const int e1 = B.he[0];
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(B.hbi);
+    int e = B.hs[0];
+    for (; e + 4 <= e1; e += 4) {
+        const uint4 t = h4[e >> 2];
+        const Sv v0 = gx(Xg + (size_t)(t.x + r) * sizeof(Sv)), v1 = gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
+        const Sv v2 = gx(Xg + (size_t)(t.z + r) * sizeof(Sv)), v3 = gx(Xg + (size_t)(t.w + r) * sizeof(Sv));
+        a = pb_fma(B.hbc[e], xo - v0, a);
+        a = pb_fma(B.hbc[e + 1], xo - v1, a);
+        a = pb_fma(B.hbc[e + 2], xo - v2, a);
+        a = pb_fma(B.hbc[e + 3], xo - v3, a);
+    }
+    for (; e < e1; ++e) a = pb_fma(B.hbc[e], xo - gx(Xg + (size_t)(B.hbi[e] + r) * sizeof(Sv)), a);
+    for (int f = B.fs[0]; f < B.fe[0]; ++f) {
+        const Sv v = gx(Xg + (size_t)(B.hbf[f] - r) * sizeof(Sv));
+        a = pb_fma(B.hbfc[f], xo - (P.par < 0 ? -v : v), a);
+    }
     return a;
 }
 
@@ -178,6 +214,7 @@ template <int NC>
 struct RowGeneric {
 static constexpr int kPad = BLK_XPAD;
 static constexpr bool kRelUS = false;
+static constexpr bool kPerBond = false;      // per-bond plans run only specialised (jit.cu)
 template <class Sv>
 static __device__ __forceinline__ void stage(const BlkParams &P, unsigned char *) {
     const uint16_t *Ug = (const uint16_t *)((const unsigned char *)P.tab + P.off_U);
@@ -319,8 +356,14 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
                 const int b0 = popc_below(hm, P.hb_start[c]), b1 = popc_below(hm, P.hb_start[c + 1]);
                 const int f0 = popc_below(fm, P.hb_start[c]), f1 = popc_below(fm, P.hb_start[c + 1]);
                 if (tid >= P.hb_start[c] && tid < P.hb_start[c + 1]) {
-                    if (hval) B.hbi[start + popc_below(hm, tid) - b0] = hidx;
-                    if (hflip) B.hbf[popc_below(fm, tid)] = hidx;
+                    if (hval) {
+                        B.hbi[start + popc_below(hm, tid) - b0] = hidx;
+                        if (P.perbond) B.hbc[start + popc_below(hm, tid) - b0] = P.pb_hh[tid];
+                    }
+                    if (hflip) {
+                        B.hbf[popc_below(fm, tid)] = hidx;
+                        if (P.perbond) B.hbfc[popc_below(fm, tid)] = P.pb_hh[tid];
+                    }
                 }
                 if (tid == c) { B.hs[c] = start; B.he[c] = start + (b1 - b0); B.fs[c] = f0; B.fe[c] = f1; }
                 start += (b1 - b0 + 3) & ~3;
@@ -337,10 +380,14 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
             if (r + BLK_NT < n) l_next = (uint32_t)__ldg(lw + r + BLK_NT);
             const auto pv = pref(off + r);                 // the row's other operand, ahead of the sums
             const Sv xo = Xs[r];
-            Sv acc[NC];
-            int cnt[NC];
-            Row::template sums<Sv>(P, B, Xsb, X, l, r, gx, xo, acc, cnt);
-            rowf(off, r, xo, acc, cnt, pv);
+            if constexpr (Row::kPerBond) {
+                rowf(off, r, xo, Row::template sums_pb<Sv>(P, B, Xsb, X, l, r, gx, xo), pv);
+            } else {
+                Sv acc[NC];
+                int cnt[NC];
+                Row::template sums<Sv>(P, B, Xsb, X, l, r, gx, xo, acc, cnt);
+                rowf(off, r, xo, acc, cnt, pv);
+            }
         }
         endf(it);
         h_prev = h;
@@ -404,19 +451,35 @@ __device__ __forceinline__ void matvec_body(const BlkParams &P, const T *__restr
         const int E = Eptr ? *Eptr : 0;
         const int u = E - 1022 - ef::FIX_BITS;
         unsigned long long *yb = (unsigned long long *)y;
-        blk_sweep<int64_t, NC, false, Row>(P, (const unsigned char *)x, GF64{E}, nullptr, [](uint32_t) { return 0; },
-                                      [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt, int) {
-                                          int64_t Tc[NC], ts;
-                                          blk_classes<NC>(P, acc, cnt, xo, Tc);
-                                          yb[off + r] = blk_y_bits<NC>(P, Tc, u, &ts);
-                                      },
-                                      [](int) {}, [](uint32_t, int) {});
+        if constexpr (Row::kPerBond) {
+            blk_sweep<int64_t, NC, false, Row>(P, (const unsigned char *)x, GF64{E}, nullptr, [](uint32_t) { return 0; },
+                                          [&](uint32_t off, uint32_t r, int64_t xo, double sv, int) {
+                                              yb[off + r] = ef::d2u(ldexp(fma(P.pb_g0, (double)xo, sv), u));
+                                          },
+                                          [](int) {}, [](uint32_t, int) {});
+        } else {
+            blk_sweep<int64_t, NC, false, Row>(P, (const unsigned char *)x, GF64{E}, nullptr, [](uint32_t) { return 0; },
+                                          [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt, int) {
+                                              int64_t Tc[NC], ts;
+                                              blk_classes<NC>(P, acc, cnt, xo, Tc);
+                                              yb[off + r] = blk_y_bits<NC>(P, Tc, u, &ts);
+                                          },
+                                          [](int) {}, [](uint32_t, int) {});
+        }
     } else {
-        blk_sweep<float, NC, false, Row>(P, (const unsigned char *)x, GF32{}, nullptr, [](uint32_t) { return 0; },
-                                    [&](uint32_t off, uint32_t r, float xo, const float *acc, const int *cnt, int) {
-                                        y[off + r] = blk_y_f32<NC>(P, acc, cnt, xo);
-                                    },
-                                    [](int) {}, [](uint32_t, int) {});
+        if constexpr (Row::kPerBond) {
+            blk_sweep<float, NC, false, Row>(P, (const unsigned char *)x, GF32{}, nullptr, [](uint32_t) { return 0; },
+                                        [&](uint32_t off, uint32_t r, float xo, float sv, int) {
+                                            y[off + r] = fmaf((float)P.pb_g0, xo, sv);
+                                        },
+                                        [](int) {}, [](uint32_t, int) {});
+        } else {
+            blk_sweep<float, NC, false, Row>(P, (const unsigned char *)x, GF32{}, nullptr, [](uint32_t) { return 0; },
+                                        [&](uint32_t off, uint32_t r, float xo, const float *acc, const int *cnt, int) {
+                                            y[off + r] = blk_y_f32<NC>(P, acc, cnt, xo);
+                                        },
+                                        [](int) {}, [](uint32_t, int) {});
+        }
     }
 }
 
@@ -450,30 +513,40 @@ __device__ __forceinline__ void lz64_body(const BlkParams &P, const long long *_
     const int u = E - 1022 - ef::FIX_BITS;
     __int128 d1 = 0;
     ef::df d1f{0.0f, 0.0f};
-    blk_sweep<int64_t, NC, true, Row>(
-        P, (const unsigned char *)Xc, GFix{}, S->sched, [](uint32_t) { return 0; },
-        [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt, int) {
-            int64_t Tc[NC], ts;
-            blk_classes<NC>(P, acc, cnt, xo, Tc);
-            const unsigned long long yb = blk_y_bits<NC, IR ? 1 : 0>(P, Tc, u, &ts);
-            __stcs(Y + off + r, yb);
-            if constexpr (IR) d1 += (__int128)xo * ts;
-            else d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
-        },
-        [&](int it) {
+    // row value: exact class sums, or (per-bond plan) one binary64 sum of h_b (x_i - x_t)
+    auto rowc = [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt, int) {
+        int64_t Tc[NC], ts;
+        blk_classes<NC>(P, acc, cnt, xo, Tc);
+        const unsigned long long yb = blk_y_bits<NC, IR ? 1 : 0>(P, Tc, u, &ts);
+        __stcs(Y + off + r, yb);
+        if constexpr (IR) d1 += (__int128)xo * ts;
+        else d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
+    };
+    auto rowb = [&](uint32_t off, uint32_t r, int64_t xo, double sv, int) {
+        const unsigned long long yb = ef::d2u(ldexp(fma(P.pb_g0, (double)xo, sv), u));
+        __stcs(Y + off + r, yb);
+        d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
+    };
+    auto endf = [&](int it) {
             // true units: q.y = g0 2^(2u) sum X Tsum (integer ratios) or the double-float
             // sum scaled back by 2^(2(E-1023))
-            const double q_y = IR ? ldexp(i128_to_double(d1) * P.g0, 2 * u)
-                                  : ldexp((double)d1f.hi + (double)d1f.lo, 2 * (E - 1023));
+            const double q_y = IR && !Row::kPerBond ? ldexp(i128_to_double(d1) * P.g0, 2 * u)
+                                                    : ldexp((double)d1f.hi + (double)d1f.lo, 2 * (E - 1023));
             d1 = 0; d1f = ef::df{0.0f, 0.0f};
             const double a = warp_sum(q_y);
             if ((threadIdx.x & 31) == 0) s_wpart[it & 1][threadIdx.x >> 5][0] = a;
-        },
-        [&](uint32_t h, int it) {
+        };
+    auto flushf = [&](uint32_t h, int it) {
             double a = 0.0;
             for (int w = 0; w < BLK_NT / 32; ++w) a += s_wpart[it & 1][w][0];
             part[h] = a;
-        });
+        };
+    if constexpr (Row::kPerBond)
+        blk_sweep<int64_t, NC, true, Row>(P, (const unsigned char *)Xc, GFix{}, S->sched, [](uint32_t) { return 0; },
+                                          rowb, endf, flushf);
+    else
+        blk_sweep<int64_t, NC, true, Row>(P, (const unsigned char *)Xc, GFix{}, S->sched, [](uint32_t) { return 0; },
+                                          rowc, endf, flushf);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -486,25 +559,34 @@ __device__ __forceinline__ void lz32_body(const BlkParams &P, const float *__res
     if (S->done) return;
     const float sig = (float)S->sigma_cur, gam = (float)(S->beta_prev * S->sigma_prev);
     ef::df dot{0.0f, 0.0f};
-    blk_sweep<float, NC, true, Row>(
-        P, (const unsigned char *)qc, GF32{}, S->sched,
-        [&](uint32_t i) { return qp[i]; },
-        [&](uint32_t off, uint32_t r, float xo, const float *acc, const int *cnt, float qpr) {
-            const float hv = blk_y_f32<NC>(P, acc, cnt, xo);
-            const float uu = sig * hv - gam * qpr;
-            qp[off + r] = uu;
-            dot = ef::df_add(dot, ef::two_prod(sig * xo, uu));
-        },
-        [&](int it) {
-            const double a = warp_sum((double)dot.hi + (double)dot.lo);
-            dot = ef::df{0.0f, 0.0f};
-            if ((threadIdx.x & 31) == 0) s_wpart[it & 1][threadIdx.x >> 5][0] = a;
-        },
-        [&](uint32_t h, int it) {
-            double a = 0.0;
-            for (int w = 0; w < BLK_NT / 32; ++w) a += s_wpart[it & 1][w][0];
-            part[h] = a;
-        });
+    auto pref = [&](uint32_t i) { return qp[i]; };
+    auto rowu = [&](uint32_t off, uint32_t r, float xo, float hv, float qpr) {
+        const float uu = sig * hv - gam * qpr;
+        qp[off + r] = uu;
+        dot = ef::df_add(dot, ef::two_prod(sig * xo, uu));
+    };
+    auto endf = [&](int it) {
+        const double a = warp_sum((double)dot.hi + (double)dot.lo);
+        dot = ef::df{0.0f, 0.0f};
+        if ((threadIdx.x & 31) == 0) s_wpart[it & 1][threadIdx.x >> 5][0] = a;
+    };
+    auto flushf = [&](uint32_t h, int it) {
+        double a = 0.0;
+        for (int w = 0; w < BLK_NT / 32; ++w) a += s_wpart[it & 1][w][0];
+        part[h] = a;
+    };
+    if constexpr (Row::kPerBond)
+        blk_sweep<float, NC, true, Row>(P, (const unsigned char *)qc, GF32{}, S->sched, pref,
+                                        [&](uint32_t off, uint32_t r, float xo, float sv, float qpr) {
+                                            rowu(off, r, xo, fmaf((float)P.pb_g0, xo, sv), qpr);
+                                        },
+                                        endf, flushf);
+    else
+        blk_sweep<float, NC, true, Row>(P, (const unsigned char *)qc, GF32{}, S->sched, pref,
+                                        [&](uint32_t off, uint32_t r, float xo, const float *acc, const int *cnt, float qpr) {
+                                            rowu(off, r, xo, blk_y_f32<NC>(P, acc, cnt, xo), qpr);
+                                        },
+                                        endf, flushf);
 }
 
 }  // namespace hm

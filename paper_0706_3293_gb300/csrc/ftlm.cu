@@ -907,7 +907,8 @@ static int ft_prepare(int n_sites, int two_s, int n_bonds, const int32_t *u, con
     memset(&S->F, 0, sizeof S->F);
     const int prc = blk_plan(&S->full, bp, K, &S->F.P);
     if (prc < 0) return prc;
-    if (prc > 0) return fail(HM_EINVAL, "ftlm_run: more than %d coupling classes or %d bonds", HM_BLK_MAXC, HM_BLK_MAXB);
+    if (prc > 0 || S->F.P.perbond)
+        return fail(HM_EINVAL, "ftlm_run: more than %d coupling classes or %d bonds", HM_BLK_MAXC, HM_BLK_MAXB);
     // the plan's block size was taken for A = N; use the largest over all sectors
     uint64_t mb = 1;
     for (int i = 0; i < K / 2; ++i) mb = mb * (K - i) / (i + 1);

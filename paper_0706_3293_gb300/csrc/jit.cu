@@ -117,6 +117,7 @@ std::string gen_row_slots(const BlkParams &P) {
     s += "struct RowJit {\n"
          "static constexpr int kPad = hm::BLK_XPAD;\n"
          "static constexpr bool kRelUS = false;\n"
+         "static constexpr bool kPerBond = false;\n"
          "template <class Sv>\n"
          "static __device__ __forceinline__ void stage(const hm::BlkParams &P, unsigned char *dyn) {\n"
          "    hm::RowGeneric<1>::stage<Sv>(P, dyn);\n"
@@ -176,6 +177,67 @@ std::string gen_row_slots(const BlkParams &P) {
     return s;
 }
 
+// The row policy of a per-bond plan (BlkParams::perbond): the slots of class 0 written out
+// as in gen_row_slots, each with its own coefficient h_b = J_b / 2 as a literal, summed
+// as h_b (x_i - x_t) (blk_sweep.cuh, per-bond rows).  A slot whose spins are parallel reads
+// a fixed address (a broadcast) and adds a zero difference.
+std::string gen_row_pb(const BlkParams &P, const BondParams &bp) {
+    auto hb = [&](int t) { return -bp.jm[t] / 2.0; };
+    std::string s;
+    s += "struct RowJit {\n"
+         "static constexpr int kPad = hm::BLK_XPAD;\n"
+         "static constexpr bool kRelUS = false;\n"
+         "static constexpr bool kPerBond = true;\n"
+         "template <class Sv>\n"
+         "static __device__ __forceinline__ void stage(const hm::BlkParams &P, unsigned char *dyn) {\n"
+         "    hm::RowGeneric<1>::stage<Sv>(P, dyn);\n"
+         "}\n"
+         "template <class Sv>\n"
+         "static __device__ __forceinline__ void block(const hm::BlkParams &, uint32_t) {}\n"
+         "template <class Sv, class G>\n"
+         "static __device__ __forceinline__ typename hm::PbAcc<Sv>::T sums_pb(const hm::BlkParams &P,\n"
+         "        const hm::BlkMeta &B, const unsigned char *Xsb, const unsigned char *Xg, uint32_t l, uint32_t r,\n"
+         "        const G &gx, Sv xo) {\n"
+         "    const uint32_t l4 = l << 2, lh4 = (l >> 8) << 2, lh4k = lh4 | B.kofs;\n"
+         "    const uint32_t R0own = hm::r0s_at(l4 & 0x3FCu), R1own = hm::us_at(lh4k);\n"
+         "    const uint32_t zo = (uint32_t)((P.max_block + hm::BLK_XPAD - 1) * sizeof(Sv));   // fixed address\n"
+         "    (void)R0own; (void)R1own; (void)lh4; (void)gx; (void)zo;\n"
+         "    typename hm::PbAcc<Sv>::T a = 0;\n";
+    std::set<int> ds;
+    for (int t = 0; t < 3; ++t)
+        for (int k = 0; k < P.ln[0][t]; ++k) ds.insert(P.ld[0][t][k]);
+    for (int d : ds) put(s, "    const uint32_t z%d = l ^ (l >> %d);\n", d, d);
+    for (int k = P.ln[0][0] - 1; k >= 0; --k)
+        put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = R1own + hm::r0s_at(t ? (l4 ^ 0x%xu) & 0x3FCu : 0u); "
+               "const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); a = hm::pb_fma(%.17g, t ? xo - x : Sv(0), a); }\n",
+            P.ld[0][0][k], P.lvm[0][0][k], (unsigned)P.lxa[0][0][k], hb(P.pb_lb[0][k]));
+    for (int k = P.ln[0][1] - 1; k >= 0; --k)
+        put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = R0own + hm::us_at(lh4k ^ 0x%xu); "
+               "const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); a = hm::pb_fma(%.17g, t ? xo - x : Sv(0), a); }\n",
+            P.ld[0][1][k], P.lvm[0][1][k], (unsigned)P.lxb[0][1][k], hb(P.pb_lb[1][k]));
+    for (int k = P.ln[0][2] - 1; k >= 0; --k)
+        put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = hm::us_at(lh4k ^ 0x%xu) + "
+               "hm::r0s_at(t ? (l4 ^ 0x%xu) & 0x3FCu : 0u); const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); "
+               "a = hm::pb_fma(%.17g, t ? xo - x : Sv(0), a); }\n",
+            P.ld[0][2][k], P.lvm[0][2][k], (unsigned)P.lxb[0][2][k], (unsigned)P.lxa[0][2][k], hb(P.pb_lb[2][k]));
+    auto xval = [&](int dst) -> const char * {
+        for (int e = 0; e < P.nxf; ++e)
+            if (P.xf_dst[e] == dst && P.par && P.xf_q[e] == P.H - 1)
+                return P.par < 0 ? "(-gx(x_.base - v_))" : "gx(x_.base - v_)";
+        return "gx(x_.base + v_)";
+    };
+    for (int k = P.xn[0][0] - 1; k >= 0; --k)
+        put(s, "    { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at(lh4 | x_.kofs2) + "
+               "hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu); if ((l ^ x_.wm) & x_.vm) a = hm::pb_fma(%.17g, xo - %s, a); }\n",
+            k, (unsigned)P.xxa[0][0][k], hb(P.pb_xb[0][k]), xval(k));
+    for (int k = P.xn[0][1] - 1; k >= 0; --k)
+        put(s, "    { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at((lh4 ^ 0x%xu) | x_.kofs2) + "
+               "R0own; if ((l ^ x_.wm) & x_.vm) a = hm::pb_fma(%.17g, xo - %s, a); }\n",
+            HM_BLK_SX + k, (unsigned)P.xxa[0][1][k], hb(P.pb_xb[1][k]), xval(HM_BLK_SX + k));
+    s += "    return hm::blk_high_pb<Sv>(P, B, Xg, r, gx, xo, a);\n}\n};\n";
+    return s;
+}
+
 // The row policy of a plan (interface in blk_sweep.cuh), every count, shift and mask a
 // literal.  The low bonds with both ends in one byte of the low word take their target
 // from per-byte delta tables: the target row of slot s is r + D[b][s], with D = 0 when
@@ -203,7 +265,8 @@ std::string gen_row(const BlkParams &P, bool &ok) {
         NC * 256 * w0, NC * P.nb1 * w1, 3 * P.nb1);
     s += "__device__ __forceinline__ uint32_t us3_at(uint32_t o) {\n"
          "    return *(const uint32_t *)((const unsigned char *)s_US3 + o);\n}\n";
-    s += "struct RowJit {\nstatic constexpr int kPad = 0;\nstatic constexpr bool kRelUS = true;\n";
+    s += "struct RowJit {\nstatic constexpr int kPad = 0;\nstatic constexpr bool kRelUS = true;\n"
+         "static constexpr bool kPerBond = false;\n";
     // stage: D0
     s += "template <class Sv>\nstatic __device__ __forceinline__ void stage(const hm::BlkParams &P, unsigned char *) {\n"
          "    const uint8_t *R0g = (const uint8_t *)P.tab + P.off_R0;\n"
@@ -344,17 +407,62 @@ int compile(const std::string &src, const char *name, int device, const void **o
 // k_blk_lz32_jit), compiled on first use and cached for the process.  Returns 0 and the
 // handle (usable with cudaLaunchKernel / cudaFuncSetAttribute), or 1 when the generic
 // kernel has to serve.
-int jit_lz_kernel(const BlkParams &P, int dtype, const void **kern) {
+// source of the row policy for plan P: per-bond, per-byte delta tables, or slots
+static bool jit_row_source(const BlkParams &P, const BondParams &bp, std::string *src, bool *delta) {
+    bool gen_ok = true;
+    const char *rowk = getenv("HM_JIT_ROW");
+    *delta = !P.perbond && rowk && strcmp(rowk, "delta") == 0 && !P.par;   // no spin-flip or per-bond form
+    *src = "#include \"blk_sweep.cuh\"\n" +
+           (P.perbond ? gen_row_pb(P, bp) : *delta ? gen_row(P, gen_ok) : gen_row_slots(P));
+    return gen_ok;
+}
+
+// compiles (or finds) kernel `name` of source src for the current device
+static int jit_get(const std::string &src, const char *name, int dev, int pad, const void **kern) {
+    const std::string key = std::to_string(dev) + "\n" + src;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) { *kern = it->second; return 0; }
+    if (g_failed.count(key)) return 1;
+    if (!load_nvrtc()) {
+        if (verbose()) fprintf(stderr, "[hm jit] %s\n", g_nv.why.c_str());
+        return 1;
+    }
+    const void *k = nullptr;
+    if (compile(src, name, dev, &k) != 0) { g_failed.insert(key); return 1; }
+    g_cache.emplace(key, k);
+    g_pad[k] = pad;
+    *kern = k;
+    return 0;
+}
+
+// y = H x kernel (matvec API) for a per-bond plan: k_blk_matvec_jit, one vector, dtype
+// HM_F64 (binary64 x, E = its largest exponent field in Eptr) or HM_F32
+int jit_mv_kernel(const BlkParams &P, int dtype, const BondParams &bp, const void **kern) {
+    const char *env = getenv("HM_JIT");
+    if ((env && env[0] == '0') || !P.rows_ok || !P.perbond) return 1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
+    std::string src;
+    bool delta = false;
+    if (!jit_row_source(P, bp, &src, &delta)) return 1;
+    const char *T = dtype == HM_F64 ? "double" : "float";
+    put(src,
+        "extern \"C\" __global__ void __launch_bounds__(512, 3) k_blk_matvec_jit(hm::BlkParams P,\n"
+        "        const %s *__restrict__ x, %s *__restrict__ y, const int *__restrict__ Eptr) {\n"
+        "    hm::matvec_body<%s, 1, RowJit>(P, x, y, Eptr);\n}\n", T, T, T);
+    return jit_get(src, "k_blk_matvec_jit", dev, BLK_XPAD, kern);
+}
+
+int jit_lz_kernel(const BlkParams &P, int dtype, const BondParams &bp, const void **kern) {
     const char *env = getenv("HM_JIT");
     if (env && env[0] == '0') return 1;
     if (!P.rows_ok) return 1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
-    bool gen_ok = true;
-    const char *rowk = getenv("HM_JIT_ROW");
-    const bool delta = rowk && strcmp(rowk, "delta") == 0 && !P.par;   // no spin-flip form
-    std::string src = "#include \"blk_sweep.cuh\"\n" + (delta ? gen_row(P, gen_ok) : gen_row_slots(P));
-    if (!gen_ok) return 1;
+    std::string src;
+    bool delta = false;
+    if (!jit_row_source(P, bp, &src, &delta)) return 1;
     const bool f64 = dtype == HM_F64;
     const int nc = P.nc == 1 ? 1 : (P.nc == 2 ? 2 : 4);
     const char *name = f64 ? "k_blk_lz64_jit" : "k_blk_lz32_jit";
@@ -368,28 +476,14 @@ int jit_lz_kernel(const BlkParams &P, int dtype, const void **kern) {
             "        const long long *__restrict__ Xc, unsigned long long *__restrict__ Y, hm::LzScalars *S, int pc,\n"
             "        double *__restrict__ part) {\n"
             "    hm::lz64_body<%d, %s, RowJit>(P, Xc, Y, S, pc, part);\n}\n",
-            ctas, nc, P.iratio ? "true" : "false");
+            ctas, nc, P.iratio && !P.perbond ? "true" : "false");
     else
         put(src,
             "extern \"C\" __global__ void __launch_bounds__(512, %d) k_blk_lz32_jit(hm::BlkParams P,\n"
             "        const float *__restrict__ qc, float *__restrict__ qp, hm::LzScalars *S, double *__restrict__ part) {\n"
             "    hm::lz32_body<%d, RowJit>(P, qc, qp, S, part);\n}\n",
             ctas, nc);
-    const std::string key = std::to_string(dev) + "\n" + src;
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_cache.find(key);
-    if (it != g_cache.end()) { *kern = it->second; return 0; }
-    if (g_failed.count(key)) return 1;
-    if (!load_nvrtc()) {
-        if (verbose()) fprintf(stderr, "[hm jit] %s\n", g_nv.why.c_str());
-        return 1;
-    }
-    const void *k = nullptr;
-    if (compile(src, name, dev, &k) != 0) { g_failed.insert(key); return 1; }
-    g_cache.emplace(key, k);
-    g_pad[k] = delta ? 0 : BLK_XPAD;
-    *kern = k;
-    return 0;
+    return jit_get(src, name, dev, delta ? 0 : BLK_XPAD, kern);
 }
 
 int jit_pad(const void *kern) {

@@ -13,7 +13,7 @@
 namespace hm {
 
 int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int *blocks);
-int blk_lz_jit(const BlkParams &P, int dtype, const void **kern, int *blocks);
+int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void **kern, int *blocks);
 int blk_lz64_launch(const BlkParams &P, const long long *Xc, unsigned long long *Y, LzScalars *S, int pc,
                     double *part, int blocks, cudaStream_t st, const void *jit);
 int blk_lz32_launch(const BlkParams &P, const float *qc, float *qp, LzScalars *S, double *part, int blocks,
@@ -661,16 +661,17 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
     rc = blk_lz_plan(const_cast<hm_basis *>(b), R->bp, dtype, &R->blk, &R->blk_blocks);
     if (rc < 0) { delete R; return rc; }
     R->use_blk = rc == 0 && (dtype == HM_F32 || R->L.shadow) && R->L.hpart != 0 && R->blk.H <= 17;
-    if (b->parity && !R->use_blk) {
-        delete R;
-        return fail(HM_EINVAL, "spin-flip basis: this bond list does not take the s = 1/2 block path");
-    }
     R->jit = nullptr;
     R->run = row_run_len();
     if (R->use_blk) {
         int jb = 0;
         const void *jk = nullptr;
-        if (blk_lz_jit(R->blk, dtype, &jk, &jb) == 0) { R->jit = jk; R->blk_blocks = jb; }
+        if (blk_lz_jit(R->blk, dtype, R->bp, &jk, &jb) == 0) { R->jit = jk; R->blk_blocks = jb; }
+        if (R->blk.perbond && !R->jit) R->use_blk = 0;   // per-bond rows run only specialised
+    }
+    if (b->parity && !R->use_blk) {
+        delete R;
+        return fail(HM_EINVAL, "spin-flip basis: this bond list does not take the s = 1/2 block path");
     }
     R->work = (unsigned char *)work;
     R->sc = (LzScalars *)(R->work + R->L.sc);

@@ -1,4 +1,5 @@
 // matvec.cu -- y = H x by rows (Eq. E-4-b), the bond-correlation adjoint, start vectors.
+#include <cstdio>
 #include <mutex>
 
 #include "hm_row.cuh"
@@ -156,6 +157,7 @@ size_t bond_corr_bytes(const hm_basis *b, int n_bonds) {
 
 int blk_matvec(hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype, int nvec,
                cudaStream_t st);
+const char *blk_matvec_kernel(hm_basis *b, const BondParams &bp, int dtype, int nvec);
 
 int matvec_dev(const hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype,
                int nvec, cudaStream_t st) {
@@ -234,6 +236,18 @@ int matvec(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, c
     BondParams bp;
     HM_TRY(make_bonds(b, n_bonds, u, v, J, &bp));
     return matvec_dev(b, bp, x, y, dtype, nvec, as_stream(stream));
+}
+
+int matvec_kernel_name(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, const double *J,
+                       int dtype, int nvec, char *name, int cap) {
+    if (!b || !name || cap < 1) return fail(HM_EINVAL, "NULL argument");
+    if (dtype != HM_F64 && dtype != HM_F32) return fail(HM_EINVAL, "dtype must be HM_F64 or HM_F32");
+    BondParams bp;
+    HM_TRY(make_bonds(b, n_bonds, u, v, J, &bp));
+    const char *n = blk_matvec_kernel(const_cast<hm_basis *>(b), bp, dtype, nvec);
+    if (!n && b->parity) return fail(HM_EINVAL, "spin-flip basis: this bond list or vector count does not take the s = 1/2 block path");
+    snprintf(name, (size_t)cap, "%s", n ? n : "k_matvec");
+    return HM_OK;
 }
 
 int count_nnz(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, int64_t *nnz,

@@ -518,3 +518,77 @@ def test_block_product_specialised_equals_generic_full_size(hm, monkeypatch):
     assert out["1"][0] == "k_blk_lz64_jit" and out["0"][0] == "k_blk_lz64"
     (a1, b1, _), (a0, b0, _) = out["1"][1], out["0"][1]
     assert np.array_equal(a1, a0) and np.array_equal(b1, b0)
+
+
+# ---- per-bond plans: more distinct couplings than the block path's classes ---------------
+
+def randj_ring(N, seed, j2=-0.4):
+    inst = W.small_ring(N, -1.0, j2)
+    return inst, np.random.default_rng(seed).uniform(-1.3, -0.5, inst.n_bonds)
+
+
+@pytest.mark.parametrize("jit", ["1", "0"])
+@pytest.mark.parametrize("N,seed", [(12, 1), (16, 2), (20, 3), (24, 4)])
+def test_perbond_matvec_vs_oracle(hm, N, seed, jit, monkeypatch):
+    """Every bond its own coupling: the specialised per-bond block kernel (jit=1) and the
+    general row kernel it falls back to without run-time compilation (jit=0), FP64 and FP32."""
+    monkeypatch.setenv("HM_JIT", jit)
+    inst, J = randj_ring(N, seed)
+    b = hm.Basis(N, 1, 0)
+    ob = oracle.Basis(N, 1, N // 2)
+    bl = hm.BondList.make(inst.u, inst.v, J)
+    obl = oracle.Bonds(inst.u, inst.v, J)
+    x = oracle.start_uniform(7, b.dim)
+    ref = ob.matvec(obl, x)
+    y = hm.matvec(b, bl, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, ref) <= TOL_F64
+    x32 = x.astype(np.float32)
+    ref32 = ob.matvec(obl, x32.astype(np.float64))
+    y32 = hm.matvec(b, bl, torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
+    assert rel(y32, ref32) <= TOL_F32
+
+
+@pytest.mark.parametrize("parity", [1, -1])
+def test_perbond_flip_matvec_vs_oracle(hm, parity):
+    inst, J = randj_ring(20, 6)
+    b = hm.Basis(20, 1, 0, parity=parity)
+    ob = oracle.Basis(20, 1, 10)
+    x = oracle.start_uniform(8, b.dim)
+    ref = oracle.flip_matvec(ob, oracle.Bonds(inst.u, inst.v, J), x, parity)
+    y = hm.matvec(b, hm.BondList.make(inst.u, inst.v, J), torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, ref) <= TOL_F64
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_perbond_lanczos_vs_oracle(hm, dtype):
+    """N = 20 ring with 40 distinct couplings: the Lanczos product runs the specialised
+    per-bond kernel; alpha, beta of the first steps and E0 against the oracle."""
+    inst, J = randj_ring(20, 9)
+    b = hm.Basis(20, 1, 0)
+    ob = oracle.Basis(20, 1, 10)
+    bl = hm.BondList.make(inst.u, inst.v, J)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    run = hm.LanczosRun(b, bl, 10, seed=4, dtype=tdt)
+    assert run.kernel_name() == ("k_blk_lz64_jit" if dtype == "f64" else "k_blk_lz32_jit")
+    run.close()
+    res = hm.lanczos_run(b, bl, 200, seed=4, n_ritz=1, dtype=tdt)
+    al, be = ob.lanczos(oracle.Bonds(inst.u, inst.v, J), oracle.start_uniform(4, b.dim), 200)
+    e_ref = oracle.tridiag_lowest(al, be, 1)[0]
+    if dtype == "f64":
+        np.testing.assert_allclose(res.alpha[:20], al[:20], rtol=0, atol=1e-12 * np.abs(al).max())
+        np.testing.assert_allclose(res.beta[:20], be[:20], rtol=0, atol=1e-12 * np.abs(al).max())
+        assert abs(res.ritz[0] - e_ref) <= TOL_E0 * abs(e_ref)
+    else:
+        assert abs(res.ritz[0] - e_ref) <= 1e-6 * abs(e_ref)
+
+
+def test_matvec_kernel_name_dispatch(hm):
+    """The kernel matvec takes: block kernel (few couplings), block kernel compiled for the
+    bond list (per-bond couplings), general row kernel (s = 1, or several vectors)."""
+    inst, J = randj_ring(16, 2)
+    b = hm.Basis(16, 1, 0)
+    assert hm.matvec_kernel_name(b, hm.bonds_of(W.ring16())) == "k_blk_matvec"
+    assert hm.matvec_kernel_name(b, hm.BondList.make(inst.u, inst.v, J)) == "k_blk_matvec_jit"
+    assert hm.matvec_kernel_name(b, hm.bonds_of(W.ring16()), nvec=2) == "k_matvec"
+    s1 = W.s1_random_graph(10, 21)
+    assert hm.matvec_kernel_name(hm.Basis(10, 2, 0), hm.bonds_of(s1)) == "k_matvec"
