@@ -106,6 +106,9 @@ static int blk_tables(hm_basis *b, int K, const void **dev, int *bytes, int *oU,
     return HM_OK;
 }
 
+// integer coefficient of a per-bond plan: round(h 2^pb_s)
+long long pb_coef(const BlkParams &P, double h) { return std::llround(std::ldexp(h, P.pb_s)); }
+
 // Compile-time slots of the thread-per-row kernels (BlkParams::ln ..).  Sets rows_ok = 0
 // when a class has more bonds of one kind than the slots hold.
 static void blk_plan_slots(const BondParams &bp, const std::vector<int> &bc, int K, BlkParams *P) {
@@ -171,9 +174,17 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
         P->perbond = 1;
         cls.clear();
         std::fill(bc.begin(), bc.end(), 0);
-        double g0 = 0.0;
-        for (int t = 0; t < bp.nb; ++t) g0 += bp.jm[t] / 4.0;      // -J_b / 4
+        double g0 = 0.0, mx = 0.0;
+        for (int t = 0; t < bp.nb; ++t) {
+            g0 += bp.jm[t] / 4.0;                                 // -J_b / 4
+            mx = std::max(mx, std::fabs(bp.jm[t] / 2.0));
+        }
         P->pb_g0 = g0;
+        mx = std::max(mx, std::fabs(g0));
+        int ex = 0;
+        std::frexp(mx, &ex);                                      // mx < 2^ex
+        P->pb_s = mx > 0.0 ? 61 - ex : 0;                         // |C| <= 2^61
+        P->pb_c0 = std::llround(std::ldexp(g0, P->pb_s));
     }
     P->nc = (int)cls.size() > 0 ? (int)cls.size() : 1;
     if (P->perbond) P->ntot[0] = 0;
@@ -248,7 +259,7 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
         for (auto &e : hi[c]) {
             P->hb_p[nh] = (uint8_t)std::get<0>(e);
             P->hb_q[nh] = (uint8_t)std::get<1>(e);
-            P->pb_hh[nh] = -bp.jm[std::get<2>(e)] / 2.0;                 // J_b / 2
+            if (P->perbond) P->pb_hc[nh] = pb_coef(*P, -bp.jm[std::get<2>(e)] / 2.0);   // J_b / 2
             ++nh;
         }
         P->cb_start[c] = ncr;

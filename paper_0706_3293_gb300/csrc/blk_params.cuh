@@ -69,12 +69,16 @@ struct BlkParams {
     // the blocks swept are those whose site N-1 (high bit H - 1) is up
     int par;
     // per-bond couplings (more than HM_BLK_MAXC distinct J): every bond sits in the slots of
-    // class 0 and a row is y_i = pb_g0 x_i + sum over its allowed exchanges of
-    // h_b (x_i - x_target), h_b = J_b / 2, pb_g0 = -sum_b J_b / 4 (Eq. E-2-1)
+    // class 0 and a row is y_i = g0 x_i + sum over its allowed exchanges of
+    // h_b (x_i - x_target), h_b = J_b / 2, g0 = -sum_b J_b / 4 (Eq. E-2-1).  In FP64 the
+    // coefficients are integers scaled by 2^pb_s (|C| < 2^62): C_b = round(h_b 2^pb_s),
+    // pb_c0 = round(g0 2^pb_s), and a row is one exact int128 sum, rounded once
     int perbond;
+    int pb_s;
+    long long pb_c0;
     double pb_g0;
     uint8_t pb_lb[3][HM_BLK_SL], pb_xb[2][HM_BLK_SX];   // bond index of each low / cross slot
-    double pb_hh[HM_BLK_MAXB];                        // h_b of each high bond (hb_p / hb_q order)
+    long long pb_hc[HM_BLK_MAXB];                     // C_b of each high bond (hb_p / hb_q order)
 };
 
 

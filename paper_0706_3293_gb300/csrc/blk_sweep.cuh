@@ -50,8 +50,10 @@ struct BlkMeta {                     // per-block data, double-buffered
     // target is row n - 1 - r of the complement block, hbf[e] its last row, by class
     uint32_t hbf[HM_BLK_MAXB];
     int fs[HM_BLK_MAXC], fe[HM_BLK_MAXC];
-    // per-bond plan: h_b of each entry of hbi and of hbf
-    double hbc[BLK_HBI], hbfc[HM_BLK_MAXB];
+    // per-bond plan: coefficient of each entry of hbi and of hbf, integer (C_b, FP64 rows)
+    // and float (FP32 rows)
+    long long hbc[BLK_HBI], hbfc[HM_BLK_MAXB];
+    float hbcf[BLK_HBI], hbfcf[HM_BLK_MAXB];
     uint32_t hv[2], hf[2];
     uint32_t off, n, kofs, lwo;
 };
@@ -95,13 +97,19 @@ __device__ __forceinline__ Sv blk_flip_sum(const BlkMeta &B, int c, const unsign
     return a;
 }
 
-// ---- per-bond rows: y_i = pb_g0 x_i + sum over allowed exchanges of h_b (x_i - x_t) ----------
-// accumulator: binary64 for the fixed-point rows (the difference of two fixed-point values
-// is exact; one rounding per term), float for FP32 rows
-template <class Sv> struct PbAcc { using T = double; };
+// ---- per-bond rows: y_i = g0 x_i + sum over allowed exchanges of h_b (x_i - x_t) ----------
+// fixed-point rows: exact int128 sum of C_b (x_i - x_t) (|C_b| <= 2^61, |x_i - x_t| < 2^54,
+// at most 64 terms and C0 x_i: below 2^123); FP32 rows: float multiply-adds
+template <class Sv> struct PbAcc { using T = __int128; };
 template <> struct PbAcc<float> { using T = float; };
-__device__ __forceinline__ double pb_fma(double h, int64_t d, double a) { return fma(h, (double)d, a); }
-__device__ __forceinline__ float pb_fma(double h, float d, float a) { return fmaf((float)h, d, a); }
+__device__ __forceinline__ __int128 pb_mac(long long C, float, int64_t d, __int128 a) { return a + (__int128)C * d; }
+__device__ __forceinline__ float pb_mac(long long, float Cf, float d, float a) { return fmaf(Cf, d, a); }
+
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo = (unsigned long long)v;
+    return (double)hi * 18446744073709551616.0 + (double)lo;
+}
 
 // high exchanges of a per-bond plan (class 0 lists), four gathers at a time; flipped
 // targets carry the parity
@@ -116,15 +124,15 @@ __device__ __forceinline__ typename PbAcc<Sv>::T blk_high_pb(const BlkParams &P,
         const uint4 t = h4[e >> 2];
         const Sv v0 = gx(Xg + (size_t)(t.x + r) * sizeof(Sv)), v1 = gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
         const Sv v2 = gx(Xg + (size_t)(t.z + r) * sizeof(Sv)), v3 = gx(Xg + (size_t)(t.w + r) * sizeof(Sv));
-        a = pb_fma(B.hbc[e], xo - v0, a);
-        a = pb_fma(B.hbc[e + 1], xo - v1, a);
-        a = pb_fma(B.hbc[e + 2], xo - v2, a);
-        a = pb_fma(B.hbc[e + 3], xo - v3, a);
+        a = pb_mac(B.hbc[e], B.hbcf[e], xo - v0, a);
+        a = pb_mac(B.hbc[e + 1], B.hbcf[e + 1], xo - v1, a);
+        a = pb_mac(B.hbc[e + 2], B.hbcf[e + 2], xo - v2, a);
+        a = pb_mac(B.hbc[e + 3], B.hbcf[e + 3], xo - v3, a);
     }
-    for (; e < e1; ++e) a = pb_fma(B.hbc[e], xo - gx(Xg + (size_t)(B.hbi[e] + r) * sizeof(Sv)), a);
+    for (; e < e1; ++e) a = pb_mac(B.hbc[e], B.hbcf[e], xo - gx(Xg + (size_t)(B.hbi[e] + r) * sizeof(Sv)), a);
     for (int f = B.fs[0]; f < B.fe[0]; ++f) {
         const Sv v = gx(Xg + (size_t)(B.hbf[f] - r) * sizeof(Sv));
-        a = pb_fma(B.hbfc[f], xo - (P.par < 0 ? -v : v), a);
+        a = pb_mac(B.hbfc[f], B.hbfcf[f], xo - (P.par < 0 ? -v : v), a);
     }
     return a;
 }
@@ -356,13 +364,17 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
                 const int b0 = popc_below(hm, P.hb_start[c]), b1 = popc_below(hm, P.hb_start[c + 1]);
                 const int f0 = popc_below(fm, P.hb_start[c]), f1 = popc_below(fm, P.hb_start[c + 1]);
                 if (tid >= P.hb_start[c] && tid < P.hb_start[c + 1]) {
+                    const float cf = P.perbond ? (float)ldexp((double)P.pb_hc[tid], -P.pb_s) : 0.0f;
                     if (hval) {
                         B.hbi[start + popc_below(hm, tid) - b0] = hidx;
-                        if (P.perbond) B.hbc[start + popc_below(hm, tid) - b0] = P.pb_hh[tid];
+                        if (P.perbond) {
+                            B.hbc[start + popc_below(hm, tid) - b0] = P.pb_hc[tid];
+                            B.hbcf[start + popc_below(hm, tid) - b0] = cf;
+                        }
                     }
                     if (hflip) {
                         B.hbf[popc_below(fm, tid)] = hidx;
-                        if (P.perbond) B.hbfc[popc_below(fm, tid)] = P.pb_hh[tid];
+                        if (P.perbond) { B.hbfc[popc_below(fm, tid)] = P.pb_hc[tid]; B.hbfcf[popc_below(fm, tid)] = cf; }
                     }
                 }
                 if (tid == c) { B.hs[c] = start; B.he[c] = start + (b1 - b0); B.fs[c] = f0; B.fe[c] = f1; }
@@ -453,8 +465,9 @@ __device__ __forceinline__ void matvec_body(const BlkParams &P, const T *__restr
         unsigned long long *yb = (unsigned long long *)y;
         if constexpr (Row::kPerBond) {
             blk_sweep<int64_t, NC, false, Row>(P, (const unsigned char *)x, GF64{E}, nullptr, [](uint32_t) { return 0; },
-                                          [&](uint32_t off, uint32_t r, int64_t xo, double sv, int) {
-                                              yb[off + r] = ef::d2u(ldexp(fma(P.pb_g0, (double)xo, sv), u));
+                                          [&](uint32_t off, uint32_t r, int64_t xo, __int128 sv, int) {
+                                              const __int128 t = (__int128)P.pb_c0 * xo + sv;
+                                              yb[off + r] = ef::d2u(ldexp(i128_to_double(t), u - P.pb_s));
                                           },
                                           [](int) {}, [](uint32_t, int) {});
         } else {
@@ -488,11 +501,6 @@ __device__ __forceinline__ void matvec_body(const BlkParams &P, const T *__restr
 // integer load), written as binary64 to Y; the exact integer dot q.y gives alpha
 // (with q.q_prev from the fixed-point copy kernel) without re-reading y.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ double i128_to_double(__int128 v) {
-    const long long hi = (long long)(v >> 64);
-    const unsigned long long lo = (unsigned long long)v;
-    return (double)hi * 18446744073709551616.0 + (double)lo;
-}
 
 // per-warp partial sums of the current and previous block (blk_sweep's endf / flushf)
 __shared__ double s_wpart[2][BLK_NT / 32][1];
@@ -522,8 +530,9 @@ __device__ __forceinline__ void lz64_body(const BlkParams &P, const long long *_
         if constexpr (IR) d1 += (__int128)xo * ts;
         else d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
     };
-    auto rowb = [&](uint32_t off, uint32_t r, int64_t xo, double sv, int) {
-        const unsigned long long yb = ef::d2u(ldexp(fma(P.pb_g0, (double)xo, sv), u));
+    auto rowb = [&](uint32_t off, uint32_t r, int64_t xo, __int128 sv, int) {
+        const __int128 t = (__int128)P.pb_c0 * xo + sv;
+        const unsigned long long yb = ef::d2u(ldexp(i128_to_double(t), u - P.pb_s));
         __stcs(Y + off + r, yb);
         d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
     };

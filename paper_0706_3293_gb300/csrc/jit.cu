@@ -34,6 +34,8 @@
 #endif
 
 namespace hm {
+long long pb_coef(const BlkParams &P, double h);   // blk.cu: round(h 2^pb_s)
+
 namespace {
 
 struct Nvrtc {
@@ -183,6 +185,12 @@ std::string gen_row_slots(const BlkParams &P) {
 // a fixed address (a broadcast) and adds a zero difference.
 std::string gen_row_pb(const BlkParams &P, const BondParams &bp) {
     auto hb = [&](int t) { return -bp.jm[t] / 2.0; };
+    // coefficient arguments of hm::pb_mac: C_b (integer, FP64 rows) and h_b (float, FP32 rows)
+    auto cf = [&](int t) {
+        char buf[96];
+        snprintf(buf, sizeof buf, "%lldLL, %.9gf", pb_coef(P, hb(t)), hb(t));
+        return std::string(buf);
+    };
     std::string s;
     s += "struct RowJit {\n"
          "static constexpr int kPad = hm::BLK_XPAD;\n"
@@ -209,17 +217,17 @@ std::string gen_row_pb(const BlkParams &P, const BondParams &bp) {
     for (int d : ds) put(s, "    const uint32_t z%d = l ^ (l >> %d);\n", d, d);
     for (int k = P.ln[0][0] - 1; k >= 0; --k)
         put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = R1own + hm::r0s_at(t ? (l4 ^ 0x%xu) & 0x3FCu : 0u); "
-               "const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); a = hm::pb_fma(%.17g, t ? xo - x : Sv(0), a); }\n",
-            P.ld[0][0][k], P.lvm[0][0][k], (unsigned)P.lxa[0][0][k], hb(P.pb_lb[0][k]));
+               "const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); a = hm::pb_mac(%s, t ? xo - x : Sv(0), a); }\n",
+            P.ld[0][0][k], P.lvm[0][0][k], (unsigned)P.lxa[0][0][k], cf(P.pb_lb[0][k]).c_str());
     for (int k = P.ln[0][1] - 1; k >= 0; --k)
         put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = R0own + hm::us_at(lh4k ^ 0x%xu); "
-               "const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); a = hm::pb_fma(%.17g, t ? xo - x : Sv(0), a); }\n",
-            P.ld[0][1][k], P.lvm[0][1][k], (unsigned)P.lxb[0][1][k], hb(P.pb_lb[1][k]));
+               "const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); a = hm::pb_mac(%s, t ? xo - x : Sv(0), a); }\n",
+            P.ld[0][1][k], P.lvm[0][1][k], (unsigned)P.lxb[0][1][k], cf(P.pb_lb[1][k]).c_str());
     for (int k = P.ln[0][2] - 1; k >= 0; --k)
         put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = hm::us_at(lh4k ^ 0x%xu) + "
                "hm::r0s_at(t ? (l4 ^ 0x%xu) & 0x3FCu : 0u); const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); "
-               "a = hm::pb_fma(%.17g, t ? xo - x : Sv(0), a); }\n",
-            P.ld[0][2][k], P.lvm[0][2][k], (unsigned)P.lxb[0][2][k], (unsigned)P.lxa[0][2][k], hb(P.pb_lb[2][k]));
+               "a = hm::pb_mac(%s, t ? xo - x : Sv(0), a); }\n",
+            P.ld[0][2][k], P.lvm[0][2][k], (unsigned)P.lxb[0][2][k], (unsigned)P.lxa[0][2][k], cf(P.pb_lb[2][k]).c_str());
     auto xval = [&](int dst) -> const char * {
         for (int e = 0; e < P.nxf; ++e)
             if (P.xf_dst[e] == dst && P.par && P.xf_q[e] == P.H - 1)
@@ -228,12 +236,12 @@ std::string gen_row_pb(const BlkParams &P, const BondParams &bp) {
     };
     for (int k = P.xn[0][0] - 1; k >= 0; --k)
         put(s, "    { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at(lh4 | x_.kofs2) + "
-               "hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu); if ((l ^ x_.wm) & x_.vm) a = hm::pb_fma(%.17g, xo - %s, a); }\n",
-            k, (unsigned)P.xxa[0][0][k], hb(P.pb_xb[0][k]), xval(k));
+               "hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu); if ((l ^ x_.wm) & x_.vm) a = hm::pb_mac(%s, xo - %s, a); }\n",
+            k, (unsigned)P.xxa[0][0][k], cf(P.pb_xb[0][k]).c_str(), xval(k));
     for (int k = P.xn[0][1] - 1; k >= 0; --k)
         put(s, "    { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at((lh4 ^ 0x%xu) | x_.kofs2) + "
-               "R0own; if ((l ^ x_.wm) & x_.vm) a = hm::pb_fma(%.17g, xo - %s, a); }\n",
-            HM_BLK_SX + k, (unsigned)P.xxa[0][1][k], hb(P.pb_xb[1][k]), xval(HM_BLK_SX + k));
+               "R0own; if ((l ^ x_.wm) & x_.vm) a = hm::pb_mac(%s, xo - %s, a); }\n",
+            HM_BLK_SX + k, (unsigned)P.xxa[0][1][k], cf(P.pb_xb[1][k]).c_str(), xval(HM_BLK_SX + k));
     s += "    return hm::blk_high_pb<Sv>(P, B, Xg, r, gx, xo, a);\n}\n};\n";
     return s;
 }
