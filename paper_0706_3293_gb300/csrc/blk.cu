@@ -1,6 +1,7 @@
 // blk.cu -- host planning and the matvec kernel of the s = 1/2 block path (blk.cuh).
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 #include <cmath>
 #include <map>
@@ -338,7 +339,14 @@ static int launch_blk_matvec(hm_basis *b, const BlkParams &P, const T *x, T *y, 
 
 // split position: 15 low sites (blocks <= 6435 rows: three 512-thread CTAs per SM), or
 // the largest K <= 15 that leaves two high sites
-static int blk_K(const hm_basis *b) { return std::min(15, b->view.N - 2); }
+// split position of the block path: the low part holds K = min(15, N - 2) sites
+// (HM_BLK_K = 8..15 overrides, for tuning); the thread-per-row slots need K <= 15.  The
+// Lanczos workspace sizes its per-block partials (2^(N-K) blocks) with the same function.
+int blk_K(const hm_basis *b) {
+    int K = 15;
+    if (const char *e = getenv("HM_BLK_K")) K = std::max(8, std::min(15, atoi(e)));
+    return std::min(K, b->view.N - 2);
+}
 
 // f(kernel) for the FP64 block-product instance of the plan (class count, integer ratios)
 template <class F>

@@ -46,16 +46,25 @@ struct BlkMeta {                     // per-block data, double-buffered
     // occupies [hs[c], he[c]) with hs[c] a multiple of 4, so four entries are one 16-byte load
     __align__(16) uint32_t hbi[BLK_HBI];
     int hs[HM_BLK_MAXC], he[HM_BLK_MAXC];
+    uint32_t hv[2];
+    uint32_t off, n, kofs, lwo;
+    struct BlkMetaX *x;              // spin-flip / per-bond data of the block, or nullptr
+};
+
+// Per-block data that only spin-flip and per-bond plans use, in a shared-memory region of
+// its own (allocated only for those plans, so the others keep the smaller footprint).
+struct BlkMetaXF {
     // spin-flip basis: exchanges that move site N-1 lead out of the representatives; their
     // target is row n - 1 - r of the complement block, hbf[e] its last row, by class
     uint32_t hbf[HM_BLK_MAXB];
     int fs[HM_BLK_MAXC], fe[HM_BLK_MAXC];
-    // per-bond plan: coefficient of each entry of hbi and of hbf, integer (C_b, FP64 rows)
-    // and float (FP32 rows)
+    uint32_t hf[2];
+};
+struct BlkMetaX : BlkMetaXF {
+    // per-bond plan (a spin-flip plan with classes allocates only the BlkMetaXF part):
+    // coefficient of each entry of hbi and of hbf, integer (C_b, FP64 rows) and float (FP32 rows)
     long long hbc[BLK_HBI], hbfc[HM_BLK_MAXB];
     float hbcf[BLK_HBI], hbfcf[HM_BLK_MAXB];
-    uint32_t hv[2], hf[2];
-    uint32_t off, n, kofs, lwo;
 };
 
 // bits below position e of the 64-bit mask m
@@ -93,7 +102,8 @@ template <class Sv, class G>
 __device__ __forceinline__ Sv blk_flip_sum(const BlkMeta &B, int c, const unsigned char *Xg, uint32_t r,
                                            const G &gx) {
     Sv a = Sv(0);
-    for (int e = B.fs[c]; e < B.fe[c]; ++e) a += gx(Xg + (size_t)(B.hbf[e] - r) * sizeof(Sv));
+    const BlkMetaX &X = *B.x;
+    for (int e = X.fs[c]; e < X.fe[c]; ++e) a += gx(Xg + (size_t)(X.hbf[e] - r) * sizeof(Sv));
     return a;
 }
 
@@ -117,6 +127,7 @@ template <class Sv, class G>
 __device__ __forceinline__ typename PbAcc<Sv>::T blk_high_pb(const BlkParams &P, const BlkMeta &B,
                                                              const unsigned char *Xg, uint32_t r, const G &gx,
                                                              Sv xo, typename PbAcc<Sv>::T a) {
+    const BlkMetaX &X = *B.x;
     const int e1 = B.he[0];
     const uint4 *h4 = reinterpret_cast<const uint4 *>(B.hbi);
     int e = B.hs[0];
@@ -124,15 +135,15 @@ __device__ __forceinline__ typename PbAcc<Sv>::T blk_high_pb(const BlkParams &P,
         const uint4 t = h4[e >> 2];
         const Sv v0 = gx(Xg + (size_t)(t.x + r) * sizeof(Sv)), v1 = gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
         const Sv v2 = gx(Xg + (size_t)(t.z + r) * sizeof(Sv)), v3 = gx(Xg + (size_t)(t.w + r) * sizeof(Sv));
-        a = pb_mac(B.hbc[e], B.hbcf[e], xo - v0, a);
-        a = pb_mac(B.hbc[e + 1], B.hbcf[e + 1], xo - v1, a);
-        a = pb_mac(B.hbc[e + 2], B.hbcf[e + 2], xo - v2, a);
-        a = pb_mac(B.hbc[e + 3], B.hbcf[e + 3], xo - v3, a);
+        a = pb_mac(X.hbc[e], X.hbcf[e], xo - v0, a);
+        a = pb_mac(X.hbc[e + 1], X.hbcf[e + 1], xo - v1, a);
+        a = pb_mac(X.hbc[e + 2], X.hbcf[e + 2], xo - v2, a);
+        a = pb_mac(X.hbc[e + 3], X.hbcf[e + 3], xo - v3, a);
     }
-    for (; e < e1; ++e) a = pb_mac(B.hbc[e], B.hbcf[e], xo - gx(Xg + (size_t)(B.hbi[e] + r) * sizeof(Sv)), a);
-    for (int f = B.fs[0]; f < B.fe[0]; ++f) {
-        const Sv v = gx(Xg + (size_t)(B.hbf[f] - r) * sizeof(Sv));
-        a = pb_mac(B.hbfc[f], B.hbfcf[f], xo - (P.par < 0 ? -v : v), a);
+    for (; e < e1; ++e) a = pb_mac(X.hbc[e], X.hbcf[e], xo - gx(Xg + (size_t)(B.hbi[e] + r) * sizeof(Sv)), a);
+    for (int f = X.fs[0]; f < X.fe[0]; ++f) {
+        const Sv v = gx(Xg + (size_t)(X.hbf[f] - r) * sizeof(Sv));
+        a = pb_mac(X.hbfc[f], X.hbfcf[f], xo - (P.par < 0 ? -v : v), a);
     }
     return a;
 }
@@ -148,8 +159,12 @@ __device__ __forceinline__ uint32_t r0s_at(uint32_t byte_off) {
 __host__ __device__ __forceinline__ size_t blk_row_xs_bytes(const BlkParams &P, int esize, int pad) {
     return al16(((size_t)P.max_block + pad) * esize);
 }
+// bytes of one BlkMetaX copy the plan uses (0: none)
+__host__ __device__ __forceinline__ size_t blk_x_bytes(const BlkParams &P) {
+    return P.perbond ? al16(sizeof(BlkMetaX)) : P.par ? al16(sizeof(BlkMetaXF)) : 0;
+}
 __host__ __device__ __forceinline__ size_t blk_row_smem_bytes(const BlkParams &P, int esize, int pad) {
-    return blk_row_xs_bytes(P, esize, pad) + 2 * al16(sizeof(BlkMeta));
+    return blk_row_xs_bytes(P, esize, pad) + 2 * al16(sizeof(BlkMeta)) + 2 * blk_x_bytes(P);
 }
 
 __device__ __forceinline__ bool blk_h_valid(const BlkParams &P, uint32_t h) {
@@ -255,7 +270,7 @@ static __device__ __forceinline__ void sums(const BlkParams &P, const BlkMeta &B
             a += P.par < 0 ? -f : f;
         }
         acc[c] = a;
-        cnt[c] = m + (B.he[c] - B.hs[c]) + (B.fe[c] - B.fs[c]);
+        cnt[c] = m + (B.he[c] - B.hs[c]) + (P.par ? B.x->fe[c] - B.x->fs[c] : 0);
     }
 }
 };
@@ -283,6 +298,7 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
     const unsigned char *Xsb = smem;
     Sv *Xs = (Sv *)smem;
     BlkMeta *meta = (BlkMeta *)(smem + blk_row_xs_bytes(P, sizeof(Sv), Row::kPad));
+    unsigned char *metax = blk_x_bytes(P) ? (unsigned char *)meta + 2 * al16(sizeof(BlkMeta)) : nullptr;
     const int tid = threadIdx.x;
     const uint32_t *Cg = (const uint32_t *)((const unsigned char *)P.tab + P.off_C);
     {
@@ -309,6 +325,7 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
         }
         if (h >= nH) break;
         BlkMeta &B = meta[it & 1];
+        BlkMetaX *BX = metax ? (BlkMetaX *)(metax + (it & 1) * blk_x_bytes(P)) : nullptr;
         const int k = P.A - __popc(h);
         // setup 1: targets of the high and cross exchanges, own offset, next block
         if (DYN && tid == 0) s_hnext[(it + 1) & 1] = blk_fetch(P, sched, nH);
@@ -328,7 +345,10 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
         }
         if (tid < 64) {
             const unsigned bal = __ballot_sync(0xffffffffu, hval), balf = __ballot_sync(0xffffffffu, hflip);
-            if ((tid & 31) == 0) { B.hv[tid >> 5] = bal; B.hf[tid >> 5] = balf; }
+            if ((tid & 31) == 0) {
+                B.hv[tid >> 5] = bal;
+                if (BX) BX->hf[tid >> 5] = balf;
+            }
         }
         if (tid >= 64 && tid < 64 + P.nxf) {
             const int e = tid - 64, p = P.xf_p[e], q = P.xf_q[e];
@@ -347,6 +367,7 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
             B.xs[P.xf_dst[e]] = xs;
         }
         if (tid == 128) {
+            B.x = BX;
             B.off = blk_off(P, tb, h, k);
             B.n = Cg[P.K * (P.A + 1) + k];
             B.kofs = (uint32_t)k << P.kshift;
@@ -358,7 +379,7 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
         // multiple of 4 entries; stage the block's x
         if (hval || hflip || tid < HM_BLK_MAXC) {
             const uint64_t hm = ((uint64_t)B.hv[1] << 32) | B.hv[0];
-            const uint64_t fm = ((uint64_t)B.hf[1] << 32) | B.hf[0];
+            const uint64_t fm = BX ? ((uint64_t)BX->hf[1] << 32) | BX->hf[0] : 0ull;
             int start = 0;                           // padded start of the class
             for (int c = 0; c < HM_BLK_MAXC; ++c) {
                 const int b0 = popc_below(hm, P.hb_start[c]), b1 = popc_below(hm, P.hb_start[c + 1]);
@@ -368,16 +389,20 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
                     if (hval) {
                         B.hbi[start + popc_below(hm, tid) - b0] = hidx;
                         if (P.perbond) {
-                            B.hbc[start + popc_below(hm, tid) - b0] = P.pb_hc[tid];
-                            B.hbcf[start + popc_below(hm, tid) - b0] = cf;
+                            BX->hbc[start + popc_below(hm, tid) - b0] = P.pb_hc[tid];
+                            BX->hbcf[start + popc_below(hm, tid) - b0] = cf;
                         }
                     }
                     if (hflip) {
-                        B.hbf[popc_below(fm, tid)] = hidx;
-                        if (P.perbond) { B.hbfc[popc_below(fm, tid)] = P.pb_hc[tid]; B.hbfcf[popc_below(fm, tid)] = cf; }
+                        BX->hbf[popc_below(fm, tid)] = hidx;
+                        if (P.perbond) { BX->hbfc[popc_below(fm, tid)] = P.pb_hc[tid]; BX->hbfcf[popc_below(fm, tid)] = cf; }
                     }
                 }
-                if (tid == c) { B.hs[c] = start; B.he[c] = start + (b1 - b0); B.fs[c] = f0; B.fe[c] = f1; }
+                if (tid == c) {
+                    B.hs[c] = start;
+                    B.he[c] = start + (b1 - b0);
+                    if (BX) { BX->fs[c] = f0; BX->fe[c] = f1; }
+                }
                 start += (b1 - b0 + 3) & ~3;
             }
         }

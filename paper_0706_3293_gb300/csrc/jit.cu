@@ -169,7 +169,7 @@ std::string gen_row_slots(const BlkParams &P) {
         put(s, "        a += hm::blk_high_sum<Sv>(B, %d, Xg, r, gx);\n", c);
         if (P.par) {
             put(s, "        a %s= hm::blk_flip_sum<Sv>(B, %d, Xg, r, gx);\n", P.par < 0 ? "-" : "+", c);
-            put(s, "        acc[%d] = a;\n        cnt[%d] = m + (B.he[%d] - B.hs[%d]) + (B.fe[%d] - B.fs[%d]);\n    }\n",
+            put(s, "        acc[%d] = a;\n        cnt[%d] = m + (B.he[%d] - B.hs[%d]) + (B.x->fe[%d] - B.x->fs[%d]);\n    }\n",
                 c, c, c, c, c, c);
         } else {
             put(s, "        acc[%d] = a;\n        cnt[%d] = m + (B.he[%d] - B.hs[%d]);\n    }\n", c, c, c, c);

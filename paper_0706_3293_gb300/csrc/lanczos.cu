@@ -14,6 +14,7 @@ namespace hm {
 
 int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int *blocks);
 int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void **kern, int *blocks);
+int blk_K(const hm_basis *b);   // blk.cu: split position of the block path
 int blk_lz64_launch(const BlkParams &P, const long long *Xc, unsigned long long *Y, LzScalars *S, int pc,
                     double *part, int blocks, cudaStream_t st, const void *jit);
 int blk_lz32_launch(const BlkParams &P, const float *qc, float *qp, LzScalars *S, double *part, int blocks,
@@ -39,7 +40,8 @@ struct LzLayout {
     size_t buf[2], part, sc, alpha, beta, ritz, psi, coef, res, gout, tri, bpart, total;
     size_t ybuf, xs[2];     // FP64 block path: y = H q and the fixed-point copies of q
     size_t qqp;             // FP64 block path: partials of q_cur . q_prev (k_fix)
-    size_t hpart;           // s = 1/2 block path: per-block partial sums, 2 x 2^H doubles
+    size_t hpart;           // s = 1/2 block path: per-block partial sums, 2 x 2^hpart_H doubles
+    int hpart_H;
     bool shadow;
 };
 
@@ -65,7 +67,8 @@ static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad
     }
     // per-block partials of the s = 1/2 block path (split K = min(15, N - 2): H <= 17)
     if (b->view.S2 == 1 && b->view.N >= 10 && b->view.N <= 32 && !b->view.idx64) {
-        const int H = b->view.N - std::min(15, b->view.N - 2);
+        const int H = b->view.N - blk_K(b);
+        L.hpart_H = H;
         L.hpart = o; o += al256(((size_t)2 << H) * sizeof(double));
     }
     L.sc = o; o += al256(sizeof(LzScalars));
@@ -660,7 +663,9 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
     R->use_blk = 0;
     rc = blk_lz_plan(const_cast<hm_basis *>(b), R->bp, dtype, &R->blk, &R->blk_blocks);
     if (rc < 0) { delete R; return rc; }
-    R->use_blk = rc == 0 && (dtype == HM_F32 || R->L.shadow) && R->L.hpart != 0 && R->blk.H <= 17;
+    // the per-block partials were sized for 2^hpart_H blocks
+    R->use_blk = rc == 0 && (dtype == HM_F32 || R->L.shadow) && R->L.hpart != 0 && R->blk.H <= R->L.hpart_H &&
+                 R->blk.H <= 17;
     R->jit = nullptr;
     R->run = row_run_len();
     if (R->use_blk) {

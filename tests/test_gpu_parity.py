@@ -592,3 +592,18 @@ def test_matvec_kernel_name_dispatch(hm):
     assert hm.matvec_kernel_name(b, hm.bonds_of(W.ring16()), nvec=2) == "k_matvec"
     s1 = W.s1_random_graph(10, 21)
     assert hm.matvec_kernel_name(hm.Basis(10, 2, 0), hm.bonds_of(s1)) == "k_matvec"
+
+
+@pytest.mark.parametrize("K", [11, 13])
+def test_block_split_override(hm, K, monkeypatch):
+    """HM_BLK_K moves the block split: more blocks (2^(N-K)) with fewer rows each.  The
+    workspace sizes its per-block partials by the same split, and the Lanczos coefficients
+    agree with the default split's to rounding."""
+    inst = W.small_ring(24, -1.0, -0.5)
+    b = hm.Basis(24, 1, 0)
+    ref = hm.lanczos_run(b, hm.bonds_of(inst), 30, seed=6, n_ritz=1)
+    monkeypatch.setenv("HM_BLK_K", str(K))
+    b2 = hm.Basis(24, 1, 0)
+    res = hm.lanczos_run(b2, hm.bonds_of(inst), 30, seed=6, n_ritz=1)
+    np.testing.assert_allclose(res.alpha, ref.alpha, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(res.beta, ref.beta, rtol=0, atol=1e-13)
