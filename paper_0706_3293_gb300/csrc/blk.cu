@@ -152,7 +152,7 @@ static void blk_plan_slots(const BondParams &bp, const std::vector<int> &bc, int
     }
 }
 
-int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
+int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P, bool bond_corr) {
     const SectorView &sv = b->view;
     if (sv.S2 != 1 || sv.N > 32 || sv.N < K + 2 || K < 8 || K > 16 || bp.nb > HM_BLK_MAXB ||
         sv.idx64)
@@ -171,8 +171,9 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
         if (c == (int)cls.size()) cls.push_back(J);
         bc[t] = c;
     }
-    if ((int)cls.size() > HM_BLK_MAXC) {
+    if ((int)cls.size() > HM_BLK_MAXC || bond_corr) {
         P->perbond = 1;
+        P->bcmode = bond_corr ? 1 : 0;
         cls.clear();
         std::fill(bc.begin(), bc.end(), 0);
         double g0 = 0.0, mx = 0.0;
@@ -261,6 +262,7 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P) {
             P->hb_p[nh] = (uint8_t)std::get<0>(e);
             P->hb_q[nh] = (uint8_t)std::get<1>(e);
             if (P->perbond) P->pb_hc[nh] = pb_coef(*P, -bp.jm[std::get<2>(e)] / 2.0);   // J_b / 2
+            P->pb_hbb[nh] = (uint8_t)std::get<2>(e);
             ++nh;
         }
         P->cb_start[c] = ncr;
@@ -465,6 +467,88 @@ static int launch_blk_matvec_pb(hm_basis *b, const BlkParams &P, const BondParam
     const int blocks = std::min<int>(sm_count() * std::max(per, 1), 1 << P.H);
     void *args[] = {(void *)&P, (void *)&x, (void *)&y, (void *)&Ed};
     HM_CUDA(cudaLaunchKernel(k, dim3(blocks), dim3(BLK_NT), args, sm, st));
+    return HM_OK;
+}
+
+// ---- bond correlations on the block path -------------------------------------------------
+int jit_bc_kernel(const BlkParams &P, int dtype, int nbk, const void **kern);
+
+constexpr int BC_CHUNK = 16;               // bonds per bond-correlation launch
+constexpr uint64_t BC_MIN_ROWS = 100000;   // smaller sectors: the general kernel (no compile)
+
+// out[k] = sign 2^u (T0 / 4 - C_k / 2) / div from the CTA partials of one chunk (fixed order)
+__global__ void k_bc_final(const double *__restrict__ part, int nctas, int nbk, const int *Eptr, double sign,
+                           const double *div, double *__restrict__ out) {
+    __shared__ double t0s;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int c = 0; c < nctas; ++c) t += part[(size_t)c * (nbk + 1) + nbk];
+        t0s = t;
+    }
+    __syncthreads();
+    const int k = threadIdx.x;
+    if (k >= nbk) return;
+    double ck = 0.0;
+    for (int c = 0; c < nctas; ++c) ck += part[(size_t)c * (nbk + 1) + k];
+    double v = 0.25 * t0s - 0.5 * ck;
+    if (Eptr) v = ldexp(v, *Eptr - 1022 - ef::FIX_BITS);
+    out[k] = sign * (div ? v / *div : v);
+}
+
+// bytes of partial sums the block-path bond correlations need at most
+size_t blk_bond_corr_bytes() { return (size_t)sm_count() * 4 * (BC_CHUNK + 1) * sizeof(double); }
+
+// out[b] = sign g^T (s_u.s_v) x / div for every bond, s = 1/2 sectors through the block
+// kernels compiled per chunk of bonds; 1 = not applicable (the caller runs the general kernel)
+int blk_bond_corr(hm_basis *b, const BondParams &bp, const void *g, const void *x, double *out, int dtype,
+                  void *work, size_t work_bytes, double sign, const double *div, cudaStream_t st) {
+    const SectorView &sv = b->view;
+    if (sv.S2 != 1 || b->parity || bp.nb == 0 || sv.dim < BC_MIN_ROWS) return 1;
+    const int nch = (bp.nb + BC_CHUNK - 1) / BC_CHUNK;
+    std::vector<BlkParams> plans(nch);
+    std::vector<const void *> kerns(nch);
+    std::vector<int> blocks(nch);
+    const int es = dtype == HM_F64 ? 8 : 4;
+    for (int c = 0; c < nch; ++c) {               // every chunk planned and compiled before any launch
+        BondParams bc = bp;
+        const int c0 = c * BC_CHUNK, nbk = std::min(BC_CHUNK, bp.nb - c0);
+        bc.nb = nbk;
+        for (int i = 0; i < nbk; ++i) {
+            bc.p[i] = bp.p[c0 + i]; bc.q[i] = bp.q[c0 + i];
+            bc.jm[i] = bp.jm[c0 + i]; bc.jmf[i] = bp.jmf[c0 + i];
+        }
+        BlkParams &P = plans[c];
+        if (blk_plan(b, bc, blk_K(b), &P, true) != 0 || !P.rows_ok) return 1;
+        const size_t sm = blk_row_smem_bytes(P, es, BLK_XPAD);
+        if (sm > 200 * 1024 || jit_bc_kernel(P, dtype, nbk, &kerns[c]) != 0) return 1;
+        if (cudaFuncSetAttribute(kerns[c], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+            cudaGetLastError();
+            return 1;
+        }
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kerns[c], BLK_NT, sm) != cudaSuccess || per < 1) {
+            cudaGetLastError();
+            return 1;
+        }
+        blocks[c] = std::min<int>(sm_count() * std::min(per, 4), 1 << P.H);
+        if (!work || work_bytes < (size_t)blocks[c] * (nbk + 1) * sizeof(double)) return 1;
+    }
+    int *Ed = nullptr;
+    if (dtype == HM_F64) {
+        Ed = (int *)b->d_scratch;
+        HM_CUDA(cudaMemsetAsync(Ed, 0, sizeof(int), st));
+        k_max_exp<<<grid_blocks(sv.dim, 256), 256, 0, st>>>((const unsigned long long *)x, sv.dim, Ed);
+        HM_CUDA(cudaGetLastError());
+    }
+    double *part = (double *)work;
+    for (int c = 0; c < nch; ++c) {
+        const int nbk = std::min(BC_CHUNK, bp.nb - c * BC_CHUNK);
+        const size_t sm = blk_row_smem_bytes(plans[c], es, BLK_XPAD);
+        void *args[] = {(void *)&plans[c], (void *)&x, (void *)&g, (void *)&Ed, (void *)&part};
+        HM_CUDA(cudaLaunchKernel(kerns[c], dim3(blocks[c]), dim3(BLK_NT), args, sm, st));
+        k_bc_final<<<1, 32, 0, st>>>(part, blocks[c], nbk, Ed, sign, div, out + c * BC_CHUNK);
+        HM_CUDA(cudaGetLastError());
+    }
     return HM_OK;
 }
 

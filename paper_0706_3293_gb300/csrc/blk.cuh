@@ -31,7 +31,7 @@
 namespace hm {
 
 // host: builds the plan; returns 0 if the bond list and sector take the fast path
-int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *out);
+int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *out, bool bond_corr = false);
 
 // ---- device helpers ----------------------------------------------------------------------
 __device__ __forceinline__ BlkTabs stage_blk_tables(const BlkParams &P, unsigned char *smem) {

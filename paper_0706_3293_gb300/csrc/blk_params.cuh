@@ -78,7 +78,11 @@ struct BlkParams {
     long long pb_c0;
     double pb_g0;
     uint8_t pb_lb[3][HM_BLK_SL], pb_xb[2][HM_BLK_SX];   // bond index of each low / cross slot
+    uint8_t pb_hbb[HM_BLK_MAXB];                      // bond index of each high bond
     long long pb_hc[HM_BLK_MAXB];                     // C_b of each high bond (hb_p / hb_q order)
+    // bond-correlation plan (one chunk of bonds, per-bond slots): the block setup keeps the
+    // high targets uncompacted, hbi[j] for high bond j or ~0 when its spins are parallel
+    int bcmode;
 };
 
 

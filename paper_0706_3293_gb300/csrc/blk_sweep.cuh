@@ -238,6 +238,7 @@ struct RowGeneric {
 static constexpr int kPad = BLK_XPAD;
 static constexpr bool kRelUS = false;
 static constexpr bool kPerBond = false;      // per-bond plans run only specialised (jit.cu)
+static constexpr bool kBC = false;           // bond-correlation rows (jit.cu) neither
 template <class Sv>
 static __device__ __forceinline__ void stage(const BlkParams &P, unsigned char *) {
     const uint16_t *Ug = (const uint16_t *)((const unsigned char *)P.tab + P.off_U);
@@ -377,7 +378,9 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
         if (tid == BLK_NT - 1 && it_prev >= 0) flushf(h_prev, it_prev);
         // setup 2: compact the allowed high exchanges by class, each class's run padded to a
         // multiple of 4 entries; stage the block's x
-        if (hval || hflip || tid < HM_BLK_MAXC) {
+        if (P.bcmode) {                              // bond correlations: high bond j at hbi[j]
+            if (tid < P.nhb) B.hbi[tid] = hval ? hidx : 0xFFFFFFFFu;
+        } else if (hval || hflip || tid < HM_BLK_MAXC) {
             const uint64_t hm = ((uint64_t)B.hv[1] << 32) | B.hv[0];
             const uint64_t fm = BX ? ((uint64_t)BX->hf[1] << 32) | BX->hf[0] : 0ull;
             int start = 0;                           // padded start of the class
@@ -417,7 +420,9 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
             if (r + BLK_NT < n) l_next = (uint32_t)__ldg(lw + r + BLK_NT);
             const auto pv = pref(off + r);                 // the row's other operand, ahead of the sums
             const Sv xo = Xs[r];
-            if constexpr (Row::kPerBond) {
+            if constexpr (Row::kBC) {
+                rowf(off, r, xo, pv, B, Xsb, l);
+            } else if constexpr (Row::kPerBond) {
                 rowf(off, r, xo, Row::template sums_pb<Sv>(P, B, Xsb, X, l, r, gx, xo), pv);
             } else {
                 Sv acc[NC];
@@ -621,6 +626,52 @@ __device__ __forceinline__ void lz32_body(const BlkParams &P, const float *__res
                                             rowu(off, r, xo, blk_y_f32<NC>(P, acc, cnt, xo), qpr);
                                         },
                                         endf, flushf);
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Bond correlations (the adjoint of the couplings): out_b = g^T (s_u.s_v) x.  By Eq. E-2-1
+// [(s_u.s_v) x]_i = x_i / 4 - (x_i - x_t) / 2 when the exchange of b is allowed at row i
+// (x_t its target) and x_i / 4 otherwise, so out_b = T0 / 4 - C_b / 2 with T0 = g.x and
+// C_b = sum over the rows where b's spins differ of g_i (x_i - x_t).  One launch serves the
+// Row::kNB bonds of a chunk plan (bcmode); every thread keeps their C_b and T0 in registers
+// over its rows, and part[cta][k] (k = kNB: T0) gets the CTA sums (fixed order, static block
+// schedule, so the result does not depend on timing).  FP64: x is gathered as fixed point
+// of exponent E (units 2^(E - 1022 - FIX_BITS)), FP32: as float.
+template <class T> struct BcSv { using S = int64_t; };
+template <> struct BcSv<float> { using S = float; };
+
+template <class T, class Row, class Sv, class G>
+__device__ __forceinline__ void bc_sweep(const BlkParams &P, const T *__restrict__ x, const T *__restrict__ g,
+                                         const G &gx, double *acc, double &t0) {
+    blk_sweep<Sv, 1, false, Row>(
+        P, (const unsigned char *)x, gx, nullptr, [&](uint32_t i) { return (double)g[i]; },
+        [&](uint32_t, uint32_t r, Sv xo, double gi, const BlkMeta &B, const unsigned char *Xsb, uint32_t l) {
+            t0 = fma(gi, (double)xo, t0);
+            Row::template sums_bc<Sv>(P, B, Xsb, (const unsigned char *)x, l, r, gx, xo, gi, acc);
+        },
+        [](int) {}, [](uint32_t, int) {});
+}
+
+template <class T, class Row>
+__device__ __forceinline__ void bc_body(const BlkParams &P, const T *__restrict__ x, const T *__restrict__ g,
+                                        const int *__restrict__ Eptr, double *__restrict__ part) {
+    using Sv = typename BcSv<T>::S;
+    double acc[Row::kNB];
+#pragma unroll
+    for (int k = 0; k < Row::kNB; ++k) acc[k] = 0.0;
+    double t0 = 0.0;
+    if constexpr (sizeof(T) == 8) bc_sweep<T, Row, Sv>(P, x, g, GF64{Eptr ? *Eptr : 0}, acc, t0);
+    else bc_sweep<T, Row, Sv>(P, x, g, GF32{}, acc, t0);
+    __shared__ double red[BLK_NT / 32];
+    double *pc = part + (size_t)blockIdx.x * (Row::kNB + 1);
+#pragma unroll
+    for (int k = 0; k < Row::kNB; ++k) {
+        const double v = block_sum<BLK_NT>(acc[k], red);
+        if (threadIdx.x == 0) pc[k] = v;
+    }
+    const double v = block_sum<BLK_NT>(t0, red);
+    if (threadIdx.x == 0) pc[Row::kNB] = v;
 }
 
 }  // namespace hm

@@ -35,7 +35,6 @@
 
 namespace hm {
 
-int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *out);
 __host__ __device__ __forceinline__ size_t al16f(size_t x) { return (x + 15) & ~(size_t)15; }
 
 constexpr int FT_NT = 512;          // threads per CTA of the persistent kernel

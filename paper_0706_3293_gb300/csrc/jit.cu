@@ -120,6 +120,7 @@ std::string gen_row_slots(const BlkParams &P) {
          "static constexpr int kPad = hm::BLK_XPAD;\n"
          "static constexpr bool kRelUS = false;\n"
          "static constexpr bool kPerBond = false;\n"
+         "static constexpr bool kBC = false;\n"
          "template <class Sv>\n"
          "static __device__ __forceinline__ void stage(const hm::BlkParams &P, unsigned char *dyn) {\n"
          "    hm::RowGeneric<1>::stage<Sv>(P, dyn);\n"
@@ -196,6 +197,7 @@ std::string gen_row_pb(const BlkParams &P, const BondParams &bp) {
          "static constexpr int kPad = hm::BLK_XPAD;\n"
          "static constexpr bool kRelUS = false;\n"
          "static constexpr bool kPerBond = true;\n"
+         "static constexpr bool kBC = false;\n"
          "template <class Sv>\n"
          "static __device__ __forceinline__ void stage(const hm::BlkParams &P, unsigned char *dyn) {\n"
          "    hm::RowGeneric<1>::stage<Sv>(P, dyn);\n"
@@ -246,6 +248,71 @@ std::string gen_row_pb(const BlkParams &P, const BondParams &bp) {
     return s;
 }
 
+// The row policy of a bond-correlation chunk plan (BlkParams::bcmode, per-bond slots):
+// every slot of bond k adds g_i (x_i - x_t) to acc[k] when the bond's spins differ at the
+// row (blk_sweep.cuh, bc_body).  High bond j reads its block target hbi[j] (~0: parallel).
+std::string gen_row_bc(const BlkParams &P, int nbk) {
+    std::string s;
+    put(s, "struct RowJit {\n"
+           "static constexpr int kPad = hm::BLK_XPAD;\n"
+           "static constexpr bool kRelUS = false;\n"
+           "static constexpr bool kPerBond = false;\n"
+           "static constexpr bool kBC = true;\n"
+           "static constexpr int kNB = %d;\n", nbk);
+    s += "template <class Sv>\n"
+         "static __device__ __forceinline__ void stage(const hm::BlkParams &P, unsigned char *dyn) {\n"
+         "    hm::RowGeneric<1>::stage<Sv>(P, dyn);\n"
+         "}\n"
+         "template <class Sv>\n"
+         "static __device__ __forceinline__ void block(const hm::BlkParams &, uint32_t) {}\n"
+         "template <class Sv, class G>\n"
+         "static __device__ __forceinline__ void sums_bc(const hm::BlkParams &P, const hm::BlkMeta &B,\n"
+         "        const unsigned char *Xsb, const unsigned char *Xg, uint32_t l, uint32_t r, const G &gx, Sv xo,\n"
+         "        double gi, double *acc) {\n"
+         "    const uint32_t l4 = l << 2, lh4 = (l >> 8) << 2, lh4k = lh4 | B.kofs;\n"
+         "    const uint32_t R0own = hm::r0s_at(l4 & 0x3FCu), R1own = hm::us_at(lh4k);\n"
+         "    const uint32_t zo = (uint32_t)((P.max_block + hm::BLK_XPAD - 1) * sizeof(Sv));   // fixed address\n"
+         "    (void)R0own; (void)R1own; (void)lh4; (void)gx; (void)zo; (void)Xg;\n";
+    std::set<int> ds;
+    for (int t = 0; t < 3; ++t)
+        for (int k = 0; k < P.ln[0][t]; ++k) ds.insert(P.ld[0][t][k]);
+    for (int d : ds) put(s, "    const uint32_t z%d = l ^ (l >> %d);\n", d, d);
+    const char *add = "acc[%d] = fma(gi, (double)(t ? xo - x : Sv(0)), acc[%d]); }\n";
+    for (int k = 0; k < P.ln[0][0]; ++k) {
+        put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = R1own + hm::r0s_at(t ? (l4 ^ 0x%xu) & 0x3FCu : 0u); "
+               "const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); ",
+            P.ld[0][0][k], P.lvm[0][0][k], (unsigned)P.lxa[0][0][k]);
+        put(s, add, P.pb_lb[0][k], P.pb_lb[0][k]);
+    }
+    for (int k = 0; k < P.ln[0][1]; ++k) {
+        put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = R0own + hm::us_at(lh4k ^ 0x%xu); "
+               "const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); ",
+            P.ld[0][1][k], P.lvm[0][1][k], (unsigned)P.lxb[0][1][k]);
+        put(s, add, P.pb_lb[1][k], P.pb_lb[1][k]);
+    }
+    for (int k = 0; k < P.ln[0][2]; ++k) {
+        put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = hm::us_at(lh4k ^ 0x%xu) + "
+               "hm::r0s_at(t ? (l4 ^ 0x%xu) & 0x3FCu : 0u); const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); ",
+            P.ld[0][2][k], P.lvm[0][2][k], (unsigned)P.lxb[0][2][k], (unsigned)P.lxa[0][2][k]);
+        put(s, add, P.pb_lb[2][k], P.pb_lb[2][k]);
+    }
+    for (int k = 0; k < P.xn[0][0]; ++k)
+        put(s, "    { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at(lh4 | x_.kofs2) + "
+               "hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu); if ((l ^ x_.wm) & x_.vm) "
+               "acc[%d] = fma(gi, (double)(xo - gx(x_.base + v_)), acc[%d]); }\n",
+            k, (unsigned)P.xxa[0][0][k], P.pb_xb[0][k], P.pb_xb[0][k]);
+    for (int k = 0; k < P.xn[0][1]; ++k)
+        put(s, "    { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at((lh4 ^ 0x%xu) | x_.kofs2) + "
+               "R0own; if ((l ^ x_.wm) & x_.vm) acc[%d] = fma(gi, (double)(xo - gx(x_.base + v_)), acc[%d]); }\n",
+            HM_BLK_SX + k, (unsigned)P.xxa[0][1][k], P.pb_xb[1][k], P.pb_xb[1][k]);
+    for (int j = 0; j < P.nhb; ++j)
+        put(s, "    { const uint32_t o = B.hbi[%d]; if (o != 0xFFFFFFFFu) "
+               "acc[%d] = fma(gi, (double)(xo - gx(Xg + (size_t)(o + r) * sizeof(Sv))), acc[%d]); }\n",
+            j, P.pb_hbb[j], P.pb_hbb[j]);
+    s += "}\n};\n";
+    return s;
+}
+
 // The row policy of a plan (interface in blk_sweep.cuh), every count, shift and mask a
 // literal.  The low bonds with both ends in one byte of the low word take their target
 // from per-byte delta tables: the target row of slot s is r + D[b][s], with D = 0 when
@@ -274,7 +341,8 @@ std::string gen_row(const BlkParams &P, bool &ok) {
     s += "__device__ __forceinline__ uint32_t us3_at(uint32_t o) {\n"
          "    return *(const uint32_t *)((const unsigned char *)s_US3 + o);\n}\n";
     s += "struct RowJit {\nstatic constexpr int kPad = 0;\nstatic constexpr bool kRelUS = true;\n"
-         "static constexpr bool kPerBond = false;\n";
+         "static constexpr bool kPerBond = false;\n"
+         "static constexpr bool kBC = false;\n";
     // stage: D0
     s += "template <class Sv>\nstatic __device__ __forceinline__ void stage(const hm::BlkParams &P, unsigned char *) {\n"
          "    const uint8_t *R0g = (const uint8_t *)P.tab + P.off_R0;\n"
@@ -460,6 +528,23 @@ int jit_mv_kernel(const BlkParams &P, int dtype, const BondParams &bp, const voi
         "        const %s *__restrict__ x, %s *__restrict__ y, const int *__restrict__ Eptr) {\n"
         "    hm::matvec_body<%s, 1, RowJit>(P, x, y, Eptr);\n}\n", T, T, T);
     return jit_get(src, "k_blk_matvec_jit", dev, BLK_XPAD, kern);
+}
+
+// bond-correlation kernel of a chunk plan (bcmode) with nbk bonds: k_blk_bc_jit, dtype
+// HM_F64 (binary64 x and g, E = largest exponent field of x in Eptr) or HM_F32
+int jit_bc_kernel(const BlkParams &P, int dtype, int nbk, const void **kern) {
+    const char *env = getenv("HM_JIT");
+    if ((env && env[0] == '0') || !P.rows_ok || !P.bcmode) return 1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
+    std::string src = "#include \"blk_sweep.cuh\"\n" + gen_row_bc(P, nbk);
+    const char *T = dtype == HM_F64 ? "double" : "float";
+    put(src,
+        "extern \"C\" __global__ void __launch_bounds__(512, 2) k_blk_bc_jit(hm::BlkParams P,\n"
+        "        const %s *__restrict__ x, const %s *__restrict__ g, const int *__restrict__ Eptr,\n"
+        "        double *__restrict__ part) {\n"
+        "    hm::bc_body<%s, RowJit>(P, x, g, Eptr, part);\n}\n", T, T, T);
+    return jit_get(src, "k_blk_bc_jit", dev, BLK_XPAD, kern);
 }
 
 int jit_lz_kernel(const BlkParams &P, int dtype, const BondParams &bp, const void **kern) {

@@ -1,4 +1,5 @@
 // matvec.cu -- y = H x by rows (Eq. E-4-b), the bond-correlation adjoint, start vectors.
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -133,12 +134,19 @@ static int bond_corr_t(const SectorView &sv, const BondParams &bp, const T *g, c
     return HM_OK;
 }
 
+int blk_bond_corr(hm_basis *b, const BondParams &bp, const void *g, const void *x, double *out, int dtype,
+                  void *work, size_t work_bytes, double sign, const double *div, cudaStream_t st);
+size_t blk_bond_corr_bytes();
+
 int bond_corr_dev(const hm_basis *b, const BondParams &bp, const void *g, const void *x,
                   double *out, int dtype, void *work, size_t work_bytes, double sign,
                   const double *div, cudaStream_t st) {
     const SectorView &sv = b->view;
     const int nblk = grid_blocks(sv.dim, 256);
     if (bp.nb == 0) return HM_OK;
+    // s = 1/2 sectors: the block kernels compiled per chunk of bonds (blk.cu)
+    const int brc = blk_bond_corr(const_cast<hm_basis *>(b), bp, g, x, out, dtype, work, work_bytes, sign, div, st);
+    if (brc <= 0) return brc;
     if (!work || work_bytes < (size_t)nblk * bp.nb * sizeof(double))
         return fail(HM_EWORKSPACE, "bond_corr needs %zu workspace bytes",
                     (size_t)nblk * bp.nb * sizeof(double));
@@ -152,7 +160,8 @@ int bond_corr_dev(const hm_basis *b, const BondParams &bp, const void *g, const 
 }
 
 size_t bond_corr_bytes(const hm_basis *b, int n_bonds) {
-    return (size_t)grid_blocks(b->view.dim, 256) * (size_t)(n_bonds > 0 ? n_bonds : 1) * sizeof(double);
+    const size_t gen = (size_t)grid_blocks(b->view.dim, 256) * (size_t)(n_bonds > 0 ? n_bonds : 1) * sizeof(double);
+    return std::max(gen, blk_bond_corr_bytes());
 }
 
 int blk_matvec(hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype, int nvec,

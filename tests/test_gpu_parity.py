@@ -607,3 +607,28 @@ def test_block_split_override(hm, K, monkeypatch):
     res = hm.lanczos_run(b2, hm.bonds_of(inst), 30, seed=6, n_ritz=1)
     np.testing.assert_allclose(res.alpha, ref.alpha, rtol=0, atol=1e-13)
     np.testing.assert_allclose(res.beta, ref.beta, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("N,extra", [(20, 0), (22, 0), (22, 5)])
+def test_bond_corr_block_path(hm, N, extra):
+    """Sectors of >= 100k rows: the bond correlations run through the block kernels compiled
+    per chunk of 16 bonds (40-49 bonds: 3-4 chunks, the last one partial), FP64 and FP32
+    inputs, against the oracle; extra bonds between distant sites add long exchanges."""
+    inst = W.small_ring(N, -1.0, -0.5)
+    rng = np.random.default_rng(N + extra)
+    u, v = list(inst.u), list(inst.v)
+    for _ in range(extra):
+        a = int(rng.integers(0, N))
+        u.append(a); v.append((a + N // 2 - 1) % N)
+    u, v = np.array(u, np.int32), np.array(v, np.int32)
+    J = rng.uniform(-1.3, -0.5, len(u))
+    b = hm.Basis(N, 1, 0)
+    ob = oracle.Basis(N, 1, N // 2)
+    g, x = oracle.start_uniform(8, b.dim), oracle.start_uniform(9, b.dim)
+    ref = ob.bond_corr(oracle.Bonds(u, v, J), g, x)
+    got = hm.bond_corr(b, hm.BondList.make(u, v, J), torch.from_numpy(g).cuda(), torch.from_numpy(x).cuda())
+    np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+    g32, x32 = g.astype(np.float32), x.astype(np.float32)
+    ref32 = ob.bond_corr(oracle.Bonds(u, v, J), g32.astype(np.float64), x32.astype(np.float64))
+    got32 = hm.bond_corr(b, hm.BondList.make(u, v, J), torch.from_numpy(g32).cuda(), torch.from_numpy(x32).cuda())
+    np.testing.assert_allclose(got32.cpu().numpy(), ref32, rtol=1e-5, atol=1e-5 * np.abs(ref32).max())
