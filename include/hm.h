@@ -195,7 +195,8 @@ int lanczos_kernel_name(const hm_lanczos *run, char *name, int cap);
 /* Name of the kernel `matvec` launches for these arguments (the same dispatch, nothing
  * launched): "k_blk_matvec" (s = 1/2 block kernel, up to 4 distinct couplings),
  * "k_blk_matvec_jit" (block kernel compiled at run time for a bond list with more distinct
- * couplings) or "k_matvec" (general row kernel).  name: host buffer of cap bytes. */
+ * couplings), "k_s1_mv" (s = 1 block kernel, FP32, one vector) or "k_matvec" (general row
+ * kernel).  name: host buffer of cap bytes. */
 int matvec_kernel_name(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
                        const double *J, int dtype, int nvec, char *name, int cap);
 

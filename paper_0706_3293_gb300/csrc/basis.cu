@@ -264,6 +264,8 @@ int basis_free(hm_basis *b) {
     if (b->d_scratch && (e2 = cudaFree(b->d_scratch)) != cudaSuccess) e = e2;
     for (auto &kv : b->blk_tabs)
         if (kv.second.dev && (e2 = cudaFree(kv.second.dev)) != cudaSuccess) e = e2;
+    for (auto &kv : b->s1_tabs)
+        if (kv.second.dev && (e2 = cudaFree(kv.second.dev)) != cudaSuccess) e = e2;
     delete b;
     if (e != cudaSuccess) return cuda_fail(e, "basis_free");
     return HM_OK;

@@ -64,6 +64,18 @@ struct BlkTab {                     // byte-chunk rank tables of the s = 1/2 blo
 };
 }  // namespace hm
 
+namespace hm {
+constexpr int S1_KMAX = 10;         // s = 1 block path: at most 10 low sites (rank table of 4^K entries)
+struct S1Tab {                      // tables of the s = 1 block path (s1blk.cu), one split K
+    void *dev = nullptr;            // one device allocation holding the three arrays below
+    uint16_t *lut = nullptr;        // rank of every packed low word among words of its digit sum
+    uint32_t *lw = nullptr;         // low words by digit sum, each run in rank order
+    uint4 *blocks = nullptr;        // {h, off, k, rows} per block, in row order
+    int nblocks = 0, max_block = 0, K = -1;
+    int lwoff[2 * S1_KMAX + 2] = {};
+};
+}  // namespace hm
+
 struct hm_basis {
     hm::SectorView view;
     std::vector<uint64_t> D;        // host D(k, a), (N+1) x (S2*N+1)
@@ -71,6 +83,7 @@ struct hm_basis {
     void *d_cd = nullptr;           // device copy (owned)
     void *d_scratch = nullptr;      // 256 bytes of device scratch (owned), e.g. exponents
     std::map<int, hm::BlkTab> blk_tabs;   // per split position K (owned device memory)
+    std::map<int, hm::S1Tab> s1_tabs;     // s = 1 block path, per split K (owned device memory)
     int parity = 0;                 // spin-flip basis (basis_build_flip): +1 / -1, view.dim halved
     int device = 0;
 };

@@ -9,6 +9,7 @@
 #include "blk.cuh"
 #include "ef64.cuh"
 #include "hm_row.cuh"
+#include "s1blk.cuh"
 
 namespace hm {
 
@@ -42,6 +43,8 @@ struct LzLayout {
     size_t qqp;             // FP64 block path: partials of q_cur . q_prev (k_fix)
     size_t hpart;           // s = 1/2 block path: per-block partial sums, 2 x 2^hpart_H doubles
     int hpart_H;
+    size_t s1part;          // s = 1 block path (FP32): one partial sum per block, s1n of them
+    uint64_t s1n;
     bool shadow;
 };
 
@@ -71,6 +74,8 @@ static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad
         L.hpart_H = H;
         L.hpart = o; o += al256(((size_t)2 << H) * sizeof(double));
     }
+    // per-block partials of the s = 1 block path (FP32 products)
+    if (dtype == HM_F32 && (L.s1n = s1_block_count(b)) > 0) { L.s1part = o; o += al256(L.s1n * sizeof(double)); }
     L.sc = o; o += al256(sizeof(LzScalars));
     L.alpha = o; o += al256((size_t)max_steps * 8);
     L.beta = o; o += al256((size_t)max_steps * 8);
@@ -97,6 +102,8 @@ struct hm_lanczos {
     int use_blk, blk_blocks;
     const void *jit;        // block product specialised to the bonds (jit.cu), or nullptr
     int run;                // rows per thread run of the general product (row_runs)
+    int use_s1;             // s = 1 block path (FP32 products, s1blk.cu)
+    hm::S1Plan s1;
     int dtype, max_steps, host_j, next_phase;
     unsigned char *work;
     hm::LzLayout L;
@@ -554,6 +561,10 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
         } else if (R->use_blk) {
             HM_TRY(blk_lz32_launch(R->blk, (const float *)qc, (float *)qp, R->sc, R->hpart, R->blk_blocks, st, R->jit));
             k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->alpha, pprev);
+        } else if (R->use_s1) {
+            double *s1part = (double *)(R->work + R->L.s1part);
+            HM_TRY(s1_lz32(R->s1, (const float *)qc, (float *)qp, R->sc, s1part, st));
+            k_lz_alpha<<<1, NT, 0, st>>>(R->sc, s1part, R->s1.nblocks, R->alpha, pprev);
         } else {
             const size_t sm = row_smem_bytes<I>(sv);
             k_lz_matvec<I, T, Acc><<<nblk, NT, sm, st>>>(sv, R->bp, qc, qp, R->sc, R->part, R->run);
@@ -674,6 +685,12 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
         if (blk_lz_jit(R->blk, dtype, R->bp, &jk, &jb) == 0) { R->jit = jk; R->blk_blocks = jb; }
         if (R->blk.perbond && !R->jit) R->use_blk = 0;   // per-bond rows run only specialised
     }
+    R->use_s1 = 0;
+    if (!R->use_blk && R->L.s1part) {
+        rc = s1_plan(const_cast<hm_basis *>(b), R->bp, &R->s1);
+        if (rc < 0) { delete R; return rc; }
+        R->use_s1 = rc == 0 && (uint64_t)R->s1.nblocks <= R->L.s1n;
+    }
     if (b->parity && !R->use_blk) {
         delete R;
         return fail(HM_EINVAL, "spin-flip basis: this bond list does not take the s = 1/2 block path");
@@ -792,7 +809,8 @@ int lanczos_free(hm_lanczos *R) {
 int lanczos_kernel_name(const hm_lanczos *R, char *name, int cap) {
     if (!R || !name || cap < 1) return fail(HM_EINVAL, "NULL argument");
     const bool f64 = R->dtype == HM_F64;
-    const char *n = !R->use_blk ? "k_lz_matvec"
+    const char *n = R->use_s1 ? "k_s1_lz32"
+                    : !R->use_blk ? "k_lz_matvec"
                     : R->jit    ? (f64 ? "k_blk_lz64_jit" : "k_blk_lz32_jit")
                                 : (f64 ? "k_blk_lz64" : "k_blk_lz32");
     snprintf(name, (size_t)cap, "%s", n);

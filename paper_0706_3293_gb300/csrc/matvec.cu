@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "hm_row.cuh"
+#include "s1blk.cuh"
 
 namespace hm {
 
@@ -174,6 +175,13 @@ int matvec_dev(const hm_basis *b, const BondParams &bp, const void *x, void *y, 
     // s = 1/2 sectors with few coupling classes take the block path (blk.cu)
     const int brc = blk_matvec(const_cast<hm_basis *>(b), bp, x, y, dtype, nvec, st);
     if (brc <= 0) return brc;
+    // s = 1 FP32 products: the block kernel of s1blk.cu
+    if (dtype == HM_F32 && nvec == 1 && sv.S2 == 2) {
+        S1Plan P;
+        const int src = s1_plan(const_cast<hm_basis *>(b), bp, &P);
+        if (src < 0) return src;
+        if (src == 0) return s1_matvec(P, (const float *)x, (float *)y, st);
+    }
     if (b->parity)
         return fail(HM_EINVAL, "spin-flip basis: this bond list or vector count does not take the s = 1/2 block path");
     if (dtype == HM_F64) {
@@ -254,6 +262,12 @@ int matvec_kernel_name(const hm_basis *b, int n_bonds, const int32_t *u, const i
     BondParams bp;
     HM_TRY(make_bonds(b, n_bonds, u, v, J, &bp));
     const char *n = blk_matvec_kernel(const_cast<hm_basis *>(b), bp, dtype, nvec);
+    if (!n && dtype == HM_F32 && nvec == 1 && b->view.S2 == 2) {
+        S1Plan P;
+        const int src = s1_plan(const_cast<hm_basis *>(b), bp, &P);
+        if (src < 0) return src;
+        if (src == 0) n = "k_s1_mv";
+    }
     if (!n && b->parity) return fail(HM_EINVAL, "spin-flip basis: this bond list or vector count does not take the s = 1/2 block path");
     snprintf(name, (size_t)cap, "%s", n ? n : "k_matvec");
     return HM_OK;

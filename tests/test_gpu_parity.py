@@ -632,3 +632,25 @@ def test_bond_corr_block_path(hm, N, extra):
     ref32 = ob.bond_corr(oracle.Bonds(u, v, J), g32.astype(np.float64), x32.astype(np.float64))
     got32 = hm.bond_corr(b, hm.BondList.make(u, v, J), torch.from_numpy(g32).cuda(), torch.from_numpy(x32).cuda())
     np.testing.assert_allclose(got32.cpu().numpy(), ref32, rtol=1e-5, atol=1e-5 * np.abs(ref32).max())
+
+
+@pytest.mark.parametrize("two_m", [0, 4])
+def test_s1_block_path(hm, two_m):
+    """s = 1 FP32 products through the s = 1 block kernel (N = 14 random 4-regular graph):
+    rows against the oracle, the Lanczos kernel name, and E0 against the oracle's FP64 run."""
+    inst = W.s1_random_graph(14, 5)
+    b = hm.Basis(14, 2, two_m)
+    ob = oracle.Basis(14, 2, 14 - two_m // 2)
+    bl = hm.bonds_of(inst)
+    assert hm.matvec_kernel_name(b, bl, dtype=torch.float32) == "k_s1_mv"
+    x32 = oracle.start_uniform(4, b.dim).astype(np.float32)
+    ref = ob.matvec(obonds(inst), x32.astype(np.float64))
+    y = hm.matvec(b, bl, torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
+    assert rel(y, ref) <= TOL_F32
+    run = hm.LanczosRun(b, bl, 5, seed=3, dtype=torch.float32)
+    assert run.kernel_name() == "k_s1_lz32"
+    run.close()
+    res = hm.lanczos_run(b, bl, 150, seed=3, n_ritz=1, dtype=torch.float32)
+    al, be = ob.lanczos(obonds(inst), oracle.start_uniform(3, b.dim), 150)
+    e_ref = oracle.tridiag_lowest(al, be, 1)[0]
+    assert abs(res.ritz[0] - e_ref) <= 1e-6 * abs(e_ref)
