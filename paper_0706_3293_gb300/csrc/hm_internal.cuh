@@ -67,10 +67,13 @@ struct BlkTab {                     // byte-chunk rank tables of the s = 1/2 blo
 namespace hm {
 constexpr int S1_KMAX = 10;         // s = 1 block path: at most 10 low sites (rank table of 4^K entries)
 struct S1Tab {                      // tables of the s = 1 block path (s1blk.cu), one split K
-    void *dev = nullptr;            // one device allocation holding the three arrays below
+    void *dev = nullptr;            // one device allocation holding the arrays below
     uint16_t *lut = nullptr;        // rank of every packed low word among words of its digit sum
     uint32_t *lw = nullptr;         // low words by digit sum, each run in rank order
     uint4 *blocks = nullptr;        // {h, off, k, rows} per block, in row order
+    uint16_t *rl = nullptr;         // exchange rank tables of the low words (s1_sweep.cuh)
+    uint16_t *rx = nullptr;
+    int nlw = 0;
     int nblocks = 0, max_block = 0, K = -1;
     int lwoff[2 * S1_KMAX + 2] = {};
 };

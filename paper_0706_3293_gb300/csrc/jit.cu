@@ -27,6 +27,7 @@
 
 #include "blk.cuh"
 #include "blk_sweep.cuh"
+#include "s1blk.cuh"
 #include "jit_embed.inc"   // kJitHeaderNames / kJitHeaderTexts: the .cuh files above, as text
 
 #ifndef HM_CUDA_LIBDIR
@@ -444,6 +445,73 @@ std::string gen_row(const BlkParams &P, bool &ok) {
     return s;
 }
 
+// The s = 1 row terms of the low sites of plan P written out (s1_sweep.cuh): every rank
+// table entry of the row is loaded first (coalesced: consecutive rows read consecutive
+// entries), then each low bond adds its diagonal term and its exchanges gathered from the
+// staged block, and each low site with cross bonds its share of the diagonal and the
+// gathers from the blocks one unit of digit sum away.  f64: integer couplings C_b and an
+// exact int128 sum (row64), else float -J_b (row32).
+std::string gen_s1_row(const S1Plan &P, bool f64) {
+    std::string s = "#include \"s1_sweep.cuh\"\nstruct S1Row {\n";
+    if (f64)
+        s += "static __device__ __forceinline__ void row64(uint32_t l, const long long *Xs,\n"
+             "        const long long *__restrict__ x, const uint16_t *__restrict__ rl, const uint16_t *__restrict__ rx,\n"
+             "        const uint32_t *cb, const long long *cc, long long &dg, __int128 &acc) {\n";
+    else
+        s += "static __device__ __forceinline__ void row32(uint32_t l, const float *Xs, const float *__restrict__ x,\n"
+             "        const uint16_t *__restrict__ rl, const uint16_t *__restrict__ rx, const uint32_t *cb,\n"
+             "        const float *cc, float &dg, float &acc) {\n";
+    bool used[S1_MAXK] = {}, crs[S1_MAXK] = {};
+    for (int j = 0; j < P.nlo; ++j) used[P.lo_p[j]] = used[P.lo_q[j]] = true;
+    for (int j = 0; j < P.ncr; ++j) used[P.cr_p[j]] = crs[P.cr_p[j]] = true;
+    const unsigned nl = (unsigned)P.nlw;
+    for (int j = 0; j < P.nlo; ++j) {
+        const int p = P.lo_p[j], q = P.lo_q[j], pi = q * (q - 1) / 2 + p;
+        put(s, "    const uint32_t L%d_0 = rl[%uu], L%d_1 = rl[%uu];\n", j, 2u * pi * nl, j, (2u * pi + 1u) * nl);
+    }
+    for (int p = 0; p < P.K; ++p)
+        if (crs[p]) put(s, "    const uint32_t X%d_0 = rx[%uu], X%d_1 = rx[%uu];\n", p, 2u * p * nl, p, (2u * p + 1u) * nl);
+    for (int p = 0; p < P.K; ++p)
+        if (used[p]) {
+            if (f64) put(s, "    const int m%d = 1 - (int)((l >> %d) & 3u);\n", p, 2 * p);
+            else put(s, "    const float m%d = (float)(1 - (int)((l >> %d) & 3u));\n", p, 2 * p);
+        }
+    for (int j = 0; j < P.nlo; ++j) {
+        const int p = P.lo_p[j], q = P.lo_q[j];
+        if (f64) {
+            const long long c = P.lo_c[j];
+            put(s, "    dg += (long long)(m%d * m%d) * (%lldLL);\n", p, q, c);
+            put(s, "    if (L%d_0 != 0xFFFFu) acc += (__int128)Xs[L%d_0] * (%lldLL);\n", j, j, c);
+            put(s, "    if (L%d_1 != 0xFFFFu) acc += (__int128)Xs[L%d_1] * (%lldLL);\n", j, j, c);
+        } else {
+            const double c = (double)P.lo_j[j];
+            put(s, "    dg = fmaf(%af, m%d * m%d, dg);\n", c, p, q);
+            put(s, "    if (L%d_0 != 0xFFFFu) acc = fmaf(%af, Xs[L%d_0], acc);\n", j, c, j);
+            put(s, "    if (L%d_1 != 0xFFFFu) acc = fmaf(%af, Xs[L%d_1], acc);\n", j, c, j);
+        }
+    }
+    for (int p = 0; p < P.K; ++p) {
+        if (!crs[p]) continue;
+        if (f64) put(s, "    dg += (long long)m%d * cc[%d];\n", p, p);
+        else put(s, "    dg = fmaf(cc[%d], m%d, dg);\n", p, p);
+        for (int j = 0; j < P.ncr; ++j) {
+            if (P.cr_p[j] != p) continue;
+            put(s, "    { const uint32_t b0 = cb[%d], b1 = cb[%d];\n", 2 * j, 2 * j + 1);
+            for (int d = 0; d < 2; ++d) {
+                if (f64)
+                    put(s, "      if (X%d_%d != 0xFFFFu && b%d != 0xFFFFFFFFu) acc += (__int128)__ldg(x + (b%d + X%d_%d)) * (%lldLL);\n",
+                        p, d, d, d, p, d, P.cr_c[j]);
+                else
+                    put(s, "      if (X%d_%d != 0xFFFFu && b%d != 0xFFFFFFFFu) acc = fmaf(%af, __ldg(x + (b%d + X%d_%d)), acc);\n",
+                        p, d, d, (double)P.cr_j[j], d, p, d);
+            }
+            s += "    }\n";
+        }
+    }
+    s += "}\n};\n";
+    return s;
+}
+
 int compile(const std::string &src, const char *name, int device, const void **out) {
     nvrtcProgram prog;
     if (g_nv.create(&prog, src.c_str(), "hm_jit.cu", (int)(sizeof kJitHeaderNames / sizeof *kJitHeaderNames),
@@ -577,6 +645,29 @@ int jit_lz_kernel(const BlkParams &P, int dtype, const BondParams &bp, const voi
             "    hm::lz32_body<%d, RowJit>(P, qc, qp, S, part);\n}\n",
             ctas, nc);
     return jit_get(src, name, dev, delta ? 0 : BLK_XPAD, kern);
+}
+
+int jit_s1_kernel(const S1Plan &P, int mode, const void **kern) {
+    if (mode < 0 || mode > 2) return 1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
+    std::string src = gen_s1_row(P, mode == 2);
+    static const char *const names[3] = {"k_s1_mv_jit", "k_s1_lz32_jit", "k_s1_lz64_jit"};
+    if (mode == 0)
+        src += "extern \"C\" __global__ void __launch_bounds__(512, 2) k_s1_mv_jit(hm::S1Plan P,\n"
+               "        const float *__restrict__ x, float *__restrict__ y) {\n"
+               "    hm::s1j_body32<S1Row, false>(P, x, y, nullptr, nullptr);\n}\n";
+    else if (mode == 1)
+        src += "extern \"C\" __global__ void __launch_bounds__(512, 2) k_s1_lz32_jit(hm::S1Plan P,\n"
+               "        const float *__restrict__ qc, float *__restrict__ qp, const hm::LzScalars *__restrict__ S,\n"
+               "        double *__restrict__ part) {\n"
+               "    hm::s1j_body32<S1Row, true>(P, qc, qp, S, part);\n}\n";
+    else
+        src += "extern \"C\" __global__ void __launch_bounds__(512, 2) k_s1_lz64_jit(hm::S1Plan P,\n"
+               "        const long long *__restrict__ Xc, unsigned long long *__restrict__ Y,\n"
+               "        const hm::LzScalars *__restrict__ S, int pc, double *__restrict__ part) {\n"
+               "    hm::s1j_body64<S1Row>(P, Xc, Y, S, pc, part);\n}\n";
+    return jit_get(src, names[mode], dev, 0, kern);
 }
 
 int jit_pad(const void *kern) {

@@ -60,8 +60,10 @@ static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad
     L.buf[1] = o; o += al256(dim * es);
     const size_t npart = std::max<size_t>((size_t)nblk, (size_t)sm_count() * 8);
     L.part = o; o += al256(npart * 2 * sizeof(double));
-    // the s = 1/2 block path of FP64 runs needs y and two fixed-point copies
-    L.shadow = dtype == HM_F64 && b->view.S2 == 1 && b->view.N >= 10 && b->view.N <= 32 && !b->view.idx64;
+    // the block paths of FP64 runs (s = 1/2, s = 1) need y and two fixed-point copies
+    const uint64_t s1n = s1_block_count(b);
+    L.shadow = dtype == HM_F64 && !b->view.idx64 &&
+               ((b->view.S2 == 1 && b->view.N >= 10 && b->view.N <= 32) || (b->view.S2 == 2 && s1n > 0));
     if (L.shadow) {
         L.ybuf = o; o += al256(dim * 8);
         L.xs[0] = o; o += al256(dim * 8);
@@ -74,8 +76,8 @@ static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad
         L.hpart_H = H;
         L.hpart = o; o += al256(((size_t)2 << H) * sizeof(double));
     }
-    // per-block partials of the s = 1 block path (FP32 products)
-    if (dtype == HM_F32 && (L.s1n = s1_block_count(b)) > 0) { L.s1part = o; o += al256(L.s1n * sizeof(double)); }
+    // per-block partials of the s = 1 block path
+    if ((L.s1n = s1n) > 0) { L.s1part = o; o += al256(L.s1n * sizeof(double)); }
     L.sc = o; o += al256(sizeof(LzScalars));
     L.alpha = o; o += al256((size_t)max_steps * 8);
     L.beta = o; o += al256((size_t)max_steps * 8);
@@ -102,7 +104,7 @@ struct hm_lanczos {
     int use_blk, blk_blocks;
     const void *jit;        // block product specialised to the bonds (jit.cu), or nullptr
     int run;                // rows per thread run of the general product (row_runs)
-    int use_s1;             // s = 1 block path (FP32 products, s1blk.cu)
+    int use_s1;             // s = 1 block path (s1blk.cu)
     hm::S1Plan s1;
     int dtype, max_steps, host_j, next_phase;
     unsigned char *work;
@@ -550,12 +552,16 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
     T *qp = parity ? b0 : b1;
     const int nblk = grid_blocks(sv.dim, NT);
     const int pprev = parity ^ 1;   // buffer of q_prev, receives u then w
-    const bool b64 = R->use_blk && R->dtype == HM_F64;
+    const bool b64 = (R->use_blk || R->use_s1) && R->dtype == HM_F64;
     long long *xs[2] = {R->L.shadow ? (long long *)(R->work + R->L.xs[0]) : nullptr,
                         R->L.shadow ? (long long *)(R->work + R->L.xs[1]) : nullptr};
     unsigned long long *Y = R->L.shadow ? (unsigned long long *)(R->work + R->L.ybuf) : nullptr;
     if (phase == 0) {
-        if (b64) {
+        if (b64 && R->use_s1) {
+            double *s1part = (double *)(R->work + R->L.s1part);
+            HM_TRY(s1_lz64(R->s1, xs[parity], Y, R->sc, parity, s1part, st));
+            k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, s1part, R->s1.nblocks, R->qqp, nblk, R->alpha, pprev);
+        } else if (b64) {
             HM_TRY(blk_lz64_launch(R->blk, xs[parity], Y, R->sc, parity, R->hpart, R->blk_blocks, st, R->jit));
             k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->qqp, nblk, R->alpha, pprev);
         } else if (R->use_blk) {
@@ -638,7 +644,7 @@ static int enqueue_start(hm_lanczos *R, const void *v0, uint64_t seed, cudaStrea
     if (R->dtype == HM_F64) k_sumsq<double><<<nblk, NT, 0, st>>>((const double *)b0, sv.dim, R->part, &R->sc->emax[0]);
     else k_sumsq<float><<<nblk, NT, 0, st>>>((const float *)b0, sv.dim, R->part, nullptr);
     k_lz_start<<<1, NT, 0, st>>>(R->sc, R->part, nblk);
-    if (R->use_blk && R->dtype == HM_F64) {
+    if ((R->use_blk || R->use_s1) && R->dtype == HM_F64) {
         HM_CUDA(cudaMemsetAsync(R->work + R->L.xs[1], 0, sv.dim * 8, st));
         k_fix<<<nblk, NT, 0, st>>>((const unsigned long long *)b0, (long long *)(R->work + R->L.xs[0]),
                                    (const long long *)(R->work + R->L.xs[1]), sv.dim, R->sc, 0, R->qqp);
@@ -690,6 +696,10 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
         rc = s1_plan(const_cast<hm_basis *>(b), R->bp, &R->s1);
         if (rc < 0) { delete R; return rc; }
         R->use_s1 = rc == 0 && (uint64_t)R->s1.nblocks <= R->L.s1n;
+        // FP64 runs only specialised (and with the fixed-point copies); FP32 compiles its
+        // specialised kernel here, outside any graph capture (the generic one serves without)
+        if (R->use_s1 && dtype == HM_F64) R->use_s1 = R->L.shadow && s1_jit_ready(R->s1, 2);
+        else if (R->use_s1) (void)s1_jit_ready(R->s1, 1);
     }
     if (b->parity && !R->use_blk) {
         delete R;
@@ -809,7 +819,7 @@ int lanczos_free(hm_lanczos *R) {
 int lanczos_kernel_name(const hm_lanczos *R, char *name, int cap) {
     if (!R || !name || cap < 1) return fail(HM_EINVAL, "NULL argument");
     const bool f64 = R->dtype == HM_F64;
-    const char *n = R->use_s1 ? "k_s1_lz32"
+    const char *n = R->use_s1 ? s1_kernel_name(R->s1, f64 ? 2 : 1)
                     : !R->use_blk ? "k_lz_matvec"
                     : R->jit    ? (f64 ? "k_blk_lz64_jit" : "k_blk_lz32_jit")
                                 : (f64 ? "k_blk_lz64" : "k_blk_lz32");

@@ -266,7 +266,7 @@ int matvec_kernel_name(const hm_basis *b, int n_bonds, const int32_t *u, const i
         S1Plan P;
         const int src = s1_plan(const_cast<hm_basis *>(b), bp, &P);
         if (src < 0) return src;
-        if (src == 0) n = "k_s1_mv";
+        if (src == 0) n = s1_kernel_name(P, 0);
     }
     if (!n && b->parity) return fail(HM_EINVAL, "spin-flip basis: this bond list or vector count does not take the s = 1/2 block path");
     snprintf(name, (size_t)cap, "%s", n ? n : "k_matvec");

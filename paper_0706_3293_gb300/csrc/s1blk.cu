@@ -1,41 +1,23 @@
-// s1blk.cu -- block-structured FP32 products for s = 1 sectors.
+// s1blk.cu -- block-structured products for s = 1 sectors (layout in s1_sweep.cuh).
 //
-// The rank of Sec. 3.2 is additive over positions for any spin, so with the low part l
-// (sites 0..K-1) and the high part h (sites K..N-1) of a state
-//     index = off(h) + rank_K(l),   off(h) = sum_{p >= K} CD[p][S_p][a_p],
-// where the running digit sums S_p of the high positions start from k = A - sum(h), the
-// digit sum of the low part; all states with the same h form one contiguous block of
-// D(K, k) rows, ordered by rank_K.  As on the s = 1/2 block path (blk.cuh):
-//   * a CTA stages its block's x in shared memory; exchanges among low sites gather there,
-//     their target rank read from a table of rank_K over all packed low words;
+// As on the s = 1/2 block path (blk.cuh):
+//   * a CTA stages its block's x in shared memory; exchanges among low sites gather there;
 //   * exchanges among high sites keep the low word, so they gather the same row of another
 //     block (coalesced), its offset encoded once per block;
 //   * exchanges across the split read one other block, shared by all rows of the block.
-// For s = 1 every allowed exchange element 1/2 s+_u s-_v is 1 (Eq. E-2-1 with the ladder
-// factors sqrt(2) sqrt(2) / 2), so an exchange adds -J_b x_t; the diagonal is
-// -J_b m_u m_v with m = 1 - a.  Digits are packed two bits per site.
+// The kernels specialised to the bond list at run time (jit.cu, bodies in s1_sweep.cuh)
+// read the exchange targets among the low words from the rank tables rl / rx; the generic
+// kernel below (the fallback without NVRTC, HM_JIT=0) walks its bond lists at run time and
+// re-encodes every target word with the rank table of all packed low words.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "ef64.cuh"
 #include "s1blk.cuh"
 
 namespace hm {
-
-__device__ __forceinline__ int s1_dig(uint32_t w, int p) { return (int)((w >> (2 * p)) & 3u); }
-
-// off(h) for a block whose low part has digit sum k (cd: the CD table in shared memory)
-__device__ __forceinline__ uint32_t s1_off(const S1Plan &P, const uint32_t *cd, uint32_t h, int k) {
-    int S = k;
-    uint32_t off = 0;
-    for (int t = 0; t < P.H; ++t) {
-        const int a = s1_dig(h, t);
-        S += a;
-        off += cd[(P.K + t) * P.cd_rowlen + S * P.cd_w + a];
-    }
-    return off;
-}
 
 // Every block through rowf(r, l, x_r, y_r) after its set-up; LZ: Lanczos product
 // u = sigma H q - gamma q_prev written over q_prev and part[block] = sum (sigma q . u)
@@ -184,17 +166,57 @@ static int s1_tables(hm_basis *b, int K, S1Tab *out) {
         mb = std::max(mb, n);
     }
     std::sort(blocks.begin(), blocks.end(), [](const uint4 &x, const uint4 &y) { return x.y < y.y; });
-    const size_t b_lut = ((nlut * 2 + 255) & ~(size_t)255), b_lw = ((lw.size() * 4 + 255) & ~(size_t)255);
-    const size_t bytes = b_lut + b_lw + blocks.size() * sizeof(uint4);
+    // exchange rank tables of the low words: rl[(2 pi + d) nlw + g] for the site pair
+    // pi = q (q - 1) / 2 + p (p < q), rx[(2 p + d) nlw + g]; 0xFFFF where not allowed.
+    // Only the digit sums kmin..kmax of the sector's blocks have ranks (the CD table of
+    // the sector holds no others); every entry is checked to be a row of the class it
+    // addresses.
+    const int nlw = lwoff[2 * K + 1], kmax = std::min(A, 2 * K), kmin = std::max(0, A - 2 * H);
+    const int npair = K * (K - 1) / 2;
+    for (int k = 0; k <= 2 * K; ++k)
+        if (D(K, k) >= 0xFFFF) return 1;               // ranks and the 0xFFFF mark share 16 bits
+    std::vector<uint16_t> rl((size_t)2 * npair * nlw, 0xFFFF), rx((size_t)2 * K * nlw, 0xFFFF);
+    bool bad = false;
+    auto rank_of = [&](uint32_t w, int k2) -> uint16_t {
+        const uint16_t v = lut[w];
+        if (k2 < kmin || k2 > kmax || (uint64_t)v >= D(K, k2)) bad = true;
+        return v;
+    };
+    for (int k = kmin; k <= kmax; ++k)
+        for (int g = lwoff[k]; g < lwoff[k + 1]; ++g) {
+            const uint32_t l = lw[g];
+            for (int p = 0; p < K; ++p) {
+                const int ap = (int)((l >> (2 * p)) & 3);
+                if (ap >= 1 && k - 1 >= kmin) rx[(size_t)(2 * p) * nlw + g] = rank_of(l - (1u << (2 * p)), k - 1);
+                if (ap <= 1 && k + 1 <= kmax) rx[(size_t)(2 * p + 1) * nlw + g] = rank_of(l + (1u << (2 * p)), k + 1);
+                for (int q = p + 1; q < K; ++q) {
+                    const int aq = (int)((l >> (2 * q)) & 3), pi = q * (q - 1) / 2 + p;
+                    if (ap >= 1 && aq <= 1)
+                        rl[(size_t)(2 * pi) * nlw + g] = rank_of(l - (1u << (2 * p)) + (1u << (2 * q)), k);
+                    if (ap <= 1 && aq >= 1)
+                        rl[(size_t)(2 * pi + 1) * nlw + g] = rank_of(l + (1u << (2 * p)) - (1u << (2 * q)), k);
+                }
+            }
+        }
+    if (bad) return 1;                                 // not used: the general kernel serves
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t b_lut = al(nlut * 2), b_lw = al(lw.size() * 4), b_bl = al(blocks.size() * sizeof(uint4));
+    const size_t b_rl = al(rl.size() * 2), b_rx = al(rx.size() * 2);
+    const size_t bytes = b_lut + b_lw + b_bl + b_rl + b_rx;
     unsigned char *dev = nullptr;
     HM_CUDA(cudaMalloc(&dev, bytes));
     HM_CUDA(cudaMemcpy(dev, lut.data(), nlut * 2, cudaMemcpyHostToDevice));
     HM_CUDA(cudaMemcpy(dev + b_lut, lw.data(), lw.size() * 4, cudaMemcpyHostToDevice));
     HM_CUDA(cudaMemcpy(dev + b_lut + b_lw, blocks.data(), blocks.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+    if (!rl.empty()) HM_CUDA(cudaMemcpy(dev + b_lut + b_lw + b_bl, rl.data(), rl.size() * 2, cudaMemcpyHostToDevice));
+    HM_CUDA(cudaMemcpy(dev + b_lut + b_lw + b_bl + b_rl, rx.data(), rx.size() * 2, cudaMemcpyHostToDevice));
     out->dev = dev;
     out->lut = (uint16_t *)dev;
     out->lw = (uint32_t *)(dev + b_lut);
     out->blocks = (uint4 *)(dev + b_lut + b_lw);
+    out->rl = (uint16_t *)(dev + b_lut + b_lw + b_bl);
+    out->rx = (uint16_t *)(dev + b_lut + b_lw + b_bl + b_rl);
+    out->nlw = nlw;
     out->nblocks = (int)blocks.size();
     out->max_block = mb;
     out->K = K;
@@ -235,13 +257,32 @@ int s1_plan(hm_basis *b, const BondParams &bp, S1Plan *P) {
     auto it = b->s1_tabs.find(K);
     if (it == b->s1_tabs.end()) {
         S1Tab t;
-        HM_TRY(s1_tables(b, K, &t));
+        const int rc = s1_tables(b, K, &t);
+        if (rc != 0) return rc;
         it = b->s1_tabs.emplace(K, t).first;
     }
     const S1Tab &T = it->second;
     P->N = sv.N; P->K = K; P->H = H; P->A = sv.A;
     P->nblocks = T.nblocks; P->max_block = T.max_block;
     P->lut = T.lut; P->lw = T.lw; P->blocks = T.blocks;
+    P->nlw = T.nlw; P->rl = T.rl; P->rx = T.rx;
+    // FP64 couplings: C_b = round(-J_b 2^cs) with sum |J_b| 2^cs < 2^62, so every row's
+    // diagonal sum of C_b m_u m_v fits in int64 and a row sum in int128
+    double sumj = 0.0;
+    for (int t = 0; t < bp.nb; ++t) sumj += std::fabs(bp.jm[t]);
+    int e2 = 0;
+    if (sumj > 0.0) std::frexp(sumj, &e2);            // sumj < 2^e2
+    P->cs = 62 - e2;
+    auto cfix = [&](double jm) { return (long long)std::llround(std::ldexp(jm, P->cs)); };
+    {
+        int il = 0, ih = 0, ic = 0;
+        for (int t = 0; t < bp.nb; ++t) {
+            const int p = bp.p[t], q = bp.q[t];
+            if (q < K) P->lo_c[il++] = cfix(bp.jm[t]);
+            else if (p >= K) P->hi_c[ih++] = cfix(bp.jm[t]);
+            else P->cr_c[ic++] = cfix(bp.jm[t]);
+        }
+    }
     P->cd = (const uint32_t *)sv.cd; P->cd_w = sv.cd_w; P->cd_rowlen = sv.cd_rowlen; P->cd_len = sv.cd_len;
     for (int k = 0; k <= 2 * K + 1; ++k) P->lwoff[k] = T.lwoff[k];
     const size_t sm = ((size_t)(P->cd_len * 4 + 15) & ~(size_t)15) + (size_t)P->max_block * 4;
@@ -259,7 +300,9 @@ uint64_t s1_block_count(const hm_basis *b) {
     return n;
 }
 
-static size_t s1_smem(const S1Plan &P) { return ((size_t)(P.cd_len * 4 + 15) & ~(size_t)15) + (size_t)P.max_block * 4; }
+static size_t s1_smem(const S1Plan &P, int es) {
+    return ((size_t)(P.cd_len * 4 + 15) & ~(size_t)15) + (size_t)P.max_block * es;
+}
 
 static int s1_grid(const S1Plan &P, const void *kern, size_t sm) {
     int per = 0;
@@ -270,22 +313,56 @@ static int s1_grid(const S1Plan &P, const void *kern, size_t sm) {
     return std::max(1, std::min(sm_count() * std::max(per, 1), P.nblocks));
 }
 
+// the kernel of plan P specialised to its bonds (mode as in jit_s1_kernel), or nullptr
+// when NVRTC cannot serve or HM_JIT=0 asks for the generic kernels
+static const void *s1_jit(const S1Plan &P, int mode) {
+    const char *e = getenv("HM_JIT");
+    if (e && e[0] == '0') return nullptr;
+    const void *k = nullptr;
+    return jit_s1_kernel(P, mode, &k) == 0 ? k : nullptr;
+}
+
+static int s1_launch(const void *kern, const S1Plan &P, size_t sm, void **args, cudaStream_t st) {
+    HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HM_CUDA(cudaLaunchKernel(kern, dim3(s1_grid(P, kern, sm)), dim3(S1_NT), args, sm, st));
+    return HM_OK;
+}
+
 // y = H x, FP32, one vector
 int s1_matvec(const S1Plan &P, const float *x, float *y, cudaStream_t st) {
-    const size_t sm = s1_smem(P);
-    HM_CUDA(cudaFuncSetAttribute(k_s1_mv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_s1_mv<<<s1_grid(P, (const void *)k_s1_mv, sm), S1_NT, sm, st>>>(P, x, y);
-    HM_CUDA(cudaGetLastError());
-    return HM_OK;
+    const void *k = s1_jit(P, 0);
+    if (!k) k = (const void *)k_s1_mv;
+    void *args[] = {(void *)&P, (void *)&x, (void *)&y};
+    return s1_launch(k, P, s1_smem(P, 4), args, st);
 }
 
 // Lanczos product, FP32: q_prev <- sigma H q - gamma q_prev, part[block] = (sigma q . u) per block
 int s1_lz32(const S1Plan &P, const float *qc, float *qp, const LzScalars *S, double *part, cudaStream_t st) {
-    const size_t sm = s1_smem(P);
-    HM_CUDA(cudaFuncSetAttribute(k_s1_lz32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_s1_lz32<<<s1_grid(P, (const void *)k_s1_lz32, sm), S1_NT, sm, st>>>(P, qc, qp, S, part);
-    HM_CUDA(cudaGetLastError());
-    return HM_OK;
+    const void *k = s1_jit(P, 1);
+    if (!k) k = (const void *)k_s1_lz32;
+    void *args[] = {(void *)&P, (void *)&qc, (void *)&qp, (void *)&S, (void *)&part};
+    return s1_launch(k, P, s1_smem(P, 4), args, st);
+}
+
+bool s1_jit_ready(const S1Plan &P, int mode) {
+    if (mode == 2 && s1_smem(P, 8) > 200 * 1024) return false;
+    return s1_jit(P, mode) != nullptr;
+}
+
+// Lanczos product, FP64 (specialised kernel only): Y = H q, part[block] = (q . y)
+int s1_lz64(const S1Plan &P, const long long *Xc, unsigned long long *Y, const LzScalars *S, int pc, double *part,
+            cudaStream_t st) {
+    const void *k = s1_smem(P, 8) > 200 * 1024 ? nullptr : s1_jit(P, 2);
+    if (!k) return fail(HM_EINVAL, "the FP64 s = 1 product needs its run-time compiled kernel");
+    void *args[] = {(void *)&P, (void *)&Xc, (void *)&Y, (void *)&S, (void *)&pc, (void *)&part};
+    return s1_launch(k, P, s1_smem(P, 8), args, st);
+}
+
+const char *s1_kernel_name(const S1Plan &P, int mode) {
+    const bool j = s1_jit(P, mode) != nullptr;
+    if (mode == 0) return j ? "k_s1_mv_jit" : "k_s1_mv";
+    if (mode == 1) return j ? "k_s1_lz32_jit" : "k_s1_lz32";
+    return j ? "k_s1_lz64_jit" : "none";
 }
 
 }  // namespace hm

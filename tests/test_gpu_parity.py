@@ -635,22 +635,100 @@ def test_bond_corr_block_path(hm, N, extra):
 
 
 @pytest.mark.parametrize("two_m", [0, 4])
-def test_s1_block_path(hm, two_m):
-    """s = 1 FP32 products through the s = 1 block kernel (N = 14 random 4-regular graph):
-    rows against the oracle, the Lanczos kernel name, and E0 against the oracle's FP64 run."""
+def test_s1_block_path(hm, two_m, monkeypatch):
+    """s = 1 FP32 products through the s = 1 block kernels (N = 14 random 4-regular graph):
+    rows of the kernel specialised to the bonds and of the generic one (HM_JIT=0) against
+    the oracle, the Lanczos kernel names, and E0 against the oracle's FP64 run."""
     inst = W.s1_random_graph(14, 5)
     b = hm.Basis(14, 2, two_m)
     ob = oracle.Basis(14, 2, 14 - two_m // 2)
     bl = hm.bonds_of(inst)
-    assert hm.matvec_kernel_name(b, bl, dtype=torch.float32) == "k_s1_mv"
     x32 = oracle.start_uniform(4, b.dim).astype(np.float32)
     ref = ob.matvec(obonds(inst), x32.astype(np.float64))
-    y = hm.matvec(b, bl, torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
-    assert rel(y, ref) <= TOL_F32
-    run = hm.LanczosRun(b, bl, 5, seed=3, dtype=torch.float32)
-    assert run.kernel_name() == "k_s1_lz32"
-    run.close()
+    for jit, name in (("1", "k_s1_mv_jit"), ("0", "k_s1_mv")):
+        monkeypatch.setenv("HM_JIT", jit)
+        assert hm.matvec_kernel_name(b, bl, dtype=torch.float32) == name
+        y = hm.matvec(b, bl, torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
+        assert rel(y, ref) <= TOL_F32
+        run = hm.LanczosRun(b, bl, 5, seed=3, dtype=torch.float32)
+        assert run.kernel_name() == name.replace("mv", "lz32")
+        run.close()
+    monkeypatch.setenv("HM_JIT", "1")
     res = hm.lanczos_run(b, bl, 150, seed=3, n_ritz=1, dtype=torch.float32)
     al, be = ob.lanczos(obonds(inst), oracle.start_uniform(3, b.dim), 150)
     e_ref = oracle.tridiag_lowest(al, be, 1)[0]
     assert abs(res.ritz[0] - e_ref) <= 1e-6 * abs(e_ref)
+
+
+@pytest.mark.parametrize("n,two_m", [(6, 0), (8, 0), (10, 2), (12, 0), (12, 4), (14, 6)])
+def test_s1_lanczos_f64_block_path(hm, n, two_m, monkeypatch):
+    """FP64 s = 1 Lanczos through the block product specialised to the bonds (exact int128
+    row sums of integer-scaled couplings): the first 20 coefficients against the oracle's
+    FP64 run to 1e-12, and the same run on the general row kernel (HM_JIT=0).  (Later
+    coefficients of two valid runs drift apart by amplified rounding: at N = 6, dim 141,
+    step 28 differs by 4e-9.)"""
+    inst = W.s1_random_graph(n, 100 + n)
+    b = hm.Basis(n, 2, two_m)
+    ob = oracle.Basis(n, 2, n - two_m // 2)
+    bl = hm.bonds_of(inst)
+    steps = min(20, b.dim - 1)
+    al, be = ob.lanczos(obonds(inst), oracle.start_uniform(9, b.dim), steps)
+    m = len(al)
+    for jit, name in (("1", "k_s1_lz64_jit"), ("0", "k_lz_matvec")):
+        monkeypatch.setenv("HM_JIT", jit)
+        run = hm.LanczosRun(b, bl, steps, seed=9)
+        assert run.kernel_name() == name
+        run.step(m)
+        ga, gb, _ = run.read()
+        run.close()
+        np.testing.assert_allclose(ga[:m], al, rtol=0, atol=1e-12 * np.abs(al).max())
+        np.testing.assert_allclose(gb[:m - 1], be[:m - 1], rtol=0, atol=1e-12 * np.abs(al).max())
+    monkeypatch.setenv("HM_JIT", "1")
+
+
+def test_s1_full_size_rows_and_first_steps(hm):
+    """The s = 1, N = 20 sector (377,379,369 rows) of the s = 1 benchmark workload: sampled
+    rows of the FP32 block product against the oracle one by one; the first FP64 Lanczos
+    coefficients of the block product, in the launch configuration the benchmark times,
+    against alpha_1, beta_1, alpha_2 formed from the general FP64 row kernel, whose
+    sampled rows match the oracle to 1e-12."""
+    inst = W.s1_random_graph()
+    b = hm.Basis(20, 2, 0)
+    ob = oracle.Basis(20, 2, 20)
+    bl = hm.bonds_of(inst)
+    ob_b = obonds(inst)
+    x = oracle.start_uniform(inst.seed, b.dim)
+    xt = torch.from_numpy(x).cuda()
+    rng = np.random.default_rng(11)
+    starts = [0, b.dim - 256] + [int(r) for r in rng.integers(0, b.dim - 256, 6)]
+    # FP32 rows of the block product
+    assert hm.matvec_kernel_name(b, bl, dtype=torch.float32) == "k_s1_mv_jit"
+    x32 = xt.float()
+    y32 = hm.matvec(b, bl, x32)
+    x32h = x32.double().cpu().numpy()
+    for r0 in starts:
+        ref = ob.matvec_rows(ob_b, x32h, r0, r0 + 256)
+        assert rel(y32[r0:r0 + 256].double().cpu().numpy(), ref) <= TOL_F32
+    del y32, x32, x32h
+    # FP64: general row kernel, checked on samples, then alpha_1, beta_1, alpha_2
+    y = hm.matvec(b, bl, xt)
+    for r0 in starts[:4]:
+        assert rel(y[r0:r0 + 256].cpu().numpy(), ob.matvec_rows(ob_b, x, r0, r0 + 256)) <= TOL_F64
+    nx = torch.linalg.vector_norm(xt)
+    q1 = xt / nx
+    y = y / nx
+    a1 = float(torch.dot(q1, y))
+    w = y - a1 * q1
+    b1 = float(torch.linalg.vector_norm(w))
+    q2 = w / b1
+    del w, y
+    a2 = float(torch.dot(q2, hm.matvec(b, bl, q2)))
+    del q2, q1
+    run = hm.LanczosRun(b, bl, 4, v0=xt)
+    assert run.kernel_name() == "k_s1_lz64_jit"
+    run.step(2)
+    ga, gb, _ = run.read()
+    run.close()
+    scale = max(abs(a1), abs(a2))
+    assert abs(ga[0] - a1) <= 1e-12 * scale and abs(gb[0] - b1) <= 1e-12 * scale
+    assert abs(ga[1] - a2) <= 1e-12 * scale
