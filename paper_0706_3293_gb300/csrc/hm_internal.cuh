@@ -71,8 +71,8 @@ struct S1Tab {                      // tables of the s = 1 block path (s1blk.cu)
     uint16_t *lut = nullptr;        // rank of every packed low word among words of its digit sum
     uint32_t *lw = nullptr;         // low words by digit sum, each run in rank order
     uint4 *blocks = nullptr;        // {h, off, k, rows} per block, in row order
-    uint16_t *rl = nullptr;         // exchange rank tables of the low words (s1_sweep.cuh)
-    uint16_t *rx = nullptr;
+    uint32_t *rl = nullptr;         // exchange rank tables of the low words (s1_sweep.cuh)
+    uint32_t *rx = nullptr;
     int nlw = 0;
     int nblocks = 0, max_block = 0, K = -1;
     int lwoff[2 * S1_KMAX + 2] = {};

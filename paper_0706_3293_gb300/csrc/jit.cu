@@ -447,19 +447,20 @@ std::string gen_row(const BlkParams &P, bool &ok) {
 
 // The s = 1 row terms of the low sites of plan P written out (s1_sweep.cuh): every rank
 // table entry of the row is loaded first (coalesced: consecutive rows read consecutive
-// entries), then each low bond adds its diagonal term and its exchanges gathered from the
-// staged block, and each low site with cross bonds its share of the diagonal and the
-// gathers from the blocks one unit of digit sum away.  f64: integer couplings C_b and an
-// exact int128 sum (row64), else float -J_b (row32).
+// entries, both directions of a pair or site in one word), then each low bond adds its
+// diagonal term and its exchanges gathered from the staged block, and each low site with
+// cross bonds its share of the diagonal and the gathers from the blocks one unit of digit
+// sum away.  f64: integer couplings C_b and one exact int128 product per bond of C_b and
+// the sum of its (up to two) gathered values (row64), else float -J_b (row32).
 std::string gen_s1_row(const S1Plan &P, bool f64) {
     std::string s = "#include \"s1_sweep.cuh\"\nstruct S1Row {\n";
     if (f64)
         s += "static __device__ __forceinline__ void row64(uint32_t l, const long long *Xs,\n"
-             "        const long long *__restrict__ x, const uint16_t *__restrict__ rl, const uint16_t *__restrict__ rx,\n"
-             "        const uint32_t *cb, const long long *cc, long long &dg, __int128 &acc) {\n";
+             "        const long long *__restrict__ x, const uint32_t *__restrict__ rl, const uint32_t *__restrict__ rx,\n"
+             "        const uint32_t *cb, const long long *cc, long long &dg, __int128 &a) {\n";
     else
         s += "static __device__ __forceinline__ void row32(uint32_t l, const float *Xs, const float *__restrict__ x,\n"
-             "        const uint16_t *__restrict__ rl, const uint16_t *__restrict__ rx, const uint32_t *cb,\n"
+             "        const uint32_t *__restrict__ rl, const uint32_t *__restrict__ rx, const uint32_t *cb,\n"
              "        const float *cc, float &dg, float &acc) {\n";
     bool used[S1_MAXK] = {}, crs[S1_MAXK] = {};
     for (int j = 0; j < P.nlo; ++j) used[P.lo_p[j]] = used[P.lo_q[j]] = true;
@@ -467,10 +468,10 @@ std::string gen_s1_row(const S1Plan &P, bool f64) {
     const unsigned nl = (unsigned)P.nlw;
     for (int j = 0; j < P.nlo; ++j) {
         const int p = P.lo_p[j], q = P.lo_q[j], pi = q * (q - 1) / 2 + p;
-        put(s, "    const uint32_t L%d_0 = rl[%uu], L%d_1 = rl[%uu];\n", j, 2u * pi * nl, j, (2u * pi + 1u) * nl);
+        put(s, "    const uint32_t L%d = rl[%uu];\n", j, (unsigned)pi * nl);
     }
     for (int p = 0; p < P.K; ++p)
-        if (crs[p]) put(s, "    const uint32_t X%d_0 = rx[%uu], X%d_1 = rx[%uu];\n", p, 2u * p * nl, p, (2u * p + 1u) * nl);
+        if (crs[p]) put(s, "    const uint32_t X%d = rx[%uu];\n", p, (unsigned)p * nl);
     for (int p = 0; p < P.K; ++p)
         if (used[p]) {
             if (f64) put(s, "    const int m%d = 1 - (int)((l >> %d) & 3u);\n", p, 2 * p);
@@ -478,35 +479,40 @@ std::string gen_s1_row(const S1Plan &P, bool f64) {
         }
     for (int j = 0; j < P.nlo; ++j) {
         const int p = P.lo_p[j], q = P.lo_q[j];
+        put(s, "    { const uint32_t t0 = L%d & 0xFFFFu, t1 = L%d >> 16;\n", j, j);
         if (f64) {
             const long long c = P.lo_c[j];
-            put(s, "    dg += (long long)(m%d * m%d) * (%lldLL);\n", p, q, c);
-            put(s, "    if (L%d_0 != 0xFFFFu) acc += (__int128)Xs[L%d_0] * (%lldLL);\n", j, j, c);
-            put(s, "    if (L%d_1 != 0xFFFFu) acc += (__int128)Xs[L%d_1] * (%lldLL);\n", j, j, c);
+            put(s, "      dg += (long long)(m%d * m%d) * (%lldLL);\n", p, q, c);
+            // both directions of the bond summed first: one 128-bit product per bond
+            s += "      long long v = t0 != 0xFFFFu ? Xs[t0] : 0ll;\n      if (t1 != 0xFFFFu) v += Xs[t1];\n";
+            put(s, "      a += (__int128)v * (%lldLL);\n", c);
         } else {
             const double c = (double)P.lo_j[j];
-            put(s, "    dg = fmaf(%af, m%d * m%d, dg);\n", c, p, q);
-            put(s, "    if (L%d_0 != 0xFFFFu) acc = fmaf(%af, Xs[L%d_0], acc);\n", j, c, j);
-            put(s, "    if (L%d_1 != 0xFFFFu) acc = fmaf(%af, Xs[L%d_1], acc);\n", j, c, j);
+            put(s, "      dg = fmaf(%af, m%d * m%d, dg);\n", c, p, q);
+            for (int d = 0; d < 2; ++d) put(s, "      if (t%d != 0xFFFFu) acc = fmaf(%af, Xs[t%d], acc);\n", d, c, d);
         }
+        s += "    }\n";
     }
     for (int p = 0; p < P.K; ++p) {
         if (!crs[p]) continue;
-        if (f64) put(s, "    dg += (long long)m%d * cc[%d];\n", p, p);
-        else put(s, "    dg = fmaf(cc[%d], m%d, dg);\n", p, p);
+        put(s, "    { const uint32_t t0 = X%d & 0xFFFFu, t1 = X%d >> 16;\n", p, p);
+        if (f64) put(s, "      dg += (long long)m%d * cc[%d];\n", p, p);
+        else put(s, "      dg = fmaf(cc[%d], m%d, dg);\n", p, p);
         for (int j = 0; j < P.ncr; ++j) {
             if (P.cr_p[j] != p) continue;
-            put(s, "    { const uint32_t b0 = cb[%d], b1 = cb[%d];\n", 2 * j, 2 * j + 1);
-            for (int d = 0; d < 2; ++d) {
-                if (f64)
-                    put(s, "      if (X%d_%d != 0xFFFFu && b%d != 0xFFFFFFFFu) acc += (__int128)__ldg(x + (b%d + X%d_%d)) * (%lldLL);\n",
-                        p, d, d, d, p, d, P.cr_c[j]);
-                else
-                    put(s, "      if (X%d_%d != 0xFFFFu && b%d != 0xFFFFFFFFu) acc = fmaf(%af, __ldg(x + (b%d + X%d_%d)), acc);\n",
-                        p, d, d, (double)P.cr_j[j], d, p, d);
+            put(s, "      { const uint32_t b0 = cb[%d], b1 = cb[%d];\n", 2 * j, 2 * j + 1);
+            if (f64) {
+                s += "        long long v = t0 != 0xFFFFu && b0 != 0xFFFFFFFFu ? __ldg(x + (b0 + t0)) : 0ll;\n"
+                     "        if (t1 != 0xFFFFu && b1 != 0xFFFFFFFFu) v += __ldg(x + (b1 + t1));\n";
+                put(s, "        a += (__int128)v * (%lldLL);\n", P.cr_c[j]);
+            } else {
+                for (int d = 0; d < 2; ++d)
+                    put(s, "        if (t%d != 0xFFFFu && b%d != 0xFFFFFFFFu) acc = fmaf(%af, __ldg(x + (b%d + t%d)), acc);\n",
+                        d, d, (double)P.cr_j[j], d, d);
             }
-            s += "    }\n";
+            s += "      }\n";
         }
+        s += "    }\n";
     }
     s += "}\n};\n";
     return s;
@@ -653,15 +659,18 @@ int jit_s1_kernel(const S1Plan &P, int mode, const void **kern) {
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
     std::string src = gen_s1_row(P, mode == 2);
     static const char *const names[3] = {"k_s1_mv_jit", "k_s1_lz32_jit", "k_s1_lz64_jit"};
+    // FP32: resident CTAs per SM the register budget is cut for (HM_S1_CTAS: 2 or 3)
+    int ctas = 3;
+    if (const char *e = getenv("HM_S1_CTAS")) ctas = atoi(e) == 2 ? 2 : 3;
     if (mode == 0)
-        src += "extern \"C\" __global__ void __launch_bounds__(512, 2) k_s1_mv_jit(hm::S1Plan P,\n"
-               "        const float *__restrict__ x, float *__restrict__ y) {\n"
-               "    hm::s1j_body32<S1Row, false>(P, x, y, nullptr, nullptr);\n}\n";
+        put(src, "extern \"C\" __global__ void __launch_bounds__(512, %d) k_s1_mv_jit(hm::S1Plan P,\n"
+                 "        const float *__restrict__ x, float *__restrict__ y) {\n"
+                 "    hm::s1j_body32<S1Row, false>(P, x, y, nullptr, nullptr);\n}\n", ctas);
     else if (mode == 1)
-        src += "extern \"C\" __global__ void __launch_bounds__(512, 2) k_s1_lz32_jit(hm::S1Plan P,\n"
-               "        const float *__restrict__ qc, float *__restrict__ qp, const hm::LzScalars *__restrict__ S,\n"
-               "        double *__restrict__ part) {\n"
-               "    hm::s1j_body32<S1Row, true>(P, qc, qp, S, part);\n}\n";
+        put(src, "extern \"C\" __global__ void __launch_bounds__(512, %d) k_s1_lz32_jit(hm::S1Plan P,\n"
+                 "        const float *__restrict__ qc, float *__restrict__ qp, const hm::LzScalars *__restrict__ S,\n"
+                 "        double *__restrict__ part) {\n"
+                 "    hm::s1j_body32<S1Row, true>(P, qc, qp, S, part);\n}\n", ctas);
     else
         src += "extern \"C\" __global__ void __launch_bounds__(512, 2) k_s1_lz64_jit(hm::S1Plan P,\n"
                "        const long long *__restrict__ Xc, unsigned long long *__restrict__ Y,\n"

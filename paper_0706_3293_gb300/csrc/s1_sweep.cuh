@@ -12,11 +12,12 @@
 //
 // The bodies below serve the kernels compiled at run time for one bond list (jit.cu):
 // the bond terms of the low sites are written out, and every exchange target among the
-// low words is read from a rank table indexed by the row's position in the list of low
-// words (coalesced reads, 0xFFFF where the exchange is not allowed):
-//   rl[(2 pi + d) nlw + g]: site pair pi = (p < q < K), d = 0: l - e_p + e_q, d = 1:
-//                           l + e_p - e_q, rank within the same digit sum;
-//   rx[(2 p + d) nlw + g]:  d = 0: l - e_p (digit sum k - 1), d = 1: l + e_p (k + 1).
+// low words is read from a rank table indexed by the row's position g in the list of low
+// words (coalesced reads; two 16-bit ranks per entry, the low half for direction d = 0,
+// the high half for d = 1; 0xFFFF where the exchange is not allowed):
+//   rl[pi nlw + g]: site pair pi = q (q - 1) / 2 + p (p < q < K), d = 0: l - e_p + e_q,
+//                   d = 1: l + e_p - e_q, rank within the same digit sum;
+//   rx[p nlw + g]:  d = 0: l - e_p (digit sum k - 1), d = 1: l + e_p (k + 1).
 // Exchanges among the high sites read the same row of another block (one offset per
 // block), exchanges across the split a row of a block one unit of digit sum away.
 #pragma once
@@ -46,8 +47,8 @@ struct S1Plan {
     float lo_j[S1_MAXB], hi_j[S1_MAXB], cr_j[S1_MAXB];   // -J_b
     // exchange rank tables of the low words (see above; independent of the couplings)
     int nlw;                         // low words in the lists: lwoff[2K + 1]
-    const uint16_t *rl, *rx;
-    // FP64: the couplings as integers C_b = round(-J_b 2^cs), sum |C_b| < 2^62
+    const uint32_t *rl, *rx;
+    // FP64: the couplings as integers C_b = round(-J_b 2^cs), |C_b| <= 2^52
     int cs;
     long long lo_c[S1_MAXB], hi_c[S1_MAXB], cr_c[S1_MAXB];
 };
@@ -201,7 +202,8 @@ __device__ __forceinline__ void s1j_body32(const S1Plan &P, const float *__restr
     }
 }
 
-// value of a 128-bit integer as a double (two roundings: the high word, then the sum)
+// value of a 128-bit integer (|T| < 2^117) as a double: the high word exactly, the low
+// word and the sum rounded (within one unit in the last place)
 __device__ __forceinline__ double s1_i128_to_double(__int128 v) {
     const long long hi = (long long)(v >> 64);
     const unsigned long long lo = (unsigned long long)v;
@@ -209,10 +211,10 @@ __device__ __forceinline__ double s1_i128_to_double(__int128 v) {
 }
 
 // ---- FP64 Lanczos product: Xc = q_cur as fixed point of exponent E = S->emax[pc] (unit
-// 2^u, u = E - 1022 - FIX_BITS); every row is one exact int128 sum
-//     T = (sum_b C_b m_u m_v) X_i + sum over allowed exchanges C_b X_t
-// rounded once to binary64, y_i = T 2^(u - cs) into Y (bit patterns); part[block] =
-// (q . y) over the block's rows ---------------------------------------------------------------
+// 2^u, u = E - 1022 - FIX_BITS, |X| <= 2^53 + 1); every row is one exact int128 sum
+//     T = (sum_b C_b m_u m_v) X_i + sum_b C_b (sum over b's allowed exchanges of X_t)
+// (|C_b| <= 2^52, so |T| < 2^116 for up to 288 bonds), converted to binary64 and scaled,
+// y_i = T 2^(u - cs), into Y (bit patterns); part[block] = (q . y) over the block's rows.
 template <class Row>
 __device__ __forceinline__ void s1j_body64(const S1Plan &P, const long long *__restrict__ Xc,
                                            unsigned long long *__restrict__ Y, const LzScalars *__restrict__ S, int pc,
@@ -220,6 +222,8 @@ __device__ __forceinline__ void s1j_body64(const S1Plan &P, const long long *__r
     if (S->done) return;
     const int E = S->emax[pc];
     const int u = E - 1022 - ef::FIX_BITS;
+    const int ky = u - P.cs;
+    const double sy = ky >= -1022 && ky <= 1023 ? ef::u2d((unsigned long long)(ky + 1023) << 52) : ldexp(1.0, ky);
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *cd = (uint32_t *)smem;                                        // [cd_len]
     long long *Xs = (long long *)(smem + ((P.cd_len * 4 + 15) & ~15));      // [max_block]
@@ -245,12 +249,12 @@ __device__ __forceinline__ void s1j_body64(const S1Plan &P, const long long *__r
             const uint32_t l = __ldg(P.lw + g);
             const long long xo = Xs[r];
             long long dg = sb.bdiag;
-            __int128 acc = 0;
-            Row::row64(l, Xs, Xc, P.rl + g, P.rx + g, sb.cb, sb.cc, dg, acc);
+            __int128 a = 0;
+            Row::row64(l, Xs, Xc, P.rl + g, P.rx + g, sb.cb, sb.cc, dg, a);
 #pragma unroll 2
-            for (int e = 0; e < nh; ++e) acc += (__int128)sb.hc[e] * __ldg(Xc + (sb.ht[e] + (uint32_t)r));
-            const __int128 t = (__int128)dg * xo + acc;
-            const unsigned long long yb = ef::d2u(ldexp(s1_i128_to_double(t), u - P.cs));
+            for (int e = 0; e < nh; ++e) a += (__int128)__ldg(Xc + (sb.ht[e] + (uint32_t)r)) * sb.hc[e];
+            const __int128 t = a + (__int128)dg * xo;
+            const unsigned long long yb = ef::d2u(s1_i128_to_double(t) * sy);
             __stcs(Y + off + r, yb);
             d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
         }

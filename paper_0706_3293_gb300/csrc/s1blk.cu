@@ -166,8 +166,9 @@ static int s1_tables(hm_basis *b, int K, S1Tab *out) {
         mb = std::max(mb, n);
     }
     std::sort(blocks.begin(), blocks.end(), [](const uint4 &x, const uint4 &y) { return x.y < y.y; });
-    // exchange rank tables of the low words: rl[(2 pi + d) nlw + g] for the site pair
-    // pi = q (q - 1) / 2 + p (p < q), rx[(2 p + d) nlw + g]; 0xFFFF where not allowed.
+    // exchange rank tables of the low words: rl[pi nlw + g] for the site pair
+    // pi = q (q - 1) / 2 + p (p < q), rx[p nlw + g]; direction d in the low (d = 0) or high
+    // (d = 1) 16 bits, 0xFFFF where not allowed.
     // Only the digit sums kmin..kmax of the sector's blocks have ranks (the CD table of
     // the sector holds no others); every entry is checked to be a row of the class it
     // addresses.
@@ -175,7 +176,10 @@ static int s1_tables(hm_basis *b, int K, S1Tab *out) {
     const int npair = K * (K - 1) / 2;
     for (int k = 0; k <= 2 * K; ++k)
         if (D(K, k) >= 0xFFFF) return 1;               // ranks and the 0xFFFF mark share 16 bits
-    std::vector<uint16_t> rl((size_t)2 * npair * nlw, 0xFFFF), rx((size_t)2 * K * nlw, 0xFFFF);
+    std::vector<uint32_t> rl((size_t)npair * nlw, 0xFFFFFFFFu), rx((size_t)K * nlw, 0xFFFFFFFFu);
+    auto put_rank = [](uint32_t &e, int d, uint16_t v) {
+        e = d == 0 ? (e & 0xFFFF0000u) | v : (e & 0xFFFFu) | ((uint32_t)v << 16);
+    };
     bool bad = false;
     auto rank_of = [&](uint32_t w, int k2) -> uint16_t {
         const uint16_t v = lut[w];
@@ -187,35 +191,35 @@ static int s1_tables(hm_basis *b, int K, S1Tab *out) {
             const uint32_t l = lw[g];
             for (int p = 0; p < K; ++p) {
                 const int ap = (int)((l >> (2 * p)) & 3);
-                if (ap >= 1 && k - 1 >= kmin) rx[(size_t)(2 * p) * nlw + g] = rank_of(l - (1u << (2 * p)), k - 1);
-                if (ap <= 1 && k + 1 <= kmax) rx[(size_t)(2 * p + 1) * nlw + g] = rank_of(l + (1u << (2 * p)), k + 1);
+                uint32_t &ex = rx[(size_t)p * nlw + g];
+                if (ap >= 1 && k - 1 >= kmin) put_rank(ex, 0, rank_of(l - (1u << (2 * p)), k - 1));
+                if (ap <= 1 && k + 1 <= kmax) put_rank(ex, 1, rank_of(l + (1u << (2 * p)), k + 1));
                 for (int q = p + 1; q < K; ++q) {
                     const int aq = (int)((l >> (2 * q)) & 3), pi = q * (q - 1) / 2 + p;
-                    if (ap >= 1 && aq <= 1)
-                        rl[(size_t)(2 * pi) * nlw + g] = rank_of(l - (1u << (2 * p)) + (1u << (2 * q)), k);
-                    if (ap <= 1 && aq >= 1)
-                        rl[(size_t)(2 * pi + 1) * nlw + g] = rank_of(l + (1u << (2 * p)) - (1u << (2 * q)), k);
+                    uint32_t &el = rl[(size_t)pi * nlw + g];
+                    if (ap >= 1 && aq <= 1) put_rank(el, 0, rank_of(l - (1u << (2 * p)) + (1u << (2 * q)), k));
+                    if (ap <= 1 && aq >= 1) put_rank(el, 1, rank_of(l + (1u << (2 * p)) - (1u << (2 * q)), k));
                 }
             }
         }
     if (bad) return 1;                                 // not used: the general kernel serves
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t b_lut = al(nlut * 2), b_lw = al(lw.size() * 4), b_bl = al(blocks.size() * sizeof(uint4));
-    const size_t b_rl = al(rl.size() * 2), b_rx = al(rx.size() * 2);
+    const size_t b_rl = al(rl.size() * 4), b_rx = al(rx.size() * 4);
     const size_t bytes = b_lut + b_lw + b_bl + b_rl + b_rx;
     unsigned char *dev = nullptr;
     HM_CUDA(cudaMalloc(&dev, bytes));
     HM_CUDA(cudaMemcpy(dev, lut.data(), nlut * 2, cudaMemcpyHostToDevice));
     HM_CUDA(cudaMemcpy(dev + b_lut, lw.data(), lw.size() * 4, cudaMemcpyHostToDevice));
     HM_CUDA(cudaMemcpy(dev + b_lut + b_lw, blocks.data(), blocks.size() * sizeof(uint4), cudaMemcpyHostToDevice));
-    if (!rl.empty()) HM_CUDA(cudaMemcpy(dev + b_lut + b_lw + b_bl, rl.data(), rl.size() * 2, cudaMemcpyHostToDevice));
-    HM_CUDA(cudaMemcpy(dev + b_lut + b_lw + b_bl + b_rl, rx.data(), rx.size() * 2, cudaMemcpyHostToDevice));
+    if (!rl.empty()) HM_CUDA(cudaMemcpy(dev + b_lut + b_lw + b_bl, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice));
+    HM_CUDA(cudaMemcpy(dev + b_lut + b_lw + b_bl + b_rl, rx.data(), rx.size() * 4, cudaMemcpyHostToDevice));
     out->dev = dev;
     out->lut = (uint16_t *)dev;
     out->lw = (uint32_t *)(dev + b_lut);
     out->blocks = (uint4 *)(dev + b_lut + b_lw);
-    out->rl = (uint16_t *)(dev + b_lut + b_lw + b_bl);
-    out->rx = (uint16_t *)(dev + b_lut + b_lw + b_bl + b_rl);
+    out->rl = (uint32_t *)(dev + b_lut + b_lw + b_bl);
+    out->rx = (uint32_t *)(dev + b_lut + b_lw + b_bl + b_rl);
     out->nlw = nlw;
     out->nblocks = (int)blocks.size();
     out->max_block = mb;
@@ -266,13 +270,13 @@ int s1_plan(hm_basis *b, const BondParams &bp, S1Plan *P) {
     P->nblocks = T.nblocks; P->max_block = T.max_block;
     P->lut = T.lut; P->lw = T.lw; P->blocks = T.blocks;
     P->nlw = T.nlw; P->rl = T.rl; P->rx = T.rx;
-    // FP64 couplings: C_b = round(-J_b 2^cs) with sum |J_b| 2^cs < 2^62, so every row's
-    // diagonal sum of C_b m_u m_v fits in int64 and a row sum in int128
-    double sumj = 0.0;
-    for (int t = 0; t < bp.nb; ++t) sumj += std::fabs(bp.jm[t]);
+    // FP64 couplings: C_b = round(-J_b 2^cs) with max |J_b| 2^cs < 2^52, so |C_b| <= 2^52
+    // (the split products of s1_mac) and every row's diagonal sum fits in int64
+    double maxj = 0.0;
+    for (int t = 0; t < bp.nb; ++t) maxj = std::max(maxj, std::fabs(bp.jm[t]));
     int e2 = 0;
-    if (sumj > 0.0) std::frexp(sumj, &e2);            // sumj < 2^e2
-    P->cs = 62 - e2;
+    if (maxj > 0.0) std::frexp(maxj, &e2);            // maxj < 2^e2
+    P->cs = 52 - e2;
     auto cfix = [&](double jm) { return (long long)std::llround(std::ldexp(jm, P->cs)); };
     {
         int il = 0, ih = 0, ic = 0;
