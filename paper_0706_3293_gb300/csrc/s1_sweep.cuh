@@ -69,10 +69,13 @@ __device__ __forceinline__ uint32_t s1_off(const S1Plan &P, const uint32_t *cd, 
 
 // ---- per-block set-up of the specialised bodies -------------------------------------------
 // Cf: coupling type (float -J_b in FP32, integer C_b in FP64)
+template <class Cf> struct S1Hi {  // a valid high exchange: target block offset, coupling
+    uint32_t t;
+    Cf c;
+};
 template <class Cf> struct S1Blk {
     uint32_t raw[2 * S1_MAXB];       // high exchange (bond, direction): target block or ~0
-    uint32_t ht[2 * S1_MAXB];        // the valid ones, compacted in bond order
-    Cf hc[2 * S1_MAXB];              //   and their couplings
+    S1Hi<Cf> hx[2 * S1_MAXB];        // the valid ones, compacted in bond order
     uint32_t cb[2 * S1_MAXB];        // cross exchange (bond, direction): target block or ~0
     int8_t cm[S1_MAXB];              // cross bond: m of its high site in this block
     Cf cc[S1_MAXK];                  // low site p: sum over its cross bonds of coupling x m_q
@@ -130,8 +133,8 @@ __device__ __forceinline__ void s1_compact(const S1Plan &P, S1Blk<Cf> &sb) {
             const uint32_t b = __ballot_sync(0xffffffffu, v);
             if (v) {
                 const int o = base + __popc(b & ((1u << lane) - 1u));
-                sb.ht[o] = t;
-                sb.hc[o] = s1_cpl_hi<Cf>(P, e >> 1);
+                sb.hx[o].t = t;
+                sb.hx[o].c = s1_cpl_hi<Cf>(P, e >> 1);
             }
             base += __popc(b);
         }
@@ -184,7 +187,10 @@ __device__ __forceinline__ void s1j_body32(const S1Plan &P, const float *__restr
             float dg = sb.bdiag, acc = 0.0f;
             Row::row32(l, Xs, x, P.rl + g, P.rx + g, sb.cb, sb.cc, dg, acc);
 #pragma unroll 4
-            for (int e = 0; e < nh; ++e) acc = fmaf(sb.hc[e], __ldg(x + (sb.ht[e] + (uint32_t)r)), acc);
+            for (int e = 0; e < nh; ++e) {
+                const S1Hi<float> he = sb.hx[e];
+                acc = fmaf(he.c, __ldg(x + (he.t + (uint32_t)r)), acc);
+            }
             const float hv = fmaf(dg, xo, acc);
             if constexpr (LZ) {
                 const float u = sg * hv - gm * y[off + r];
@@ -214,7 +220,8 @@ __device__ __forceinline__ double s1_i128_to_double(__int128 v) {
 // 2^u, u = E - 1022 - FIX_BITS, |X| <= 2^53 + 1); every row is one exact int128 sum
 //     T = (sum_b C_b m_u m_v) X_i + sum_b C_b (sum over b's allowed exchanges of X_t)
 // (|C_b| <= 2^52, so |T| < 2^116 for up to 288 bonds), converted to binary64 and scaled,
-// y_i = T 2^(u - cs), into Y (bit patterns); part[block] = (q . y) over the block's rows.
+// y_i = T 2^(u - cs), into Y (bit patterns); part[block] = (q . y) over the block's rows
+// (double-float products and sums: no binary64 instruction per row for the dot).
 template <class Row>
 __device__ __forceinline__ void s1j_body64(const S1Plan &P, const long long *__restrict__ Xc,
                                            unsigned long long *__restrict__ Y, const LzScalars *__restrict__ S, int pc,
@@ -252,7 +259,10 @@ __device__ __forceinline__ void s1j_body64(const S1Plan &P, const long long *__r
             __int128 a = 0;
             Row::row64(l, Xs, Xc, P.rl + g, P.rx + g, sb.cb, sb.cc, dg, a);
 #pragma unroll 2
-            for (int e = 0; e < nh; ++e) a += (__int128)__ldg(Xc + (sb.ht[e] + (uint32_t)r)) * sb.hc[e];
+            for (int e = 0; e < nh; ++e) {
+                const S1Hi<long long> he = sb.hx[e];
+                a += (__int128)__ldg(Xc + (he.t + (uint32_t)r)) * he.c;
+            }
             const __int128 t = a + (__int128)dg * xo;
             const unsigned long long yb = ef::d2u(s1_i128_to_double(t) * sy);
             __stcs(Y + off + r, yb);
