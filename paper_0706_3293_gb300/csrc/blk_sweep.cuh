@@ -494,10 +494,11 @@ __device__ __forceinline__ void matvec_body(const BlkParams &P, const T *__restr
         const int u = E - 1022 - ef::FIX_BITS;
         unsigned long long *yb = (unsigned long long *)y;
         if constexpr (Row::kPerBond) {
+            const double sy = ef::pow2d(u - P.pb_s);
             blk_sweep<int64_t, NC, false, Row>(P, (const unsigned char *)x, GF64{E}, nullptr, [](uint32_t) { return 0; },
                                           [&](uint32_t off, uint32_t r, int64_t xo, __int128 sv, int) {
                                               const __int128 t = (__int128)P.pb_c0 * xo + sv;
-                                              yb[off + r] = ef::d2u(ldexp(i128_to_double(t), u - P.pb_s));
+                                              yb[off + r] = ef::d2u(i128_to_double(t) * sy);
                                           },
                                           [](int) {}, [](uint32_t, int) {});
         } else {
@@ -560,9 +561,10 @@ __device__ __forceinline__ void lz64_body(const BlkParams &P, const long long *_
         if constexpr (IR) d1 += (__int128)xo * ts;
         else d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
     };
+    const double sy = ef::pow2d(u - P.pb_s);
     auto rowb = [&](uint32_t off, uint32_t r, int64_t xo, __int128 sv, int) {
         const __int128 t = (__int128)P.pb_c0 * xo + sv;
-        const unsigned long long yb = ef::d2u(ldexp(i128_to_double(t), u - P.pb_s));
+        const unsigned long long yb = ef::d2u(i128_to_double(t) * sy);
         __stcs(Y + off + r, yb);
         d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
     };

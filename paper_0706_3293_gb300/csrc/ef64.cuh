@@ -248,6 +248,13 @@ EF_HD uint64_t bits_from_int(int64_t T, int k) {
     return sign | ((uint64_t)be << 52) | (mant & 0xFFFFFFFFFFFFFull);
 }
 
+// 2^k as a double, exactly (through ldexp outside the normal exponent range); v * pow2d(k)
+// then equals ldexp(v, k) with one multiply per use
+EF_HD double pow2d(int k) {
+    if (k >= -1022 && k <= 1023) return u2d((uint64_t)(k + 1023) << 52);
+    return ldexp(1.0, k);
+}
+
 // double-float (true value (hi + lo) 2^scale) -> fixed point with unit
 // 2^(E - 1022 - FIX_BITS): each float is its 24-bit significand shifted into place with
 // 8 guard bits (bits of lo below them dropped), the sum rounded half up, so the result

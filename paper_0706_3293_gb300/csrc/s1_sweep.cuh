@@ -229,8 +229,7 @@ __device__ __forceinline__ void s1j_body64(const S1Plan &P, const long long *__r
     if (S->done) return;
     const int E = S->emax[pc];
     const int u = E - 1022 - ef::FIX_BITS;
-    const int ky = u - P.cs;
-    const double sy = ky >= -1022 && ky <= 1023 ? ef::u2d((unsigned long long)(ky + 1023) << 52) : ldexp(1.0, ky);
+    const double sy = ef::pow2d(u - P.cs);
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *cd = (uint32_t *)smem;                                        // [cd_len]
     long long *Xs = (long long *)(smem + ((P.cd_len * 4 + 15) & ~15));      // [max_block]
