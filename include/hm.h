@@ -236,6 +236,48 @@ int e0_grad(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t 
             const double *J, const void *v0, uint64_t seed, int steps, void *work,
             size_t work_bytes, double *e0, double *dE0_dJ, double *psi_out, void *stream);
 
+/* ---- Arnoldi and projection methods on the same product -------------------------------- */
+/* The paper's closing summary ports its product to related Krylov-type methods such as
+ * Arnoldi or the projection method without spelling them out; these are the textbook
+ * iterations on the products of Eq. (E-4-b), FP64 vectors, no host round trip per step.
+ *
+ * Arnoldi with full re-orthogonalisation (classical Gram-Schmidt applied twice):
+ *   v_1 = v0/|v0|;  for j = 1..steps: w = H v_j;  twice { h = V_j^T w; w -= V_j h;
+ *   H[1..j, j] += h };  H[j+1, j] = |w|;  v_{j+1} = w / |w|.
+ * V_j = (v_1 .. v_j) is kept in the workspace ((steps + 1) vectors).  The run stops after
+ * step j when |w| <= 1e-12 * max |H entries| (Krylov space exhausted; HM_BREAKDOWN).
+ * hess: host, (steps + 1) x steps doubles, column major (H[i, j] at hess[j (steps + 1) + i]),
+ * may be NULL; *steps_done = columns formed; ritz: host, the n_ritz lowest eigenvalues of
+ * the symmetric part of the leading steps_done x steps_done block (H is Hermitian, so in
+ * exact arithmetic that block is the Lanczos tridiagonal matrix), NaN past steps_done.
+ * v0: device double[dim] or NULL for the seeded uniform start vector (start_vector kind
+ * 0).  Errors: HM_EINVAL (bad argument, zero start vector, spin-flip basis),
+ * HM_EWORKSPACE, HM_ECUDA.  Synchronises the stream once at the end. */
+int arnoldi_workspace(const hm_basis *basis, int steps, size_t *bytes);
+int arnoldi_run(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
+                const double *J, const void *v0, uint64_t seed, int steps, void *work,
+                size_t work_bytes, double *hess, int *steps_done, double *ritz, int n_ritz,
+                void *stream);
+
+/* Projection (shifted power) method: psi_0 = v0/|v0|;  for k = 0..steps-1:
+ *   y = H psi_k;  E_k = psi_k . y;  psi_{k+1} = (sigma psi_k - y) / |sigma psi_k - y|,
+ * with |sigma psi_k - y|^2 = sigma^2 - 2 sigma E_k + y . y.  For sigma >= the largest
+ * eigenvalue, psi_k tends to the ground state (largest eigenvalue of sigma - H) and E_k
+ * decreases to E0.  sigma = 0 selects sum_b |J_b| s (s + 1), a bound on |E| of H.
+ * energies: host double[steps] (E_0 .. E_{steps-1}); psi_out: device double[dim] or NULL,
+ * receives psi_steps.  Errors as arnoldi_run.  Synchronises the stream once. */
+int projection_workspace(const hm_basis *basis, int steps, size_t *bytes);
+int projection_run(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
+                   const double *J, const void *v0, uint64_t seed, int steps, double sigma,
+                   void *work, size_t work_bytes, double *energies, double *psi_out,
+                   void *stream);
+
+/* Eigenvalues (ascending, host ev[n]) of the symmetric n x n host matrix a (row major; only
+ * its symmetric part is used; not modified) by cyclic Jacobi rotations: the small dense
+ * eigensolver arnoldi_run applies to its Hessenberg matrix.  No GPU involved.  HM_EINVAL
+ * for NULL or n outside 1..4096. */
+int sym_eigenvalues(int n, const double *a, double *ev);
+
 /* ---- finite-temperature Lanczos over all sectors ---------------------------------------- */
 /* Jaklic-Prelovsek estimator (cited by the paper, Sec. 1, as an application of the Lanczos
  * machinery) for s = 1/2 (two_s = 1), 10 <= n_sites <= 32, at most 4 distinct couplings and

@@ -16,8 +16,9 @@ Two layers:
   Lanczos recurrence and a Sturm bisection for the tridiagonal matrix.
 * this module: ctypes bindings plus pure-Python/numpy brute force for tiny systems
   (stored sorted basis and binary search, Sec. 3.1 / Sec. 1; dense H built from
-  Kronecker products of spin matrices), the ground-state gradient and the
-  finite-temperature Lanczos estimator.  Library primitives used as single steps:
+  Kronecker products of spin matrices), the ground-state gradient, the
+  finite-temperature Lanczos estimator, and the Arnoldi and projection iterations the
+  paper's summary ports the product to.  Library primitives used as single steps:
   ``numpy.linalg.eigh``/``eigvalsh`` and ``scipy.linalg.eigh_tridiagonal``.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` against
@@ -378,6 +379,67 @@ def e0_grad(basis: Basis, bonds: Bonds, v0: np.ndarray, steps: int):
     """dE0/dJ_b = -<psi0| s_u.s_v |psi0> (Hellmann-Feynman on Eq. E-2-1)."""
     e0, psi, _ = ground_state(basis, bonds, v0, steps)
     return e0, -basis.bond_corr(bonds, psi, psi)
+
+
+# ----------------------------------------------------------------------------------------
+# Arnoldi and projection methods on the same product.  The paper's closing summary names
+# them as methods its product ports to but gives no steps; these are the textbook
+# iterations (Arnoldi 1951 with classical Gram-Schmidt applied twice; the power method on
+# sigma - H), written plainly on Basis.matvec.
+# ----------------------------------------------------------------------------------------
+
+ARNOLDI_TOL = 1e-12
+
+
+def arnoldi(basis: Basis, bonds: Bonds, v0: np.ndarray, steps: int, tol: float = ARNOLDI_TOL):
+    """Arnoldi with full re-orthogonalisation: v_1 = v0/|v0|; per step w = H v_j, then
+    twice h = V^T w, w -= V h, H[:j, j] += h; H[j+1, j] = |w|; stop when |w| <= tol times
+    the largest |H| entry so far.  Returns (H of shape [m+1, m], m)."""
+    V = [np.asarray(v0, dtype=np.float64) / np.linalg.norm(v0)]
+    H = np.zeros((steps + 1, steps))
+    scale = 0.0
+    m = 0
+    for j in range(steps):
+        w = basis.matvec(bonds, V[j])
+        for _ in range(2):
+            h = np.array([np.dot(V[i], w) for i in range(j + 1)])
+            for i in range(j + 1):
+                w = w - h[i] * V[i]
+            H[: j + 1, j] += h
+        beta = np.linalg.norm(w)
+        scale = max(scale, np.abs(H[: j + 1, j]).max())
+        H[j + 1, j] = beta
+        m = j + 1
+        if beta <= tol * scale:
+            break
+        scale = max(scale, beta)
+        V.append(w / beta)
+    return H[: m + 1, :m], m
+
+
+def arnoldi_ritz(H: np.ndarray, m: int, k: int) -> np.ndarray:
+    """k lowest eigenvalues of the symmetric part of H[:m, :m] (library eigensolver)."""
+    A = H[:m, :m]
+    return np.linalg.eigvalsh(0.5 * (A + A.T))[:k]
+
+
+def projection(basis: Basis, bonds: Bonds, v0: np.ndarray, steps: int, sigma: float) -> np.ndarray:
+    """Shifted power method: psi_0 = v0/|v0|; E_k = psi_k . H psi_k;
+    psi_{k+1} = (sigma psi_k - H psi_k) / |sigma psi_k - H psi_k|.  Returns E_0..E_{steps-1}."""
+    psi = np.asarray(v0, dtype=np.float64) / np.linalg.norm(v0)
+    E = np.zeros(steps)
+    for k in range(steps):
+        y = basis.matvec(bonds, psi)
+        E[k] = np.dot(psi, y)
+        nxt = sigma * psi - y
+        psi = nxt / np.linalg.norm(nxt)
+    return E
+
+
+def projection_default_sigma(two_s: int, J: Sequence[float]) -> float:
+    """sum_b |J_b| s (s + 1): |s_u.s_v| <= s (s + 1), so this bounds the spectrum of H."""
+    s = two_s / 2.0
+    return float(sum(abs(j) for j in J) * s * (s + 1.0))
 
 
 def ftlm_sector(basis: Basis, bonds: Bonds, seed: int, R: int, steps: int):

@@ -22,6 +22,7 @@ EXPORTS = [
     "lanczos_kernel_name", "matvec_kernel_name",
     "lanczos_run", "sector_ground_energies_workspace", "sector_ground_energies", "e0_grad_workspace", "e0_grad",
     "ftlm_workspace", "ftlm_run",
+    "arnoldi_workspace", "arnoldi_run", "projection_workspace", "projection_run", "sym_eigenvalues",
 ]
 
 _lib = None
@@ -82,6 +83,11 @@ def load() -> ctypes.CDLL:
         "ftlm_workspace": (i32, [i32, i32, i32, vp, vp, vp, i32, i32, i32, szp]),
         "ftlm_run": (i32, [i32, i32, i32, vp, vp, vp, i32, i32, u64, vp, i32, vp, vp, dp, vp, vp,
                            vp, i32, vp, sz, vp]),
+        "arnoldi_workspace": (i32, [vp, i32, szp]),
+        "arnoldi_run": (i32, [vp, i32, vp, vp, vp, vp, u64, i32, vp, sz, dp, ip, dp, i32, vp]),
+        "projection_workspace": (i32, [vp, i32, szp]),
+        "projection_run": (i32, [vp, i32, vp, vp, vp, vp, u64, i32, ctypes.c_double, vp, sz, dp, vp, vp]),
+        "sym_eigenvalues": (i32, [i32, dp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -347,3 +347,66 @@ def ftlm_run(n_sites: int, bonds: BondList, R: int, steps: int, seed: int, temps
                           _vp(work), work.numel(), _stream()))
     return FTLMResult(Z[:n_t], E[:n_t], eref.value, theta.reshape(nsec, 32, steps),
                       tau.reshape(nsec, 32, steps), mlen.reshape(nsec, 32), rc)
+
+
+# ---- Arnoldi and projection methods on the same product -----------------------------------
+
+@dataclass
+class ArnoldiResult:
+    H: np.ndarray          # [steps_done + 1, steps_done] Hessenberg matrix
+    steps: int
+    ritz: np.ndarray       # lowest eigenvalues of the symmetric part of H[:steps, :steps]
+    rc: int
+
+
+def arnoldi_run(basis: Basis, bonds: BondList, steps: int, v0: torch.Tensor | None = None,
+                seed: int = 0, n_ritz: int = 5, device="cuda") -> ArnoldiResult:
+    """Arnoldi with full re-orthogonalisation (arnoldi_run), FP64 vectors."""
+    L = _capi.load()
+    n = ctypes.c_size_t()
+    check(L.arnoldi_workspace(basis.handle, steps, ctypes.byref(n)))
+    work = _workspace(n.value, device)
+    hess = np.zeros((steps, steps + 1))          # column major: row j = column j of H
+    rz = np.zeros(max(n_ritz, 1))
+    done = ctypes.c_int()
+    if v0 is not None:
+        assert v0.dtype == torch.float64 and v0.shape == (basis.dim,)
+        v0 = v0.contiguous()
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rc = check(L.arnoldi_run(basis.handle, *bonds.args(), _vp(v0) if v0 is not None else None,
+                             seed & (2**64 - 1), steps, _vp(work), work.numel(), dp(hess),
+                             ctypes.byref(done), dp(rz), n_ritz, _stream()))
+    m = done.value
+    return ArnoldiResult(hess.T[: m + 1, :m].copy(), m, rz[:n_ritz], rc)
+
+
+def projection_run(basis: Basis, bonds: BondList, steps: int, sigma: float = 0.0,
+                   v0: torch.Tensor | None = None, seed: int = 0, want_psi: bool = False,
+                   device="cuda"):
+    """Shifted power (projection) method (projection_run): energies E_0..E_{steps-1} and,
+    if asked, the last iterate psi_steps (device)."""
+    L = _capi.load()
+    n = ctypes.c_size_t()
+    check(L.projection_workspace(basis.handle, steps, ctypes.byref(n)))
+    work = _workspace(n.value, device)
+    E = np.zeros(steps)
+    psi = torch.empty(basis.dim, dtype=torch.float64, device=device) if want_psi else None
+    if v0 is not None:
+        assert v0.dtype == torch.float64 and v0.shape == (basis.dim,)
+        v0 = v0.contiguous()
+    check(L.projection_run(basis.handle, *bonds.args(), _vp(v0) if v0 is not None else None,
+                           seed & (2**64 - 1), steps, float(sigma), _vp(work), work.numel(),
+                           E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           _vp(psi) if psi is not None else None, _stream()))
+    return (E, psi) if want_psi else E
+
+
+def sym_eigenvalues(a: np.ndarray) -> np.ndarray:
+    """Eigenvalues of the symmetric part of a small dense host matrix (the library's Jacobi
+    solver that arnoldi_run applies to its Hessenberg matrix; no GPU involved)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    n = a.shape[0]
+    ev = np.zeros(n)
+    check(_capi.load().sym_eigenvalues(n, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return ev

@@ -70,3 +70,19 @@ def test_last_error_is_per_call(lib):
     d = ctypes.c_int64()
     assert lib.basis_dim_query(16, 1, 3, ctypes.byref(d)) == _capi.HM_EPARITY
     assert b"magnetic" in lib.hm_last_error()
+
+
+def test_sym_eigenvalues_host_solver():
+    """The library's host Jacobi eigensolver (used by arnoldi_run on its Hessenberg
+    matrix) against numpy's eigvalsh on symmetric parts of random and tridiagonal
+    matrices; NULL and bad sizes are rejected.  No GPU involved."""
+    from paper_0706_3293_gb300 import api, _capi
+    rng = np.random.default_rng(4)
+    for n in (1, 2, 5, 33, 90):
+        a = rng.standard_normal((n, n))
+        ref = np.linalg.eigvalsh(0.5 * (a + a.T))
+        np.testing.assert_allclose(api.sym_eigenvalues(a), ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))
+    t = np.diag(rng.standard_normal(40)) + np.diag(np.full(39, 0.5), 1) + np.diag(np.full(39, 0.5), -1)
+    np.testing.assert_allclose(api.sym_eigenvalues(t), np.linalg.eigvalsh(t), rtol=0, atol=1e-13)
+    L = _capi.load()
+    assert L.sym_eigenvalues(0, None, None) == _capi.HM_EINVAL

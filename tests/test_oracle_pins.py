@@ -535,3 +535,73 @@ def test_flip_majumdar_ghosh_parity(orc):
     em = np.linalg.eigvalsh(_flip_dense(b, bonds, -1))
     assert abs(ep[0] + 3.0) < 1e-12
     assert em[0] > -3.0 + 1e-6
+
+
+# ---- Arnoldi and projection iterations (the summary's other Krylov-type methods) ----------
+
+def _kron_spectrum(N, S2, A, bonds):
+    """Spectrum of the sector block of the Kronecker-product Hamiltonian (no codec)."""
+    return np.linalg.eigvalsh(oracle.dense_hamiltonian_sector(N, S2, A, bonds))
+
+
+@pytest.mark.parametrize("N,S2,A,seed", [(8, 1, 4, 1), (7, 1, 3, 2), (5, 2, 5, 3)])
+def test_arnoldi_ritz_values_in_the_spectrum(orc, N, S2, A, seed):
+    """Run to exhaustion of the Krylov space: every Ritz value is an eigenvalue of the
+    Kronecker-product sector Hamiltonian (1e-10), the lowest one is E0, and H is
+    tridiagonal (Hermitian H: entries above the superdiagonal vanish to rounding)."""
+    rng = np.random.default_rng(seed)
+    u, v = np.triu_indices(N, 1)
+    keep = rng.random(len(u)) < 0.6
+    bonds = Bonds(u[keep].astype(np.int32), v[keep].astype(np.int32), rng.uniform(-1.3, 0.4, keep.sum()))
+    b = Basis(N, S2, A)
+    H, m = oracle.arnoldi(b, bonds, oracle.start_uniform(seed, b.dim), b.dim + 5)
+    assert m <= b.dim
+    ev = _kron_spectrum(N, S2, A, bonds)
+    ritz = oracle.arnoldi_ritz(H, m, m)
+    for t in ritz:
+        assert np.abs(ev - t).min() < 1e-10 * max(1.0, abs(ev).max())
+    assert abs(ritz[0] - ev[0]) < 1e-10 * max(1.0, abs(ev[0]))
+    scale = np.abs(H).max()
+    assert np.abs(np.triu(H[:m, :m], 2)).max() < 1e-12 * scale
+
+
+def test_arnoldi_equals_lanczos_early(orc):
+    """Before rounding separates them, Arnoldi's diagonal and subdiagonal are the
+    Lanczos alpha_j and beta_j of the C oracle's three-term recurrence (same start)."""
+    inst = W.small_ring(12, -1.0, -0.4)
+    bonds = bonds_of(inst)
+    b = Basis(12, 1, 6)
+    v0 = oracle.start_uniform(5, b.dim)
+    H, m = oracle.arnoldi(b, bonds, v0, 15)
+    al, be = b.lanczos(bonds, v0, 15)
+    assert m == 15
+    np.testing.assert_allclose(np.diag(H[:m, :m]), al, rtol=0, atol=1e-12 * np.abs(al).max())
+    np.testing.assert_allclose(np.diag(H, -1), be, rtol=0, atol=1e-12 * np.abs(al).max())
+
+
+def test_arnoldi_four_site_ring(orc):
+    """Four-site s = 1/2 antiferromagnetic ring (J = -1): E0 = -2 |J| (closed form)."""
+    inst = W.small_ring(4, -1.0)
+    b = Basis(4, 1, 2)
+    H, m = oracle.arnoldi(b, bonds_of(inst), oracle.start_uniform(1, b.dim), 10)
+    assert abs(oracle.arnoldi_ritz(H, m, 1)[0] - (-2.0)) < 1e-13
+
+
+def test_projection_monotone_and_converges(orc):
+    """Power method on sigma - H with sigma >= E_max: the energies E_k never increase
+    (sigma - H is positive semi-definite) and tend to E0 of the Kronecker-product
+    Hamiltonian; for the four-site ring to -2 |J|."""
+    inst = W.small_ring(8, -1.0, -0.3)
+    bonds = bonds_of(inst)
+    b = Basis(8, 1, 4)
+    sigma = oracle.projection_default_sigma(1, inst.J)
+    ev = _kron_spectrum(8, 1, 4, bonds)
+    assert sigma >= ev[-1]
+    E = oracle.projection(b, bonds, oracle.start_uniform(2, b.dim), 3000, sigma)
+    assert np.all(np.diff(E) <= 1e-12)
+    assert abs(E[-1] - ev[0]) < 1e-8 * abs(ev[0])
+    r4 = W.small_ring(4, -1.0)
+    b4 = Basis(4, 1, 2)
+    E4 = oracle.projection(b4, bonds_of(r4), oracle.start_uniform(1, b4.dim), 400,
+                           oracle.projection_default_sigma(1, r4.J))
+    assert abs(E4[-1] - (-2.0)) < 1e-12
