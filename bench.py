@@ -51,6 +51,9 @@ WORKLOADS = {
     "ring24_grad": 70425628,
     # s = 1 random 4-regular graph, N = 20 (FP32 vectors by default); nnz from count_nnz
     "s1_rrg20": None,
+    # Arnoldi with full re-orthogonalisation on the N = 24 J1-J2 ring: one step = one whole
+    # 60-step run; Gnnz/s counts its products (48 bonds, M = 0)
+    "arnoldi_ring24": 2704156 + 2 * 48 * 705432,
 }
 DEFAULT_DTYPE = {"s1_rrg20": "f32"}
 PARITY = {"j1j2_ring32_flip": 1}     # spin-flip block (basis_build_flip) of the workload's sector
@@ -63,7 +66,7 @@ def instance(name):
     from paper_0706_3293_gb300 import workloads as W
     return {"j1j2_ring32": W.j1j2_ring32, "j1j2_ring32_flip": W.j1j2_ring32, "j1j2_ring28": lambda: W.j1j2_ring(28),
             "ring24_randJ": W.ring24_random_j, "ring24_grad": W.ring24_random_j, "ring16": W.ring16,
-            "ftlm_ring24": W.ftlm_ring24,
+            "ftlm_ring24": W.ftlm_ring24, "arnoldi_ring24": W.arnoldi_ring24,
             "s1_rrg20": W.s1_random_graph}[name]()
 
 
@@ -230,6 +233,27 @@ def run_reference(args):
     import numpy as np
     import oracle
     inst = instance(args.workload)
+    if args.workload == "arnoldi_ring24":
+        # one step = the oracle's Arnoldi on the first 6 steps of the run (bounded sample)
+        nnz = WORKLOADS[args.workload]
+        for _ in range(args.warmup):
+            arnoldi_oracle_rate(inst, nnz, 2)
+        vals, tsum = [], 0.0
+        for _ in range(args.steps):
+            cb, dt = arnoldi_oracle_rate(inst, nnz, 6)
+            vals.append(cb["value"])
+            tsum += dt
+        val = float(np.mean(vals))
+        cb["value"] = val
+        out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": tsum / args.steps * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": {"workload": inst.name, "n_sites": inst.n_sites,
+                                              "step": "the first 6 Arnoldi steps"},
+               "cpu_baseline": cb,
+               "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return 0
     if args.workload == "ring24_grad":
         nnz = WORKLOADS[args.workload]
         for _ in range(args.warmup):
@@ -491,7 +515,116 @@ def run_ftlm(args):
     return 0
 
 
+def arnoldi_algo_bytes(dim: int, m: int) -> float:
+    """Minimum bytes of an m-step Arnoldi run with classical Gram-Schmidt applied twice:
+    per step the product (read v_j, write w: 16 B a row), per pass the dots (read the j
+    basis vectors and w) and the update (read them again, read and write w), then |w| (read
+    w) and v_{j+1} = w / |w| (read w, write v)."""
+    tot = 0
+    for j in range(1, m + 1):
+        tot += 16 + 2 * 8 * (2 * j + 3) + 8 + 16
+    return float(tot) * dim
+
+
+def arnoldi_oracle_rate(inst, nnz, steps):
+    """The oracle's Arnoldi (C products, numpy Gram-Schmidt) on the first `steps` steps of
+    the same run, all host cores: products' nnz per second."""
+    import oracle
+    ob = oracle.Basis(inst.n_sites, inst.two_s, inst.A)
+    bonds = oracle.Bonds(inst.u, inst.v, inst.J)
+    v0 = oracle.start_uniform(inst.seed, ob.dim)
+    t0 = time.perf_counter()
+    _, m = oracle.arnoldi(ob, bonds, v0, steps)
+    dt = time.perf_counter() - t0
+    return {"value": nnz * m / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"the first {m} of the {inst.steps} Arnoldi steps ({dt:.1f} s)"}, dt
+
+
+def run_arnoldi(args):
+    """One step = one whole Arnoldi run (60 steps, full re-orthogonalisation) through the C
+    ABI (arnoldi_run): products and Gram-Schmidt kernels, Ritz values on the host."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0706_3293_gb300 import api
+    inst = instance(args.workload)
+    b = api.Basis(inst.n_sites, inst.two_s, inst.two_m)
+    bl = api.bonds_of(inst)
+    nnz = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        res = api.arnoldi_run(b, bl, inst.steps, seed=inst.seed, n_ritz=3)
+    m = res.steps
+    st = torch.cuda.current_stream()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        res = api.arnoldi_run(b, bl, inst.steps, seed=inst.seed, n_ritz=3)
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
+    # end to end: the start vector from pinned host memory, H and the Ritz values back
+    x_host = torch.empty(b.dim, dtype=torch.float64, pin_memory=True)
+    x_host.copy_(api.start_vector(b, inst.seed, dtype=torch.float64).cpu())
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        v0 = x_host.to("cuda", non_blocking=True)
+        res2 = api.arnoldi_run(b, bl, inst.steps, v0=v0, n_ritz=3)
+    e1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
+    if ws > 1 and rank != 0:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+        return 0
+    value = nnz * m * args.steps * ws / (ms * 1e-3) / 1e9
+    peak, peak_src = read_peaks()
+    algo = arnoldi_algo_bytes(b.dim, m)
+    achieved = algo / (ms / args.steps * 1e-3) / 1e9
+    # launches per run: start (seeded vector, norm, start, scale), per step the product
+    # (exponent pre-pass + block kernel), 2 x (dots, their sums, update), norm, beta, scale
+    launches = 4 + m * (2 + 2 * 3 + 3)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": inst.name, "n_sites": inst.n_sites, "dim": b.dim, "arnoldi_steps": m,
+                      "nnz_per_product": nnz, "step": "one whole Arnoldi run",
+                      "l2": "inputs larger than L2 (%d basis vectors of %.1f MB)" % (m + 1, b.dim * 8 / 1e6)},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "arnoldi_run (all kernels of the run)", "peak_source": peak_src,
+                        "algorithmic_bytes_per_launch": algo},
+           "e2e": {"value": nnz * m * args.steps * ws / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+                   "h2d_bytes_per_step": 8 * b.dim, "d2h_bytes_per_step": 8 * (inst.steps + 1) * inst.steps + 24},
+           "gpu_launches": launches * args.steps, "clocks": clocks,
+           "ritz": list(map(float, res.ritz))}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"], _ = arnoldi_oracle_rate(inst, nnz, 6)
+    print(json.dumps(out))
+    return 0
+
+
 def run_ours(args):
+    if args.workload == "arnoldi_ring24":
+        return run_arnoldi(args)
     if args.workload == "ring24_grad":
         return run_grad(args)
     if args.workload == "ftlm_ring24":

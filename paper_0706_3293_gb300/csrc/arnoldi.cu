@@ -7,10 +7,15 @@
 // FP64 vectors, one vector per product, every step enqueued on the caller's stream with
 // no host round trip: the scalars (h, beta, energies, the stop flag) stay on the device.
 // Reductions run over a fixed grid in a fixed order, so every run is reproducible.
+// The Arnoldi basis is kept as double-float pairs (47 significant bits, relative error
+// below 2^-46) and the Gram-Schmidt dots and updates run in double-float arithmetic on
+// the FP32 pipe: binary64 multiply-adds run at a small fraction of that rate on this GPU
+// and bounded the first version (2.2 TB/s for the dots).
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "ef64.cuh"
 #include "hm_internal.cuh"
 
 namespace hm {
@@ -22,7 +27,7 @@ int start_vector_dev(uint64_t n, uint64_t seed, int kind, void *x, int dtype, cu
 namespace {
 
 constexpr int AR_NT = 256;
-constexpr int AR_CH = 8;             // vectors per pass of k_mdot
+constexpr int AR_RB = 4096;          // rows of a tile of k_mdot
 constexpr int AR_MAXM = 1024;        // Arnoldi steps at most
 constexpr double AR_TOL = 1e-12;     // breakdown: beta_j <= tol * max |H entries|
 
@@ -36,58 +41,80 @@ struct ArState {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// part[blk][c] = sum over the block's rows of V_{i0+c}[r] w[r] (c < nc <= AR_CH)
-__global__ void __launch_bounds__(AR_NT) k_mdot(const double *__restrict__ V, size_t ldv, int i0, int nc,
+__device__ __forceinline__ ef::df ar_df(double v) { return ef::df_from_bits(ef::d2u(v), 0); }
+__device__ __forceinline__ double ar_dbl(ef::df v) { return ef::u2d(ef::bits_from_df(v, 0)); }
+
+// part[tile][i] = sum over the AR_RB rows of a tile of V_i[r] w[r] for every i < nv (ps:
+// stride of a tile's partials).  The CTA stages its tile of w (as double-float pairs) in
+// shared memory; warp k then streams the tile's slices of V_k, V_{k+8}, ... and reduces
+// each by a fixed shuffle tree, so every vector slice and w are read once.
+__global__ void __launch_bounds__(AR_NT) k_mdot(const float2 *__restrict__ V, size_t ldv, int nv,
                                                  const double *__restrict__ w, uint64_t n, double *__restrict__ part,
-                                                 const ArState *__restrict__ st) {
+                                                 int ps, const ArState *__restrict__ st) {
     if (st->done) return;
-    __shared__ double red[AR_NT / 32];
-    double acc[AR_CH];
-#pragma unroll
-    for (int c = 0; c < AR_CH; ++c) acc[c] = 0.0;
-    for (uint64_t r = (uint64_t)blockIdx.x * AR_NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * AR_NT) {
-        const double wr = w[r];
-#pragma unroll
-        for (int c = 0; c < AR_CH; ++c)
-            if (c < nc) acc[c] = fma(V[(size_t)(i0 + c) * ldv + r], wr, acc[c]);
+    __shared__ float2 ws[AR_RB];
+    const uint64_t r0 = (uint64_t)blockIdx.x * AR_RB;
+    const int rows = (int)min((uint64_t)AR_RB, n - r0);
+    for (int t = threadIdx.x; t < rows; t += AR_NT) {
+        const ef::df d = ar_df(w[r0 + t]);
+        ws[t] = make_float2(d.hi, d.lo);
     }
-    for (int c = 0; c < nc; ++c) {
-        const double t = block_sum<AR_NT>(acc[c], red);
-        if (threadIdx.x == 0) part[(size_t)blockIdx.x * AR_CH + c] = t;
-        __syncthreads();
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < nv; i += AR_NT / 32) {
+        const float2 *vi = V + (size_t)i * ldv + r0;
+        ef::df a0{0.0f, 0.0f}, a1{0.0f, 0.0f};
+        int t = lane;
+        for (; t + 32 < rows; t += 64) {                  // two independent chains
+            const float2 v = vi[t], x = ws[t], v2 = vi[t + 32], x2 = ws[t + 32];
+            a0 = ef::df_add(a0, ef::df_mul(ef::df{v.x, v.y}, ef::df{x.x, x.y}));
+            a1 = ef::df_add(a1, ef::df_mul(ef::df{v2.x, v2.y}, ef::df{x2.x, x2.y}));
+        }
+        if (t < rows) {
+            const float2 v = vi[t], x = ws[t];
+            a0 = ef::df_add(a0, ef::df_mul(ef::df{v.x, v.y}, ef::df{x.x, x.y}));
+        }
+        double s = ((double)a0.hi + (double)a0.lo) + ((double)a1.hi + (double)a1.lo);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) part[(size_t)blockIdx.x * ps + i] = s;
     }
 }
 
-// h[i0+c] = sum over blocks of part[blk][c] (fixed order); hcol[i0+c] += h[i0+c]
-__global__ void __launch_bounds__(AR_NT) k_mdot_fin(const double *__restrict__ part, int nb, int i0, int nc,
+// h[i] = sum over blocks of part[blk][i] (fixed order), hcol[i] += h[i]: CTA i sums the
+// partials of vector i
+__global__ void __launch_bounds__(AR_NT) k_mdot_fin(const double *__restrict__ part, int nb, int ps,
                                                      double *__restrict__ h, double *__restrict__ hcol,
                                                      const ArState *__restrict__ st) {
     if (st->done) return;
     __shared__ double red[AR_NT / 32];
-    for (int c = 0; c < nc; ++c) {
-        double s = 0.0;
-        for (int b = threadIdx.x; b < nb; b += AR_NT) s += part[(size_t)b * AR_CH + c];
-        s = block_sum<AR_NT>(s, red);
-        if (threadIdx.x == 0) {
-            h[i0 + c] = s;
-            hcol[i0 + c] += s;
-        }
-        __syncthreads();
+    const int i = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += AR_NT) s += part[(size_t)b * ps + i];
+    s = block_sum<AR_NT>(s, red);
+    if (threadIdx.x == 0) {
+        h[i] = s;
+        hcol[i] += s;
     }
 }
 
-// w[r] -= sum_{i < nv} h[i] V_i[r]
-__global__ void __launch_bounds__(AR_NT) k_gs_sub(const double *__restrict__ V, size_t ldv, int nv,
+// w[r] -= sum_{i < nv} h[i] V_i[r]  (double-float sum, w rounded back to binary64)
+__global__ void __launch_bounds__(AR_NT) k_gs_sub(const float2 *__restrict__ V, size_t ldv, int nv,
                                                    const double *__restrict__ h, double *__restrict__ w, uint64_t n,
                                                    const ArState *__restrict__ st) {
     if (st->done) return;
-    __shared__ double hs[AR_MAXM + 1];
-    for (int i = threadIdx.x; i < nv; i += AR_NT) hs[i] = h[i];
+    __shared__ float2 hs[AR_MAXM + 1];
+    for (int i = threadIdx.x; i < nv; i += AR_NT) {
+        const ef::df t = ar_df(-h[i]);
+        hs[i] = make_float2(t.hi, t.lo);
+    }
     __syncthreads();
     for (uint64_t r = (uint64_t)blockIdx.x * AR_NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * AR_NT) {
-        double s = w[r];
-        for (int i = 0; i < nv; ++i) s = fma(-hs[i], V[(size_t)i * ldv + r], s);
-        w[r] = s;
+        ef::df s = ar_df(w[r]);
+        for (int i = 0; i < nv; ++i) {
+            const float2 v = V[(size_t)i * ldv + r], c = hs[i];
+            s = ef::df_add(s, ef::df_mul(ef::df{c.x, c.y}, ef::df{v.x, v.y}));
+        }
+        w[r] = ar_dbl(s);
     }
 }
 
@@ -149,13 +176,19 @@ __global__ void __launch_bounds__(AR_NT) k_ar_beta(const double *__restrict__ pa
     }
 }
 
-// y[r] = x[r] / beta (next Krylov vector)
-__global__ void __launch_bounds__(AR_NT) k_ar_scale(const double *__restrict__ x, double *__restrict__ y, uint64_t n,
+// next Krylov vector x / beta: into the basis (double-float) and, as binary64, into q,
+// the input of the next product
+__global__ void __launch_bounds__(AR_NT) k_ar_scale(const double *__restrict__ x, float2 *__restrict__ vout,
+                                                     double *__restrict__ q, uint64_t n,
                                                      const ArState *__restrict__ st) {
     if (st->done) return;
-    const double inv = 1.0 / st->beta;
-    for (uint64_t r = (uint64_t)blockIdx.x * AR_NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * AR_NT)
-        y[r] = x[r] * inv;
+    const double inv = 1.0 / st->beta;       // the scaled entries lie in double-float range
+    for (uint64_t r = (uint64_t)blockIdx.x * AR_NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * AR_NT) {
+        const double t = x[r] * inv;
+        const ef::df d = ar_df(t);
+        vout[r] = make_float2(d.hi, d.lo);
+        q[r] = t;
+    }
 }
 
 // Eigenvalues of a symmetric n x n matrix (row major, overwritten) by cyclic Jacobi
@@ -240,19 +273,23 @@ __global__ void __launch_bounds__(AR_NT) k_pr_scale(const double *__restrict__ v
 }
 
 struct ArLayout {
-    size_t V, w, part, part2, h, H, st, total;
-    size_t ldv;                      // doubles between consecutive Krylov vectors
-    int nb;
+    size_t V, q, w, part, part2, h, H, st, total;
+    size_t ldv;                      // elements between consecutive Krylov vectors
+    int nb, ps;                      // blocks of the reductions, partials per block
+    int nt;                          // row tiles of k_mdot
 };
 
 ArLayout ar_layout(uint64_t dim, int steps) {
     ArLayout L{};
     L.nb = grid_blocks(dim, AR_NT);
     L.ldv = al256(dim * 8) / 8;
+    L.ps = steps + 1;
     size_t o = 0;
     L.V = o; o += (size_t)(steps + 1) * L.ldv * 8;
+    L.q = o; o += al256(dim * 8);
     L.w = o; o += al256(dim * 8);
-    L.part = o; o += al256((size_t)L.nb * AR_CH * 8);
+    L.nt = (int)((dim + AR_RB - 1) / AR_RB);
+    L.part = o; o += al256((size_t)std::max(L.nb, L.nt) * L.ps * 8);
     L.part2 = o; o += al256((size_t)L.nb * 8);
     L.h = o; o += al256((size_t)(steps + 1) * 8);
     L.H = o; o += al256((size_t)(steps + 1) * steps * 8);
@@ -290,7 +327,8 @@ int arnoldi_run(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t 
         return fail(HM_EWORKSPACE, "workspace must be >= %zu bytes, 256-byte aligned", L.total);
     cudaStream_t st = as_stream(stream);
     unsigned char *W = (unsigned char *)work;
-    double *V = (double *)(W + L.V), *w = (double *)(W + L.w), *part = (double *)(W + L.part);
+    float2 *V = (float2 *)(W + L.V);
+    double *q = (double *)(W + L.q), *w = (double *)(W + L.w), *part = (double *)(W + L.part);
     double *h = (double *)(W + L.h), *H = (double *)(W + L.H);
     ArState *S = (ArState *)(W + L.st);
     const int nb = L.nb;
@@ -301,24 +339,22 @@ int arnoldi_run(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t 
     else HM_TRY(start_vector_dev(dim, seed, 0, w, HM_F64, st));
     k_dot2<<<nb, AR_NT, 0, st>>>(w, w, dim, part, nullptr, S);
     k_ar_start<<<1, AR_NT, 0, st>>>(part, nb, S);
-    k_ar_scale<<<nb, AR_NT, 0, st>>>(w, V, dim, S);
+    k_ar_scale<<<nb, AR_NT, 0, st>>>(w, V, q, dim, S);
     HM_CUDA(cudaGetLastError());
     for (int j = 0; j < steps; ++j) {
-        double *vj = V + (size_t)j * L.ldv, *hcol = H + (size_t)j * (steps + 1);
-        // w = H v_j (a stopped run still launches the product; its result is not used)
-        HM_TRY(matvec_dev(b, bp, vj, w, HM_F64, 1, st));
+        double *hcol = H + (size_t)j * (steps + 1);
+        // w = H v_j from its binary64 copy q (a stopped run still launches the product;
+        // its result is not used)
+        HM_TRY(matvec_dev(b, bp, q, w, HM_F64, 1, st));
         // classical Gram-Schmidt, twice: h = V^T w, w -= V h, H[:, j] += h
         for (int pass = 0; pass < 2; ++pass) {
-            for (int i0 = 0; i0 <= j; i0 += AR_CH) {
-                const int nc = std::min(AR_CH, j + 1 - i0);
-                k_mdot<<<nb, AR_NT, 0, st>>>(V, L.ldv, i0, nc, w, dim, part, S);
-                k_mdot_fin<<<1, AR_NT, 0, st>>>(part, nb, i0, nc, h, hcol, S);
-            }
+            k_mdot<<<L.nt, AR_NT, 0, st>>>(V, L.ldv, j + 1, w, dim, part, L.ps, S);
+            k_mdot_fin<<<j + 1, AR_NT, 0, st>>>(part, L.nt, L.ps, h, hcol, S);
             k_gs_sub<<<nb, AR_NT, 0, st>>>(V, L.ldv, j + 1, h, w, dim, S);
         }
         k_dot2<<<nb, AR_NT, 0, st>>>(w, w, dim, part, nullptr, S);
         k_ar_beta<<<1, AR_NT, 0, st>>>(part, nb, hcol, j, S);
-        k_ar_scale<<<nb, AR_NT, 0, st>>>(w, V + (size_t)(j + 1) * L.ldv, dim, S);
+        k_ar_scale<<<nb, AR_NT, 0, st>>>(w, V + (size_t)(j + 1) * L.ldv, q, dim, S);
         HM_CUDA(cudaGetLastError());
     }
     ArState hs{};

@@ -130,6 +130,12 @@ def ftlm_ring24() -> Instance:
                     meta={"R": 32})
 
 
+def arnoldi_ring24() -> Instance:
+    """s = 1/2 J1-J2 ring N = 24 (J1 = -1, J2 = -0.3), M = 0, 60 Arnoldi steps, seed 1006."""
+    u, v, J = ring_bonds(24, -1.0, -0.3)
+    return Instance("arnoldi_ring24_j1j2", 24, 1, 0, u, v, J, steps=60, seed=1006)
+
+
 def small_ring(n_sites: int, j1: float = -1.0, j2: float | None = None, two_s: int = 1,
                two_m: int | None = None) -> Instance:
     """A small ring for tests (M = lowest |M| unless given)."""
