@@ -188,15 +188,18 @@ int lanczos_free(hm_lanczos *run);
  * name[0..cap): "k_blk_lz64_jit" / "k_blk_lz32_jit" (s = 1/2 block product compiled for
  * this bond list at run time with NVRTC), "k_blk_lz64" / "k_blk_lz32" (the same block
  * product reading its bonds from the parameters; used when NVRTC is unavailable or the
- * environment sets HM_JIT=0) or "k_lz_matvec" (row kernel of Eq. E-4-b for any s).  No
- * counterpart in the paper: it reports an implementation choice.  HM_EINVAL on NULL. */
+ * environment sets HM_JIT=0), "k_s1_lz64_jit" / "k_s1_lz32_jit" (s = 1 block product
+ * compiled for the bond list), "k_s1_lz32" (its generic FP32 form) or "k_lz_matvec" (row
+ * kernel of Eq. E-4-b for any s).  No counterpart in the paper: it reports an
+ * implementation choice.  HM_EINVAL on NULL. */
 int lanczos_kernel_name(const hm_lanczos *run, char *name, int cap);
 
-/* Name of the kernel `matvec` launches for these arguments (the same dispatch, nothing
- * launched): "k_blk_matvec" (s = 1/2 block kernel, up to 4 distinct couplings),
- * "k_blk_matvec_jit" (block kernel compiled at run time for a bond list with more distinct
- * couplings), "k_s1_mv" (s = 1 block kernel, FP32, one vector) or "k_matvec" (general row
- * kernel).  name: host buffer of cap bytes. */
+/* Name of the kernel `matvec` launches for these arguments (the same dispatch; nothing
+ * is launched, though a kernel specialised to the bonds may be compiled): "k_blk_matvec"
+ * (s = 1/2 block kernel, up to 4 distinct couplings), "k_blk_matvec_jit" (block kernel
+ * compiled at run time for a bond list with more distinct couplings), "k_s1_mv_jit" /
+ * "k_s1_mv" (s = 1 block kernel compiled for the bond list / generic; FP32, one vector) or
+ * "k_matvec" (general row kernel).  name: host buffer of cap bytes. */
 int matvec_kernel_name(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
                        const double *J, int dtype, int nvec, char *name, int cap);
 
