@@ -99,6 +99,19 @@ int basis_build(int n_sites, int two_s, int two_m, hm_basis **out);
  * the block, through the s = 1/2 block kernels only (a bond list they cannot take fails
  * with HM_EINVAL); count_nnz, bond_corr and e0_grad return HM_EINVAL.  parity: +1 or -1. */
 int basis_build_flip(int n_sites, int parity, hm_basis **out);
+/* Momentum basis of a ring (translation symmetry; the paper names symmetries as a further
+ * reduction of H(M) without constructing them): the sector (n_sites, two_s, two_m) split by
+ * the cyclic translation T: site u -> u + 1 mod N, keeping the block of momentum k = 0 or,
+ * for even N, k = N/2 (the real characters chi(n) = 1 and (-1)^n).  Basis states: one per
+ * orbit of T whose period p has chi(p) = 1, |r^> = p^(-1/2) sum_{m<p} chi(m) T^m |r>, r the
+ * orbit member with the smallest packed digit word, numbered in the order of the sector
+ * index of r; basis_dim gives their number.  matvec, lanczos_*, arnoldi_run and
+ * projection_run accept such a basis (one vector per product; the bonds must map onto
+ * themselves under T with equal couplings, else HM_EINVAL); the other calls reject it.
+ * Needs a sector of fewer than 2^32 states with N digits in 64 bits.  The device holds 8
+ * bytes per sector state (a table from sector index to orbit, shift and period) plus 4 per
+ * basis state.  HM_EINVAL for a bad k, or when no state has momentum k. */
+int basis_build_momentum(int n_sites, int two_s, int two_m, int k, hm_basis **out);
 int basis_free(hm_basis *basis);
 int basis_dim(const hm_basis *basis, int64_t *dim);
 

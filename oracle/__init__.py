@@ -17,8 +17,8 @@ Two layers:
 * this module: ctypes bindings plus pure-Python/numpy brute force for tiny systems
   (stored sorted basis and binary search, Sec. 3.1 / Sec. 1; dense H built from
   Kronecker products of spin matrices), the ground-state gradient, the
-  finite-temperature Lanczos estimator, and the Arnoldi and projection iterations the
-  paper's summary ports the product to.  Library primitives used as single steps:
+  finite-temperature Lanczos estimator, the Arnoldi and projection iterations the
+  paper's summary ports the product to, and the momentum blocks of a ring.  Library primitives used as single steps:
   ``numpy.linalg.eigh``/``eigvalsh`` and ``scipy.linalg.eigh_tridiagonal``.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` against
@@ -379,6 +379,51 @@ def e0_grad(basis: Basis, bonds: Bonds, v0: np.ndarray, steps: int):
     """dE0/dJ_b = -<psi0| s_u.s_v |psi0> (Hellmann-Feynman on Eq. E-2-1)."""
     e0, psi, _ = ground_state(basis, bonds, v0, steps)
     return e0, -basis.bond_corr(bonds, psi, psi)
+
+
+# ----------------------------------------------------------------------------------------
+# Translation symmetry of a ring: the momentum blocks k = 0 and k = pi of a sector.  The
+# paper names symmetries as a further reduction of H(M) without constructing them; this
+# is the textbook projection onto the real characters of the cyclic group of the ring.
+# ----------------------------------------------------------------------------------------
+
+def packed_word(digits: Sequence[int], two_s: int) -> int:
+    """The digits packed site by site, 1, 2 or 4 bits per digit (2s = 1, 2..3, 4..7), site u
+    at bits u*b .. u*b + b - 1: the order that picks an orbit's representative."""
+    b = 1 if two_s == 1 else (2 if two_s <= 3 else 4)
+    return sum(int(a) << (u * b) for u, a in enumerate(digits))
+
+
+def momentum_vectors(basis: Basis, k_pi: bool) -> np.ndarray:
+    """Columns = the momentum basis as sector vectors: for every orbit of the translation T
+    (the digit of site u moves to site u + 1 mod N) whose period p has chi(p) = 1 (any p for
+    k = 0, even p for k = pi), |r^> = p^(-1/2) sum_{m<p} chi(m) T^m |r>, chi(m) = 1 or
+    (-1)^m, r the orbit member with the smallest packed word; ordered by the sector index
+    of r."""
+    N = basis.N
+    cols = []
+    for i in range(basis.dim):
+        d = basis.decode(i)
+        orbit = [np.roll(d, m) for m in range(N)]
+        words = [packed_word(o, basis.S2) for o in orbit]
+        if words[0] != min(words):
+            continue                                   # i is not its orbit's representative
+        p = next(m for m in range(1, N + 1) if m == N or words[m] == words[0])
+        if k_pi and p % 2:
+            continue
+        v = np.zeros(basis.dim)
+        for m in range(p):
+            v[basis.encode(orbit[m])] += (-1.0) ** m if k_pi else 1.0
+        cols.append(v / math.sqrt(p))
+    return np.column_stack(cols) if cols else np.zeros((basis.dim, 0))
+
+
+def momentum_hamiltonian(basis: Basis, bonds: Bonds, k_pi: bool) -> np.ndarray:
+    """<r'^| H |r^> for the momentum basis of momentum_vectors (dense, small N): the sector
+    product applied to each basis vector, projected back."""
+    B = momentum_vectors(basis, k_pi)
+    HB = np.column_stack([basis.matvec(bonds, B[:, c]) for c in range(B.shape[1])])
+    return B.T @ HB
 
 
 # ----------------------------------------------------------------------------------------

@@ -15,7 +15,8 @@ HM_MAX_BONDS = 512
 
 # every function the header declares (checked by tests/test_abi.py)
 EXPORTS = [
-    "hm_last_error", "basis_dim_query", "bonds_check", "basis_build", "basis_build_flip", "basis_free", "basis_dim",
+    "hm_last_error", "basis_dim_query", "bonds_check", "basis_build", "basis_build_flip", "basis_build_momentum",
+    "basis_free", "basis_dim",
     "basis_encode", "basis_decode", "matvec", "count_nnz", "bond_corr_workspace", "bond_corr", "bond_corr_static",
     "start_vector",
     "lanczos_workspace", "lanczos_init", "lanczos_step", "lanczos_substep", "lanczos_read", "lanczos_free",
@@ -55,6 +56,7 @@ def load() -> ctypes.CDLL:
         "bonds_check": (i32, [i32, i32, vp, vp, vp]),
         "basis_build": (i32, [i32, i32, i32, ctypes.POINTER(vp)]),
         "basis_build_flip": (i32, [i32, i32, ctypes.POINTER(vp)]),
+        "basis_build_momentum": (i32, [i32, i32, i32, i32, ctypes.POINTER(vp)]),
         "basis_free": (i32, [vp]),
         "basis_dim": (i32, [vp, i64p]),
         "basis_encode": (i32, [vp, vp, vp, i64, vp]),

@@ -64,13 +64,17 @@ def bonds_check(n_sites: int, bonds: BondList) -> None:
 class Basis:
     """hm_basis: the tables of one sector H(M) on the current device (Sec. 3)."""
 
-    def __init__(self, n_sites: int, two_s: int, two_m: int, parity: int = 0):
-        """parity = +1 / -1: the spin-flip block of the s = 1/2 sector M = 0 (basis_build_flip)."""
+    def __init__(self, n_sites: int, two_s: int, two_m: int, parity: int = 0, momentum: int | None = None):
+        """parity = +1 / -1: the spin-flip block of the s = 1/2 sector M = 0 (basis_build_flip);
+        momentum = 0 or n_sites // 2: the momentum block of a ring (basis_build_momentum)."""
         self.n_sites, self.two_s, self.two_m, self.parity = n_sites, two_s, two_m, parity
+        self.momentum = momentum
         h = ctypes.c_void_p()
         if parity:
             assert two_s == 1 and two_m == 0, "the spin-flip basis is the s = 1/2 sector M = 0"
             check(_capi.load().basis_build_flip(n_sites, parity, ctypes.byref(h)))
+        elif momentum is not None:
+            check(_capi.load().basis_build_momentum(n_sites, two_s, two_m, momentum, ctypes.byref(h)))
         else:
             check(_capi.load().basis_build(n_sites, two_s, two_m, ctypes.byref(h)))
         self._h = h

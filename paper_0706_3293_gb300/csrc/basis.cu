@@ -136,6 +136,7 @@ int make_bonds(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *
             out->hs_pdn[ap * 8 + aq] = 0.5 * std::sqrt((double)(up_p * dn_q));
             out->hs_pup[ap * 8 + aq] = 0.5 * std::sqrt((double)(dn_p * up_q));
         }
+    if (b->mom_k >= 0) HM_TRY(mom_check_bonds(b, n_bonds, u, v, J));
     return HM_OK;
 }
 
@@ -266,6 +267,7 @@ int basis_free(hm_basis *b) {
         if (kv.second.dev && (e2 = cudaFree(kv.second.dev)) != cudaSuccess) e = e2;
     for (auto &kv : b->s1_tabs)
         if (kv.second.dev && (e2 = cudaFree(kv.second.dev)) != cudaSuccess) e = e2;
+    if (b->d_mom && (e2 = cudaFree(b->d_mom)) != cudaSuccess) e = e2;
     delete b;
     if (e != cudaSuccess) return cuda_fail(e, "basis_free");
     return HM_OK;
@@ -279,6 +281,7 @@ int basis_dim(const hm_basis *b, int64_t *dim) {
 
 int basis_decode(const hm_basis *b, const int64_t *idx, uint64_t *states, int64_t n, void *stream) {
     if (!b || n < 0 || (n > 0 && (!idx || !states))) return fail(HM_EINVAL, "bad argument");
+    if (b->mom_k >= 0) return fail(HM_EINVAL, "basis_decode: not available on a momentum basis");
     if (n == 0) return HM_OK;
     const SectorView &sv = b->view;
     int blocks = grid_blocks((uint64_t)n, 256);
@@ -297,6 +300,7 @@ int basis_decode(const hm_basis *b, const int64_t *idx, uint64_t *states, int64_
 
 int basis_encode(const hm_basis *b, const uint64_t *states, int64_t *idx, int64_t n, void *stream) {
     if (!b || n < 0 || (n > 0 && (!idx || !states))) return fail(HM_EINVAL, "bad argument");
+    if (b->mom_k >= 0) return fail(HM_EINVAL, "basis_encode: not available on a momentum basis");
     if (n == 0) return HM_OK;
     const SectorView &sv = b->view;
     int blocks = grid_blocks((uint64_t)n, 256);

@@ -89,11 +89,20 @@ struct hm_basis {
     std::map<int, hm::S1Tab> s1_tabs;     // s = 1 block path, per split K (owned device memory)
     int parity = 0;                 // spin-flip basis (basis_build_flip): +1 / -1, view.dim halved
     int device = 0;
+    // momentum basis (basis_build_momentum, momentum.cu): k = 0 or N/2, else -1.  view.dim is
+    // then the number of representatives; mom_sector keeps the sector's own view
+    int mom_k = -1;
+    hm::SectorView mom_sector{};
+    void *d_mom = nullptr;          // one allocation (owned): the sector map, then the list of representatives
+    void *d_mom_map = nullptr;      // uint64 per sector index: representative | shift << 32 | period << 40
+    void *d_mom_reps = nullptr;     // uint32 per representative: its sector index
 };
 
 namespace hm {
 
 int digit_bits(int two_s);
+// bonds of a momentum basis must map onto themselves under u -> u + 1 (momentum.cu)
+int mom_check_bonds(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, const double *J);
 // host helpers shared by the translation units
 int build_tables(int n_sites, int two_s, int two_m, hm_basis *b);
 int check_sector(int n_sites, int two_s, int two_m, int *A);
@@ -115,6 +124,8 @@ struct BondParams {
 
 int make_bonds(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v,
                const double *J, BondParams *out);
+// y = H x on a momentum basis (momentum.cu), one vector
+int mom_matvec(const hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------
 // device codec

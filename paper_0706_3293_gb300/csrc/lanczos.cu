@@ -43,7 +43,8 @@ struct LzLayout {
     size_t qqp;             // FP64 block path: partials of q_cur . q_prev (k_fix)
     size_t hpart;           // s = 1/2 block path: per-block partial sums, 2 x 2^hpart_H doubles
     int hpart_H;
-    size_t s1part;          // s = 1 block path (FP32): one partial sum per block, s1n of them
+    size_t s1part;          // s = 1 block path: one partial sum per block, s1n of them
+    size_t mv;              // momentum basis: y = H q from the momentum product
     uint64_t s1n;
     bool shadow;
 };
@@ -60,10 +61,13 @@ static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad
     L.buf[1] = o; o += al256(dim * es);
     const size_t npart = std::max<size_t>((size_t)nblk, (size_t)sm_count() * 8);
     L.part = o; o += al256(npart * 2 * sizeof(double));
-    // the block paths of FP64 runs (s = 1/2, s = 1) need y and two fixed-point copies
-    const uint64_t s1n = s1_block_count(b);
-    L.shadow = dtype == HM_F64 && !b->view.idx64 &&
+    // the block paths of FP64 runs (s = 1/2, s = 1) need y and two fixed-point copies; a
+    // momentum basis takes neither block path but needs y = H q
+    const bool mom = b->mom_k >= 0;
+    const uint64_t s1n = mom ? 0 : s1_block_count(b);
+    L.shadow = !mom && dtype == HM_F64 && !b->view.idx64 &&
                ((b->view.S2 == 1 && b->view.N >= 10 && b->view.N <= 32) || (b->view.S2 == 2 && s1n > 0));
+    if (mom) { L.mv = o; o += al256(dim * es); }
     if (L.shadow) {
         L.ybuf = o; o += al256(dim * 8);
         L.xs[0] = o; o += al256(dim * 8);
@@ -71,7 +75,7 @@ static LzLayout lz_layout(const hm_basis *b, int dtype, int max_steps, bool grad
         L.qqp = o; o += al256(npart * sizeof(double));
     }
     // per-block partials of the s = 1/2 block path (split K = min(15, N - 2): H <= 17)
-    if (b->view.S2 == 1 && b->view.N >= 10 && b->view.N <= 32 && !b->view.idx64) {
+    if (!mom && b->view.S2 == 1 && b->view.N >= 10 && b->view.N <= 32 && !b->view.idx64) {
         const int H = b->view.N - blk_K(b);
         L.hpart_H = H;
         L.hpart = o; o += al256(((size_t)2 << H) * sizeof(double));
@@ -105,6 +109,7 @@ struct hm_lanczos {
     const void *jit;        // block product specialised to the bonds (jit.cu), or nullptr
     int run;                // rows per thread run of the general product (row_runs)
     int use_s1;             // s = 1 block path (s1blk.cu)
+    int use_mom;            // momentum basis: product k_mom_matvec, then the epilogue kernel
     hm::S1Plan s1;
     int dtype, max_steps, host_j, next_phase;
     unsigned char *work;
@@ -190,6 +195,33 @@ k_lz_matvec(SectorView sv, BondParams bp, const T *__restrict__ qc, T *__restric
             dotf = ef::df_add(dotf, ef::two_prod(scf * (float)qc[r], u));
         }
     });
+    dot = block_sum<NT>(dot + (double)dotf.hi + (double)dotf.lo, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = dot;
+}
+
+// the epilogue of k_lz_matvec for a product formed by another kernel (momentum basis):
+// u = sigma_cur y - beta_prev sigma_prev q_prev over q_prev, part[blk] = sum (sigma_cur q_cur) . u
+template <class T>
+__global__ void __launch_bounds__(NT) k_lz_mv_epi(const T *__restrict__ y, const T *__restrict__ qc,
+                                                   T *__restrict__ qp, uint64_t n, const LzScalars *__restrict__ S,
+                                                   double *__restrict__ part) {
+    if (S->done) return;
+    __shared__ double red[NT / 32];
+    const double sc = S->sigma_cur, bp_ = S->beta_prev * S->sigma_prev;
+    const float scf = (float)sc, bpf = (float)bp_;
+    double dot = 0.0;
+    ef::df dotf{0.0f, 0.0f};
+    for (uint64_t r = (uint64_t)blockIdx.x * NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
+        if constexpr (sizeof(T) == 8) {
+            const T u = (T)(sc * (double)y[r] - bp_ * (double)qp[r]);
+            qp[r] = u;
+            dot += (sc * (double)qc[r]) * (double)u;
+        } else {
+            const float u = scf * (float)y[r] - bpf * (float)qp[r];
+            qp[r] = (T)u;
+            dotf = ef::df_add(dotf, ef::two_prod(scf * (float)qc[r], u));
+        }
+    }
     dot = block_sum<NT>(dot + (double)dotf.hi + (double)dotf.lo, red);
     if (threadIdx.x == 0) part[blockIdx.x] = dot;
 }
@@ -557,7 +589,12 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
                         R->L.shadow ? (long long *)(R->work + R->L.xs[1]) : nullptr};
     unsigned long long *Y = R->L.shadow ? (unsigned long long *)(R->work + R->L.ybuf) : nullptr;
     if (phase == 0) {
-        if (b64 && R->use_s1) {
+        if (R->use_mom) {
+            T *y = (T *)(R->work + R->L.mv);
+            HM_TRY(matvec_dev(R->basis, R->bp, qc, y, R->dtype, 1, st));
+            k_lz_mv_epi<T><<<nblk, NT, 0, st>>>(y, qc, qp, sv.dim, R->sc, R->part);
+            k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->alpha, pprev);
+        } else if (b64 && R->use_s1) {
             double *s1part = (double *)(R->work + R->L.s1part);
             HM_TRY(s1_lz64(R->s1, xs[parity], Y, R->sc, parity, s1part, st));
             k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, s1part, R->s1.nblocks, R->qqp, nblk, R->alpha, pprev);
@@ -678,7 +715,8 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
     rc = prepare(b, dtype);
     if (rc < 0) { delete R; return rc; }
     R->use_blk = 0;
-    rc = blk_lz_plan(const_cast<hm_basis *>(b), R->bp, dtype, &R->blk, &R->blk_blocks);
+    R->use_mom = b->mom_k >= 0;
+    rc = R->use_mom ? 1 : blk_lz_plan(const_cast<hm_basis *>(b), R->bp, dtype, &R->blk, &R->blk_blocks);
     if (rc < 0) { delete R; return rc; }
     // the per-block partials were sized for 2^hpart_H blocks
     R->use_blk = rc == 0 && (dtype == HM_F32 || R->L.shadow) && R->L.hpart != 0 && R->blk.H <= R->L.hpart_H &&
@@ -692,7 +730,7 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
         if (R->blk.perbond && !R->jit) R->use_blk = 0;   // per-bond rows run only specialised
     }
     R->use_s1 = 0;
-    if (!R->use_blk && R->L.s1part) {
+    if (!R->use_blk && !R->use_mom && R->L.s1part) {
         rc = s1_plan(const_cast<hm_basis *>(b), R->bp, &R->s1);
         if (rc < 0) { delete R; return rc; }
         R->use_s1 = rc == 0 && (uint64_t)R->s1.nblocks <= R->L.s1n;
@@ -819,7 +857,8 @@ int lanczos_free(hm_lanczos *R) {
 int lanczos_kernel_name(const hm_lanczos *R, char *name, int cap) {
     if (!R || !name || cap < 1) return fail(HM_EINVAL, "NULL argument");
     const bool f64 = R->dtype == HM_F64;
-    const char *n = R->use_s1 ? s1_kernel_name(R->s1, f64 ? 2 : 1)
+    const char *n = R->use_mom ? "k_mom_matvec"
+                    : R->use_s1 ? s1_kernel_name(R->s1, f64 ? 2 : 1)
                     : !R->use_blk ? "k_lz_matvec"
                     : R->jit    ? (f64 ? "k_blk_lz64_jit" : "k_blk_lz32_jit")
                                 : (f64 ? "k_blk_lz64" : "k_blk_lz32");
@@ -855,6 +894,7 @@ int e0_grad(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, 
             const void *v0, uint64_t seed, int steps, void *work, size_t work_bytes, double *e0,
             double *dE0_dJ, double *psi_out, void *stream) {
     if (b && b->parity) return fail(HM_EINVAL, "e0_grad: not available on a spin-flip basis");
+    if (b && b->mom_k >= 0) return fail(HM_EINVAL, "e0_grad: not available on a momentum basis");
     if (!e0 || (n_bonds > 0 && !dE0_dJ)) return fail(HM_EINVAL, "NULL output");
     hm_lanczos *R = nullptr;
     HM_TRY(lz_create(b, n_bonds, u, v, J, HM_F64, steps, work, work_bytes, true, &R));

@@ -172,6 +172,10 @@ const char *blk_matvec_kernel(hm_basis *b, const BondParams &bp, int dtype, int 
 int matvec_dev(const hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype,
                int nvec, cudaStream_t st) {
     const SectorView &sv = b->view;
+    if (b->mom_k >= 0) {
+        if (nvec != 1) return fail(HM_EINVAL, "momentum basis: one vector per product");
+        return mom_matvec(b, bp, x, y, dtype, st);
+    }
     // s = 1/2 sectors with few coupling classes take the block path (blk.cu)
     const int brc = blk_matvec(const_cast<hm_basis *>(b), bp, x, y, dtype, nvec, st);
     if (brc <= 0) return brc;
@@ -261,6 +265,10 @@ int matvec_kernel_name(const hm_basis *b, int n_bonds, const int32_t *u, const i
     if (dtype != HM_F64 && dtype != HM_F32) return fail(HM_EINVAL, "dtype must be HM_F64 or HM_F32");
     BondParams bp;
     HM_TRY(make_bonds(b, n_bonds, u, v, J, &bp));
+    if (b->mom_k >= 0) {
+        snprintf(name, (size_t)cap, "%s", "k_mom_matvec");
+        return HM_OK;
+    }
     const char *n = blk_matvec_kernel(const_cast<hm_basis *>(b), bp, dtype, nvec);
     if (!n && dtype == HM_F32 && nvec == 1 && b->view.S2 == 2) {
         S1Plan P;
@@ -276,6 +284,7 @@ int matvec_kernel_name(const hm_basis *b, int n_bonds, const int32_t *u, const i
 int count_nnz(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, int64_t *nnz,
               void *stream) {
     if (b && b->parity) return fail(HM_EINVAL, "count_nnz: not available on a spin-flip basis");
+    if (b && b->mom_k >= 0) return fail(HM_EINVAL, "count_nnz: not available on a momentum basis");
     if (!b || !nnz) return fail(HM_EINVAL, "NULL argument");
     std::vector<double> ones(n_bonds > 0 ? n_bonds : 1, 1.0);
     BondParams bp;
@@ -305,6 +314,7 @@ int bond_corr_workspace(const hm_basis *b, int n_bonds, size_t *bytes) {
 int bond_corr(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, const void *g,
               const void *x, double *out, int dtype, void *work, size_t work_bytes, void *stream) {
     if (b && b->parity) return fail(HM_EINVAL, "bond_corr: not available on a spin-flip basis");
+    if (b && b->mom_k >= 0) return fail(HM_EINVAL, "bond_corr: not available on a momentum basis");
     if (!b) return fail(HM_EINVAL, "basis is NULL");
     if (dtype != HM_F64 && dtype != HM_F32) return fail(HM_EINVAL, "dtype must be HM_F64 or HM_F32");
     if (!g || !x || (n_bonds > 0 && !out)) return fail(HM_EINVAL, "NULL vector");
@@ -349,6 +359,7 @@ int bc_static_ptr(double **out) {
 int bond_corr_static(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, const void *g,
                      const void *x, double *out, int dtype, void *stream) {
     if (b && b->parity) return fail(HM_EINVAL, "bond_corr: not available on a spin-flip basis");
+    if (b && b->mom_k >= 0) return fail(HM_EINVAL, "bond_corr: not available on a momentum basis");
     if (!b) return fail(HM_EINVAL, "basis is NULL");
     if (dtype != HM_F64 && dtype != HM_F32) return fail(HM_EINVAL, "dtype must be HM_F64 or HM_F32");
     if (!g || !x || (n_bonds > 0 && !out)) return fail(HM_EINVAL, "NULL vector");

@@ -605,3 +605,59 @@ def test_projection_monotone_and_converges(orc):
     E4 = oracle.projection(b4, bonds_of(r4), oracle.start_uniform(1, b4.dim), 400,
                            oracle.projection_default_sigma(1, r4.J))
     assert abs(E4[-1] - (-2.0)) < 1e-12
+
+
+# ---- momentum blocks of a ring (translation symmetry) ------------------------------------
+
+def _ring_bonds(N, j1, j2):
+    inst = W.small_ring(N, j1, j2)
+    return Bonds(inst.u, inst.v, inst.J)
+
+
+@pytest.mark.parametrize("N,S2,two_m,k_pi", [(4, 1, 0, False), (4, 1, 0, True), (8, 1, 0, True),
+                                             (9, 1, 1, False), (6, 2, 0, True), (7, 2, 2, False)])
+def test_momentum_basis_invariant_and_orthonormal(orc, N, S2, two_m, k_pi):
+    """The momentum vectors are orthonormal, H maps their span into itself (H commutes
+    with the translation for a ring), and every eigenvalue of the block is an eigenvalue
+    of the Kronecker-product sector Hamiltonian."""
+    A = oracle.sector_A(N, S2, two_m)
+    b = Basis(N, S2, A)
+    bonds = _ring_bonds(N, -1.0, -0.35)
+    B = oracle.momentum_vectors(b, k_pi)
+    np.testing.assert_allclose(B.T @ B, np.eye(B.shape[1]), atol=1e-13)
+    Hk = oracle.momentum_hamiltonian(b, bonds, k_pi)
+    HB = np.column_stack([b.matvec(bonds, B[:, c]) for c in range(B.shape[1])])
+    assert np.abs(HB - B @ Hk).max() < 1e-12
+    np.testing.assert_allclose(Hk, Hk.T, atol=1e-13)
+    ev = np.linalg.eigvalsh(oracle.dense_hamiltonian_sector(N, S2, A, bonds))
+    for t in np.linalg.eigvalsh(Hk):
+        assert np.abs(ev - t).min() < 1e-10
+
+
+def test_momentum_four_site_ring_and_marshall_rule(orc):
+    """Four-site s = 1/2 ring, M = 0: orbits {0011, 0110, 1100, 1001} (period 4) and
+    {0101, 1010} (period 2), so k = 0 and k = pi each hold two states, and E0 = -2 |J|.
+    Nearest-neighbour antiferromagnetic rings (Marshall's sign rule): the ground state has
+    momentum 0 when N/2 is even and pi when N/2 is odd, strictly below the other block."""
+    b = Basis(4, 1, 2)
+    bonds = _ring_bonds(4, -1.0, None)
+    H0 = oracle.momentum_hamiltonian(b, bonds, False)
+    Hpi = oracle.momentum_hamiltonian(b, bonds, True)
+    assert H0.shape == (2, 2) and Hpi.shape == (2, 2)
+    assert abs(np.linalg.eigvalsh(H0)[0] - (-2.0)) < 1e-13
+    for N in (4, 6, 8, 10):
+        b = Basis(N, 1, N // 2)
+        bonds = _ring_bonds(N, -1.0, None)
+        e = [np.linalg.eigvalsh(oracle.momentum_hamiltonian(b, bonds, kp))[0] for kp in (False, True)]
+        gs_pi = (N // 2) % 2 == 1
+        assert (e[1] < e[0] - 1e-9) if gs_pi else (e[0] < e[1] - 1e-9)
+
+
+def test_momentum_blocks_hold_the_ground_state(orc):
+    """Even J1-J2 rings: the sector ground state lies in the k = 0 or the k = pi block."""
+    for N in (8, 10):
+        b = Basis(N, 1, N // 2)
+        bonds = _ring_bonds(N, -1.0, -0.3)
+        ev = np.linalg.eigvalsh(oracle.dense_hamiltonian_sector(N, 1, N // 2, bonds))
+        e0 = min(np.linalg.eigvalsh(oracle.momentum_hamiltonian(b, bonds, kp))[0] for kp in (False, True))
+        assert abs(e0 - ev[0]) < 1e-10
