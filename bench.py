@@ -54,9 +54,13 @@ WORKLOADS = {
     # Arnoldi with full re-orthogonalisation on the N = 24 J1-J2 ring: one step = one whole
     # 60-step run; Gnnz/s counts its products (48 bonds, M = 0)
     "arnoldi_ring24": 2704156 + 2 * 48 * 705432,
+    # momentum block k = 0 of the default ring sector (18.8 million states); nnz = the terms
+    # its product processes (count_nnz on the momentum basis)
+    "j1j2_ring32_k0": None,
 }
 DEFAULT_DTYPE = {"s1_rrg20": "f32"}
 PARITY = {"j1j2_ring32_flip": 1}     # spin-flip block (basis_build_flip) of the workload's sector
+MOMENTUM = {"j1j2_ring32_k0": 0}     # momentum block (basis_build_momentum) of the workload's sector
 
 # bytes one product must move at minimum: read x once, write y once (FP64)
 ALGO_BYTES_PER_ROW = 16
@@ -64,14 +68,16 @@ ALGO_BYTES_PER_ROW = 16
 
 def instance(name):
     from paper_0706_3293_gb300 import workloads as W
-    return {"j1j2_ring32": W.j1j2_ring32, "j1j2_ring32_flip": W.j1j2_ring32, "j1j2_ring28": lambda: W.j1j2_ring(28),
+    return {"j1j2_ring32": W.j1j2_ring32, "j1j2_ring32_flip": W.j1j2_ring32, "j1j2_ring32_k0": W.j1j2_ring32,
+            "j1j2_ring28": lambda: W.j1j2_ring(28),
             "ring24_randJ": W.ring24_random_j, "ring24_grad": W.ring24_random_j, "ring16": W.ring16,
             "ftlm_ring24": W.ftlm_ring24, "arnoldi_ring24": W.arnoldi_ring24,
             "s1_rrg20": W.s1_random_graph}[name]()
 
 
-def workload_name(inst, parity):
-    return inst.name + (f"_flip{parity:+d}" if parity else "")
+def workload_name(inst, parity, momentum=None):
+    name = inst.name + (f"_flip{parity:+d}" if parity else "")
+    return name + ("" if momentum is None else ("_k0" if momentum == 0 else "_kpi"))
 
 
 def sector_nnz_s12(n_sites: int, n_bonds: int, A: int) -> int:
@@ -233,6 +239,10 @@ def run_reference(args):
     import numpy as np
     import oracle
     inst = instance(args.workload)
+    if args.workload in MOMENTUM:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle builds momentum blocks densely, "
+                          "for small N only; no bounded sample of this workload exists"}))
+        return 0
     if args.workload == "arnoldi_ring24":
         # one step = the oracle's Arnoldi on the first 6 steps of the run (bounded sample)
         nnz = WORKLOADS[args.workload]
@@ -647,7 +657,8 @@ def run_ours(args):
     tdt = torch.float64 if dtype == "f64" else torch.float32
     dev = torch.device("cuda", torch.cuda.current_device())
     parity = PARITY.get(args.workload, 0)
-    b = api.Basis(inst.n_sites, inst.two_s, inst.two_m, parity=parity)
+    momentum = MOMENTUM.get(args.workload)
+    b = api.Basis(inst.n_sites, inst.two_s, inst.two_m, parity=parity, momentum=momentum)
     bl = api.bonds_of(inst)
     nnz = WORKLOADS[args.workload] or api.count_nnz(b, bl)
     total = args.warmup + args.steps
@@ -717,12 +728,12 @@ def run_ours(args):
     mv_mean = float(np.mean(mv_ms))
     algo_row = ALGO_BYTES_PER_ROW if dtype == "f64" else ALGO_BYTES_PER_ROW // 2
     achieved = algo_row * b.dim / (mv_mean * 1e-3) / 1e9
-    traffic = read_traffic(kname, workload_name(inst, parity))
+    traffic = read_traffic(kname, workload_name(inst, parity, momentum))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": workload_name(inst, parity), "n_sites": inst.n_sites, "two_s": inst.two_s,
+        "config": {"workload": workload_name(inst, parity, momentum), "n_sites": inst.n_sites, "two_s": inst.two_s,
                    "two_m": inst.two_m, "dim": b.dim, "nnz_per_product": nnz,
                    "bonds": inst.n_bonds, "start_seed": inst.seed, "parallelism": f"replicas{ws}",
                    "l2": "inputs larger than L2 (2 x %.1f GB vectors)" % (b.dim * 8 / 1e9)},
@@ -733,13 +744,17 @@ def run_ours(args):
                      "mean_launch_ms": mv_mean},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": b.dim * (8 if dtype == "f64" else 4) / args.steps,
                 "d2h_bytes_per_step": 16},
-        "gpu_launches": 4 * args.steps,
+        # per step: product, alpha, update, beta (+ the separate epilogue on a momentum basis)
+        "gpu_launches": (4 if momentum is None else 5) * args.steps,
         "clocks": clocks,
         "lanczos": {"alpha_last": float(al[-1]) if len(al) else None,
                     "steps_done": int(len(al)), "status": int(rc)},
     }
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and momentum is None:
         out["cpu_baseline"] = cpu_baseline(inst, nnz, parity=parity)
+    elif ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle",
+                               "sample": "none: the oracle builds momentum blocks densely, for small N only"}
     print(json.dumps(out))
     if ws > 1:
         import torch.distributed as dist

@@ -105,7 +105,7 @@ int basis_build_flip(int n_sites, int parity, hm_basis **out);
  * for even N, k = N/2 (the real characters chi(n) = 1 and (-1)^n).  Basis states: one per
  * orbit of T whose period p has chi(p) = 1, |r^> = p^(-1/2) sum_{m<p} chi(m) T^m |r>, r the
  * orbit member with the smallest packed digit word, numbered in the order of the sector
- * index of r; basis_dim gives their number.  matvec, lanczos_*, arnoldi_run and
+ * index of r; basis_dim gives their number.  matvec, count_nnz, lanczos_*, arnoldi_run and
  * projection_run accept such a basis (one vector per product; the bonds must map onto
  * themselves under T with equal couplings, else HM_EINVAL); the other calls reject it.
  * Needs a sector of fewer than 2^32 states with N digits in 64 bits.  The device holds 8
@@ -134,8 +134,10 @@ int matvec(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *
            const double *J, const void *x, void *y, int dtype, int nvec, void *stream);
 
 /* Number of non-zero elements of H(M) for the bond list (one diagonal element per row plus
- * every allowed exchange, Sec. 4 "N^{1..2} x dim non-zero entries"), accumulated on the
- * device into *nnz (device int64, overwritten).  The figure behind Gnnz/s. */
+ * every allowed exchange; Sec. 4 counts of order N to N^2 of them per row), accumulated on
+ * the device into *nnz (device int64, overwritten).  The figure behind Gnnz/s.  On a
+ * momentum basis: the terms its product processes, one per row plus every allowed exchange
+ * whose target orbit has a basis state. */
 int count_nnz(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v, int64_t *nnz,
               void *stream);
 

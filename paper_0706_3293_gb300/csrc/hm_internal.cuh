@@ -126,6 +126,8 @@ int make_bonds(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *
                const double *J, BondParams *out);
 // y = H x on a momentum basis (momentum.cu), one vector
 int mom_matvec(const hm_basis *b, const BondParams &bp, const void *x, void *y, int dtype, cudaStream_t st);
+// terms of that product (1 per row + the exchanges that land on a basis state), into *nnz (device)
+int mom_count_nnz(const hm_basis *b, const BondParams &bp, int64_t *nnz, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------
 // device codec

@@ -284,11 +284,11 @@ int matvec_kernel_name(const hm_basis *b, int n_bonds, const int32_t *u, const i
 int count_nnz(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v, int64_t *nnz,
               void *stream) {
     if (b && b->parity) return fail(HM_EINVAL, "count_nnz: not available on a spin-flip basis");
-    if (b && b->mom_k >= 0) return fail(HM_EINVAL, "count_nnz: not available on a momentum basis");
     if (!b || !nnz) return fail(HM_EINVAL, "NULL argument");
     std::vector<double> ones(n_bonds > 0 ? n_bonds : 1, 1.0);
     BondParams bp;
     HM_TRY(make_bonds(b, n_bonds, u, v, ones.data(), &bp));
+    if (b->mom_k >= 0) return mom_count_nnz(b, bp, nnz, as_stream(stream));
     const SectorView &sv = b->view;
     cudaStream_t st = as_stream(stream);
     HM_CUDA(cudaMemsetAsync(nnz, 0, sizeof(int64_t), st));

@@ -148,23 +148,28 @@ __global__ void __launch_bounds__(MOM_NT) k_mom_map(SectorView sv, int kpi, uint
     }
 }
 
-// y = H x on the momentum basis (Acc = double, T = double or float)
+// y = H x on the momentum basis (sums in binary64, T = double or float).  A target's
+// sector index is the row's own index plus the rank change of positions p..q (Sec. 3.2,
+// Codec::delta), so nearest- and next-nearest-neighbour exchanges cost two or three table
+// reads instead of a full encode; the factor sqrt(p_r) is applied once per row.
 template <class T>
 __global__ void __launch_bounds__(MOM_NT) k_mom_matvec(SectorView sv, BondParams bp, int kpi, uint64_t nrep,
                                                         const uint32_t *__restrict__ reps,
                                                         const uint64_t *__restrict__ map, const T *__restrict__ x,
                                                         T *__restrict__ y) {
     __shared__ uint32_t cd[4096];
-    __shared__ double sq[65];        // sqrt(p), p = 0..64
+    __shared__ double sq[65], isq[65];   // sqrt(p), 1 / sqrt(p), p = 0..64
     for (int k = threadIdx.x; k < sv.cd_len; k += MOM_NT) cd[k] = ((const uint32_t *)sv.cd)[k];
-    for (int k = threadIdx.x; k <= 64; k += MOM_NT) sq[k] = sqrt((double)k);
+    for (int k = threadIdx.x; k <= 64; k += MOM_NT) {
+        sq[k] = sqrt((double)k);
+        isq[k] = k ? 1.0 / sqrt((double)k) : 0.0;
+    }
     __syncthreads();
     Codec<uint32_t> c{cd, sv.N, sv.S2, sv.A, sv.bits, sv.cd_w, sv.cd_rowlen};
     const double s = sv.S2 * 0.5;
     for (uint64_t r = (uint64_t)blockIdx.x * MOM_NT + threadIdx.x; r < nrep; r += (uint64_t)gridDim.x * MOM_NT) {
         const uint32_t i = reps[r];
         const uint64_t w = c.decode(i);
-        const double sp = sq[(map[i] >> 40) & 0xFF];
         double dg = 0.0, acc = 0.0;
         for (int b = 0; b < bp.nb; ++b) {
             const int p = bp.p[b], q = bp.q[b];
@@ -174,22 +179,60 @@ __global__ void __launch_bounds__(MOM_NT) k_mom_matvec(SectorView sv, BondParams
             for (int d = 0; d < 2; ++d) {
                 const bool ok = d == 0 ? (ap >= 1 && aq < sv.S2) : (ap < sv.S2 && aq >= 1);
                 if (!ok) continue;
-                const double f = d == 0 ? bp.hs_pdn[ap * 8 + aq] : bp.hs_pup[ap * 8 + aq];
-                const uint64_t up = (uint64_t)1 << (p * sv.bits), uq = (uint64_t)1 << (q * sv.bits);
-                const uint64_t t = d == 0 ? w - up + uq : w + up - uq;
-                const uint64_t e = map[c.encode(t)];
+                const uint64_t e = map[i + c.delta(w, p, q, d == 0 ? -1 : 1)];
                 if (e == MOM_NONE) continue;
-                const uint32_t r2 = (uint32_t)e;
-                const int l = (int)((e >> 32) & 0xFF);
-                const double chi = (kpi && (l & 1)) ? -1.0 : 1.0;
-                acc += bp.jm[b] * f * chi * sp / sq[(e >> 40) & 0xFF] * (double)x[r2];
+                const double f = bp.jm[b] * (d == 0 ? bp.hs_pdn[ap * 8 + aq] : bp.hs_pup[ap * 8 + aq]);
+                const double v = f * isq[(e >> 40) & 0xFF] * (double)x[(uint32_t)e];
+                acc += (kpi && ((e >> 32) & 1)) ? -v : v;
             }
         }
-        y[r] = (T)(dg * (double)x[r] + acc);
+        y[r] = (T)(dg * (double)x[r] + sq[(map[i] >> 40) & 0xFF] * acc);
+    }
+}
+
+// terms of the product: per representative 1 (the diagonal) + its allowed exchanges whose
+// target orbit has a basis state; summed into *out
+__global__ void __launch_bounds__(MOM_NT) k_mom_count_nnz(SectorView sv, BondParams bp, uint64_t nrep,
+                                                           const uint32_t *__restrict__ reps,
+                                                           const uint64_t *__restrict__ map,
+                                                           unsigned long long *out) {
+    __shared__ uint32_t cd[4096];
+    __shared__ unsigned long long red[MOM_NT / 32];
+    for (int k = threadIdx.x; k < sv.cd_len; k += MOM_NT) cd[k] = ((const uint32_t *)sv.cd)[k];
+    __syncthreads();
+    Codec<uint32_t> c{cd, sv.N, sv.S2, sv.A, sv.bits, sv.cd_w, sv.cd_rowlen};
+    unsigned long long n = 0;
+    for (uint64_t r = (uint64_t)blockIdx.x * MOM_NT + threadIdx.x; r < nrep; r += (uint64_t)gridDim.x * MOM_NT) {
+        const uint64_t w = c.decode(reps[r]);
+        n += 1;
+        for (int b = 0; b < bp.nb; ++b) {
+            const int p = bp.p[b], q = bp.q[b];
+            const int ap = dig(w, p, sv.bits), aq = dig(w, q, sv.bits);
+            const uint64_t up = (uint64_t)1 << (p * sv.bits), uq = (uint64_t)1 << (q * sv.bits);
+            if (ap >= 1 && aq < sv.S2 && map[c.encode(w - up + uq)] != MOM_NONE) ++n;   // full encode: an
+            if (ap < sv.S2 && aq >= 1 && map[c.encode(w + up - uq)] != MOM_NONE) ++n;   // independent count
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int k = 0; k < MOM_NT / 32; ++k) t += red[k];
+        atomicAdd(out, t);
     }
 }
 
 // ---- host -----------------------------------------------------------------------------------
+
+int mom_count_nnz(const hm_basis *b, const BondParams &bp, int64_t *nnz, cudaStream_t st) {
+    HM_CUDA(cudaMemsetAsync(nnz, 0, sizeof(int64_t), st));
+    k_mom_count_nnz<<<grid_blocks(b->view.dim, MOM_NT), MOM_NT, 0, st>>>(
+        b->mom_sector, bp, b->view.dim, (const uint32_t *)b->d_mom_reps, (const uint64_t *)b->d_mom_map,
+        (unsigned long long *)nnz);
+    HM_CUDA(cudaGetLastError());
+    return HM_OK;
+}
 
 // the bond list must map onto itself under u -> u + 1 (mod N) with equal couplings (summed
 // over repeated pairs), so that H commutes with T

@@ -117,8 +117,40 @@ def test_momentum_rejections(hm):
         hm.Basis(9, 1, 1, momentum=4)
     bl = hm.bonds_of(inst)
     with pytest.raises(HMError):
-        hm.count_nnz(b, bl)
-    with pytest.raises(HMError):
         hm.e0_grad(b, bl, 20)
     with pytest.raises(HMError):
         hm.bond_corr(b, bl, x, x)
+
+
+@pytest.mark.parametrize("N,S2,two_m,k", [(8, 1, 0, 0), (8, 1, 0, 4), (7, 2, 2, 0), (10, 1, 2, 5)], ids=lambda v: str(v))
+def test_momentum_count_nnz(hm, N, S2, two_m, k):
+    """count_nnz on a momentum basis: one term per representative plus every allowed
+    exchange whose target orbit has a basis state, counted here from the oracle's codec."""
+    inst = W.small_ring(N, -1.0, -0.35, two_s=S2, two_m=two_m)
+    ob = oracle.Basis(N, S2, oracle.sector_A(N, S2, two_m))
+    kpi = k != 0
+
+    def orbit(d):
+        words = [oracle.packed_word(np.roll(d, m), S2) for m in range(N)]
+        p = next(m for m in range(1, N + 1) if m == N or words[m] == words[0])
+        return words, p
+
+    want = 0
+    for i in range(ob.dim):
+        d = ob.decode(i)
+        words, p = orbit(d)
+        if words[0] != min(words) or (kpi and p % 2):
+            continue
+        want += 1
+        for u, v in zip(inst.u, inst.v):
+            a, c = min(u, v), max(u, v)
+            for da in (-1, 1):
+                t = d.copy()
+                t[a] += da
+                t[c] -= da
+                if min(t[a], t[c]) < 0 or max(t[a], t[c]) > S2:
+                    continue
+                _, p2 = orbit(t)
+                want += 0 if (kpi and p2 % 2) else 1
+    b = hm.Basis(N, S2, two_m, momentum=k)
+    assert hm.count_nnz(b, hm.bonds_of(inst)) == want
