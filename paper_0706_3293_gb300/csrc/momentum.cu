@@ -159,22 +159,56 @@ __global__ void __launch_bounds__(MOM_NT) k_mom_matvec(SectorView sv, BondParams
                                                         T *__restrict__ y) {
     __shared__ uint32_t cd[4096];
     __shared__ double sq[65], isq[65];   // sqrt(p), 1 / sqrt(p), p = 0..64
+    // per bond -J_b / 4 and -J_b / 2: the diagonal term is jq (2s - 2a_p)(2s - 2a_q) and
+    // the s = 1/2 exchange coefficient jh (few binary64 operations per bond: this GPU's
+    // FP64 pipe bounded the first version at 82 %)
+    __shared__ double jq[HM_MAX_BONDS], jh[HM_MAX_BONDS];
     for (int k = threadIdx.x; k < sv.cd_len; k += MOM_NT) cd[k] = ((const uint32_t *)sv.cd)[k];
     for (int k = threadIdx.x; k <= 64; k += MOM_NT) {
         sq[k] = sqrt((double)k);
         isq[k] = k ? 1.0 / sqrt((double)k) : 0.0;
     }
+    __shared__ double jqsum;
+    for (int k = threadIdx.x; k < bp.nb; k += MOM_NT) {
+        jq[k] = 0.25 * bp.jm[k];
+        jh[k] = 0.5 * bp.jm[k];
+    }
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < bp.nb; ++k) t += 0.25 * bp.jm[k];
+        jqsum = t;
+    }
     __syncthreads();
     Codec<uint32_t> c{cd, sv.N, sv.S2, sv.A, sv.bits, sv.cd_w, sv.cd_rowlen};
-    const double s = sv.S2 * 0.5;
     for (uint64_t r = (uint64_t)blockIdx.x * MOM_NT + threadIdx.x; r < nrep; r += (uint64_t)gridDim.x * MOM_NT) {
         const uint32_t i = reps[r];
         const uint64_t w = c.decode(i);
+        if (sv.S2 == 1) {
+            // s = 1/2: a bond's exchange is allowed exactly when its spins differ, and then
+            // its diagonal term is -jq instead of +jq: dg = sum jq - 2 sum over those bonds of
+            // jq.  Targets of full period N share the factor 1 / sqrt(N).
+            double sd = 0.0, accn = 0.0, acco = 0.0;
+            for (int b = 0; b < bp.nb; ++b) {
+                const int p = bp.p[b], q = bp.q[b];
+                const int ap = dig(w, p, 1), aq = dig(w, q, 1);
+                if (ap == aq) continue;
+                sd += jq[b];
+                const uint64_t e = map[i + c.delta(w, p, q, ap ? -1 : 1)];
+                if (e == MOM_NONE) continue;
+                const double f = (kpi && ((e >> 32) & 1)) ? -jh[b] : jh[b];
+                const int per = (int)((e >> 40) & 0xFF);
+                if (per == sv.N) accn = fma(f, (double)x[(uint32_t)e], accn);
+                else acco = fma(f * isq[per], (double)x[(uint32_t)e], acco);
+            }
+            const double dg = jqsum - 2.0 * sd;
+            y[r] = (T)(dg * (double)x[r] + sq[(map[i] >> 40) & 0xFF] * (isq[sv.N] * accn + acco));
+            continue;
+        }
         double dg = 0.0, acc = 0.0;
         for (int b = 0; b < bp.nb; ++b) {
             const int p = bp.p[b], q = bp.q[b];
             const int ap = dig(w, p, sv.bits), aq = dig(w, q, sv.bits);
-            dg += bp.jm[b] * (s - ap) * (s - aq);
+            dg = fma((double)((sv.S2 - 2 * ap) * (sv.S2 - 2 * aq)), jq[b], dg);
             // s+_p s-_q (a_p - 1, a_q + 1) and s-_p s+_q (a_p + 1, a_q - 1), Eq. E-2-1
             for (int d = 0; d < 2; ++d) {
                 const bool ok = d == 0 ? (ap >= 1 && aq < sv.S2) : (ap < sv.S2 && aq >= 1);
