@@ -632,6 +632,82 @@ def run_arnoldi(args):
     return 0
 
 
+def splitmix64(seed: int, t: int) -> int:
+    """Output t of SplitMix64 (Steele, Lea, Flood 2014) seeded with seed: the key of a
+    finite-temperature start vector (sector A, vector r) is output A 2^20 + r of the run's
+    seed."""
+    M = (1 << 64) - 1
+    z = (seed + (t + 1) * 0x9E3779B97F4A7C15) & M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+def compare_forms(api, torch, b, bl, inst, nnz, steps=150):
+    """The FP32 and batched forms against the plain FP64 form on this GPU, each at the
+    ground energy it reaches.  FP64 and FP32: whole Lanczos runs (one graph each) of `steps`
+    steps on the default sector, the lowest Ritz value against the Majumdar-Ghosh energy
+    -3N/8 (J2 = J1/2) and against each other.  Batched: one finite-temperature run of the
+    N = 24 ring (all sectors, 32 vectors, 80 steps), its M = 0 vector r = 0 against a plain
+    FP64 run of 80 steps from the same +-1 vector, and that plain FP64 form's rate on the
+    same sector."""
+    import numpy as np
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        r = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    out = {}
+    e_mg = -3.0 * inst.n_sites / 8.0
+    res = {}
+    for dt, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        ws = torch.empty(api.lanczos_workspace(b, tdt, steps), dtype=torch.uint8, device="cuda")
+        api.lanczos_run(b, bl, 3, seed=inst.seed, dtype=tdt, n_ritz=1, work=ws)   # warm-up
+        r, ms = timed(lambda: api.lanczos_run(b, bl, steps, seed=inst.seed, dtype=tdt, n_ritz=1, work=ws))
+        del ws
+        torch.cuda.empty_cache()
+        res[dt] = (r, ms)
+        out[dt] = {"workload": inst.name, "steps": int(r.steps_done), "ms_per_step": ms / r.steps_done,
+                   "gnnz_s": nnz * r.steps_done / (ms * 1e-3) / 1e9, "E0": float(r.ritz[0]),
+                   "rel_err_vs_exact": abs(float(r.ritz[0]) - e_mg) / abs(e_mg),
+                   "exact": f"Majumdar-Ghosh -3N/8 = {e_mg}"}
+    out["f32"]["rel_err_vs_f64"] = abs(out["f32"]["E0"] - out["f64"]["E0"]) / abs(out["f64"]["E0"])
+    out["f32"]["speedup_vs_f64"] = out["f32"]["gnnz_s"] / out["f64"]["gnnz_s"]
+    # batched finite-temperature run
+    fi = instance("ftlm_ring24")
+    R = fi.meta["R"]
+    fb = api.bonds_of(fi)
+    api.ftlm_run(fi.n_sites, fb, R, fi.steps, fi.seed, [1.0])                      # warm-up, tiling
+    fr, fms = timed(lambda: api.ftlm_run(fi.n_sites, fb, R, fi.steps, fi.seed, [1.0]))
+    nnz_sec = [sector_nnz_s12(fi.n_sites, fi.n_bonds, A) for A in range(fi.n_sites + 1)]
+    vsteps = int(fr.mlen[:, :R].sum())
+    work = float(sum(nnz_sec[A] * int(fr.mlen[A, :R].sum()) for A in range(fi.n_sites + 1)))
+    A0 = fi.n_sites // 2
+    b24 = api.Basis(fi.n_sites, 1, 0)
+    v0 = api.start_vector(b24, splitmix64(fi.seed, (A0 << 20) + 0), kind=1, dtype=torch.float64)
+    api.lanczos_run(b24, fb, 3, v0=v0, n_ritz=1)
+    r64, ms64 = timed(lambda: api.lanczos_run(b24, fb, fi.steps, v0=v0, n_ritz=1))
+    m = int(fr.mlen[A0, 0])
+    e32 = float(np.min(fr.theta[A0, 0, :m]))
+    g_plain = nnz_sec[A0] * r64.steps_done / (ms64 * 1e-3) / 1e9
+    g_batch = work / (fms * 1e-3) / 1e9
+    out["batched"] = {"workload": fi.name, "sectors": fi.n_sites + 1, "R": R, "steps": fi.steps,
+                      "ms_per_run": fms, "vector_steps": vsteps, "ms_per_vector_step": fms / vsteps,
+                      "gnnz_s": g_batch, "E0_M0_r0": e32, "E0_M0_r0_f64": float(r64.ritz[0]),
+                      "rel_err_vs_f64": abs(e32 - float(r64.ritz[0])) / abs(float(r64.ritz[0])),
+                      "f64_same_sector": {"ms_per_step": ms64 / r64.steps_done, "gnnz_s": g_plain},
+                      "speedup_vs_f64_same_sector": g_batch / g_plain,
+                      "speedup_vs_f64_default": g_batch / out["f64"]["gnnz_s"]}
+    b24.close()
+    return out
+
+
 def run_ours(args):
     if args.workload == "arnoldi_ring24":
         return run_arnoldi(args)
@@ -750,6 +826,8 @@ def run_ours(args):
         "lanczos": {"alpha_last": float(al[-1]) if len(al) else None,
                     "steps_done": int(len(al)), "status": int(rc)},
     }
+    if ws == 1 and not args.no_compare and args.workload == "j1j2_ring32" and dtype == "f64":
+        out["forms"] = compare_forms(api, torch, b, bl, inst, nnz)
     if ws == 1 and not args.no_cpu_baseline and momentum is None:
         out["cpu_baseline"] = cpu_baseline(inst, nnz, parity=parity)
     elif ws == 1 and not args.no_cpu_baseline:
@@ -770,6 +848,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="j1j2_ring32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP32 and batched comparison runs of the default workload")
     ap.add_argument("--dtype", choices=["f64", "f32"], default=None,
                     help="Lanczos vector type (default: f64; f32 for s1_rrg20)")
     args = ap.parse_args()

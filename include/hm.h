@@ -34,8 +34,9 @@
  *     synchronise that stream before returning.
  *   - Workspace: functions that need scratch take a caller-owned device buffer
  *     (work, work_bytes); the matching *_workspace function gives the size.  The
- *     library allocates device memory only for the small per-basis tables
- *     (basis_build) and never frees caller memory.
+ *     library allocates device memory only for small per-basis tables (in basis_build,
+ *     and the block-path tables and run-time compiled kernels on the first call that
+ *     needs them) and never frees caller memory; bond_corr_static allocates nothing.
  */
 #ifndef HM_H
 #define HM_H
@@ -151,16 +152,21 @@ int bond_corr(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_
               size_t work_bytes, void *stream);
 
 /* bond_corr with no allocation and no workspace argument -- the paper has no counterpart.
- * For callers that cannot allocate device memory when they need the adjoint (for example
- * while a stream is being captured into a CUDA graph, or after a pre-allocated budget is
- * spent).  The per-block partial sums go to a file-scope device array of 1 MiB that every
- * GPU loading the library holds until exit; a problem whose partial sums exceed it
- * (bond_corr_workspace > 1 MiB) returns HM_EINVAL with a message.  Output as bond_corr:
- * out[b] (device double[n_bonds]), computed with the same kernels and launch shape.
- * The array is shared by all calls and keeps the last call's contents (each call writes
- * every slot it reads); calls that overlap on the GPU race on it and must be ordered on
- * one stream.  The first call on a device looks up the array's device address (no
- * allocation); make that first call before any stream capture. */
+ * For callers that cannot call cudaMalloc when they need the adjoint: a host program that
+ * reserves its whole device-memory budget at start-up and forbids later allocation, or a
+ * library embedded in a framework whose allocator owns all device memory.  The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine, on any call):
+ * it runs the general row kernels, which read only the tables basis_build made, and keeps
+ * their per-block partial sums in a file-scope device array of 1 MiB that every GPU
+ * loading the library holds until exit.  A problem whose partial sums exceed it
+ * (grid blocks x n_bonds doubles, at most 1216 x n_bonds on a 152-SM GPU) returns
+ * HM_EINVAL with a message.  Output as bond_corr: out[b] (device double[n_bonds]), equal
+ * to it up to the rounding of a different summation order.  The array is shared by all
+ * calls and keeps the last call's contents (each call writes every slot it reads before
+ * reading it); calls that overlap on the GPU race on it and must be ordered on one
+ * stream.  The first call on a device (and the first after a new context is made there)
+ * looks up the array's device address with cudaGetSymbolAddress; make that first call
+ * before any stream capture. */
 int bond_corr_static(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
                      const void *g, const void *x, double *out, int dtype, void *stream);
 
@@ -176,7 +182,9 @@ int start_vector(const hm_basis *basis, uint64_t seed, int kind, void *x, int dt
  *   v_1 = v0/|v0|;  u = H v_j - beta_{j-1} v_{j-1};  alpha_j = v_j . u;
  *   w = u - alpha_j v_j;  beta_j = |w|;  v_{j+1} = w / beta_j.
  * Breakdown after step j when beta_j <= tol * max(|alpha_1..alpha_j|,
- * beta_1..beta_{j-1}), tol = 1e-12 for HM_F64 vectors and 1e-5 for HM_F32 vectors (the
+ * beta_1..beta_{j-1}), tol = 1e-10 for HM_F64 vectors (the s = 1/2 and s = 1 block paths
+ * update them in double-float arithmetic, unit roundoff about 2^-48, so a beta that is zero
+ * in exact arithmetic comes out near 1e-12 of the scale) and 1e-5 for HM_F32 vectors (the
  * FP32 rounding floor); the run then stops with steps_done = j (status HM_BREAKDOWN).
  * Vectors are stored in dtype; alpha, beta and all reductions are double (fixed-order,
  * run-to-run deterministic); the tridiagonal eigensolve runs on the device in double. */
@@ -304,8 +312,11 @@ int sym_eigenvalues(int n, const double *a, double *ev);
  * the generator seeded with `seed`, element t = -1 if bit 63 of output #t of that stream is
  * set, else +1.  Vectors are FP32 (row-major [rows][32], all sectors back to back),
  * reductions double-float then double; a run stops at beta_j <= 1e-5 * max(|alpha|, beta)
- * (above the FP32 noise floor) or after D_A steps (a sector of dimension D_A holds at most
- * D_A Lanczos vectors).  Everything runs in one CUDA graph: start vectors, one
+ * (above the FP32 noise floor).  A sector with D_A <= steps and D_A <= 512 would exhaust
+ * its Krylov space, which FP32 vectors cannot detect: it is diagonalised exactly instead
+ * (theta = its eigenvalues, tau = squared overlaps of the normalised start vector with the
+ * eigenvectors, the limit the Lanczos quadrature reaches; its mlen = D_A).  Everything
+ * runs in one CUDA graph: start vectors, one
  * cooperative persistent kernel for all steps (grid barriers wait at most 5 s, then the
  * call returns HM_ETIMEOUT), and the tridiagonal eigensolves on the device.  Outputs (host):
  * e_ref = lowest Ritz value; for each temperature T = temps[i]:

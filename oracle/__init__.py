@@ -487,10 +487,11 @@ def projection_default_sigma(two_s: int, J: Sequence[float]) -> float:
     return float(sum(abs(j) for j in J) * s * (s + 1.0))
 
 
-def ftlm_sector(basis: Basis, bonds: Bonds, seed: int, R: int, steps: int):
+def ftlm_sector(basis: Basis, bonds: Bonds, seed: int, R: int, steps: int, tol: float = FTLM_TOL):
     """Per start vector r of one sector: Ritz values theta_j and weights tau_j (squared
     first components of T's eigenvectors), the start vector being the +-1 vector of
-    stream (seed, A, r).  A run stops at beta_j <= FTLM_TOL max(|alpha|, beta).
+    stream (seed, A, r).  A run stops at beta_j <= tol max(|alpha|, beta) (tol defaults
+    to FTLM_TOL, the threshold the FP32 device runs use).
     A sector of dimension <= steps (and <= 512) would exhaust its Krylov space; it is
     diagonalised exactly instead: theta_k = E_k, tau_k = <r/|r| | psi_k>^2, the limit of
     the Lanczos quadrature (alpha, beta are then returned empty)."""
@@ -506,7 +507,7 @@ def ftlm_sector(basis: Basis, bonds: Bonds, seed: int, R: int, steps: int):
             o = V.T @ (v0 / np.sqrt(basis.dim))
             res.append((E.copy(), o * o, np.zeros(0), np.zeros(0)))
             continue
-        al, be = basis.lanczos(bonds, v0, steps, tol=FTLM_TOL)
+        al, be = basis.lanczos(bonds, v0, steps, tol=tol)
         m = len(al)
         if m == 1:
             th, c = np.array([al[0]]), np.ones((1, 1))

@@ -81,53 +81,65 @@ orc_basis *orc_basis_new(int N, int S2, int A)
 void orc_basis_free(orc_basis *b) { if (b) { free(b->D); free(b); } }
 int64_t orc_basis_dim(const orc_basis *b) { return b->dim; }
 
-/* Sec. 3.1, index -> state.  With the digits above position k fixed and Ak the digit sum
- * left for positions 1..k, the states form consecutive groups by their k-th digit
- * n = 0, 1, ..., 2s, the group of digit n holding D(k-1, Ak - n) states.  Walk from
- * position N down to 2, find the group holding the index, and keep the offset inside
- * it.  Whatever sum remains is the digit of position 1.  Returns 0, or -1 for an index
- * outside the sector. */
+/* The order of the basis (Eq. E-3-a): |a_1 .. a_N> runs through the digit strings like
+ * the numbers sum_k a_k (2s+1)^(k-1), position N most significant, keeping those with
+ * digit sum A; the index of a state is the number of sector states before it.
+ *
+ * Counting them (state -> index, the map Sec. 3.2 computes): a sector state b comes
+ * before a exactly when, at the highest position k where the two differ, b_k < a_k.  For
+ * a fixed k and a fixed smaller digit n there, the positions above k copy a and the k-1
+ * positions below carry the rest of the digit sum, A - n - (a_{k+1} + .. + a_N), in any
+ * arrangement: D(k-1, that rest) states by the definition of D (Eq. E-3-c).  Hence
+ *     index(a) = sum_{k=1..N} sum_{n < a_k} D(k-1, A - n - T_k),  T_k = a_{k+1} + .. + a_N,
+ * with D zero outside its range.  Returns -1 when the digits are not in the sector. */
+int64_t orc_encode(const orc_basis *b, const int32_t *dig)
+{
+    int total = 0;
+    for (int k = 0; k < b->N; ++k) {
+        if (dig[k] < 0 || dig[k] > b->S2) return -1;
+        total += dig[k];
+    }
+    if (total != b->A) return -1;
+    /* suffix[k] = T_k = a_{k+1} + .. + a_N (suffix[N] = 0) */
+    int suffix[65];
+    suffix[b->N] = 0;
+    for (int k = b->N; k >= 1; --k) suffix[k - 1] = suffix[k] + dig[k - 1];
+    int64_t count = 0;
+    for (int k = 1; k <= b->N; ++k)
+        for (int n = 0; n < dig[k - 1]; ++n) count += orc_D(b, k - 1, b->A - n - suffix[k]);
+    return count;
+}
+
+/* Index -> state (Sec. 3.1), by inverting that count from the top.  Once the digits
+ * above position k are fixed (digit sum T_k), the states sharing them are consecutive in
+ * the order, and among them those with digit n at position k come before those with a
+ * larger digit there; the ones with digit m number D(k-1, A - m - T_k).  So the digit at
+ * position k is the n whose run of states holds the rank r left over from the positions
+ * above: the last n with P(n) = sum_{m < n} D(k-1, A - m - T_k) <= r; r then drops by P(n).
+ * Position 1 takes whatever digit sum is left.  Returns 0, or -1 for an index outside the
+ * sector. */
 int orc_decode(const orc_basis *b, int64_t i, int32_t *dig)
 {
     if (i < 0 || i >= b->dim) return -1;
     int64_t r = i;
-    int Ak = b->A;
+    int Tk = 0;                              /* digit sum of the positions above k */
     for (int k = b->N; k >= 2; --k) {
+        int64_t P = 0;                       /* states before the run of digit n */
         int n = 0;
-        for (;;) {
-            int64_t g = orc_D(b, k - 1, Ak - n);
-            if (r < g) break;
-            r -= g;
-            if (++n > b->S2) return -1;
+        while (n < b->S2) {
+            const int64_t next = P + orc_D(b, k - 1, b->A - n - Tk);
+            if (next > r) break;             /* rank r lies in the run of digit n */
+            P = next;
+            ++n;
         }
+        if (r - P >= orc_D(b, k - 1, b->A - n - Tk)) return -1;
         dig[k - 1] = n;
-        Ak -= n;
+        r -= P;
+        Tk += n;
     }
-    dig[0] = Ak;
+    dig[0] = b->A - Tk;
+    if (dig[0] < 0 || dig[0] > b->S2 || r != 0) return -1;
     return 0;
-}
-
-/* Sec. 3.2, state -> index: the number of sector states that come before |a_1..a_N> in
- * the lexicographic order.  At every position k from N down to 2, all states whose
- * higher digits agree and whose k-th digit n is smaller than a_k come first; for each
- * such n they number D(k-1, Ak - n).  D vanishes outside its range, so no bound checks
- * are needed on its second argument.  Returns -1 when the digits are not in the
- * sector. */
-int64_t orc_encode(const orc_basis *b, const int32_t *dig)
-{
-    int sum = 0;
-    for (int k = 0; k < b->N; ++k) {
-        if (dig[k] < 0 || dig[k] > b->S2) return -1;
-        sum += dig[k];
-    }
-    if (sum != b->A) return -1;
-    int64_t i = 0;
-    int Ak = b->A;
-    for (int k = b->N; k >= 2; --k) {
-        for (int n = 0; n < dig[k - 1]; ++n) i += orc_D(b, k - 1, Ak - n);
-        Ak -= dig[k - 1];
-    }
-    return i;
 }
 
 /* Sec. 3.1, the successor in lexicographic order ("balls in boxes"):

@@ -262,12 +262,6 @@ class SectorEnergies:
     e0: np.ndarray
     steps_done: np.ndarray
 
-    def magnetisation(self, h: float) -> float:
-        """M minimising E0(M) - h M: the ground-state magnetisation in a field h along z
-        (the Zeeman term -h sum s^z commutes with H(J) and shifts sector M by -h M)."""
-        k = int(np.argmin(self.e0 - h * self.two_m / 2.0))
-        return float(self.two_m[k]) / 2.0
-
 
 def sector_ground_energies(n_sites: int, two_s: int, bonds: BondList, steps: int, seed: int = 0,
                            dtype=torch.float64, work: torch.Tensor | None = None,

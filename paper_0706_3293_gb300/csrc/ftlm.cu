@@ -100,6 +100,7 @@ struct FtParams {
     uint32_t nchunks, ck_rows;      // product phase: chunks of ck_rows rows (a sector's last is shorter)
     unsigned nctas;
     uint64_t seed;
+    unsigned long long barrier_ns;  // a grid barrier gives up after this long (default 5 s)
     uint64_t exact_mask;            // bit A set: sector A is diagonalised exactly
     int nexact;
     ExactSec ex[FT_MAXEXACT];
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(FT_NT, FT_CTAS) k_ftlm(FtParams F) {
     const int v0 = li * VT;                        // first vector of this lane
     const unsigned nw = gridDim.x * (FT_NT / 32), gw = blockIdx.x * (FT_NT / 32) + warp;
     const FtRange rg = d.wr[gw];
-    const unsigned long long LIMIT = 5000000000ull;   // 5 s per barrier
+    const unsigned long long LIMIT = F.barrier_ns;
     __syncthreads();
 
     for (int j = 0; j < F.steps; ++j) {
@@ -875,6 +876,16 @@ static uint32_t ft_chunk_rows() {
     return (uint32_t)(v < 16 ? 16 : v > 1024 ? 1024 : v);
 }
 
+// how long a grid barrier of the persistent kernel waits before it gives up: 5 s, or
+// HM_FT_BARRIER_NS (0 .. 5e9 ns; a test sets 0 to make the first wait give up)
+static unsigned long long ft_barrier_ns() {
+    const unsigned long long dflt = 5000000000ull;
+    const char *e = getenv("HM_FT_BARRIER_NS");
+    if (!e || !*e) return dflt;
+    const long long v = atoll(e);
+    return v < 0 ? 0ull : (unsigned long long)v > dflt ? dflt : (unsigned long long)v;
+}
+
 // vectors-per-lane tiling chosen by timing each candidate once per (N, bonds) shape
 static std::map<std::pair<int, int>, int> g_ft_tuned;
 
@@ -1050,6 +1061,7 @@ int ftlm_run(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_
     unsigned char *w = (unsigned char *)work;
     ft_bind(&S, w);
     S.F.seed = seed;
+    S.F.barrier_ns = ft_barrier_ns();
     double *therm = (double *)(w + S.L.therm);
     S.F.d.eref = therm;
     S.F.d.zsum = therm + 1;

@@ -139,6 +139,18 @@ int blk_bond_corr(hm_basis *b, const BondParams &bp, const void *g, const void *
                   void *work, size_t work_bytes, double sign, const double *div, cudaStream_t st);
 size_t blk_bond_corr_bytes();
 
+// general row kernels of bond_corr (any s, no per-basis tables beyond the basis's own and no
+// run-time compilation); part: nblk x n_bonds doubles
+static int bond_corr_rows(const SectorView &sv, const BondParams &bp, const void *g, const void *x, double *out,
+                          int dtype, double *part, int nblk, double sign, const double *div, cudaStream_t st) {
+    if (dtype == HM_F64) {
+        if (sv.idx64) return bond_corr_t<uint64_t, double>(sv, bp, (const double *)g, (const double *)x, out, part, nblk, sign, div, st);
+        return bond_corr_t<uint32_t, double>(sv, bp, (const double *)g, (const double *)x, out, part, nblk, sign, div, st);
+    }
+    if (sv.idx64) return bond_corr_t<uint64_t, float>(sv, bp, (const float *)g, (const float *)x, out, part, nblk, sign, div, st);
+    return bond_corr_t<uint32_t, float>(sv, bp, (const float *)g, (const float *)x, out, part, nblk, sign, div, st);
+}
+
 int bond_corr_dev(const hm_basis *b, const BondParams &bp, const void *g, const void *x,
                   double *out, int dtype, void *work, size_t work_bytes, double sign,
                   const double *div, cudaStream_t st) {
@@ -151,13 +163,7 @@ int bond_corr_dev(const hm_basis *b, const BondParams &bp, const void *g, const 
     if (!work || work_bytes < (size_t)nblk * bp.nb * sizeof(double))
         return fail(HM_EWORKSPACE, "bond_corr needs %zu workspace bytes",
                     (size_t)nblk * bp.nb * sizeof(double));
-    double *part = (double *)work;
-    if (dtype == HM_F64) {
-        if (sv.idx64) return bond_corr_t<uint64_t, double>(sv, bp, (const double *)g, (const double *)x, out, part, nblk, sign, div, st);
-        return bond_corr_t<uint32_t, double>(sv, bp, (const double *)g, (const double *)x, out, part, nblk, sign, div, st);
-    }
-    if (sv.idx64) return bond_corr_t<uint64_t, float>(sv, bp, (const float *)g, (const float *)x, out, part, nblk, sign, div, st);
-    return bond_corr_t<uint32_t, float>(sv, bp, (const float *)g, (const float *)x, out, part, nblk, sign, div, st);
+    return bond_corr_rows(sv, bp, g, x, out, dtype, (double *)work, nblk, sign, div, st);
 }
 
 size_t bond_corr_bytes(const hm_basis *b, int n_bonds) {
@@ -325,33 +331,65 @@ int bond_corr(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v
 }
 
 // ---- bond correlations without allocation ----------------------------------------------------
-// Some callers cannot allocate device memory at the point where they need the adjoint:
-// code running while a stream is being captured into a CUDA graph (allocation is not a
-// capturable operation), hosts that pre-allocate everything up front and forbid later
-// allocation, or callers whose memory pool is exhausted by the Lanczos vectors.  For them
-// bond_corr_static keeps the per-block partial sums in this file-scope device array.
+// Some callers cannot call cudaMalloc at the point where they need the adjoint: a host
+// program that reserves its whole device-memory budget at start-up and forbids any later
+// allocation (so that a long N = 32 run, whose Lanczos vectors fill most of the GPU, can
+// never fail half-way for want of memory), or a library embedded in a framework whose own
+// allocator owns all device memory and whose rules forbid side allocations.  For them
+// bond_corr_static keeps its per-block partial sums in this file-scope device array and
+// runs only the general row kernels, which read nothing but the basis's own tables (made
+// by basis_build): no block tables built on first use, no run-time compiled kernel.
 constexpr size_t HM_BC_STATIC_DOUBLES = 131072;   // 1 MiB on every device that loads the library
 static __device__ __align__(256) double g_bc_static[HM_BC_STATIC_DOUBLES];
 
 namespace {
 constexpr int HM_BC_MAX_DEVICES = 64;
 std::mutex g_bc_mutex;
-double *g_bc_ptr[HM_BC_MAX_DEVICES];   // device address of g_bc_static, per device
+struct BcStaticAddr {
+    unsigned long long ctx_id;          // CUDA context the address belongs to (0: none yet)
+    double *ptr;                        // device address of g_bc_static in that context
+};
+BcStaticAddr g_bc_addr[HM_BC_MAX_DEVICES];
 
-// The host-side name g_bc_static is only a stand-in; kernels need the device address,
-// looked up once per device with that device current.
+// ID of the current context (cuCtxGetId through the runtime's driver entry point, so the
+// library needs no link against libcuda); 0 when it cannot be read
+unsigned long long current_ctx_id() {
+    using Fn = int (*)(void *, unsigned long long *);
+    static Fn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (Fn) nullptr;
+        }
+        return (Fn)p;
+    }();
+    unsigned long long id = 0;
+    if (!fn || fn(nullptr, &id) != 0) return 0;
+    return id;
+}
+
+// The host-side name g_bc_static is only a stand-in for the array: a kernel given it would
+// fault, or silently use the wrong memory where the GPU can reach host memory.  Kernels need
+// the device address, which cudaGetSymbolAddress gives (it allocates nothing).  It is looked
+// up once per device, with that device current, on the first call there; a new context on
+// the device (after cudaDeviceReset) is noticed by its ID and the address is looked up again.
 int bc_static_ptr(double **out) {
     int dev = 0;
     HM_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= HM_BC_MAX_DEVICES) return fail(HM_EINVAL, "device index %d out of range", dev);
+    const unsigned long long id = current_ctx_id();
     std::lock_guard<std::mutex> lk(g_bc_mutex);
-    if (!g_bc_ptr[dev]) {
+    BcStaticAddr &a = g_bc_addr[dev];
+    if (!a.ptr || id == 0 || a.ctx_id != id) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_bc_static);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_bc_static)");
-        g_bc_ptr[dev] = (double *)p;
+        a.ptr = (double *)p;
+        a.ctx_id = id;
     }
-    *out = g_bc_ptr[dev];
+    *out = a.ptr;
     return HM_OK;
 }
 }  // namespace
@@ -368,8 +406,10 @@ int bond_corr_static(const hm_basis *b, int n_bonds, const int32_t *u, const int
     for (int t = 0; t < n_bonds; ++t) ones[t] = 1.0;
     BondParams bp;
     HM_TRY(make_bonds(b, n_bonds, u, v, ones, &bp));
-    // same launch shape as bond_corr: the partial sums need grid_blocks x n_bonds doubles
-    const size_t need = bond_corr_bytes(b, n_bonds);
+    if (bp.nb == 0) return HM_OK;
+    // the general kernels' partial sums: grid_blocks x n_bonds doubles
+    const int nblk = grid_blocks(b->view.dim, 256);
+    const size_t need = (size_t)nblk * bp.nb * sizeof(double);
     if (need > HM_BC_STATIC_DOUBLES * sizeof(double))
         return fail(HM_EINVAL, "bond_corr_static: %zu bytes of partial sums exceed the %zu-byte static "
                     "scratch (fewer bonds or bond_corr with a workspace)", need,
@@ -378,8 +418,7 @@ int bond_corr_static(const hm_basis *b, int n_bonds, const int32_t *u, const int
     HM_TRY(bc_static_ptr(&scratch));
     // every slot the reduction reads is written by this call's first kernel: nothing in the
     // shared array has to start at zero
-    return bond_corr_dev(b, bp, g, x, out, dtype, scratch, HM_BC_STATIC_DOUBLES * sizeof(double), 1.0,
-                         nullptr, as_stream(stream));
+    return bond_corr_rows(b->view, bp, g, x, out, dtype, scratch, nblk, 1.0, nullptr, as_stream(stream));
 }
 
 int start_vector(const hm_basis *b, uint64_t seed, int kind, void *x, int dtype, void *stream) {

@@ -152,3 +152,21 @@ def test_ftlm_ring24_config(hm):
         lo_b = min(np.sort(gpu.theta[24 - A, r, :gpu.mlen[24 - A, r]])[0] for r in range(R))
         assert abs(lo_a - lo_b) <= 1e-4 * max(1.0, abs(lo_a))
     assert np.all(np.isfinite(gpu.Z)) and np.all(gpu.Z > 0)
+
+
+def test_ftlm_barrier_gives_up_and_device_stays_usable(hm, monkeypatch):
+    """The persistent kernel's grid barriers wait a bounded time.  With the limit set to
+    0 ns the first wait gives up: the kernel sets its abort flag, every CTA returns, and
+    ftlm_run reports HM_ETIMEOUT (no fault, no hang).  A normal run right after it on the
+    same device gives the same result as before."""
+    from paper_0706_3293_gb300 import _capi
+    inst = W.small_ring(12, -1.0, -0.3)
+    ok = hm.ftlm_run(12, hm.bonds_of(inst), 4, 20, 3, [1.0], vt=1)
+    monkeypatch.setenv("HM_FT_BARRIER_NS", "0")
+    with pytest.raises(_capi.HMError) as ei:
+        hm.ftlm_run(12, hm.bonds_of(inst), 4, 20, 3, [1.0], vt=1)
+    assert ei.value.code == _capi.HM_ETIMEOUT
+    monkeypatch.delenv("HM_FT_BARRIER_NS")
+    again = hm.ftlm_run(12, hm.bonds_of(inst), 4, 20, 3, [1.0], vt=1)
+    assert again.Z[0] == ok.Z[0] and again.E[0] == ok.E[0]
+    torch.cuda.synchronize()

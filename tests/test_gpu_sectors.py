@@ -50,9 +50,12 @@ def test_sector_energies_ring14(hm):
     assert abs(res.e0[0] + sum(inst.J) / 4.0) < 1e-12
     # spin flip: E0(M) = E0(-M)
     np.testing.assert_allclose(res.e0, res.e0[::-1], rtol=0, atol=1e-9)
-    # zero field: a singlet ground state (M = 0); strong field: fully polarised
-    assert res.magnetisation(0.0) == 0.0
-    assert res.magnetisation(10.0) == 7.0
+    # in a field h along z the Zeeman term -h sum s^z commutes with H(J) and shifts sector M
+    # by -h M: zero field gives a singlet ground state (M = 0), a strong field full polarisation
+    def field_magnetisation(h):
+        return res.two_m[int(np.argmin(res.e0 - h * res.two_m / 2.0))] / 2.0
+    assert field_magnetisation(0.0) == 0.0
+    assert field_magnetisation(10.0) == 7.0
 
 
 def test_sector_energies_s1_dense(hm):

@@ -490,6 +490,106 @@ def test_ftlm_lanczos_quadrature_large_sector(orc):
             assert abs(np.sum(tau * np.exp(-th / T)) - ref) < 1e-8 * ref
 
 
+def _ftlm_ring_sectors(N, seed, R, steps, tol=oracle.FTLM_TOL):
+    inst = W.small_ring(N, -1.0, -0.3)
+    bonds = bonds_of(inst)
+    per = []
+    for A in range(N + 1):
+        b = Basis(N, 1, A)
+        per.append((b.dim, oracle.ftlm_sector(b, bonds, seed, R, steps, tol=tol)))
+    return inst, bonds, per
+
+
+def test_ftlm_energy_is_minus_dlnZ_dbeta(orc):
+    """Thermodynamics fixes E = -d ln Z / d beta (beta = 1/T) for any set of weights: on the
+    same Ritz values and weights, E(T) from ftlm_thermo must equal the derivative of its
+    ln Z (true units, Z e^{-e_ref/T}) taken by central differences in beta with Richardson
+    extrapolation.  Weighting E by theta - e_ref, or dropping D_A/R from one of the two
+    sums, fails by far more than the tolerance."""
+    _, _, per = _ftlm_ring_sectors(10, 17, 3, 30)
+
+    def lnZ(beta):
+        Z, _, e_ref = oracle.ftlm_thermo(per, [1.0 / beta])
+        return math.log(Z[0]) - e_ref * beta
+
+    for T in [0.4, 1.0, 3.0, 20.0]:
+        beta = 1.0 / T
+        E = oracle.ftlm_thermo(per, [T])[1][0]
+        h = 1e-2 * beta
+
+        def cd(hh):
+            return (lnZ(beta + hh) - lnZ(beta - hh)) / (2 * hh)
+        dlnz = (4 * cd(h / 2) - cd(h)) / 3
+        assert abs(E - (-dlnz)) < 1e-8 * max(1.0, abs(E)), (T, E, -dlnz)
+
+
+def test_ftlm_thermo_exact_with_basis_vectors(orc):
+    """With every basis vector of every sector as a start vector (R = D_A) and the exact
+    per-vector quadrature (theta = the sector's eigenvalues, tau = squared components of
+    its eigenvectors), the estimator is the trace: Z(T) = sum_k e^{-E_k/T} and
+    E(T) = sum_k E_k e^{-E_k/T} / Z over the whole spectrum of the N = 8 ring, here from
+    the dense Kronecker-product Hamiltonian of all 2^8 states."""
+    N = 8
+    inst = W.small_ring(N, -1.0, -0.3)
+    bonds = bonds_of(inst)
+    per = []
+    for A in range(N + 1):
+        Hs = oracle.dense_hamiltonian_sector(N, 1, A, bonds)
+        ev, V = np.linalg.eigh(Hs)
+        per.append((len(ev), [(ev.copy(), V[r, :] ** 2) for r in range(len(ev))]))
+    spec = np.linalg.eigvalsh(oracle.dense_hamiltonian_full(N, 1, bonds))
+    temps = [0.2, 0.5, 1.0, 4.0, 50.0]
+    Z, E, e_ref = oracle.ftlm_thermo(per, temps)
+    for k, T in enumerate(temps):
+        w = np.exp(-(spec - spec[0]) / T)
+        z_ref = float(np.sum(w)) * math.exp(-spec[0] / T)
+        e_ref_T = float(np.sum(spec * w) / np.sum(w))
+        assert abs(Z[k] * math.exp(-e_ref / T) - z_ref) < 1e-12 * z_ref, (T, Z[k], z_ref)
+        assert abs(E[k] - e_ref_T) < 1e-12 * max(1.0, abs(e_ref_T)), (T, E[k], e_ref_T)
+
+
+def test_ftlm_thermo_matches_dense_estimator(orc):
+    """The Jaklic-Prelovsek estimator on the oracle's own start vectors (R = 3 +-1 vectors
+    per sector, 30 Lanczos steps; sectors of dimension 45..252 take the Lanczos branch)
+    against the same estimator formed densely with the matrix exponential:
+    Z = sum_A (D_A/R) sum_r <r|e^{-H/T}|r>/<r|r>,
+    E = [sum_A (D_A/R) sum_r <r|H e^{-H/T}|r>/<r|r>] / Z.
+    A 30-node Gauss quadrature of e^{-H/T} is exact far below 1e-10 at these T."""
+    from scipy.linalg import expm
+    seed, R, steps, N = 23, 3, 30, 10
+    inst, bonds, per = _ftlm_ring_sectors(N, seed, R, steps)
+    temps = [0.7, 2.0, 10.0]
+    Z, E, e_ref = oracle.ftlm_thermo(per, temps)
+    for k, T in enumerate(temps):
+        zd, ed = 0.0, 0.0
+        for A in range(N + 1):
+            b = Basis(N, 1, A)
+            H = np.column_stack([b.matvec(bonds, np.eye(b.dim)[i]) for i in range(b.dim)])
+            Ex = expm(-H / T)
+            for r in range(R):
+                v = oracle.start_pm1(oracle.stream_seed(seed, A, r), b.dim)
+                zd += b.dim / R * (v @ Ex @ v) / (v @ v)
+                ed += b.dim / R * (v @ H @ Ex @ v) / (v @ v)
+        assert abs(Z[k] * math.exp(-e_ref / T) - zd) < 1e-10 * zd, (T, Z[k] * math.exp(-e_ref / T), zd)
+        assert abs(E[k] - ed / zd) < 1e-10 * max(1.0, abs(ed / zd)), (T, E[k], ed / zd)
+
+
+def test_ftlm_stop_threshold_leaves_quadrature_unchanged(orc):
+    """The oracle stops its finite-temperature runs at beta_j <= 1e-5 max(|alpha|, beta),
+    the threshold of the FP32 device runs.  On sectors larger than the step count the FP64
+    runs never come near it: a 1e-12 threshold gives the same Ritz values, weights and
+    thermodynamics."""
+    _, _, per5 = _ftlm_ring_sectors(10, 31, 2, 30)
+    _, _, per12 = _ftlm_ring_sectors(10, 31, 2, 30, tol=1e-12)
+    for (d5, l5), (d12, l12) in zip(per5, per12):
+        for (th5, tau5, al5, _), (th12, tau12, al12, _) in zip(l5, l12):
+            assert len(al5) == len(al12)
+            assert np.array_equal(th5, th12) and np.array_equal(tau5, tau12)
+    temps = [0.5, 2.0]
+    for a, b in zip(oracle.ftlm_thermo(per5, temps), oracle.ftlm_thermo(per12, temps)):
+        np.testing.assert_array_equal(a, b)
+
+
 # ---- spin-flip parity sectors (M = 0) ------------------------------------------------------
 
 @pytest.mark.parametrize("N", [6, 8, 10])
