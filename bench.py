@@ -632,6 +632,20 @@ def run_arnoldi(args):
     return 0
 
 
+def launches_per_step(kname: str, dtype: str, momentum) -> int:
+    """Kernels one Lanczos step launches: product (+ second pass of the split product) and
+    the alpha reduction; update and beta reduction; on the FP64 block paths the fixed-point
+    copy of the new vector; on a momentum basis the product's separate epilogue."""
+    n = 4
+    if "+" in kname:
+        n += 1
+    if dtype == "f64" and ("blk_lz64" in kname or "s1_lz64" in kname):
+        n += 1
+    if momentum is not None:
+        n += 1
+    return n
+
+
 def splitmix64(seed: int, t: int) -> int:
     """Output t of SplitMix64 (Steele, Lea, Flood 2014) seeded with seed: the key of a
     finite-temperature start vector (sector A, vector r) is output A 2^20 + r of the run's
@@ -820,8 +834,9 @@ def run_ours(args):
                      "mean_launch_ms": mv_mean},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": b.dim * (8 if dtype == "f64" else 4) / args.steps,
                 "d2h_bytes_per_step": 16},
-        # per step: product, alpha, update, beta (+ the separate epilogue on a momentum basis)
-        "gpu_launches": (4 if momentum is None else 5) * args.steps,
+        # per step: the product (two passes when split), alpha, update, beta, and on the FP64
+        # block paths the fixed-point copy; on a momentum basis the product's epilogue
+        "gpu_launches": launches_per_step(kname, dtype, momentum) * args.steps,
         "clocks": clocks,
         "lanczos": {"alpha_last": float(al[-1]) if len(al) else None,
                     "steps_done": int(len(al)), "status": int(rc)},

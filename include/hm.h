@@ -209,7 +209,10 @@ int lanczos_read(hm_lanczos *run, double *alpha, double *beta, int *steps_done, 
 int lanczos_free(hm_lanczos *run);
 /* Name of the kernel that forms H q in each step of this run, NUL-terminated into
  * name[0..cap): "k_blk_lz64_jit" / "k_blk_lz32_jit" (s = 1/2 block product compiled for
- * this bond list at run time with NVRTC), "k_blk_lz64" / "k_blk_lz32" (the same block
+ * this bond list at run time with NVRTC), "k_blk_lz64a_jit+k_blk_lz64b_jit" (the same FP64
+ * product in two passes for sectors of 2^27 rows and more with couplings in integer ratios:
+ * the bonds reaching site N-7 or above in a second pass that visits the blocks with the top
+ * sites varying fastest; bit for bit the one-pass result; HM_BLK_SPLIT=0 turns it off), "k_blk_lz64" / "k_blk_lz32" (the same block
  * product reading its bonds from the parameters; used when NVRTC is unavailable or the
  * environment sets HM_JIT=0), "k_s1_lz64_jit" / "k_s1_lz32_jit" (s = 1 block product
  * compiled for the bond list), "k_s1_lz32" (its generic FP32 form) or "k_lz_matvec" (row
@@ -243,8 +246,12 @@ int lanczos_run(const hm_basis *basis, int n_bonds, const int32_t *u, const int3
  * of T (host, 2sN + 1 entries); steps_done[A] (host, may be NULL) = the run's length, less
  * than `steps` when the sector's Krylov space is exhausted (then e0[A] is exact).  The
  * paper has no routine of this name: its applications (Sec. 1) use this curve E0(M).
- * work: device memory of sector_ground_energies_workspace bytes, reused by every sector.
- * Synchronises the stream once per sector.  Errors as lanczos_run. */
+ * All 2sN + 1 runs are the branches of one CUDA graph, launched once on the stream: the
+ * sectors are independent, so the small ones run side by side, and the lowest Ritz value of
+ * each is found on the device (Sturm bisection).  work: device memory of
+ * sector_ground_energies_workspace bytes (every sector's Lanczos workspace, back to back,
+ * plus 24 bytes a sector of results), 256-byte aligned.  Synchronises the stream once, at
+ * the end.  Errors as lanczos_run. */
 int sector_ground_energies_workspace(int n_sites, int two_s, int steps, int dtype, size_t *bytes);
 int sector_ground_energies(int n_sites, int two_s, int n_bonds, const int32_t *u, const int32_t *v,
                            const double *J, int steps, uint64_t seed, int dtype, void *work,

@@ -152,8 +152,11 @@ static void blk_plan_slots(const BondParams &bp, const std::vector<int> &bc, int
     }
 }
 
-int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P, bool bond_corr) {
+static int blk_plan_bonds(hm_basis *b, const BondParams &bp, const std::vector<int> &bc, int K, BlkParams *P);
+
+int blk_plan(hm_basis *b, const BondParams &bp_all, int K, BlkParams *P, bool bond_corr, uint64_t use) {
     const SectorView &sv = b->view;
+    const BondParams &bp = bp_all;
     if (sv.S2 != 1 || sv.N > 32 || sv.N < K + 2 || K < 8 || K > 16 || bp.nb > HM_BLK_MAXB ||
         sv.idx64)
         return 1;
@@ -227,6 +230,29 @@ int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *P, bool bond_c
             P->g0_exp = ex - 1;                       // g0 = 2^(ex-1) when a power of two
         }
     }
+    // the bonds this plan applies (a subset only on the class path, where the classes and
+    // their integer ratios above come from the whole list)
+    if (use != ~0ull && (P->perbond || bp.nb > 64)) return 1;
+    BondParams sub = bp;
+    std::vector<int> sbc;
+    sub.nb = 0;
+    for (int t = 0; t < bp.nb; ++t) {
+        if (t < 64 && !((use >> t) & 1ull)) continue;
+        sub.p[sub.nb] = bp.p[t]; sub.q[sub.nb] = bp.q[t];
+        sub.jm[sub.nb] = bp.jm[t]; sub.jmf[sub.nb] = bp.jmf[t];
+        ++sub.nb;
+        sbc.push_back(bc[t]);
+    }
+    if (use != ~0ull) {
+        for (int c = 0; c < HM_BLK_MAXC; ++c) P->ntot[c] = 0;
+        for (int t = 0; t < sub.nb; ++t) P->ntot[sbc[t]]++;
+    }
+    return blk_plan_bonds(b, sub, sbc, K, P);
+}
+
+// the slots, groups and tables of a plan whose classes are set: bonds bp with classes bc
+static int blk_plan_bonds(hm_basis *b, const BondParams &bp, const std::vector<int> &bc, int K, BlkParams *P) {
+    const SectorView &sv = b->view;
     // low groups keyed by (class, type, d); high and cross bonds by class
     std::map<std::tuple<int, int, int>, uint32_t> groups;
     std::vector<std::tuple<int, int, int>> hi[HM_BLK_MAXC], cr[HM_BLK_MAXC];   // (p, q, bond)
@@ -392,15 +418,15 @@ int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int 
 }
 
 // kernel specialised to the plan (jit.cu), with its launch attributes; 1 = not available
-int jit_lz_kernel(const BlkParams &P, int dtype, const BondParams &bp, const void **kern);
+int jit_lz_kernel(const BlkParams &P, int dtype, const BondParams &bp, const void **kern, int split = 0);
 int jit_mv_kernel(const BlkParams &P, int dtype, const BondParams &bp, const void **kern);
 // pad elements after the staged rows of a specialised kernel (jit.cu)
 int jit_pad(const void *kern);
 
-int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void **kern, int *blocks) {
+int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void **kern, int *blocks, int split) {
     *kern = nullptr;
     const void *k = nullptr;
-    if (jit_lz_kernel(P, dtype, bp, &k) != 0) return 1;
+    if (jit_lz_kernel(P, dtype, bp, &k, split) != 0) return 1;
     const size_t sm = blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4, jit_pad(k));
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
         cudaGetLastError();
@@ -413,6 +439,38 @@ int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void *
     }
     *blocks = std::min<int>(sm_count() * per, 1 << P.H);
     *kern = k;
+    return 0;
+}
+
+// Split FP64 product for large s = 1/2 sectors with integer-ratio couplings.  In one pass
+// the exchanges that reach the top high sites gather blocks far away in the row order, which
+// have left L2 by then (about 105 bytes of DRAM traffic per row at N = 32 against 16).  The
+// bonds with an end at site N - 7 or above therefore go to a second pass, which takes the
+// blocks with the top high sites varying fastest (rot = 9), so that those targets are
+// neighbours in time; the first pass keeps the row order for the rest.  Pass 1 leaves the
+// exact integer row sums of its bonds in Y, pass 2 adds its own and rounds once: the result
+// is the single pass's, bit for bit.  HM_BLK_SPLIT = 0 turns the split off, 1 applies it
+// wherever it is possible (default: sectors of 2^27 rows and more).  Returns 0 with both
+// plans and their specialised kernels, 1 when the split does not apply.
+int blk_lz_split(hm_basis *b, const BondParams &bp, const BlkParams &P, int dtype, BlkParams *PA, BlkParams *PB,
+                 const void **kA, const void **kB, int *blkA, int *blkB) {
+    const char *e = getenv("HM_BLK_SPLIT");
+    const int mode = e && *e ? atoi(e) : -1;
+    if (mode == 0 || dtype != HM_F64) return 1;
+    if (mode < 0 && P.dim < (1u << 27)) return 1;
+    if (!P.iratio || !P.g0_pow2 || P.perbond || P.par || bp.nb > 64 || !P.rows_ok) return 1;
+    const int S = P.N - 7;
+    const uint64_t all = bp.nb == 64 ? ~0ull : ((1ull << bp.nb) - 1ull);
+    uint64_t far = 0;
+    for (int t = 0; t < bp.nb; ++t)
+        if (std::max(bp.p[t], bp.q[t]) >= S) far |= 1ull << t;
+    if (far == 0 || far == all) return 1;
+    if (blk_plan(b, bp, P.K, PA, false, all & ~far) != 0 || blk_plan(b, bp, P.K, PB, false, far) != 0) return 1;
+    if (!PA->rows_ok || !PB->rows_ok || !PA->iratio || !PB->iratio) return 1;
+    PA->split = 1;
+    PB->split = 2;
+    PB->rot = std::min(PB->H, 9);
+    if (blk_lz_jit(*PA, dtype, bp, kA, blkA, 1) != 0 || blk_lz_jit(*PB, dtype, bp, kB, blkB, 2) != 0) return 1;
     return 0;
 }
 

@@ -30,8 +30,11 @@
 
 namespace hm {
 
-// host: builds the plan; returns 0 if the bond list and sector take the fast path
-int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *out, bool bond_corr = false);
+// host: builds the plan; returns 0 if the bond list and sector take the fast path.  use:
+// bit t set = bond t is applied (a pass of the two-pass product applies a subset; the
+// coupling classes always come from the whole list, so both passes share them)
+int blk_plan(hm_basis *b, const BondParams &bp, int K, BlkParams *out, bool bond_corr = false,
+             uint64_t use = ~0ull);
 
 // ---- device helpers ----------------------------------------------------------------------
 __device__ __forceinline__ BlkTabs stage_blk_tables(const BlkParams &P, unsigned char *smem) {

@@ -83,6 +83,11 @@ struct BlkParams {
     // bond-correlation plan (one chunk of bonds, per-bond slots): the block setup keeps the
     // high targets uncompacted, hbi[j] for high bond j or ~0 when its spins are parallel
     int bcmode;
+    // two-pass FP64 Lanczos product (integer-ratio classes): pass 1 applies the near bonds
+    // and stores each row's exact integer class sum, pass 2 adds the far bonds (those
+    // reaching the top sites) and rounds once.  rot: pass 2 takes the blocks in the order of
+    // the high word rotated so that its top rot bits vary fastest
+    int split, rot;
 };
 
 

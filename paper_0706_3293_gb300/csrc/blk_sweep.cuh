@@ -172,10 +172,22 @@ __device__ __forceinline__ bool blk_h_valid(const BlkParams &P, uint32_t h) {
     return k >= 0 && k <= P.K;
 }
 
-// next block of the dynamic schedule (in increasing h, i.e. increasing row index)
+// block of schedule position c: h = c, or (P.rot > 0) c with its low rot bits moved to the
+// top of the high word, so that the top rot high sites vary fastest along the schedule
+__device__ __forceinline__ uint32_t blk_order(const BlkParams &P, uint32_t c) {
+    if (!P.rot) return c;
+    const int R = P.rot;
+    return (c >> R) | ((c & ((1u << R) - 1u)) << (P.H - R));
+}
+
+// next block of the dynamic schedule (positions handed out in increasing order; without
+// rotation that is increasing h, i.e. increasing row index); >= nH when none is left
 __device__ __forceinline__ uint32_t blk_fetch(const BlkParams &P, unsigned *sched, uint32_t nH) {
-    uint32_t h;
-    do { h = atomicAdd(&sched[0], 1u); } while (h < nH && !blk_h_valid(P, h));
+    uint32_t c, h;
+    do {
+        c = atomicAdd(&sched[0], 1u);
+        h = c < nH ? blk_order(P, c) : c;
+    } while (c < nH && !blk_h_valid(P, h));
     return h;
 }
 
@@ -542,12 +554,60 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // part[h] = (q . H q) over the rows of block h, in true units; entries of blocks that do
-// not exist stay as they are
-template <int NC, bool IR, class Row>
+// not exist stay as they are.
+// SPLIT = 1 / 2: the two passes of the split product (integer-ratio classes with a power-of-
+// two unit g0).  Pass 1 (plan of the near bonds) stores each row's exact integer
+// sum_c K_c T_c in Y; pass 2 (plan of the far bonds, rotated block order) adds its own,
+// rounds the total once to binary64 in place and forms q.Hq from it.  The total is the same
+// integer the single pass forms, so both give the same bits.
+template <int NC, bool IR, class Row, int SPLIT = 0>
 __device__ __forceinline__ void lz64_body(const BlkParams &P, const long long *__restrict__ Xc,
                                           unsigned long long *__restrict__ Y, LzScalars *S, int pc,
                                           double *__restrict__ part) {
     if (S->done) return;
+    if constexpr (SPLIT != 0) {
+        static_assert(IR && !Row::kPerBond, "the split product needs integer-ratio classes");
+        const int E = S->emax[pc];
+        const int u = E - 1022 - ef::FIX_BITS;
+        auto tsum = [&](int64_t xo, const int64_t *acc, const int *cnt) {
+            int64_t Tc[NC];
+            blk_classes<NC>(P, acc, cnt, xo, Tc);
+            int64_t s = 0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) s += (int64_t)P.Kc[c] * Tc[c];
+            return s;
+        };
+        if constexpr (SPLIT == 1) {
+            blk_sweep<int64_t, NC, true, Row>(
+                P, (const unsigned char *)Xc, GFix{}, S->sched, [](uint32_t) { return 0; },
+                [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt, int) {
+                    __stcs(Y + off + r, (unsigned long long)tsum(xo, acc, cnt));
+                },
+                [](int) {}, [](uint32_t, int) {});
+        } else {
+            __int128 d1 = 0;
+            blk_sweep<int64_t, NC, true, Row>(
+                P, (const unsigned char *)Xc, GFix{}, S->sched,
+                [&](uint32_t i) { return (long long)__ldcs(Y + i); },
+                [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt, long long sa) {
+                    const int64_t s = (int64_t)sa + tsum(xo, acc, cnt);
+                    __stcs(Y + off + r, ef::bits_from_int(s, u + P.g0_exp));
+                    d1 += (__int128)xo * s;
+                },
+                [&](int it) {
+                    const double q_y = ldexp(i128_to_double(d1) * P.g0, 2 * u);
+                    d1 = 0;
+                    const double a = warp_sum(q_y);
+                    if ((threadIdx.x & 31) == 0) s_wpart[it & 1][threadIdx.x >> 5][0] = a;
+                },
+                [&](uint32_t h, int it) {
+                    double a = 0.0;
+                    for (int w = 0; w < BLK_NT / 32; ++w) a += s_wpart[it & 1][w][0];
+                    part[h] = a;
+                });
+        }
+        return;
+    }
     const int E = S->emax[pc];
     const int u = E - 1022 - ef::FIX_BITS;
     __int128 d1 = 0;

@@ -621,10 +621,13 @@ int jit_bc_kernel(const BlkParams &P, int dtype, int nbk, const void **kern) {
     return jit_get(src, "k_blk_bc_jit", dev, BLK_XPAD, kern);
 }
 
-int jit_lz_kernel(const BlkParams &P, int dtype, const BondParams &bp, const void **kern) {
+// split = 1 / 2: the passes of the split FP64 product (k_blk_lz64a_jit / k_blk_lz64b_jit,
+// plans of the near and of the far bonds; blk_sweep.cuh, lz64_body)
+int jit_lz_kernel(const BlkParams &P, int dtype, const BondParams &bp, const void **kern, int split) {
     const char *env = getenv("HM_JIT");
     if (env && env[0] == '0') return 1;
     if (!P.rows_ok) return 1;
+    if (split && (dtype != HM_F64 || !P.iratio || !P.g0_pow2 || P.perbond || P.par)) return 1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
     std::string src;
@@ -632,18 +635,19 @@ int jit_lz_kernel(const BlkParams &P, int dtype, const BondParams &bp, const voi
     if (!jit_row_source(P, bp, &src, &delta)) return 1;
     const bool f64 = dtype == HM_F64;
     const int nc = P.nc == 1 ? 1 : (P.nc == 2 ? 2 : 4);
-    const char *name = f64 ? "k_blk_lz64_jit" : "k_blk_lz32_jit";
+    const char *name = !f64 ? "k_blk_lz32_jit" : split == 1 ? "k_blk_lz64a_jit" : split == 2 ? "k_blk_lz64b_jit"
+                                                                                         : "k_blk_lz64_jit";
     // resident CTAs per SM the register budget is cut for (3: 40 registers a thread, 2: 64);
     // HM_JIT_CTAS overrides the default
     int ctas = 3;
     if (const char *e = getenv("HM_JIT_CTAS")) ctas = atoi(e) == 2 ? 2 : 3;
     if (f64)
         put(src,
-            "extern \"C\" __global__ void __launch_bounds__(512, %d) k_blk_lz64_jit(hm::BlkParams P,\n"
+            "extern \"C\" __global__ void __launch_bounds__(512, %d) %s(hm::BlkParams P,\n"
             "        const long long *__restrict__ Xc, unsigned long long *__restrict__ Y, hm::LzScalars *S, int pc,\n"
             "        double *__restrict__ part) {\n"
-            "    hm::lz64_body<%d, %s, RowJit>(P, Xc, Y, S, pc, part);\n}\n",
-            ctas, nc, P.iratio && !P.perbond ? "true" : "false");
+            "    hm::lz64_body<%d, %s, RowJit, %d>(P, Xc, Y, S, pc, part);\n}\n",
+            ctas, name, nc, P.iratio && !P.perbond ? "true" : "false", split);
     else
         put(src,
             "extern \"C\" __global__ void __launch_bounds__(512, %d) k_blk_lz32_jit(hm::BlkParams P,\n"

@@ -14,7 +14,9 @@
 namespace hm {
 
 int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int *blocks);
-int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void **kern, int *blocks);
+int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void **kern, int *blocks, int split = 0);
+int blk_lz_split(hm_basis *b, const BondParams &bp, const BlkParams &P, int dtype, BlkParams *PA, BlkParams *PB,
+                 const void **kA, const void **kB, int *blkA, int *blkB);
 int blk_K(const hm_basis *b);   // blk.cu: split position of the block path
 int blk_lz64_launch(const BlkParams &P, const long long *Xc, unsigned long long *Y, LzScalars *S, int pc,
                     double *part, int blocks, cudaStream_t st, const void *jit);
@@ -107,6 +109,10 @@ struct hm_lanczos {
     hm::BlkParams blk;      // s = 1/2 block path (use_blk)
     int use_blk, blk_blocks;
     const void *jit;        // block product specialised to the bonds (jit.cu), or nullptr
+    // split FP64 product (blk_lz_split): blk / jit / blk_blocks are pass 1, these pass 2
+    int split, blk_blocks2;
+    hm::BlkParams blk2;
+    const void *jit2;
     int run;                // rows per thread run of the general product (row_runs)
     int use_s1;             // s = 1 block path (s1blk.cu)
     int use_mom;            // momentum basis: product k_mom_matvec, then the epilogue kernel
@@ -600,6 +606,8 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
             k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, s1part, R->s1.nblocks, R->qqp, nblk, R->alpha, pprev);
         } else if (b64) {
             HM_TRY(blk_lz64_launch(R->blk, xs[parity], Y, R->sc, parity, R->hpart, R->blk_blocks, st, R->jit));
+            if (R->split)
+                HM_TRY(blk_lz64_launch(R->blk2, xs[parity], Y, R->sc, parity, R->hpart, R->blk_blocks2, st, R->jit2));
             k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->qqp, nblk, R->alpha, pprev);
         } else if (R->use_blk) {
             HM_TRY(blk_lz32_launch(R->blk, (const float *)qc, (float *)qp, R->sc, R->hpart, R->blk_blocks, st, R->jit));
@@ -729,6 +737,18 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
         if (blk_lz_jit(R->blk, dtype, R->bp, &jk, &jb) == 0) { R->jit = jk; R->blk_blocks = jb; }
         if (R->blk.perbond && !R->jit) R->use_blk = 0;   // per-bond rows run only specialised
     }
+    R->split = 0;
+    R->jit2 = nullptr;
+    if (R->use_blk && R->jit && R->L.shadow) {
+        BlkParams pa, pb;
+        const void *ka = nullptr, *kb = nullptr;
+        int na = 0, nb2 = 0;
+        if (blk_lz_split(const_cast<hm_basis *>(b), R->bp, R->blk, dtype, &pa, &pb, &ka, &kb, &na, &nb2) == 0) {
+            R->blk = pa; R->jit = ka; R->blk_blocks = na;
+            R->blk2 = pb; R->jit2 = kb; R->blk_blocks2 = nb2;
+            R->split = 1;
+        }
+    }
     R->use_s1 = 0;
     if (!R->use_blk && !R->use_mom && R->L.s1part) {
         rc = s1_plan(const_cast<hm_basis *>(b), R->bp, &R->s1);
@@ -783,6 +803,79 @@ static int run_steps_graph(hm_lanczos *R, int steps, cudaStream_t st) {
     if (ge) cudaGraphExecDestroy(ge);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cap);
+    return rc;
+}
+
+// lowest Ritz value, steps done and status of one run (device, out[0..2]); NaN without steps
+__global__ void k_branch_out(const LzScalars *S, const double *alpha, const double *beta, double *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int m = S->j;
+    out[0] = m >= 1 ? tri_eig(m, alpha, beta, 1) : __longlong_as_double(0x7ff8000000000000ll);
+    out[1] = (double)m;
+    out[2] = (double)S->status;
+}
+
+size_t lz_run_workspace(const hm_basis *b, int dtype, int steps) { return lz_layout(b, dtype, steps, false, 0).total; }
+
+// One Lanczos run per basis, each from the uniform start vector of its seed, each on a branch
+// of its own in one captured graph that is launched once on st (the branches are
+// independent, so small runs overlap on the GPU).  Run i uses work[offs[i], offs[i] + its
+// workspace) and leaves its lowest Ritz value, steps done and status in out[3i .. 3i+2]
+// (device).  Everything is planned (and specialised kernels compiled) before the capture;
+// st is synchronised once, after the graph, before this returns.
+int lz_branches(const std::vector<const hm_basis *> &bases, int n_bonds, const int32_t *u, const int32_t *v,
+                const double *J, const std::vector<uint64_t> &seeds, int steps, int dtype, unsigned char *work,
+                const std::vector<size_t> &offs, double *out, cudaStream_t st) {
+    const int n = (int)bases.size();
+    std::vector<hm_lanczos *> runs(n, nullptr);
+    std::vector<cudaStream_t> br(n, nullptr);
+    std::vector<cudaEvent_t> done(n, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    int rc = HM_OK;
+    for (int i = 0; i < n && rc == HM_OK; ++i)
+        rc = lz_create(bases[i], n_bonds, u, v, J, dtype, steps, work + offs[i], lz_run_workspace(bases[i], dtype, steps),
+                       false, &runs[i]);
+    cudaError_t e = cudaSuccess;
+    if (rc == HM_OK && (e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) rc = cuda_fail(e, "stream");
+    if (rc == HM_OK && (e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess) rc = cuda_fail(e, "event");
+    for (int i = 0; i < n && rc == HM_OK; ++i) {
+        if ((e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking)) != cudaSuccess) rc = cuda_fail(e, "stream");
+        else if ((e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming)) != cudaSuccess) rc = cuda_fail(e, "event");
+    }
+    if (rc == HM_OK) {
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamBeginCapture");
+        else {
+            if ((e = cudaEventRecord(fork, cap)) != cudaSuccess) rc = cuda_fail(e, "fork");
+            for (int i = 0; i < n && rc == HM_OK; ++i) {
+                if ((e = cudaStreamWaitEvent(br[i], fork, 0)) != cudaSuccess) { rc = cuda_fail(e, "branch"); break; }
+                rc = enqueue_start(runs[i], nullptr, seeds[i], br[i]);
+                for (int k = 0; k < steps && rc == HM_OK; ++k) rc = enqueue_step(runs[i], br[i]);
+                if (rc != HM_OK) break;
+                k_branch_out<<<1, 32, 0, br[i]>>>(runs[i]->sc, runs[i]->alpha, runs[i]->beta, out + 3 * i);
+                if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_fail(e, "k_branch_out"); break; }
+                if ((e = cudaEventRecord(done[i], br[i])) != cudaSuccess || (e = cudaStreamWaitEvent(cap, done[i], 0)) != cudaSuccess)
+                    rc = cuda_fail(e, "join");
+            }
+            cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+            if (rc == HM_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
+        }
+    }
+    if (rc == HM_OK && (e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+    if (rc == HM_OK && (e = cudaGraphLaunch(ge, st)) != cudaSuccess) rc = cuda_fail(e, "cudaGraphLaunch");
+    if (rc == HM_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "sectors");
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    for (int i = 0; i < n; ++i) {
+        if (done[i]) cudaEventDestroy(done[i]);
+        if (br[i]) cudaStreamDestroy(br[i]);
+        delete runs[i];
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (cap) cudaStreamDestroy(cap);
     return rc;
 }
 
@@ -860,6 +953,7 @@ int lanczos_kernel_name(const hm_lanczos *R, char *name, int cap) {
     const char *n = R->use_mom ? "k_mom_matvec"
                     : R->use_s1 ? s1_kernel_name(R->s1, f64 ? 2 : 1)
                     : !R->use_blk ? "k_lz_matvec"
+                    : R->split  ? "k_blk_lz64a_jit+k_blk_lz64b_jit"
                     : R->jit    ? (f64 ? "k_blk_lz64_jit" : "k_blk_lz32_jit")
                                 : (f64 ? "k_blk_lz64" : "k_blk_lz32");
     snprintf(name, (size_t)cap, "%s", n);

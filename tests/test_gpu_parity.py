@@ -503,21 +503,56 @@ def test_lanczos_full_size_majumdar_ghosh_f32(hm):
 @pytest.mark.slow
 def test_block_product_specialised_equals_generic_full_size(hm, monkeypatch):
     """At N = 32 (the bench's launch configuration: dynamic block schedule over 131,070
-    blocks, 456 CTAs) the specialised and the generic FP64 block products give the same
-    Lanczos coefficients bit for bit over 4 steps."""
+    blocks, 456 CTAs) the split specialised product (the default there), the one-pass
+    specialised product and the generic FP64 block product give the same Lanczos
+    coefficients bit for bit over 4 steps."""
     inst = W.j1j2_ring32()
     b = hm.Basis(32, 1, 0)
     out = {}
-    for mode in ("1", "0"):
-        monkeypatch.setenv("HM_JIT", mode)
+    for mode, env in (("split", {}), ("one", {"HM_BLK_SPLIT": "0"}), ("generic", {"HM_JIT": "0"})):
+        monkeypatch.delenv("HM_BLK_SPLIT", raising=False)
+        monkeypatch.delenv("HM_JIT", raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
         run = hm.LanczosRun(b, hm.bonds_of(inst), 4, seed=inst.seed)
         name = run.kernel_name()
         run.step(4)
         out[mode] = (name, run.read())
         run.close()
-    assert out["1"][0] == "k_blk_lz64_jit" and out["0"][0] == "k_blk_lz64"
+        torch.cuda.empty_cache()
+    assert out["split"][0] == "k_blk_lz64a_jit+k_blk_lz64b_jit"
+    assert out["one"][0] == "k_blk_lz64_jit" and out["generic"][0] == "k_blk_lz64"
+    (a1, b1, _) = out["split"][1]
+    for mode in ("one", "generic"):
+        a0, b0, _ = out[mode][1]
+        assert np.array_equal(a1, a0) and np.array_equal(b1, b0), mode
+
+
+@pytest.mark.parametrize("N,j2,two_m", [(20, -0.5, 0), (22, -0.25, 2), (24, -0.5, 0), (26, -0.5, 4)])
+def test_split_product_equals_one_pass(hm, N, j2, two_m, monkeypatch):
+    """The split FP64 product (near bonds in a first pass that leaves exact integer row
+    sums, the bonds reaching site N-7 and above in a second pass over the blocks in rotated
+    order) forced on smaller sectors: 40 Lanczos steps bit for bit equal to the one-pass
+    product, whose first steps match the oracle."""
+    inst = W.small_ring(N, -1.0, j2)
+    b = hm.Basis(N, 1, two_m)
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("HM_BLK_SPLIT", mode)
+        run = hm.LanczosRun(b, hm.bonds_of(inst), 40, seed=5)
+        name = run.kernel_name()
+        run.step(40)
+        out[mode] = (name, run.read())
+        run.close()
+    assert out["1"][0] == "k_blk_lz64a_jit+k_blk_lz64b_jit", out["1"][0]
+    assert out["0"][0] == "k_blk_lz64_jit"
     (a1, b1, _), (a0, b0, _) = out["1"][1], out["0"][1]
     assert np.array_equal(a1, a0) and np.array_equal(b1, b0)
+    if N <= 22:
+        ob = oracle.Basis(N, 1, (N - two_m) // 2)
+        al, be = ob.lanczos(obonds(inst), oracle.start_uniform(5, ob.dim), 20)
+        np.testing.assert_allclose(a1[:20], al, rtol=0, atol=1e-11 * np.abs(al).max())
+        np.testing.assert_allclose(b1[:20], be, rtol=0, atol=1e-11 * np.abs(al).max())
 
 
 # ---- per-bond plans: more distinct couplings than the block path's classes ---------------

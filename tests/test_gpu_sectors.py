@@ -79,3 +79,32 @@ def test_sector_energies_fp32(hm):
     r64 = hm.sector_ground_energies(14, 1, hm.bonds_of(inst), 120, seed=9)
     r32 = hm.sector_ground_energies(14, 1, hm.bonds_of(inst), 120, seed=9, dtype=torch.float32)
     np.testing.assert_allclose(r32.e0, r64.e0, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("N,steps", [(16, 90), (24, 100)])
+def test_sector_graph_equals_separate_runs(hm, N, steps):
+    """The one-graph driver runs each sector on a branch of its own with the same kernels and
+    start vector (stream seed(seed, A 2^20)) as a separate lanczos_run of that sector, so
+    every sector's lowest Ritz value and step count agree bit for bit; the graph is timed
+    against the separate runs."""
+    import time
+    inst = W.small_ring(N, -1.0, -0.5)
+    bl = hm.bonds_of(inst)
+    seed = 1234
+    hm.sector_ground_energies(N, 1, bl, steps, seed=seed)            # plans and kernels ready
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = hm.sector_ground_energies(N, 1, bl, steps, seed=seed)
+    t_graph = time.perf_counter() - t0
+    t_sep = 0.0
+    for A in range(N + 1):
+        b = hm.Basis(N, 1, N - 2 * A)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = hm.lanczos_run(b, bl, steps, seed=oracle.stream_seed(seed, A, 0), n_ritz=1)
+        t_sep += time.perf_counter() - t0
+        assert res.steps_done[A] == r.steps_done, A
+        assert res.e0[A] == r.ritz[0], (A, res.e0[A], r.ritz[0])
+    print(f"N={N}: {N + 1} sectors x {steps} steps: one graph {t_graph * 1e3:.1f} ms, "
+          f"separate runs {t_sep * 1e3:.1f} ms")
+    np.testing.assert_allclose(res.e0, res.e0[::-1], rtol=0, atol=1e-9 * np.abs(res.e0).max())
