@@ -210,9 +210,9 @@ int lanczos_free(hm_lanczos *run);
 /* Name of the kernel that forms H q in each step of this run, NUL-terminated into
  * name[0..cap): "k_blk_lz64_jit" / "k_blk_lz32_jit" (s = 1/2 block product compiled for
  * this bond list at run time with NVRTC), "k_blk_lz64a_jit+k_blk_lz64b_jit" (the same FP64
- * product in two passes for sectors of 2^27 rows and more with couplings in integer ratios:
- * the bonds reaching site N-7 or above in a second pass that visits the blocks with the top
- * sites varying fastest; bit for bit the one-pass result; HM_BLK_SPLIT=0 turns it off), "k_blk_lz64" / "k_blk_lz32" (the same block
+ * product in two passes, for couplings in integer ratios, when the environment sets
+ * HM_BLK_SPLIT=1: the bonds reaching site N-7 or above in a second pass that visits the
+ * blocks with the top sites varying fastest; bit for bit the one-pass result), "k_blk_lz64" / "k_blk_lz32" (the same block
  * product reading its bonds from the parameters; used when NVRTC is unavailable or the
  * environment sets HM_JIT=0), "k_s1_lz64_jit" / "k_s1_lz32_jit" (s = 1 block product
  * compiled for the bond list), "k_s1_lz32" (its generic FP32 form) or "k_lz_matvec" (row

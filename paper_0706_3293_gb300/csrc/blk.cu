@@ -449,15 +449,18 @@ int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void *
 // blocks with the top high sites varying fastest (rot = 9), so that those targets are
 // neighbours in time; the first pass keeps the row order for the rest.  Pass 1 leaves the
 // exact integer row sums of its bonds in Y, pass 2 adds its own and rounds once: the result
-// is the single pass's, bit for bit.  HM_BLK_SPLIT = 0 turns the split off, 1 applies it
-// wherever it is possible (default: sectors of 2^27 rows and more).  Returns 0 with both
-// plans and their specialised kernels, 1 when the split does not apply.
+// is the single pass's, bit for bit.  Measured at N = 32 the split cuts DRAM traffic but
+// takes longer (20.0 against 18.6 ms per product): the one-pass kernel is bound by its
+// shared-memory wavefronts and issue, not by DRAM, and the second pass repeats the per-block
+// work.  So it is off unless HM_BLK_SPLIT = 1 asks for it (2 applies it only to sectors of
+// 2^27 rows and more).  Returns 0 with both plans and their specialised kernels, 1 when the
+// split does not apply.
 int blk_lz_split(hm_basis *b, const BondParams &bp, const BlkParams &P, int dtype, BlkParams *PA, BlkParams *PB,
                  const void **kA, const void **kB, int *blkA, int *blkB) {
     const char *e = getenv("HM_BLK_SPLIT");
-    const int mode = e && *e ? atoi(e) : -1;
-    if (mode == 0 || dtype != HM_F64) return 1;
-    if (mode < 0 && P.dim < (1u << 27)) return 1;
+    const int mode = e && *e ? atoi(e) : 0;
+    if ((mode != 1 && mode != 2) || dtype != HM_F64) return 1;
+    if (mode == 2 && P.dim < (1u << 27)) return 1;
     if (!P.iratio || !P.g0_pow2 || P.perbond || P.par || bp.nb > 64 || !P.rows_ok) return 1;
     const int S = P.N - 7;
     const uint64_t all = bp.nb == 64 ? ~0ull : ((1ull << bp.nb) - 1ull);

@@ -503,13 +503,13 @@ def test_lanczos_full_size_majumdar_ghosh_f32(hm):
 @pytest.mark.slow
 def test_block_product_specialised_equals_generic_full_size(hm, monkeypatch):
     """At N = 32 (the bench's launch configuration: dynamic block schedule over 131,070
-    blocks, 456 CTAs) the split specialised product (the default there), the one-pass
-    specialised product and the generic FP64 block product give the same Lanczos
-    coefficients bit for bit over 4 steps."""
+    blocks, 456 CTAs) the one-pass specialised product (the default), the split specialised
+    product and the generic FP64 block product give the same Lanczos coefficients bit for
+    bit over 4 steps."""
     inst = W.j1j2_ring32()
     b = hm.Basis(32, 1, 0)
     out = {}
-    for mode, env in (("split", {}), ("one", {"HM_BLK_SPLIT": "0"}), ("generic", {"HM_JIT": "0"})):
+    for mode, env in (("split", {"HM_BLK_SPLIT": "1"}), ("one", {}), ("generic", {"HM_JIT": "0"})):
         monkeypatch.delenv("HM_BLK_SPLIT", raising=False)
         monkeypatch.delenv("HM_JIT", raising=False)
         for k, v in env.items():
