@@ -287,11 +287,11 @@ int basis_decode(const hm_basis *b, const int64_t *idx, uint64_t *states, int64_
     int blocks = grid_blocks((uint64_t)n, 256);
     if (sv.idx64) {
         size_t sm = cd_bytes<uint64_t>(sv);
-        HM_CUDA(cudaFuncSetAttribute(k_decode<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HM_CUDA(raise_smem_limit(k_decode<uint64_t>, (int)sm));
         k_decode<uint64_t><<<blocks, 256, sm, as_stream(stream)>>>(sv, idx, states, n);
     } else {
         size_t sm = cd_bytes<uint32_t>(sv);
-        HM_CUDA(cudaFuncSetAttribute(k_decode<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HM_CUDA(raise_smem_limit(k_decode<uint32_t>, (int)sm));
         k_decode<uint32_t><<<blocks, 256, sm, as_stream(stream)>>>(sv, idx, states, n);
     }
     HM_CUDA(cudaGetLastError());
@@ -306,11 +306,11 @@ int basis_encode(const hm_basis *b, const uint64_t *states, int64_t *idx, int64_
     int blocks = grid_blocks((uint64_t)n, 256);
     if (sv.idx64) {
         size_t sm = cd_bytes<uint64_t>(sv);
-        HM_CUDA(cudaFuncSetAttribute(k_encode<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HM_CUDA(raise_smem_limit(k_encode<uint64_t>, (int)sm));
         k_encode<uint64_t><<<blocks, 256, sm, as_stream(stream)>>>(sv, states, idx, n);
     } else {
         size_t sm = cd_bytes<uint32_t>(sv);
-        HM_CUDA(cudaFuncSetAttribute(k_encode<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HM_CUDA(raise_smem_limit(k_encode<uint32_t>, (int)sm));
         k_encode<uint32_t><<<blocks, 256, sm, as_stream(stream)>>>(sv, states, idx, n);
     }
     HM_CUDA(cudaGetLastError());

@@ -349,7 +349,7 @@ __global__ void k_max_exp(const unsigned long long *__restrict__ x, uint64_t n, 
 template <class T, int NC>
 static int launch_blk_matvec(hm_basis *b, const BlkParams &P, const T *x, T *y, cudaStream_t st) {
     const size_t sm = blk_row_smem_bytes(P, sizeof(T) == 8 ? 8 : 4, BLK_XPAD);
-    HM_CUDA(cudaFuncSetAttribute(k_blk_matvec<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HM_CUDA(raise_smem_limit(k_blk_matvec<T, NC>, sm));
     int *Ed = nullptr;
     if constexpr (sizeof(T) == 8) {
         Ed = (int *)b->d_scratch;
@@ -391,7 +391,7 @@ static int lz64_dispatch(const BlkParams &P, F &&f) {
 
 template <class K_t>
 static int set_smem(K_t kern, size_t sm) {
-    HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HM_CUDA(raise_smem_limit(kern, (int)sm));
     return HM_OK;
 }
 
@@ -428,7 +428,7 @@ int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void *
     const void *k = nullptr;
     if (jit_lz_kernel(P, dtype, bp, &k, split) != 0) return 1;
     const size_t sm = blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4, jit_pad(k));
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+    if (raise_smem_limit(k, (int)sm) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -515,7 +515,7 @@ static int launch_blk_matvec_pb(hm_basis *b, const BlkParams &P, const BondParam
     const void *k = nullptr;
     if (jit_mv_kernel(P, dtype, bp, &k) != 0) return 1;
     const size_t sm = blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4, BLK_XPAD);
-    HM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HM_CUDA(raise_smem_limit(k, (int)sm));
     int *Ed = nullptr;
     if (dtype == HM_F64) {
         Ed = (int *)b->d_scratch;
@@ -582,7 +582,7 @@ int blk_bond_corr(hm_basis *b, const BondParams &bp, const void *g, const void *
         if (blk_plan(b, bc, blk_K(b), &P, true) != 0 || !P.rows_ok) return 1;
         const size_t sm = blk_row_smem_bytes(P, es, BLK_XPAD);
         if (sm > 200 * 1024 || jit_bc_kernel(P, dtype, nbk, &kerns[c]) != 0) return 1;
-        if (cudaFuncSetAttribute(kerns[c], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+        if (raise_smem_limit(kerns[c], (int)sm) != cudaSuccess) {
             cudaGetLastError();
             return 1;
         }

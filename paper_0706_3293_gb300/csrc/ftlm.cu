@@ -963,7 +963,7 @@ static int ft_prepare(int n_sites, int two_s, int n_bonds, const int32_t *u, con
     for (int vt : {1, 2, 4}) {
         const void *kfn = pick_kernel(S->F.P.nc, vt);
         int p = 0;
-        HM_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem));
+        HM_CUDA(raise_smem_limit(kfn, (int)S->smem));
         HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kfn, FT_NT, S->smem));
         per_sm = std::min(per_sm, p);
     }
@@ -1014,7 +1014,7 @@ static void ft_bind(FtSetup *S, unsigned char *w) {
 
 static int ft_launch_persistent(FtSetup *S, int vt, cudaStream_t st) {
     const void *kfn = pick_kernel(S->F.P.nc, vt);
-    HM_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem));
+    HM_CUDA(raise_smem_limit(kfn, (int)S->smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(S->nctas);
     cfg.blockDim = dim3(FT_NT);

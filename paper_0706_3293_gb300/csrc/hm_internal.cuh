@@ -224,6 +224,17 @@ __host__ __device__ __forceinline__ uint64_t sm64(uint64_t seed, uint64_t t) {
 
 // number of blocks used by grid-stride kernels: fixed per device so reductions are
 // reproducible run to run
+// Raises (never lowers) the dynamic shared-memory limit of a kernel.  Several plans with
+// different block sizes share one kernel, and launches captured into one graph after all of
+// them were planned must each still fit.
+template <class F>
+inline cudaError_t raise_smem_limit(F kern, size_t bytes) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, (const void *)kern);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 int grid_blocks(uint64_t rows, int threads);
 int sm_count();
 

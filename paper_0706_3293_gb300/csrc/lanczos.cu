@@ -644,8 +644,7 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
 // raises the dynamic shared-memory limit of the product kernel (outside any capture)
 template <class I, class T, class Acc>
 static int prepare_t(const hm_basis *b) {
-    HM_CUDA(cudaFuncSetAttribute(k_lz_matvec<I, T, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)row_smem_bytes<I>(b->view)));
+    HM_CUDA(raise_smem_limit(k_lz_matvec<I, T, Acc>, (int)row_smem_bytes<I>(b->view)));
     return HM_OK;
 }
 

@@ -34,8 +34,7 @@ template <class I, class T, class Acc, int NV>
 static int launch_matvec(const SectorView &sv, const BondParams &bp, const T *x, T *y, int ld,
                          int c0, cudaStream_t st) {
     size_t sm = row_smem_bytes<I>(sv);
-    HM_CUDA(cudaFuncSetAttribute(k_matvec<I, T, Acc, NV>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HM_CUDA(raise_smem_limit(k_matvec<I, T, Acc, NV>, (int)sm));
     k_matvec<I, T, Acc, NV><<<grid_blocks(sv.dim, 256), 256, sm, st>>>(sv, bp, x, y, ld, c0, row_run_len());
     HM_CUDA(cudaGetLastError());
     return HM_OK;
@@ -125,8 +124,7 @@ static int bond_corr_t(const SectorView &sv, const BondParams &bp, const T *g, c
                        double *out, double *part, int nblk, double sign, const double *div,
                        cudaStream_t st) {
     size_t sm = row_smem_bytes<I>(sv);
-    HM_CUDA(cudaFuncSetAttribute(k_bond_corr<I, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm));
+    HM_CUDA(raise_smem_limit(k_bond_corr<I, T>, (int)sm));
     dim3 grid(nblk, (bp.nb + BC - 1) / BC);
     k_bond_corr<I, T><<<grid, 256, sm, st>>>(sv, bp, g, x, part);
     HM_CUDA(cudaGetLastError());
@@ -300,11 +298,11 @@ int count_nnz(const hm_basis *b, int n_bonds, const int32_t *u, const int32_t *v
     HM_CUDA(cudaMemsetAsync(nnz, 0, sizeof(int64_t), st));
     if (sv.idx64) {
         const size_t sm = row_smem_bytes<uint64_t>(sv);
-        HM_CUDA(cudaFuncSetAttribute(k_count_nnz<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HM_CUDA(raise_smem_limit(k_count_nnz<uint64_t>, (int)sm));
         k_count_nnz<uint64_t><<<grid_blocks(sv.dim, 256), 256, sm, st>>>(sv, bp, (unsigned long long *)nnz);
     } else {
         const size_t sm = row_smem_bytes<uint32_t>(sv);
-        HM_CUDA(cudaFuncSetAttribute(k_count_nnz<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HM_CUDA(raise_smem_limit(k_count_nnz<uint32_t>, (int)sm));
         k_count_nnz<uint32_t><<<grid_blocks(sv.dim, 256), 256, sm, st>>>(sv, bp, (unsigned long long *)nnz);
     }
     HM_CUDA(cudaGetLastError());

@@ -327,7 +327,7 @@ static const void *s1_jit(const S1Plan &P, int mode) {
 }
 
 static int s1_launch(const void *kern, const S1Plan &P, size_t sm, void **args, cudaStream_t st) {
-    HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HM_CUDA(raise_smem_limit(kern, (int)sm));
     HM_CUDA(cudaLaunchKernel(kern, dim3(s1_grid(P, kern, sm)), dim3(S1_NT), args, sm, st));
     return HM_OK;
 }
