@@ -267,6 +267,8 @@ int basis_free(hm_basis *b) {
         if (kv.second.dev && (e2 = cudaFree(kv.second.dev)) != cudaSuccess) e = e2;
     for (auto &kv : b->s1_tabs)
         if (kv.second.dev && (e2 = cudaFree(kv.second.dev)) != cudaSuccess) e = e2;
+    for (auto &kv : b->blk_ttabs)
+        if (kv.second && (e2 = cudaFree(kv.second)) != cudaSuccess) e = e2;
     if (b->d_mom && (e2 = cudaFree(b->d_mom)) != cudaSuccess) e = e2;
     delete b;
     if (e != cudaSuccess) return cuda_fail(e, "basis_free");

@@ -442,6 +442,89 @@ int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void *
     return 0;
 }
 
+// Per-class target tables of a plan (the "table" row policy of the specialised kernels,
+// jit.cu).  The low part of every block of class k runs through the same C(K, k) low words
+// in the same order, so the rank of each low-site exchange target (Sec. 3.2) depends only on
+// (k, r) and the bond, not on the block.  The kernels therefore read the targets of a row
+// from a table instead of forming them from rank-table reads in shared memory: entries in
+// the order gen_row_table writes them out (classes, then slot kinds 0..2, then slots), then
+// one per low end of a cross bond, then the exchange counts (8 bits per class).  Entries are
+// byte offsets (rows times esize); a slot whose spins are parallel points at the zero row
+// after the staged block.  2^K rows x chunks x 16 bytes (2 MB at K = 15), built once per
+// basis, layout and element size.  Returns 0 and sets P->tt, or 1 when the policy does not
+// apply (spin-flip or per-bond plans, more than 48 entries, or HM_JIT_ROW selects another).
+int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
+    P->tt = nullptr;
+    const char *rowk = getenv("HM_JIT_ROW");
+    if (rowk && *rowk && strcmp(rowk, "table") != 0) return 1;
+    if (!P->rows_ok || P->perbond || P->par || P->bcmode || P->K > 15) return 1;
+    const int K = P->K;
+    std::vector<std::pair<int, int>> low;                 // (p, q) in generated order
+    for (int c = 0; c < P->nc; ++c)
+        for (int ty = 0; ty < 3; ++ty)
+            for (int k = 0; k < P->ln[c][ty]; ++k) {
+                const int p = __builtin_ctz(P->lvm[c][ty][k]);
+                low.push_back({p, p + P->ld[c][ty][k]});
+            }
+    std::vector<int> cps;
+    for (int e = 0; e < P->nxf; ++e)
+        if (std::find(cps.begin(), cps.end(), (int)P->xf_p[e]) == cps.end()) cps.push_back(P->xf_p[e]);
+    if (cps.size() > 8) return 1;
+    const int ncnt = (P->nc + 1) / 2;
+    const int n = (int)low.size() + (int)cps.size() + ncnt;
+    if (n > 48) return 1;
+    const int nch = (n + 7) / 8;
+    const uint32_t zrow = (uint32_t)(P->max_block + BLK_XPAD - 1);
+    if ((zrow + 1) * (uint32_t)esize > 65535u) return 1;
+    std::string key = std::to_string(K) + ":" + std::to_string(esize) + ":" + std::to_string(P->nc) + ":";
+    for (auto &pq : low) key += std::to_string(pq.first) + "-" + std::to_string(pq.second) + ",";
+    key += "|";
+    for (int p : cps) key += std::to_string(p) + ",";
+    auto it = b->blk_ttabs.find(key);
+    if (it == b->blk_ttabs.end()) {
+        const uint32_t rows = 1u << K;
+        std::vector<uint32_t> rank(rows);                 // colex rank within the popcount class
+        {
+            std::vector<uint32_t> seen(K + 1, 0);
+            for (uint32_t l = 0; l < rows; ++l) rank[l] = seen[__builtin_popcount(l)]++;
+        }
+        // class of each low slot, for the counts
+        std::vector<int> cls;
+        for (int c = 0; c < P->nc; ++c)
+            for (int ty = 0; ty < 3; ++ty)
+                for (int k = 0; k < P->ln[c][ty]; ++k) cls.push_back(c);
+        std::vector<uint16_t> host((size_t)nch * rows * 8, 0);
+        for (uint32_t l = 0; l < rows; ++l) {
+            const uint32_t g = rank[l] + (uint32_t)P->lwoff[__builtin_popcount(l)];   // position in the word list
+            auto put = [&](int s, uint32_t v) { host[((size_t)(s / 8) * rows + g) * 8 + (s % 8)] = (uint16_t)v; };
+            uint32_t cnt[HM_BLK_MAXC] = {0, 0, 0, 0};
+            int s = 0;
+            for (size_t i = 0; i < low.size(); ++i, ++s) {
+                const int p = low[i].first, q = low[i].second;
+                if (((l >> p) ^ (l >> q)) & 1u) {
+                    put(s, rank[l ^ ((1u << p) | (1u << q))] * (uint32_t)esize);
+                    ++cnt[cls[i]];
+                } else {
+                    put(s, zrow * (uint32_t)esize);
+                }
+            }
+            for (int p : cps) put(s++, rank[l ^ (1u << p)] * (uint32_t)esize);
+            for (int c = 0; c < P->nc; c += 2) put(s++, cnt[c] | (c + 1 < P->nc ? cnt[c + 1] << 8 : 0u));
+        }
+        void *dev = nullptr;
+        HM_CUDA(cudaMalloc(&dev, host.size() * 2));
+        cudaError_t e = cudaMemcpy(dev, host.data(), host.size() * 2, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(dev); return cuda_fail(e, "target table"); }
+        it = b->blk_ttabs.emplace(key, dev).first;
+    }
+    P->tt = (const uint4 *)it->second;
+    P->tt_stride = 1u << K;
+    P->tt_n = n;
+    P->tt_ncross = (int)cps.size();
+    for (size_t i = 0; i < cps.size(); ++i) P->tt_cross_p[i] = cps[i];
+    return 0;
+}
+
 // Split FP64 product for large s = 1/2 sectors with integer-ratio couplings.  In one pass
 // the exchanges that reach the top high sites gather blocks far away in the row order, which
 // have left L2 by then (about 105 bytes of DRAM traffic per row at N = 32 against 16).  The

@@ -83,6 +83,16 @@ struct BlkParams {
     // bond-correlation plan (one chunk of bonds, per-bond slots): the block setup keeps the
     // high targets uncompacted, hbi[j] for high bond j or ~0 when its spins are parallel
     int bcmode;
+    // per-class target tables (row policy "table", jit.cu): the row of rank r in the low-word
+    // list of class k (list position g = lwoff[k] + r) has tt_n 16-bit entries, eight to a
+    // 16-byte chunk, entry s in chunk s / 8 at tt[(s / 8) * tt_stride + g]: first the byte
+    // offset of each low slot's target row in the staged block (the zero row when the two
+    // spins are parallel), then for each low end p of a cross bond the byte offset of the rank
+    // of l ^ 2^p among the words of its popcount, then the exchange counts of the low slots,
+    // eight bits per class
+    const uint4 *tt;
+    uint32_t tt_stride;
+    int tt_n, tt_ncross, tt_cross_p[8];
     // two-pass FP64 Lanczos product (integer-ratio classes): pass 1 applies the near bonds
     // and stores each row's exact integer class sum, pass 2 adds the far bonds (those
     // reaching the top sites) and rounds once.  rot: pass 2 takes the blocks in the order of

@@ -86,6 +86,7 @@ struct hm_basis {
     void *d_cd = nullptr;           // device copy (owned)
     void *d_scratch = nullptr;      // 256 bytes of device scratch (owned), e.g. exponents
     std::map<int, hm::BlkTab> blk_tabs;   // per split position K (owned device memory)
+    std::map<std::string, void *> blk_ttabs;   // per-class target tables by layout (owned device memory)
     std::map<int, hm::S1Tab> s1_tabs;     // s = 1 block path, per split K (owned device memory)
     int parity = 0;                 // spin-flip basis (basis_build_flip): +1 / -1, view.dim halved
     int device = 0;

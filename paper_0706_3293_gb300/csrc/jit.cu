@@ -181,6 +181,75 @@ std::string gen_row_slots(const BlkParams &P) {
     return s;
 }
 
+// The row policy of a plan with per-class target tables (BlkParams::tt, blk.cu
+// blk_target_table): the row's table entries are read as 16-byte chunks (consecutive rows
+// read consecutive chunks, so the loads are coalesced and served from L2), and each low slot
+// is one shared-memory gather at the byte offset its entry holds (the zero row when the
+// spins are parallel): no rank-table reads and no per-slot spin test.  The exchange counts
+// of the low slots come from the table too; cross and high exchanges as in gen_row_slots.
+std::string gen_row_table(const BlkParams &P) {
+    std::string s;
+    s += "struct RowJit {\n"
+         "static constexpr int kPad = hm::BLK_XPAD;\n"
+         "static constexpr bool kRelUS = false;\n"
+         "static constexpr bool kPerBond = false;\n"
+         "static constexpr bool kBC = false;\n"
+         "template <class Sv>\n"
+         "static __device__ __forceinline__ void stage(const hm::BlkParams &P, unsigned char *dyn) {\n"
+         "    if (threadIdx.x == 0) *(Sv *)(dyn + (P.max_block + hm::BLK_XPAD - 1) * sizeof(Sv)) = Sv(0);\n"
+         "}\n"
+         "template <class Sv>\n"
+         "static __device__ __forceinline__ void block(const hm::BlkParams &, uint32_t) {}\n"
+         "template <class Sv, class G>\n"
+         "static __device__ __forceinline__ void sums(const hm::BlkParams &P, const hm::BlkMeta &B,\n"
+         "        const unsigned char *Xsb, const unsigned char *Xg, uint32_t l, uint32_t r, const G &gx, Sv xo,\n"
+         "        Sv *acc, int *cnt) {\n"
+         "    (void)l; (void)gx; (void)xo; (void)Xg;\n"
+         "    const uint4 *tt = P.tt + (B.lwo + r);\n";
+    const int nch = (P.tt_n + 7) / 8;
+    for (int j = 0; j < nch; ++j) put(s, "    const uint4 q%d = __ldg(tt + %uu);\n", j, (unsigned)j * P.tt_stride);
+    static const char *comp[4] = {"x", "y", "z", "w"};
+    auto entry = [&](int e) {
+        char buf[64];
+        const int j = e / 8, c = (e % 8) / 2;
+        if (e % 2 == 0) snprintf(buf, sizeof buf, "(q%d.%s & 0xFFFFu)", j, comp[c]);
+        else snprintf(buf, sizeof buf, "(q%d.%s >> 16)", j, comp[c]);
+        return std::string(buf);
+    };
+    // entry indices: low slots in class / kind / slot order, then cross low ends, then counts
+    int nlow = 0;
+    for (int c = 0; c < P.nc; ++c)
+        for (int t = 0; t < 3; ++t) nlow += P.ln[c][t];
+    auto cross_entry = [&](int c, int t, int k) {
+        const int p = __builtin_ctz((unsigned)P.xxa[c][t][k]) - 2 + (t == 1 ? 8 : 0);
+        for (int i = 0; i < P.tt_ncross; ++i)
+            if (P.tt_cross_p[i] == p) return nlow + i;
+        return -1;
+    };
+    s += "#define XS(o) (*(const Sv *)(Xsb + (o)))\n";
+    // low slots of every class first (the chunk registers are dead after them), then the
+    // cross exchanges, the counts, and the high gathers
+    for (int c = 0; c < P.nc; ++c) put(s, "    Sv a%d = Sv(0);\n    int m%d = 0;\n", c, c);
+    int e = 0;
+    for (int c = 0; c < P.nc; ++c)
+        for (int t = 0; t < 3; ++t)
+            for (int k = 0; k < P.ln[c][t]; ++k) put(s, "    a%d += XS(%s);\n", c, entry(e++).c_str());
+    for (int c = 0; c < P.nc; ++c)
+        for (int t = 0; t < 2; ++t)
+            for (int k = 0; k < P.xn[c][t]; ++k)
+                put(s, "    { const hm::XSlot x_ = B.xs[%d]; if ((l ^ x_.wm) & x_.vm) { a%d += gx(x_.base + %s); ++m%d; } }\n",
+                    (2 * c + t) * HM_BLK_SX + k, c, entry(cross_entry(c, t, k)).c_str(), c);
+    for (int c = 0; c < P.nc; ++c) {
+        const int ce = nlow + P.tt_ncross + c / 2;
+        put(s, "    m%d += (int)((%s >> %d) & 0xFFu);\n", c, entry(ce).c_str(), 8 * (c % 2));
+    }
+    for (int c = 0; c < P.nc; ++c)
+        put(s, "    acc[%d] = a%d + hm::blk_high_sum<Sv>(B, %d, Xg, r, gx);\n    cnt[%d] = m%d + (B.he[%d] - B.hs[%d]);\n",
+            c, c, c, c, c, c, c);
+    s += "#undef XS\n}\n};\n";
+    return s;
+}
+
 // The row policy of a per-bond plan (BlkParams::perbond): the slots of class 0 written out
 // as in gen_row_slots, each with its own coefficient h_b = J_b / 2 as a literal, summed
 // as h_b (x_i - x_t) (blk_sweep.cuh, per-bond rows).  A slot whose spins are parallel reads
@@ -524,8 +593,9 @@ int compile(const std::string &src, const char *name, int device, const void **o
                     kJitHeaderTexts, kJitHeaderNames) != NVRTC_SUCCESS)
         return 1;
     const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--device-int128", "-lineinfo",
-                          "--fmad=true"};
-    const nvrtcResult rc = g_nv.compile(prog, (int)(sizeof opts / sizeof *opts), opts);
+                          "--fmad=true", "--ptxas-options=-v"};
+    const int nopt = (int)(sizeof opts / sizeof *opts) - (verbose() ? 0 : 1);   // ptxas report when verbose
+    const nvrtcResult rc = g_nv.compile(prog, nopt, opts);
     if (rc != NVRTC_SUCCESS || verbose()) {
         size_t n = 0;
         g_nv.log_size(prog, &n);
@@ -563,7 +633,7 @@ static bool jit_row_source(const BlkParams &P, const BondParams &bp, std::string
     const char *rowk = getenv("HM_JIT_ROW");
     *delta = !P.perbond && rowk && strcmp(rowk, "delta") == 0 && !P.par;   // no spin-flip or per-bond form
     *src = "#include \"blk_sweep.cuh\"\n" +
-           (P.perbond ? gen_row_pb(P, bp) : *delta ? gen_row(P, gen_ok) : gen_row_slots(P));
+           (P.perbond ? gen_row_pb(P, bp) : *delta ? gen_row(P, gen_ok) : P.tt ? gen_row_table(P) : gen_row_slots(P));
     return gen_ok;
 }
 

@@ -17,6 +17,7 @@ int blk_lz_plan(hm_basis *b, const BondParams &bp, int dtype, BlkParams *P, int 
 int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void **kern, int *blocks, int split = 0);
 int blk_lz_split(hm_basis *b, const BondParams &bp, const BlkParams &P, int dtype, BlkParams *PA, BlkParams *PB,
                  const void **kA, const void **kB, int *blkA, int *blkB);
+int blk_target_table(hm_basis *b, BlkParams *P, int esize);
 int blk_K(const hm_basis *b);   // blk.cu: split position of the block path
 int blk_lz64_launch(const BlkParams &P, const long long *Xc, unsigned long long *Y, LzScalars *S, int pc,
                     double *part, int blocks, cudaStream_t st, const void *jit);
@@ -733,6 +734,8 @@ static int lz_create(const hm_basis *b, int n_bonds, const int32_t *u, const int
     if (R->use_blk) {
         int jb = 0;
         const void *jk = nullptr;
+        rc = blk_target_table(const_cast<hm_basis *>(b), &R->blk, dtype == HM_F64 ? 8 : 4);
+        if (rc < 0) { delete R; return rc; }
         if (blk_lz_jit(R->blk, dtype, R->bp, &jk, &jb) == 0) { R->jit = jk; R->blk_blocks = jb; }
         if (R->blk.perbond && !R->jit) R->use_blk = 0;   // per-bond rows run only specialised
     }

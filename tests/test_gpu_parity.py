@@ -425,15 +425,18 @@ def test_count_nnz_full_size_closed_form(hm):
     assert hm.count_nnz(b, hm.bonds_of(inst)) == math.comb(32, 16) + 2 * 64 * math.comb(30, 15)
 
 
-@pytest.mark.parametrize("case,row", [("j1j2_n20_f64", "slots"), ("three_class_n18_f64", "slots"),
+@pytest.mark.parametrize("case,row", [("j1j2_n20_f64", "table"), ("three_class_n18_f64", "table"),
+                                      ("j1j2_n20_f32", "table"),
+                                      ("j1j2_n20_f64", "slots"), ("three_class_n18_f64", "slots"),
                                       ("j1j2_n20_f32", "slots"), ("j1j2_n20_f64", "delta"),
                                       ("three_class_n18_f64", "delta"), ("j1j2_n20_f32", "delta")])
 def test_block_product_specialised_equals_generic(hm, case, row, monkeypatch):
-    """The block product compiled for the bond list at run time (NVRTC; both row policies:
-    slots written out, or per-byte delta tables) and the generic block kernel form the same
-    exact integer sums in FP64, so 60 Lanczos steps agree bit for bit.  In FP32 the sums
-    round in another order (the delta policy adds x_r for parallel bonds and takes it back
-    in the diagonal term): the recurrences agree to FP32 accuracy."""
+    """The block product compiled for the bond list at run time (NVRTC; three row policies:
+    per-class target tables (the default), slots written out, or per-byte delta tables) and
+    the generic block kernel form the same exact integer sums in FP64, so 60 Lanczos steps
+    agree bit for bit.  In FP32 the sums round in another order (the delta policy adds x_r for
+    parallel bonds and takes it back in the diagonal term): the recurrences agree to FP32
+    accuracy."""
     if case == "three_class_n18_f64":
         n, J = 18, [-1.0 if i % 3 == 0 else (0.5 if i % 3 == 1 else -0.25) for i in range(18)]
         u = list(range(18)) + [0, 3, 2]
