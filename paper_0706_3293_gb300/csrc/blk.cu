@@ -556,6 +556,7 @@ int blk_lz_split(hm_basis *b, const BondParams &bp, const BlkParams &P, int dtyp
     PA->split = 1;
     PB->split = 2;
     PB->rot = std::min(PB->H, 9);
+    if (blk_target_table(b, PA, 8) < 0 || blk_target_table(b, PB, 8) < 0) return 1;
     if (blk_lz_jit(*PA, dtype, bp, kA, blkA, 1) != 0 || blk_lz_jit(*PB, dtype, bp, kB, blkB, 2) != 0) return 1;
     return 0;
 }

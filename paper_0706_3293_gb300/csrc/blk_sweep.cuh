@@ -73,26 +73,30 @@ __device__ __forceinline__ int popc_below(uint64_t m, int e) {
 }
 
 // sum of the high-exchange gathers of class c for row r (the same low word in each target
-// block): four target offsets per 16-byte shared load
-template <class Sv, class G>
+// block), NH gathers in flight: four target offsets per 16-byte shared load (NH = 4), two per
+// 8-byte load (NH = 2), or one at a time (NH = 1; fewest live registers)
+template <class Sv, int NH = 4, class G>
 __device__ __forceinline__ Sv blk_high_sum(const BlkMeta &B, int c, const unsigned char *Xg, uint32_t r,
                                            const G &gx) {
     const int e0 = B.hs[c], e1 = B.he[c];
-    const uint4 *h4 = reinterpret_cast<const uint4 *>(B.hbi);
     Sv a = Sv(0);
     int e = e0;
-    for (; e + 4 <= e1; e += 4) {
-        const uint4 t = h4[e >> 2];
-        const Sv v0 = gx(Xg + (size_t)(t.x + r) * sizeof(Sv)), v1 = gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
-        const Sv v2 = gx(Xg + (size_t)(t.z + r) * sizeof(Sv)), v3 = gx(Xg + (size_t)(t.w + r) * sizeof(Sv));
-        a += (v0 + v1) + (v2 + v3);
+    if constexpr (NH == 4) {
+        const uint4 *h4 = reinterpret_cast<const uint4 *>(B.hbi);
+        for (; e + 4 <= e1; e += 4) {
+            const uint4 t = h4[e >> 2];
+            const Sv v0 = gx(Xg + (size_t)(t.x + r) * sizeof(Sv)), v1 = gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
+            const Sv v2 = gx(Xg + (size_t)(t.z + r) * sizeof(Sv)), v3 = gx(Xg + (size_t)(t.w + r) * sizeof(Sv));
+            a += (v0 + v1) + (v2 + v3);
+        }
+    } else if constexpr (NH == 2) {
+        const uint2 *h2 = reinterpret_cast<const uint2 *>(B.hbi);
+        for (; e + 2 <= e1; e += 2) {
+            const uint2 t = h2[e >> 1];
+            a += gx(Xg + (size_t)(t.x + r) * sizeof(Sv)) + gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
+        }
     }
-    if (e < e1) {                    // 1..3 left, the same count for every row of the block
-        const uint4 t = h4[e >> 2];
-        a += gx(Xg + (size_t)(t.x + r) * sizeof(Sv));
-        if (e + 1 < e1) a += gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
-        if (e + 2 < e1) a += gx(Xg + (size_t)(t.z + r) * sizeof(Sv));
-    }
+    for (; e < e1; ++e) a += gx(Xg + (size_t)(B.hbi[e] + r) * sizeof(Sv));
     return a;
 }
 

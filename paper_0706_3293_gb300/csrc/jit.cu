@@ -243,9 +243,13 @@ std::string gen_row_table(const BlkParams &P) {
         const int ce = nlow + P.tt_ncross + c / 2;
         put(s, "    m%d += (int)((%s >> %d) & 0xFFu);\n", c, entry(ce).c_str(), 8 * (c % 2));
     }
+    // high gathers in flight (HM_JIT_HIGH = 1, 2, 4): more hide more latency, fewer keep the
+    // registers (and local-memory spills) down
+    int nh = 4;
+    if (const char *v = getenv("HM_JIT_HIGH")) nh = atoi(v) == 1 ? 1 : atoi(v) == 2 ? 2 : 4;
     for (int c = 0; c < P.nc; ++c)
-        put(s, "    acc[%d] = a%d + hm::blk_high_sum<Sv>(B, %d, Xg, r, gx);\n    cnt[%d] = m%d + (B.he[%d] - B.hs[%d]);\n",
-            c, c, c, c, c, c, c);
+        put(s, "    acc[%d] = a%d + hm::blk_high_sum<Sv, %d>(B, %d, Xg, r, gx);\n    cnt[%d] = m%d + (B.he[%d] - B.hs[%d]);\n",
+            c, c, nh, c, c, c, c, c);
     s += "#undef XS\n}\n};\n";
     return s;
 }
@@ -588,6 +592,14 @@ std::string gen_s1_row(const S1Plan &P, bool f64) {
 }
 
 int compile(const std::string &src, const char *name, int device, const void **out) {
+    // HM_JIT_DUMP=<dir>: keep each generated source as <dir>/<kernel>_<n>.cu (for offline
+    // compilation and register reports)
+    if (const char *d = getenv("HM_JIT_DUMP")) {
+        static int seq = 0;
+        char path[4096];
+        snprintf(path, sizeof path, "%s/%s_%d.cu", d, name, seq++);
+        if (FILE *f = fopen(path, "w")) { fputs(src.c_str(), f); fclose(f); }
+    }
     nvrtcProgram prog;
     if (g_nv.create(&prog, src.c_str(), "hm_jit.cu", (int)(sizeof kJitHeaderNames / sizeof *kJitHeaderNames),
                     kJitHeaderTexts, kJitHeaderNames) != NVRTC_SUCCESS)
