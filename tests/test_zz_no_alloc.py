@@ -1,7 +1,11 @@
-"""bond_corr_static: the adjoint for callers that cannot allocate device memory when they
-need it.  It keeps its partial sums in a fixed device array instead of a workspace; its
-output must match bond_corr (same kernels, same launch shape) on consecutive calls, which
-share that array.  Kept in its own file, collected last."""
+"""bond_corr_static: the adjoint for callers that cannot call cudaMalloc when they need it --
+a host program that reserves its whole device-memory budget at start-up and forbids any
+later allocation, or a library inside a framework whose allocator owns all device memory.
+It allocates nothing: it runs the general row kernels (no block tables built on first use,
+no run-time compiled kernel) and keeps its partial sums in a fixed device array instead of
+a workspace.  Its output must match bond_corr (which may take the block kernels; the sums
+then differ only in rounding order) on two consecutive calls, which share that array.  Kept
+in its own file, collected last."""
 import ctypes
 
 import numpy as np
