@@ -196,9 +196,14 @@ __device__ __forceinline__ uint32_t blk_fetch(const BlkParams &P, unsigned *sche
 }
 
 // gathers: element at a byte address of the vector
+// read-only global loads (through the non-coherent path; the data do not change while a
+// kernel runs)
+__device__ __forceinline__ long long ldg_s64(const void *p) { return __ldg((const long long *)p); }
+__device__ __forceinline__ uint4 ldg_v4(const uint4 *p) { return __ldg(p); }
+
 struct GFix {                        // fixed-point copy
     __device__ __forceinline__ int64_t operator()(const unsigned char *p) const {
-        return (int64_t)__ldg((const long long *)p);
+        return (int64_t)ldg_s64(p);
     }
 };
 struct GF64 {                        // binary64, converted to fixed point (exponent E)

@@ -207,7 +207,7 @@ std::string gen_row_table(const BlkParams &P) {
          "    (void)l; (void)gx; (void)xo; (void)Xg;\n"
          "    const uint4 *tt = P.tt + (B.lwo + r);\n";
     const int nch = (P.tt_n + 7) / 8;
-    for (int j = 0; j < nch; ++j) put(s, "    const uint4 q%d = __ldg(tt + %uu);\n", j, (unsigned)j * P.tt_stride);
+    for (int j = 0; j < nch; ++j) put(s, "    const uint4 q%d = hm::ldg_v4(tt + %uu);\n", j, (unsigned)j * P.tt_stride);
     static const char *comp[4] = {"x", "y", "z", "w"};
     auto entry = [&](int e) {
         char buf[64];
@@ -644,7 +644,7 @@ static bool jit_row_source(const BlkParams &P, const BondParams &bp, std::string
     bool gen_ok = true;
     const char *rowk = getenv("HM_JIT_ROW");
     *delta = !P.perbond && rowk && strcmp(rowk, "delta") == 0 && !P.par;   // no spin-flip or per-bond form
-    *src = "#include \"blk_sweep.cuh\"\n" +
+    *src = std::string("#include \"blk_sweep.cuh\"\n") +
            (P.perbond ? gen_row_pb(P, bp) : *delta ? gen_row(P, gen_ok) : P.tt ? gen_row_table(P) : gen_row_slots(P));
     return gen_ok;
 }
