@@ -446,38 +446,73 @@ int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void *
 // jit.cu).  The low part of every block of class k runs through the same C(K, k) low words
 // in the same order, so the rank of each low-site exchange target (Sec. 3.2) depends only on
 // (k, r) and the bond, not on the block.  The kernels therefore read the targets of a row
-// from a table instead of forming them from rank-table reads in shared memory: entries in
-// the order gen_row_table writes them out (classes, then slot kinds 0..2, then slots), then
-// one per low end of a cross bond, then the exchange counts (8 bits per class).  Entries are
-// byte offsets (rows times esize); a slot whose spins are parallel points at the zero row
-// after the staged block.  2^K rows x chunks x 16 bytes (2 MB at K = 15), built once per
-// basis, layout and element size.  Returns 0 and sets P->tt, or 1 when the policy does not
-// apply (spin-flip or per-bond plans, more than 48 entries, or HM_JIT_ROW selects another).
+// from a table instead of forming them from rank-table reads in shared memory.
+//
+// The low slots are grouped first into edge-disjoint triangles: bonds (a, b), (b, c), (a, c)
+// among the low sites with (a, b) and (b, c) of one class.  Of the three spin pairs of a
+// triangle either none or exactly two are unequal, so two gathers serve its three slots: the
+// table holds the first and the second allowed target (in the order (a, b), (b, c), (a, c))
+// and a 2-bit code (1: the first two edges, 2: first and third, 3: second and third, 0:
+// none); the first allowed edge is always of the class of (a, b).  The remaining slots take
+// one entry each.  Entries: the triangles' two targets, the single slots' targets, the codes
+// (eight to an entry), the rank of l ^ 2^p for each low end p of a cross bond.  Targets are
+// byte offsets into the staged block (rows times esize), the zero row after the block when
+// not allowed.  16-bit entries, eight to a 16-byte chunk, chunk-major so that consecutive
+// rows read consecutive chunks (2^K rows x chunks x 16 bytes: 2 MB at K = 15), built once
+// per basis, layout and element size.  Returns 0 and sets P->tt, or 1 when the policy does
+// not apply (spin-flip or per-bond plans, more than 48 entries, or HM_JIT_ROW selects
+// another policy).
 int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
     P->tt = nullptr;
     const char *rowk = getenv("HM_JIT_ROW");
     if (rowk && *rowk && strcmp(rowk, "table") != 0) return 1;
     if (!P->rows_ok || P->perbond || P->par || P->bcmode || P->K > 15) return 1;
     const int K = P->K;
-    std::vector<std::pair<int, int>> low;                 // (p, q) in generated order
+    struct Slot { int p, q, c; bool used; };
+    std::vector<Slot> low;
     for (int c = 0; c < P->nc; ++c)
         for (int ty = 0; ty < 3; ++ty)
             for (int k = 0; k < P->ln[c][ty]; ++k) {
                 const int p = __builtin_ctz(P->lvm[c][ty][k]);
-                low.push_back({p, p + P->ld[c][ty][k]});
+                low.push_back({p, p + P->ld[c][ty][k], c, false});
             }
+    auto find = [&](int x, int y) {
+        for (size_t i = 0; i < low.size(); ++i)
+            if (!low[i].used && low[i].p == std::min(x, y) && low[i].q == std::max(x, y)) return (int)i;
+        return -1;
+    };
+    // triangles, greedily by their smallest site; e[0] = (a, b), e[1] = (b, c) share site b and
+    // a class, e[2] = (a, c) is the opposite edge
+    struct Tri { int e[3]; };
+    std::vector<Tri> tris;
+    for (int x = 0; x < K; ++x)
+        for (int y = x + 1; y < K; ++y)
+            for (int z = y + 1; z < K; ++z) {
+                const int sites[3] = {x, y, z};
+                for (int m = 0; m < 3 && tris.size() < 16; ++m) {       // m: the shared site b
+                    const int bb = sites[m], aa = sites[(m + 1) % 3], cc = sites[(m + 2) % 3];
+                    const int i0 = find(aa, bb), i1 = find(bb, cc), i2 = find(aa, cc);
+                    if (i0 < 0 || i1 < 0 || i2 < 0 || low[i0].c != low[i1].c) continue;
+                    low[i0].used = low[i1].used = low[i2].used = true;
+                    tris.push_back({{i0, i1, i2}});
+                    break;
+                }
+            }
+    std::vector<int> sgl;
+    for (size_t i = 0; i < low.size(); ++i)
+        if (!low[i].used) sgl.push_back((int)i);
     std::vector<int> cps;
     for (int e = 0; e < P->nxf; ++e)
         if (std::find(cps.begin(), cps.end(), (int)P->xf_p[e]) == cps.end()) cps.push_back(P->xf_p[e]);
-    if (cps.size() > 8) return 1;
-    const int ncnt = (P->nc + 1) / 2;
-    const int n = (int)low.size() + (int)cps.size() + ncnt;
+    if (cps.size() > 8 || sgl.size() > 48) return 1;
+    const int ntri = (int)tris.size(), nsgl = (int)sgl.size(), ncode = (ntri + 7) / 8;
+    const int n = 2 * ntri + nsgl + ncode + (int)cps.size();
     if (n > 48) return 1;
     const int nch = (n + 7) / 8;
     const uint32_t zrow = (uint32_t)(P->max_block + BLK_XPAD - 1);
     if ((zrow + 1) * (uint32_t)esize > 65535u) return 1;
-    std::string key = std::to_string(K) + ":" + std::to_string(esize) + ":" + std::to_string(P->nc) + ":";
-    for (auto &pq : low) key += std::to_string(pq.first) + "-" + std::to_string(pq.second) + ",";
+    std::string key = "tri:" + std::to_string(K) + ":" + std::to_string(esize) + ":" + std::to_string(P->nc) + ":";
+    for (auto &sl : low) key += std::to_string(sl.p) + "-" + std::to_string(sl.q) + "/" + std::to_string(sl.c) + ",";
     key += "|";
     for (int p : cps) key += std::to_string(p) + ",";
     auto it = b->blk_ttabs.find(key);
@@ -488,28 +523,29 @@ int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
             std::vector<uint32_t> seen(K + 1, 0);
             for (uint32_t l = 0; l < rows; ++l) rank[l] = seen[__builtin_popcount(l)]++;
         }
-        // class of each low slot, for the counts
-        std::vector<int> cls;
-        for (int c = 0; c < P->nc; ++c)
-            for (int ty = 0; ty < 3; ++ty)
-                for (int k = 0; k < P->ln[c][ty]; ++k) cls.push_back(c);
         std::vector<uint16_t> host((size_t)nch * rows * 8, 0);
         for (uint32_t l = 0; l < rows; ++l) {
             const uint32_t g = rank[l] + (uint32_t)P->lwoff[__builtin_popcount(l)];   // position in the word list
             auto put = [&](int s, uint32_t v) { host[((size_t)(s / 8) * rows + g) * 8 + (s % 8)] = (uint16_t)v; };
-            uint32_t cnt[HM_BLK_MAXC] = {0, 0, 0, 0};
-            int s = 0;
-            for (size_t i = 0; i < low.size(); ++i, ++s) {
-                const int p = low[i].first, q = low[i].second;
-                if (((l >> p) ^ (l >> q)) & 1u) {
-                    put(s, rank[l ^ ((1u << p) | (1u << q))] * (uint32_t)esize);
-                    ++cnt[cls[i]];
-                } else {
-                    put(s, zrow * (uint32_t)esize);
-                }
+            auto ok = [&](const Slot &sl) { return ((l >> sl.p) ^ (l >> sl.q)) & 1u; };
+            auto tgt = [&](const Slot &sl) { return rank[l ^ ((1u << sl.p) | (1u << sl.q))] * (uint32_t)esize; };
+            const uint32_t z = zrow * (uint32_t)esize;
+            std::vector<uint32_t> codes((size_t)ncode, 0);
+            for (int t = 0; t < ntri; ++t) {
+                const Slot &e0 = low[tris[t].e[0]], &e1 = low[tris[t].e[1]], &e2 = low[tris[t].e[2]];
+                const bool v0 = ok(e0), v1 = ok(e1), v2 = ok(e2);
+                uint32_t o1 = z, o2 = z, code = 0;
+                if (v0 && v1) { o1 = tgt(e0); o2 = tgt(e1); code = 1; }
+                else if (v0 && v2) { o1 = tgt(e0); o2 = tgt(e2); code = 2; }
+                else if (v1 && v2) { o1 = tgt(e1); o2 = tgt(e2); code = 3; }
+                put(2 * t, o1);
+                put(2 * t + 1, o2);
+                codes[t / 8] |= code << (2 * (t % 8));
             }
-            for (int p : cps) put(s++, rank[l ^ (1u << p)] * (uint32_t)esize);
-            for (int c = 0; c < P->nc; c += 2) put(s++, cnt[c] | (c + 1 < P->nc ? cnt[c + 1] << 8 : 0u));
+            for (int i = 0; i < nsgl; ++i) put(2 * ntri + i, ok(low[sgl[i]]) ? tgt(low[sgl[i]]) : z);
+            for (int i = 0; i < ncode; ++i) put(2 * ntri + nsgl + i, codes[i]);
+            for (size_t i = 0; i < cps.size(); ++i)
+                put(2 * ntri + nsgl + ncode + (int)i, rank[l ^ (1u << cps[i])] * (uint32_t)esize);
         }
         void *dev = nullptr;
         HM_CUDA(cudaMalloc(&dev, host.size() * 2));
@@ -522,6 +558,13 @@ int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
     P->tt_n = n;
     P->tt_ncross = (int)cps.size();
     for (size_t i = 0; i < cps.size(); ++i) P->tt_cross_p[i] = cps[i];
+    P->tt_ntri = ntri;
+    P->tt_nsgl = nsgl;
+    for (int t = 0; t < ntri; ++t) {
+        P->tt_tri_ca[t] = (uint8_t)low[tris[t].e[0]].c;
+        P->tt_tri_cb[t] = (uint8_t)low[tris[t].e[2]].c;
+    }
+    for (int i = 0; i < nsgl; ++i) P->tt_sgl_c[i] = (uint8_t)low[sgl[i]].c;
     return 0;
 }
 

@@ -93,6 +93,12 @@ struct BlkParams {
     const uint4 *tt;
     uint32_t tt_stride;
     int tt_n, tt_ncross, tt_cross_p[8];
+    // the low slots as edge-disjoint triangles of bonds (a, b), (b, c), (a, c), whose spin
+    // pairs hold exactly zero or two unequal pairs, so two gathers serve three slots (two
+    // entries each; 2-bit codes, eight to an entry, say which two), then single slots.  The
+    // first gathered edge of a triangle is always class tri_ca, the second tri_ca or tri_cb
+    int tt_ntri, tt_nsgl;
+    uint8_t tt_tri_ca[16], tt_tri_cb[16], tt_sgl_c[48];
     // two-pass FP64 Lanczos product (integer-ratio classes): pass 1 applies the near bonds
     // and stores each row's exact integer class sum, pass 2 adds the far bonds (those
     // reaching the top sites) and rounds once.  rot: pass 2 takes the blocks in the order of

@@ -183,10 +183,12 @@ std::string gen_row_slots(const BlkParams &P) {
 
 // The row policy of a plan with per-class target tables (BlkParams::tt, blk.cu
 // blk_target_table): the row's table entries are read as 16-byte chunks (consecutive rows
-// read consecutive chunks, so the loads are coalesced and served from L2), and each low slot
-// is one shared-memory gather at the byte offset its entry holds (the zero row when the
-// spins are parallel): no rank-table reads and no per-slot spin test.  The exchange counts
-// of the low slots come from the table too; cross and high exchanges as in gen_row_slots.
+// read consecutive chunks, so the loads are coalesced and served from L2).  A triangle of
+// low bonds is two shared-memory gathers at the byte offsets its two entries hold, added to
+// its two classes as its code says; a single low slot is one gather (the zero row when the
+// spins are parallel).  No rank-table reads and no per-slot spin test; the exchange counts
+// come from the plan's count groups (popc of z_d & mask).  Cross and high exchanges as in
+// gen_row_slots.
 std::string gen_row_table(const BlkParams &P) {
     std::string s;
     s += "struct RowJit {\n"
@@ -216,33 +218,41 @@ std::string gen_row_table(const BlkParams &P) {
         else snprintf(buf, sizeof buf, "(q%d.%s >> 16)", j, comp[c]);
         return std::string(buf);
     };
-    // entry indices: low slots in class / kind / slot order, then cross low ends, then counts
-    int nlow = 0;
-    for (int c = 0; c < P.nc; ++c)
-        for (int t = 0; t < 3; ++t) nlow += P.ln[c][t];
+    const int ntri = P.tt_ntri, nsgl = P.tt_nsgl, ncode = (ntri + 7) / 8;
+    const int ecode = 2 * ntri + nsgl, ecross = ecode + ncode;
     auto cross_entry = [&](int c, int t, int k) {
         const int p = __builtin_ctz((unsigned)P.xxa[c][t][k]) - 2 + (t == 1 ? 8 : 0);
         for (int i = 0; i < P.tt_ncross; ++i)
-            if (P.tt_cross_p[i] == p) return nlow + i;
+            if (P.tt_cross_p[i] == p) return ecross + i;
         return -1;
     };
-    s += "#define XS(o) (*(const Sv *)(Xsb + (o)))\n";
-    // low slots of every class first (the chunk registers are dead after them), then the
-    // cross exchanges, the counts, and the high gathers
-    for (int c = 0; c < P.nc; ++c) put(s, "    Sv a%d = Sv(0);\n    int m%d = 0;\n", c, c);
-    int e = 0;
+    // the count groups' distances
+    std::set<int> ds;
     for (int c = 0; c < P.nc; ++c)
-        for (int t = 0; t < 3; ++t)
-            for (int k = 0; k < P.ln[c][t]; ++k) put(s, "    a%d += XS(%s);\n", c, entry(e++).c_str());
+        for (int g = 0; g < P.lgn[c]; ++g) ds.insert(P.lgd[c][g]);
+    for (int d : ds) put(s, "    const uint32_t z%d = l ^ (l >> %d);\n", d, d);
+    s += "#define XS(o) (*(const Sv *)(Xsb + (o)))\n";
+    for (int c = 0; c < P.nc; ++c) {
+        put(s, "    Sv a%d = Sv(0);\n    int m%d = 0;\n", c, c);
+        for (int g = P.lgn[c] - 1; g >= 0; --g) put(s, "    m%d += __popc(z%d & 0x%xu);\n", c, P.lgd[c][g], P.lgm[c][g]);
+    }
+    for (int t = 0; t < ntri; ++t) {
+        const int ca = P.tt_tri_ca[t], cb = P.tt_tri_cb[t];
+        put(s, "    { const Sv x1 = XS(%s), x2 = XS(%s);\n", entry(2 * t).c_str(), entry(2 * t + 1).c_str());
+        if (ca == cb) {
+            put(s, "      a%d += x1 + x2; }\n", ca);
+        } else {
+            // code 1: both gathered edges are of class ca; codes 2, 3: the second is of class cb
+            put(s, "      const Sv x2a = ((%s >> %d) & 3u) == 1u ? x2 : Sv(0);\n", entry(ecode + t / 8).c_str(), 2 * (t % 8));
+            put(s, "      a%d += x1 + x2a; a%d += x2 - x2a; }\n", ca, cb);
+        }
+    }
+    for (int i = 0; i < nsgl; ++i) put(s, "    a%d += XS(%s);\n", P.tt_sgl_c[i], entry(2 * ntri + i).c_str());
     for (int c = 0; c < P.nc; ++c)
         for (int t = 0; t < 2; ++t)
             for (int k = 0; k < P.xn[c][t]; ++k)
                 put(s, "    { const hm::XSlot x_ = B.xs[%d]; if ((l ^ x_.wm) & x_.vm) { a%d += gx(x_.base + %s); ++m%d; } }\n",
                     (2 * c + t) * HM_BLK_SX + k, c, entry(cross_entry(c, t, k)).c_str(), c);
-    for (int c = 0; c < P.nc; ++c) {
-        const int ce = nlow + P.tt_ncross + c / 2;
-        put(s, "    m%d += (int)((%s >> %d) & 0xFFu);\n", c, entry(ce).c_str(), 8 * (c % 2));
-    }
     // high gathers in flight (HM_JIT_HIGH = 1, 2, 4): more hide more latency, fewer keep the
     // registers (and local-memory spills) down
     int nh = 4;
