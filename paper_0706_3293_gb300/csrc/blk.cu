@@ -460,13 +460,12 @@ int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void *
 // not allowed.  16-bit entries, eight to a 16-byte chunk, chunk-major so that consecutive
 // rows read consecutive chunks (2^K rows x chunks x 16 bytes: 2 MB at K = 15), built once
 // per basis, layout and element size.  Returns 0 and sets P->tt, or 1 when the policy does
-// not apply (spin-flip or per-bond plans, more than 48 entries, or HM_JIT_ROW selects
-// another policy).
+// not apply (per-bond plans, more than 48 entries, or HM_JIT_ROW selects another policy).
 int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
     P->tt = nullptr;
     const char *rowk = getenv("HM_JIT_ROW");
     if (rowk && *rowk && strcmp(rowk, "table") != 0) return 1;
-    if (!P->rows_ok || P->perbond || P->par || P->bcmode || P->K > 15) return 1;
+    if (!P->rows_ok || P->perbond || P->bcmode || P->K > 15) return 1;
     const int K = P->K;
     struct Slot { int p, q, c; bool used; };
     std::vector<Slot> low;

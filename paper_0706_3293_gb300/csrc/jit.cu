@@ -248,18 +248,33 @@ std::string gen_row_table(const BlkParams &P) {
         }
     }
     for (int i = 0; i < nsgl; ++i) put(s, "    a%d += XS(%s);\n", P.tt_sgl_c[i], entry(2 * ntri + i).c_str());
+    // cross exchanges; in a spin-flip basis those moving site N-1 up gather row n - 1 - r of the
+    // complement block, below its base, with the parity sign
     for (int c = 0; c < P.nc; ++c)
         for (int t = 0; t < 2; ++t)
-            for (int k = 0; k < P.xn[c][t]; ++k)
-                put(s, "    { const hm::XSlot x_ = B.xs[%d]; if ((l ^ x_.wm) & x_.vm) { a%d += gx(x_.base + %s); ++m%d; } }\n",
-                    (2 * c + t) * HM_BLK_SX + k, c, entry(cross_entry(c, t, k)).c_str(), c);
+            for (int k = 0; k < P.xn[c][t]; ++k) {
+                const int dst = (2 * c + t) * HM_BLK_SX + k;
+                const char *add = "a%d += gx(x_.base + %s)";
+                for (int e2 = 0; e2 < P.nxf; ++e2)
+                    if (P.xf_dst[e2] == dst && P.par && P.xf_q[e2] == P.H - 1)
+                        add = P.par < 0 ? "a%d -= gx(x_.base - %s)" : "a%d += gx(x_.base - %s)";
+                char buf[160];
+                snprintf(buf, sizeof buf, add, c, entry(cross_entry(c, t, k)).c_str());
+                put(s, "    { const hm::XSlot x_ = B.xs[%d]; if ((l ^ x_.wm) & x_.vm) { %s; ++m%d; } }\n", dst, buf, c);
+            }
     // high gathers in flight (HM_JIT_HIGH = 1, 2, 4): more hide more latency, fewer keep the
     // registers (and local-memory spills) down
     int nh = 4;
     if (const char *v = getenv("HM_JIT_HIGH")) nh = atoi(v) == 1 ? 1 : atoi(v) == 2 ? 2 : 4;
-    for (int c = 0; c < P.nc; ++c)
-        put(s, "    acc[%d] = a%d + hm::blk_high_sum<Sv, %d>(B, %d, Xg, r, gx);\n    cnt[%d] = m%d + (B.he[%d] - B.hs[%d]);\n",
-            c, c, nh, c, c, c, c, c);
+    for (int c = 0; c < P.nc; ++c) {
+        if (P.par)
+            put(s, "    acc[%d] = a%d + hm::blk_high_sum<Sv, %d>(B, %d, Xg, r, gx) %s hm::blk_flip_sum<Sv>(B, %d, Xg, r, gx);\n"
+                   "    cnt[%d] = m%d + (B.he[%d] - B.hs[%d]) + (B.x->fe[%d] - B.x->fs[%d]);\n",
+                c, c, nh, c, P.par < 0 ? "-" : "+", c, c, c, c, c, c, c);
+        else
+            put(s, "    acc[%d] = a%d + hm::blk_high_sum<Sv, %d>(B, %d, Xg, r, gx);\n    cnt[%d] = m%d + (B.he[%d] - B.hs[%d]);\n",
+                c, c, nh, c, c, c, c, c);
+    }
     s += "#undef XS\n}\n};\n";
     return s;
 }

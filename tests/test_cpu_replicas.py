@@ -231,3 +231,45 @@ def test_shared_rows_in_bounds():
         max_block = max(math.comb(K, k) for k in range(K + 1))
         assert max_block + BLK_XPAD - 1 < max_block + BLK_XPAD
         assert max_block <= 6435
+
+
+# ---- triangles of low bonds in the target tables --------------------------------------------
+
+def ring_triangles(K):
+    """Edge-disjoint triangles of the J1-J2 low bonds, as the table builder takes them:
+    sites (p, p+1, p+2) for even p, e1 = (p, p+1), e2 = (p+1, p+2) of class J1 sharing site
+    p+1, e3 = (p, p+2) of class J2."""
+    return [((p, p + 1), (p + 1, p + 2), (p, p + 2)) for p in range(0, K - 2, 2)]
+
+
+@pytest.mark.parametrize("K", [10, 13, 15])
+def test_triangle_encoding_of_low_exchanges(K):
+    """For three sites joined by three bonds either no spin pair or exactly two differ, so
+    the table stores two targets and a code (1: e1 e2, 2: e1 e3, 3: e2 e3); the first stored
+    target is always an e1 or e2 exchange (class J1), the second is class J1 for code 1 and
+    J2 otherwise.  Per class, the stored targets summed as the kernel sums them equal the
+    allowed exchanges' targets, for every K-bit word."""
+    tris = ring_triangles(K)
+    rank = {}
+    seen = [0] * (K + 1)
+    for l in range(1 << K):
+        rank[l] = seen[popc(l)]
+        seen[popc(l)] += 1
+    Z = -1                                           # the zero row: contributes nothing
+    for l in range(1 << K):
+        for e1, e2, e3 in tris:
+            ok = [((l >> a) ^ (l >> b)) & 1 for a, b in (e1, e2, e3)]
+            assert sum(ok) in (0, 2)
+            tg = [rank[l ^ (1 << a) ^ (1 << b)] for a, b in (e1, e2, e3)]
+            if ok[0] and ok[1]:
+                o1, o2, code = tg[0], tg[1], 1
+            elif ok[0] and ok[2]:
+                o1, o2, code = tg[0], tg[2], 2
+            elif ok[1] and ok[2]:
+                o1, o2, code = tg[1], tg[2], 3
+            else:
+                o1, o2, code = Z, Z, 0
+            cls_a = [] if code == 0 else ([o1, o2] if code == 1 else [o1])
+            cls_b = [o2] if code in (2, 3) else []
+            assert sorted(cls_a) == sorted(t for t, v in zip(tg[:2], ok[:2]) if v)
+            assert sorted(cls_b) == sorted(t for t, v in zip(tg[2:], ok[2:]) if v)
