@@ -459,14 +459,19 @@ int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void *
 // byte offsets into the staged block (rows times esize), the zero row after the block when
 // not allowed.  16-bit entries, eight to a 16-byte chunk, chunk-major so that consecutive
 // rows read consecutive chunks (2^K rows x chunks x 16 bytes: 2 MB at K = 15), built once
-// per basis, layout and element size.  Returns 0 and sets P->tt, or 1 when the policy does
-// not apply (per-bond plans, more than 48 entries, or HM_JIT_ROW selects another policy).
+// per basis, layout and element size.  A per-bond plan (each bond its own coefficient) takes
+// no triangles, and a slot whose exchange is not allowed points at the row itself, so that
+// its difference x_i - x_t vanishes.  Returns 0 and sets P->tt, or 1 when the policy does not
+// apply (more than 48 entries, or HM_JIT_ROW selects another policy).
 int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
     P->tt = nullptr;
     const char *rowk = getenv("HM_JIT_ROW");
     if (rowk && *rowk && strcmp(rowk, "table") != 0) return 1;
-    if (!P->rows_ok || P->perbond || P->bcmode || P->K > 15) return 1;
+    if (!P->rows_ok || P->bcmode || P->K > 15) return 1;
     const int K = P->K;
+    // per-bond plans: every slot keeps its own coefficient, so no triangles; an exchange that
+    // is not allowed points at the row itself, whose difference x_i - x_t is then zero
+    const bool self = P->perbond != 0;
     struct Slot { int p, q, c; bool used; };
     std::vector<Slot> low;
     for (int c = 0; c < P->nc; ++c)
@@ -484,7 +489,7 @@ int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
     // a class, e[2] = (a, c) is the opposite edge
     struct Tri { int e[3]; };
     std::vector<Tri> tris;
-    for (int x = 0; x < K; ++x)
+    for (int x = 0; x < K && !self; ++x)
         for (int y = x + 1; y < K; ++y)
             for (int z = y + 1; z < K; ++z) {
                 const int sites[3] = {x, y, z};
@@ -510,7 +515,8 @@ int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
     const int nch = (n + 7) / 8;
     const uint32_t zrow = (uint32_t)(P->max_block + BLK_XPAD - 1);
     if ((zrow + 1) * (uint32_t)esize > 65535u) return 1;
-    std::string key = "tri:" + std::to_string(K) + ":" + std::to_string(esize) + ":" + std::to_string(P->nc) + ":";
+    std::string key = std::string(self ? "self:" : "tri:") + std::to_string(K) + ":" + std::to_string(esize) + ":" +
+                      std::to_string(P->nc) + ":";
     for (auto &sl : low) key += std::to_string(sl.p) + "-" + std::to_string(sl.q) + "/" + std::to_string(sl.c) + ",";
     key += "|";
     for (int p : cps) key += std::to_string(p) + ",";
@@ -541,7 +547,8 @@ int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
                 put(2 * t + 1, o2);
                 codes[t / 8] |= code << (2 * (t % 8));
             }
-            for (int i = 0; i < nsgl; ++i) put(2 * ntri + i, ok(low[sgl[i]]) ? tgt(low[sgl[i]]) : z);
+            const uint32_t own = rank[l] * (uint32_t)esize;
+            for (int i = 0; i < nsgl; ++i) put(2 * ntri + i, ok(low[sgl[i]]) ? tgt(low[sgl[i]]) : self ? own : z);
             for (int i = 0; i < ncode; ++i) put(2 * ntri + nsgl + i, codes[i]);
             for (size_t i = 0; i < cps.size(); ++i)
                 put(2 * ntri + nsgl + ncode + (int)i, rank[l ^ (1u << cps[i])] * (uint32_t)esize);
@@ -636,8 +643,11 @@ int blk_lz32_launch(const BlkParams &P, const float *qc, float *qp, LzScalars *S
 }
 
 // per-bond plan: the specialised y = H x kernel (jit.cu); 1 when it is not available
-static int launch_blk_matvec_pb(hm_basis *b, const BlkParams &P, const BondParams &bp, const void *x, void *y,
+static int launch_blk_matvec_pb(hm_basis *b, const BlkParams &P0, const BondParams &bp, const void *x, void *y,
                                 int dtype, cudaStream_t st) {
+    BlkParams P = P0;
+    const int trc = blk_target_table(b, &P, dtype == HM_F64 ? 8 : 4);
+    if (trc < 0) return trc;
     const void *k = nullptr;
     if (jit_mv_kernel(P, dtype, bp, &k) != 0) return 1;
     const size_t sm = blk_row_smem_bytes(P, dtype == HM_F64 ? 8 : 4, BLK_XPAD);

@@ -283,7 +283,10 @@ std::string gen_row_table(const BlkParams &P) {
 // as in gen_row_slots, each with its own coefficient h_b = J_b / 2 as a literal, summed
 // as h_b (x_i - x_t) (blk_sweep.cuh, per-bond rows).  A slot whose spins are parallel reads
 // a fixed address (a broadcast) and adds a zero difference.
+std::string gen_row_pb_table(const BlkParams &P, const BondParams &bp);
+
 std::string gen_row_pb(const BlkParams &P, const BondParams &bp) {
+    if (P.tt) return gen_row_pb_table(P, bp);
     auto hb = [&](int t) { return -bp.jm[t] / 2.0; };
     // coefficient arguments of hm::pb_mac: C_b (integer, FP64 rows) and h_b (float, FP32 rows)
     auto cf = [&](int t) {
@@ -343,6 +346,72 @@ std::string gen_row_pb(const BlkParams &P, const BondParams &bp) {
         put(s, "    { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at((lh4 ^ 0x%xu) | x_.kofs2) + "
                "R0own; if ((l ^ x_.wm) & x_.vm) a = hm::pb_mac(%s, xo - %s, a); }\n",
             HM_BLK_SX + k, (unsigned)P.xxa[0][1][k], cf(P.pb_xb[1][k]).c_str(), xval(HM_BLK_SX + k));
+    s += "    return hm::blk_high_pb<Sv>(P, B, Xg, r, gx, xo, a);\n}\n};\n";
+    return s;
+}
+
+// The per-bond row policy with a target table (blk.cu blk_target_table, per-bond form): each
+// low slot gathers the row its entry names -- the exchange target, or the row itself when the
+// exchange is not allowed, so that h_b (x_i - x_t) is zero without a test -- and cross slots
+// take the rank of l ^ 2^p from the table.
+std::string gen_row_pb_table(const BlkParams &P, const BondParams &bp) {
+    auto hb = [&](int t) { return -bp.jm[t] / 2.0; };
+    auto cf = [&](int t) {
+        char buf[96];
+        snprintf(buf, sizeof buf, "%lldLL, %.9gf", pb_coef(P, hb(t)), hb(t));
+        return std::string(buf);
+    };
+    std::string s;
+    s += "struct RowJit {\n"
+         "static constexpr int kPad = hm::BLK_XPAD;\n"
+         "static constexpr bool kRelUS = false;\n"
+         "static constexpr bool kPerBond = true;\n"
+         "static constexpr bool kBC = false;\n"
+         "template <class Sv>\n"
+         "static __device__ __forceinline__ void stage(const hm::BlkParams &, unsigned char *) {}\n"
+         "template <class Sv>\n"
+         "static __device__ __forceinline__ void block(const hm::BlkParams &, uint32_t) {}\n"
+         "template <class Sv, class G>\n"
+         "static __device__ __forceinline__ typename hm::PbAcc<Sv>::T sums_pb(const hm::BlkParams &P,\n"
+         "        const hm::BlkMeta &B, const unsigned char *Xsb, const unsigned char *Xg, uint32_t l, uint32_t r,\n"
+         "        const G &gx, Sv xo) {\n"
+         "    (void)l; (void)Xg;\n"
+         "    const uint4 *tt = P.tt + (B.lwo + r);\n"
+         "    typename hm::PbAcc<Sv>::T a = 0;\n";
+    const int nch = (P.tt_n + 7) / 8;
+    for (int j = 0; j < nch; ++j) put(s, "    const uint4 q%d = hm::ldg_v4(tt + %uu);\n", j, (unsigned)j * P.tt_stride);
+    static const char *comp[4] = {"x", "y", "z", "w"};
+    auto entry = [&](int e) {
+        char buf[64];
+        const int j = e / 8, c = (e % 8) / 2;
+        if (e % 2 == 0) snprintf(buf, sizeof buf, "(q%d.%s & 0xFFFFu)", j, comp[c]);
+        else snprintf(buf, sizeof buf, "(q%d.%s >> 16)", j, comp[c]);
+        return std::string(buf);
+    };
+    // the table's single slots are the plan's low slots in order (kinds 0..2, class 0)
+    int e = 0;
+    for (int t = 0; t < 3; ++t)
+        for (int k = 0; k < P.ln[0][t]; ++k, ++e)
+            put(s, "    a = hm::pb_mac(%s, xo - *(const Sv *)(Xsb + %s), a);\n", cf(P.pb_lb[t][k]).c_str(), entry(e).c_str());
+    const int ecross = 2 * P.tt_ntri + P.tt_nsgl + (P.tt_ntri + 7) / 8;
+    auto cross_entry = [&](int t, int k) {
+        const int p = __builtin_ctz((unsigned)P.xxa[0][t][k]) - 2 + (t == 1 ? 8 : 0);
+        for (int i = 0; i < P.tt_ncross; ++i)
+            if (P.tt_cross_p[i] == p) return ecross + i;
+        return -1;
+    };
+    for (int t = 0; t < 2; ++t)
+        for (int k = 0; k < P.xn[0][t]; ++k) {
+            const int dst = t * HM_BLK_SX + k;
+            const char *val = "gx(x_.base + %s)";
+            for (int e2 = 0; e2 < P.nxf; ++e2)
+                if (P.xf_dst[e2] == dst && P.par && P.xf_q[e2] == P.H - 1)
+                    val = P.par < 0 ? "(-gx(x_.base - %s))" : "gx(x_.base - %s)";
+            char buf[128];
+            snprintf(buf, sizeof buf, val, entry(cross_entry(t, k)).c_str());
+            put(s, "    { const hm::XSlot x_ = B.xs[%d]; if ((l ^ x_.wm) & x_.vm) a = hm::pb_mac(%s, xo - %s, a); }\n",
+                dst, cf(P.pb_xb[t][k]).c_str(), buf);
+        }
     s += "    return hm::blk_high_pb<Sv>(P, B, Xg, r, gx, xo, a);\n}\n};\n";
     return s;
 }
