@@ -426,7 +426,8 @@ def test_count_nnz_full_size_closed_form(hm):
 
 
 @pytest.mark.parametrize("case,row", [("j1j2_n20_f64", "table"), ("three_class_n18_f64", "table"),
-                                      ("j1j2_n20_f32", "table"),
+                                      ("j1j2_n20_f32", "table"), ("four_class_j1j2_n20_f64", "table"),
+                                      ("four_class_j1j2_n20_f32", "table"),
                                       ("j1j2_n20_f64", "slots"), ("three_class_n18_f64", "slots"),
                                       ("j1j2_n20_f32", "slots"), ("j1j2_n20_f64", "delta"),
                                       ("three_class_n18_f64", "delta"), ("j1j2_n20_f32", "delta")])
@@ -444,6 +445,15 @@ def test_block_product_specialised_equals_generic(hm, case, row, monkeypatch):
         J = J + [-1.0, 0.5, -0.25]
         bonds = hm.BondList.make(u, v, J)
         two_m, dt = 2, torch.float64
+    elif case.startswith("four_class"):
+        # NN and NNN bonds with four couplings in integer ratios spread over both kinds, so
+        # the triangles of the target tables mix classes (or are skipped where the two edges
+        # at their shared site differ)
+        n = 20
+        inst = W.small_ring(n, -1.0, -0.5)
+        J = [(-1.0, -0.5, -0.25, -0.75)[(3 * i + i // 5) % 4] for i in range(inst.n_bonds)]
+        bonds = hm.BondList.make(inst.u, inst.v, J)
+        two_m, dt = 2, (torch.float32 if case.endswith("f32") else torch.float64)
     else:
         n = 20
         bonds = hm.bonds_of(W.small_ring(n, -1.0, -0.3))
@@ -770,3 +780,26 @@ def test_s1_full_size_rows_and_first_steps(hm):
     scale = max(abs(a1), abs(a2))
     assert abs(ga[0] - a1) <= 1e-12 * scale and abs(gb[0] - b1) <= 1e-12 * scale
     assert abs(ga[1] - a2) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_four_class_triangles_vs_oracle(hm, dtype):
+    """NN and NNN bonds with four couplings in integer ratios spread over both kinds (the
+    target tables' triangles then mix classes or are skipped): the Lanczos coefficients of the
+    block product against the oracle's (FP64 to 1e-11, FP32 to FP32 accuracy), N = 18."""
+    n = 18
+    inst = W.small_ring(n, -1.0, -0.5)
+    J = [(-1.0, -0.5, -0.25, -0.75)[(3 * i + i // 5) % 4] for i in range(inst.n_bonds)]
+    bonds = hm.BondList.make(inst.u, inst.v, J)
+    b = hm.Basis(n, 1, 0)
+    dt = torch.float64 if dtype == "f64" else torch.float32
+    run = hm.LanczosRun(b, bonds, 20, seed=3, dtype=dt)
+    assert run.kernel_name().startswith("k_blk_lz"), run.kernel_name()
+    run.step(20)
+    al, be, _ = run.read()
+    run.close()
+    ob = oracle.Basis(n, 1, n // 2)
+    oal, obe = ob.lanczos(oracle.Bonds(inst.u, inst.v, J), oracle.start_uniform(3, ob.dim), 20)
+    tol = 1e-11 if dtype == "f64" else 2e-5
+    np.testing.assert_allclose(al, oal, rtol=0, atol=tol * np.abs(oal).max())
+    np.testing.assert_allclose(be, obe, rtol=0, atol=tol * np.abs(oal).max())
