@@ -38,7 +38,13 @@ namespace hm {
 __host__ __device__ __forceinline__ size_t al16f(size_t x) { return (x + 15) & ~(size_t)15; }
 
 constexpr int FT_NT = 512;          // threads per CTA of the persistent kernel
-constexpr int FT_CTAS = 2;          // CTAs per SM the register budget is cut for
+// CTAs per SM the register budget is cut for: three (40 registers; the widest tiling then
+// spills a little) ran the N = 24 run in 825 ms against 989 ms with two (64 registers): the
+// kernel waits on gather latency, and the extra resident warps hide more of it
+#ifndef HM_FT_CTAS
+#define HM_FT_CTAS 3
+#endif
+constexpr int FT_CTAS = HM_FT_CTAS;
 constexpr int FT_W = 32;            // row stride in floats (vectors per row, padded)
 constexpr int FT_MAXS = 65;         // sectors (N + 1 for s = 1/2, N <= 64)
 constexpr double FT_TOL = 1e-5;     // breakdown threshold (above the FP32 noise floor)
