@@ -712,14 +712,25 @@ __device__ __forceinline__ void lz32_body(const BlkParams &P, const float *__res
 template <class T> struct BcSv { using S = int64_t; };
 template <> struct BcSv<float> { using S = float; };
 
+// acc += g_i d for one bond: double-float arithmetic on the FP32 pipe (GB300 runs binary64
+// multiply-adds and int64 -> binary64 conversions at about 1/70 of the FP32 rate); d is the
+// exact fixed-point difference x_i - x_t (an integer below 2^54) or a float difference
+__device__ __forceinline__ void bc_mac(ef::df &acc, const ef::df &gi, int64_t d) {
+    acc = ef::df_add(acc, ef::df_mul(gi, ef::df_from_fix(d, 1022 + ef::FIX_BITS, 0, 0)));
+}
+__device__ __forceinline__ void bc_mac(ef::df &acc, const ef::df &gi, float d) {
+    acc = ef::df_add(acc, ef::df_mulf(gi, d));
+}
+
 template <class T, class Row, class Sv, class G>
 __device__ __forceinline__ void bc_sweep(const BlkParams &P, const T *__restrict__ x, const T *__restrict__ g,
-                                         const G &gx, double *acc, double &t0) {
+                                         const G &gx, ef::df *acc, double &t0) {
     blk_sweep<Sv, 1, false, Row>(
         P, (const unsigned char *)x, gx, nullptr, [&](uint32_t i) { return (double)g[i]; },
         [&](uint32_t, uint32_t r, Sv xo, double gi, const BlkMeta &B, const unsigned char *Xsb, uint32_t l) {
             t0 = fma(gi, (double)xo, t0);
-            Row::template sums_bc<Sv>(P, B, Xsb, (const unsigned char *)x, l, r, gx, xo, gi, acc);
+            const ef::df gd = ef::df_from_bits(ef::d2u(gi), 0);
+            Row::template sums_bc<Sv>(P, B, Xsb, (const unsigned char *)x, l, r, gx, xo, gd, acc);
         },
         [](int) {}, [](uint32_t, int) {});
 }
@@ -728,9 +739,9 @@ template <class T, class Row>
 __device__ __forceinline__ void bc_body(const BlkParams &P, const T *__restrict__ x, const T *__restrict__ g,
                                         const int *__restrict__ Eptr, double *__restrict__ part) {
     using Sv = typename BcSv<T>::S;
-    double acc[Row::kNB];
+    ef::df acc[Row::kNB];
 #pragma unroll
-    for (int k = 0; k < Row::kNB; ++k) acc[k] = 0.0;
+    for (int k = 0; k < Row::kNB; ++k) acc[k] = ef::df{0.0f, 0.0f};
     double t0 = 0.0;
     if constexpr (sizeof(T) == 8) bc_sweep<T, Row, Sv>(P, x, g, GF64{Eptr ? *Eptr : 0}, acc, t0);
     else bc_sweep<T, Row, Sv>(P, x, g, GF32{}, acc, t0);
@@ -738,7 +749,7 @@ __device__ __forceinline__ void bc_body(const BlkParams &P, const T *__restrict_
     double *pc = part + (size_t)blockIdx.x * (Row::kNB + 1);
 #pragma unroll
     for (int k = 0; k < Row::kNB; ++k) {
-        const double v = block_sum<BLK_NT>(acc[k], red);
+        const double v = block_sum<BLK_NT>((double)acc[k].hi + (double)acc[k].lo, red);
         if (threadIdx.x == 0) pc[k] = v;
     }
     const double v = block_sum<BLK_NT>(t0, red);

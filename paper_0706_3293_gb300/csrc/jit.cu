@@ -436,7 +436,7 @@ std::string gen_row_bc(const BlkParams &P, int nbk) {
          "template <class Sv, class G>\n"
          "static __device__ __forceinline__ void sums_bc(const hm::BlkParams &P, const hm::BlkMeta &B,\n"
          "        const unsigned char *Xsb, const unsigned char *Xg, uint32_t l, uint32_t r, const G &gx, Sv xo,\n"
-         "        double gi, double *acc) {\n"
+         "        ef::df gi, ef::df *acc) {\n"
          "    const uint32_t l4 = l << 2, lh4 = (l >> 8) << 2, lh4k = lh4 | B.kofs;\n"
          "    const uint32_t R0own = hm::r0s_at(l4 & 0x3FCu), R1own = hm::us_at(lh4k);\n"
          "    const uint32_t zo = (uint32_t)((P.max_block + hm::BLK_XPAD - 1) * sizeof(Sv));   // fixed address\n"
@@ -445,38 +445,38 @@ std::string gen_row_bc(const BlkParams &P, int nbk) {
     for (int t = 0; t < 3; ++t)
         for (int k = 0; k < P.ln[0][t]; ++k) ds.insert(P.ld[0][t][k]);
     for (int d : ds) put(s, "    const uint32_t z%d = l ^ (l >> %d);\n", d, d);
-    const char *add = "acc[%d] = fma(gi, (double)(t ? xo - x : Sv(0)), acc[%d]); }\n";
+    const char *add = "if (t) hm::bc_mac(acc[%d], gi, xo - x); }\n";
     for (int k = 0; k < P.ln[0][0]; ++k) {
         put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = R1own + hm::r0s_at(t ? (l4 ^ 0x%xu) & 0x3FCu : 0u); "
                "const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); ",
             P.ld[0][0][k], P.lvm[0][0][k], (unsigned)P.lxa[0][0][k]);
-        put(s, add, P.pb_lb[0][k], P.pb_lb[0][k]);
+        put(s, add, P.pb_lb[0][k]);
     }
     for (int k = 0; k < P.ln[0][1]; ++k) {
         put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = R0own + hm::us_at(lh4k ^ 0x%xu); "
                "const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); ",
             P.ld[0][1][k], P.lvm[0][1][k], (unsigned)P.lxb[0][1][k]);
-        put(s, add, P.pb_lb[1][k], P.pb_lb[1][k]);
+        put(s, add, P.pb_lb[1][k]);
     }
     for (int k = 0; k < P.ln[0][2]; ++k) {
         put(s, "    { const bool t = (z%d & 0x%xu) != 0u; const uint32_t o = hm::us_at(lh4k ^ 0x%xu) + "
                "hm::r0s_at(t ? (l4 ^ 0x%xu) & 0x3FCu : 0u); const Sv x = *(const Sv *)(Xsb + (t ? o : zo)); ",
             P.ld[0][2][k], P.lvm[0][2][k], (unsigned)P.lxb[0][2][k], (unsigned)P.lxa[0][2][k]);
-        put(s, add, P.pb_lb[2][k], P.pb_lb[2][k]);
+        put(s, add, P.pb_lb[2][k]);
     }
     for (int k = 0; k < P.xn[0][0]; ++k)
         put(s, "    { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at(lh4 | x_.kofs2) + "
                "hm::r0s_at((l4 ^ 0x%xu) & 0x3FCu); if ((l ^ x_.wm) & x_.vm) "
-               "acc[%d] = fma(gi, (double)(xo - gx(x_.base + v_)), acc[%d]); }\n",
-            k, (unsigned)P.xxa[0][0][k], P.pb_xb[0][k], P.pb_xb[0][k]);
+               "hm::bc_mac(acc[%d], gi, xo - gx(x_.base + v_)); }\n",
+            k, (unsigned)P.xxa[0][0][k], P.pb_xb[0][k]);
     for (int k = 0; k < P.xn[0][1]; ++k)
         put(s, "    { const hm::XSlot x_ = B.xs[%d]; const uint32_t v_ = hm::us_at((lh4 ^ 0x%xu) | x_.kofs2) + "
-               "R0own; if ((l ^ x_.wm) & x_.vm) acc[%d] = fma(gi, (double)(xo - gx(x_.base + v_)), acc[%d]); }\n",
-            HM_BLK_SX + k, (unsigned)P.xxa[0][1][k], P.pb_xb[1][k], P.pb_xb[1][k]);
+               "R0own; if ((l ^ x_.wm) & x_.vm) hm::bc_mac(acc[%d], gi, xo - gx(x_.base + v_)); }\n",
+            HM_BLK_SX + k, (unsigned)P.xxa[0][1][k], P.pb_xb[1][k]);
     for (int j = 0; j < P.nhb; ++j)
         put(s, "    { const uint32_t o = B.hbi[%d]; if (o != 0xFFFFFFFFu) "
-               "acc[%d] = fma(gi, (double)(xo - gx(Xg + (size_t)(o + r) * sizeof(Sv))), acc[%d]); }\n",
-            j, P.pb_hbb[j], P.pb_hbb[j]);
+               "hm::bc_mac(acc[%d], gi, xo - gx(Xg + (size_t)(o + r) * sizeof(Sv))); }\n",
+            j, P.pb_hbb[j]);
     s += "}\n};\n";
     return s;
 }
