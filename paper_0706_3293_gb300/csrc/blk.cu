@@ -451,18 +451,18 @@ int blk_lz_jit(const BlkParams &P, int dtype, const BondParams &bp, const void *
 // The low slots are grouped first into edge-disjoint triangles: bonds (a, b), (b, c), (a, c)
 // among the low sites with (a, b) and (b, c) of one class.  Of the three spin pairs of a
 // triangle either none or exactly two are unequal, so two gathers serve its three slots: the
-// table holds the first and the second allowed target (in the order (a, b), (b, c), (a, c))
-// and a 2-bit code (1: the first two edges, 2: first and third, 3: second and third, 0:
-// none); the first allowed edge is always of the class of (a, b).  The remaining slots take
-// one entry each.  Entries: the triangles' two targets, the single slots' targets, the codes
-// (eight to an entry), the rank of l ^ 2^p for each low end p of a cross bond.  Targets are
-// byte offsets into the staged block (rows times esize), the zero row after the block when
-// not allowed.  16-bit entries, eight to a 16-byte chunk, chunk-major so that consecutive
-// rows read consecutive chunks (2^K rows x chunks x 16 bytes: 2 MB at K = 15), built once
-// per basis, layout and element size.  A per-bond plan (each bond its own coefficient) takes
-// no triangles, and a slot whose exchange is not allowed points at the row itself, so that
-// its difference x_i - x_t vanishes.  Returns 0 and sets P->tt, or 1 when the policy does not
-// apply (more than 48 entries, or HM_JIT_ROW selects another policy).
+// table holds the first and the second allowed target (in the order (a, b), (b, c), (a, c)).
+// The first allowed edge is always of the class of (a, b); the second is (b, c) exactly when
+// the spins of a and c are parallel, which the kernel reads off the row's own word.  The
+// remaining slots take one entry each.  Entries: the triangles' two targets, the single
+// slots' targets, the rank of l ^ 2^p for each low end p of a cross bond.  Targets are byte
+// offsets into the staged block (rows times esize), the zero row after the block when not
+// allowed.  16-bit entries, eight to a 16-byte chunk, chunk-major so that consecutive rows
+// read consecutive chunks (2^K rows x chunks x 16 bytes: 1.5 MB at K = 15 for the J1-J2
+// ring), built once per basis, layout and element size.  A per-bond plan (each bond its own
+// coefficient) takes no triangles, and a slot whose exchange is not allowed points at the
+// row itself, so that its difference x_i - x_t vanishes.  Returns 0 and sets P->tt, or 1 when
+// the policy does not apply (more than 48 entries, or HM_JIT_ROW selects another policy).
 int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
     P->tt = nullptr;
     const char *rowk = getenv("HM_JIT_ROW");
@@ -509,8 +509,8 @@ int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
     for (int e = 0; e < P->nxf; ++e)
         if (std::find(cps.begin(), cps.end(), (int)P->xf_p[e]) == cps.end()) cps.push_back(P->xf_p[e]);
     if (cps.size() > 8 || sgl.size() > 48) return 1;
-    const int ntri = (int)tris.size(), nsgl = (int)sgl.size(), ncode = (ntri + 7) / 8;
-    const int n = 2 * ntri + nsgl + ncode + (int)cps.size();
+    const int ntri = (int)tris.size(), nsgl = (int)sgl.size();
+    const int n = 2 * ntri + nsgl + (int)cps.size();
     if (n > 48) return 1;
     const int nch = (n + 7) / 8;
     const uint32_t zrow = (uint32_t)(P->max_block + BLK_XPAD - 1);
@@ -535,23 +535,20 @@ int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
             auto ok = [&](const Slot &sl) { return ((l >> sl.p) ^ (l >> sl.q)) & 1u; };
             auto tgt = [&](const Slot &sl) { return rank[l ^ ((1u << sl.p) | (1u << sl.q))] * (uint32_t)esize; };
             const uint32_t z = zrow * (uint32_t)esize;
-            std::vector<uint32_t> codes((size_t)ncode, 0);
             for (int t = 0; t < ntri; ++t) {
                 const Slot &e0 = low[tris[t].e[0]], &e1 = low[tris[t].e[1]], &e2 = low[tris[t].e[2]];
                 const bool v0 = ok(e0), v1 = ok(e1), v2 = ok(e2);
-                uint32_t o1 = z, o2 = z, code = 0;
-                if (v0 && v1) { o1 = tgt(e0); o2 = tgt(e1); code = 1; }
-                else if (v0 && v2) { o1 = tgt(e0); o2 = tgt(e2); code = 2; }
-                else if (v1 && v2) { o1 = tgt(e1); o2 = tgt(e2); code = 3; }
+                uint32_t o1 = z, o2 = z;
+                if (v0 && v1) { o1 = tgt(e0); o2 = tgt(e1); }
+                else if (v0 && v2) { o1 = tgt(e0); o2 = tgt(e2); }
+                else if (v1 && v2) { o1 = tgt(e1); o2 = tgt(e2); }
                 put(2 * t, o1);
                 put(2 * t + 1, o2);
-                codes[t / 8] |= code << (2 * (t % 8));
             }
             const uint32_t own = rank[l] * (uint32_t)esize;
             for (int i = 0; i < nsgl; ++i) put(2 * ntri + i, ok(low[sgl[i]]) ? tgt(low[sgl[i]]) : self ? own : z);
-            for (int i = 0; i < ncode; ++i) put(2 * ntri + nsgl + i, codes[i]);
             for (size_t i = 0; i < cps.size(); ++i)
-                put(2 * ntri + nsgl + ncode + (int)i, rank[l ^ (1u << cps[i])] * (uint32_t)esize);
+                put(2 * ntri + nsgl + (int)i, rank[l ^ (1u << cps[i])] * (uint32_t)esize);
         }
         void *dev = nullptr;
         HM_CUDA(cudaMalloc(&dev, host.size() * 2));
@@ -569,6 +566,8 @@ int blk_target_table(hm_basis *b, BlkParams *P, int esize) {
     for (int t = 0; t < ntri; ++t) {
         P->tt_tri_ca[t] = (uint8_t)low[tris[t].e[0]].c;
         P->tt_tri_cb[t] = (uint8_t)low[tris[t].e[2]].c;
+        P->tt_tri_a[t] = (uint8_t)low[tris[t].e[2]].p;
+        P->tt_tri_c[t] = (uint8_t)low[tris[t].e[2]].q;
     }
     for (int i = 0; i < nsgl; ++i) P->tt_sgl_c[i] = (uint8_t)low[sgl[i]].c;
     return 0;

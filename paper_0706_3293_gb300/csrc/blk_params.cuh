@@ -86,19 +86,19 @@ struct BlkParams {
     // per-class target tables (row policy "table", jit.cu): the row of rank r in the low-word
     // list of class k (list position g = lwoff[k] + r) has tt_n 16-bit entries, eight to a
     // 16-byte chunk, entry s in chunk s / 8 at tt[(s / 8) * tt_stride + g]: first the byte
-    // offset of each low slot's target row in the staged block (the zero row when the two
+    // offsets of the low slots' target rows in the staged block (the zero row when the two
     // spins are parallel), then for each low end p of a cross bond the byte offset of the rank
-    // of l ^ 2^p among the words of its popcount, then the exchange counts of the low slots,
-    // eight bits per class
+    // of l ^ 2^p among the words of its popcount
     const uint4 *tt;
     uint32_t tt_stride;
     int tt_n, tt_ncross, tt_cross_p[8];
     // the low slots as edge-disjoint triangles of bonds (a, b), (b, c), (a, c), whose spin
-    // pairs hold exactly zero or two unequal pairs, so two gathers serve three slots (two
-    // entries each; 2-bit codes, eight to an entry, say which two), then single slots.  The
-    // first gathered edge of a triangle is always class tri_ca, the second tri_ca or tri_cb
+    // pairs hold exactly zero or two unequal pairs, so two gathers (two entries) serve three
+    // slots, then single slots.  The first gathered edge of a triangle is always class
+    // tri_ca; the second is (b, c), class tri_ca, when the spins of a and c are parallel,
+    // else (a, c), class tri_cb: tri_a and tri_c are the sites of (a, c)
     int tt_ntri, tt_nsgl;
-    uint8_t tt_tri_ca[16], tt_tri_cb[16], tt_sgl_c[48];
+    uint8_t tt_tri_ca[16], tt_tri_cb[16], tt_tri_a[16], tt_tri_c[16], tt_sgl_c[48];
     // two-pass FP64 Lanczos product (integer-ratio classes): pass 1 applies the near bonds
     // and stores each row's exact integer class sum, pass 2 adds the far bonds (those
     // reaching the top sites) and rounds once.  rot: pass 2 takes the blocks in the order of

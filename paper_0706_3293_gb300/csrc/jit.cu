@@ -218,8 +218,7 @@ std::string gen_row_table(const BlkParams &P) {
         else snprintf(buf, sizeof buf, "(q%d.%s >> 16)", j, comp[c]);
         return std::string(buf);
     };
-    const int ntri = P.tt_ntri, nsgl = P.tt_nsgl, ncode = (ntri + 7) / 8;
-    const int ecode = 2 * ntri + nsgl, ecross = ecode + ncode;
+    const int ntri = P.tt_ntri, nsgl = P.tt_nsgl, ecross = 2 * ntri + nsgl;
     auto cross_entry = [&](int c, int t, int k) {
         const int p = __builtin_ctz((unsigned)P.xxa[c][t][k]) - 2 + (t == 1 ? 8 : 0);
         for (int i = 0; i < P.tt_ncross; ++i)
@@ -242,8 +241,11 @@ std::string gen_row_table(const BlkParams &P) {
         if (ca == cb) {
             put(s, "      a%d += x1 + x2; }\n", ca);
         } else {
-            // code 1: both gathered edges are of class ca; codes 2, 3: the second is of class cb
-            put(s, "      const Sv x2a = ((%s >> %d) & 3u) == 1u ? x2 : Sv(0);\n", entry(ecode + t / 8).c_str(), 2 * (t % 8));
+            // the second gathered edge is (b, c), class ca, when the spins of a and c are
+            // parallel, else (a, c), class cb
+            const int a = P.tt_tri_a[t], c = P.tt_tri_c[t], d = c - a;
+            if (ds.count(d)) put(s, "      const Sv x2a = ((z%d >> %d) & 1u) ? Sv(0) : x2;\n", d, a);
+            else put(s, "      const Sv x2a = (((l >> %d) ^ (l >> %d)) & 1u) ? Sv(0) : x2;\n", a, c);
             put(s, "      a%d += x1 + x2a; a%d += x2 - x2a; }\n", ca, cb);
         }
     }
@@ -393,7 +395,7 @@ std::string gen_row_pb_table(const BlkParams &P, const BondParams &bp) {
     for (int t = 0; t < 3; ++t)
         for (int k = 0; k < P.ln[0][t]; ++k, ++e)
             put(s, "    a = hm::pb_mac(%s, xo - *(const Sv *)(Xsb + %s), a);\n", cf(P.pb_lb[t][k]).c_str(), entry(e).c_str());
-    const int ecross = 2 * P.tt_ntri + P.tt_nsgl + (P.tt_ntri + 7) / 8;
+    const int ecross = 2 * P.tt_ntri + P.tt_nsgl;
     auto cross_entry = [&](int t, int k) {
         const int p = __builtin_ctz((unsigned)P.xxa[0][t][k]) - 2 + (t == 1 ? 8 : 0);
         for (int i = 0; i < P.tt_ncross; ++i)

@@ -245,10 +245,11 @@ def ring_triangles(K):
 @pytest.mark.parametrize("K", [10, 13, 15])
 def test_triangle_encoding_of_low_exchanges(K):
     """For three sites joined by three bonds either no spin pair or exactly two differ, so
-    the table stores two targets and a code (1: e1 e2, 2: e1 e3, 3: e2 e3); the first stored
-    target is always an e1 or e2 exchange (class J1), the second is class J1 for code 1 and
-    J2 otherwise.  Per class, the stored targets summed as the kernel sums them equal the
-    allowed exchanges' targets, for every K-bit word."""
+    the table stores two targets: the first allowed edge in the order e1, e2, e3 and the
+    second.  The first is always an e1 or e2 exchange (class J1); the second is e2 (class J1)
+    when the spins of the ends of e3 are parallel, else e3 (class J2), which the kernel reads
+    off the row's own word.  Per class, the stored targets summed as the kernel sums them
+    equal the allowed exchanges' targets, for every K-bit word."""
     tris = ring_triangles(K)
     rank = {}
     seen = [0] * (K + 1)
@@ -261,15 +262,10 @@ def test_triangle_encoding_of_low_exchanges(K):
             ok = [((l >> a) ^ (l >> b)) & 1 for a, b in (e1, e2, e3)]
             assert sum(ok) in (0, 2)
             tg = [rank[l ^ (1 << a) ^ (1 << b)] for a, b in (e1, e2, e3)]
-            if ok[0] and ok[1]:
-                o1, o2, code = tg[0], tg[1], 1
-            elif ok[0] and ok[2]:
-                o1, o2, code = tg[0], tg[2], 2
-            elif ok[1] and ok[2]:
-                o1, o2, code = tg[1], tg[2], 3
-            else:
-                o1, o2, code = Z, Z, 0
-            cls_a = [] if code == 0 else ([o1, o2] if code == 1 else [o1])
-            cls_b = [o2] if code in (2, 3) else []
+            allowed = [t for t, v in zip(tg, ok) if v]
+            o1, o2 = (allowed[0], allowed[1]) if allowed else (Z, Z)
+            second_is_e3 = ((l >> e3[0]) ^ (l >> e3[1])) & 1
+            cls_a = [x for x in (o1, o2 if not second_is_e3 else Z) if x != Z]
+            cls_b = [o2] if second_is_e3 else []
             assert sorted(cls_a) == sorted(t for t, v in zip(tg[:2], ok[:2]) if v)
             assert sorted(cls_b) == sorted(t for t, v in zip(tg[2:], ok[2:]) if v)
