@@ -74,7 +74,10 @@ __device__ __forceinline__ int popc_below(uint64_t m, int e) {
 
 // sum of the high-exchange gathers of class c for row r (the same low word in each target
 // block), NH gathers in flight: four target offsets per 16-byte shared load (NH = 4), two per
-// 8-byte load (NH = 2), or one at a time (NH = 1; fewest live registers)
+// 8-byte load (NH = 2), or one at a time (NH = 1; fewest live registers).  With NH = 4 the
+// FP32 rows predicate the last round's loads past the class's run (padded to a multiple of
+// four entries), so no gather waits for another; the FP64 rows take the rest one by one,
+// which keeps their 40 registers without spills.
 template <class Sv, int NH = 4, class G>
 __device__ __forceinline__ Sv blk_high_sum(const BlkMeta &B, int c, const unsigned char *Xg, uint32_t r,
                                            const G &gx) {
@@ -83,12 +86,16 @@ __device__ __forceinline__ Sv blk_high_sum(const BlkMeta &B, int c, const unsign
     int e = e0;
     if constexpr (NH == 4) {
         const uint4 *h4 = reinterpret_cast<const uint4 *>(B.hbi);
-        for (; e + 4 <= e1; e += 4) {
+        constexpr bool kPred = sizeof(Sv) == 4;
+        for (; kPred ? e < e1 : e + 4 <= e1; e += 4) {
             const uint4 t = h4[e >> 2];
-            const Sv v0 = gx(Xg + (size_t)(t.x + r) * sizeof(Sv)), v1 = gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
-            const Sv v2 = gx(Xg + (size_t)(t.z + r) * sizeof(Sv)), v3 = gx(Xg + (size_t)(t.w + r) * sizeof(Sv));
+            const Sv v0 = gx(Xg + (size_t)(t.x + r) * sizeof(Sv));
+            const Sv v1 = !kPred || e + 1 < e1 ? gx(Xg + (size_t)(t.y + r) * sizeof(Sv)) : Sv(0);
+            const Sv v2 = !kPred || e + 2 < e1 ? gx(Xg + (size_t)(t.z + r) * sizeof(Sv)) : Sv(0);
+            const Sv v3 = !kPred || e + 3 < e1 ? gx(Xg + (size_t)(t.w + r) * sizeof(Sv)) : Sv(0);
             a += (v0 + v1) + (v2 + v3);
         }
+        if constexpr (kPred) return a;
     } else if constexpr (NH == 2) {
         const uint2 *h2 = reinterpret_cast<const uint2 *>(B.hbi);
         for (; e + 2 <= e1; e += 2) {
@@ -621,14 +628,36 @@ __device__ __forceinline__ void lz64_body(const BlkParams &P, const long long *_
     const int u = E - 1022 - ef::FIX_BITS;
     __int128 d1 = 0;
     ef::df d1f{0.0f, 0.0f};
-    // row value: exact class sums, or (per-bond plan) one binary64 sum of h_b (x_i - x_t)
+    // row value: exact class sums, or (per-bond plan) one binary64 sum of h_b (x_i - x_t).
+    // Integer ratios: s = sum_c K_c T_c = 2 sum_c K_c acc_c + (sum_c K_c (n_c - 2 cnt_c)) x_i,
+    // one exact integer (|K_c| <= 64 and sum_c |K_c| n_c < 334, so the second factor is a
+    // small int and every partial stays below 2^63), rounded once to binary64
     auto rowc = [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt, int) {
-        int64_t Tc[NC], ts;
-        blk_classes<NC>(P, acc, cnt, xo, Tc);
-        const unsigned long long yb = blk_y_bits<NC, IR ? 1 : 0>(P, Tc, u, &ts);
-        __stcs(Y + off + r, yb);
-        if constexpr (IR) d1 += (__int128)xo * ts;
-        else d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
+        if constexpr (IR) {
+            int64_t a = 0;
+            int m = 0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                a += (int64_t)P.Kc[c] * acc[c];
+                m += P.Kc[c] * (P.ntot[c] - 2 * cnt[c]);
+            }
+            const int64_t ts = 2 * a + (int64_t)m * xo;
+            unsigned long long yb;
+            if (P.g0_pow2) {
+                yb = ef::bits_from_int(ts, u + P.g0_exp);
+            } else {
+                const ef::df t = ef::df_from_fix(ts, u + 1022 + ef::FIX_BITS, 0, 0);
+                yb = ef::bits_from_df(ef::df_mul(t, ef::df{P.g0_hi, P.g0_lo}), 0);
+            }
+            __stcs(Y + off + r, yb);
+            d1 += (__int128)xo * ts;
+        } else {
+            int64_t Tc[NC], ts;
+            blk_classes<NC>(P, acc, cnt, xo, Tc);
+            const unsigned long long yb = blk_y_bits<NC, 0>(P, Tc, u, &ts);
+            __stcs(Y + off + r, yb);
+            d1f = ef::df_add(d1f, ef::df_mul(ef::df_from_fix(xo, E, 0, E - 1023), ef::df_from_bits(yb, E - 1023)));
+        }
     };
     const double sy = ef::pow2d(u - P.pb_s);
     auto rowb = [&](uint32_t off, uint32_t r, int64_t xo, __int128 sv, int) {
