@@ -74,11 +74,14 @@ __device__ __forceinline__ int popc_below(uint64_t m, int e) {
 
 // sum of the high-exchange gathers of class c for row r (the same low word in each target
 // block), NH gathers in flight: four target offsets per 16-byte shared load (NH = 4), two per
-// 8-byte load (NH = 2), or one at a time (NH = 1; fewest live registers).  With NH = 4 the
-// FP32 rows predicate the last round's loads past the class's run (padded to a multiple of
-// four entries), so no gather waits for another; the FP64 rows take the rest one by one,
-// which keeps their 40 registers without spills.
-template <class Sv, int NH = 4, class G>
+// 8-byte load (NH = 2), or one at a time (NH = 1; fewest live registers).  PRED (NH = 4):
+// the last round's loads past the class's run (padded to a multiple of four entries) are
+// predicated off instead of taken one by one in a tail loop, so no gather waits for another.
+// Which form is faster depends on the kernel's register allocation at 40 registers: the FP32
+// rows predicate (N = 32 product 11.07 -> 10.16 ms), the FP64 rows of the sector product
+// predicate with the values added in sequence (14.80 -> 14.69 ms), the FP64 spin-flip rows
+// keep the tail loop (8.18 against 8.59 ms).
+template <class Sv, int NH = 4, bool PRED = (sizeof(Sv) == 4), class G>
 __device__ __forceinline__ Sv blk_high_sum(const BlkMeta &B, int c, const unsigned char *Xg, uint32_t r,
                                            const G &gx) {
     const int e0 = B.hs[c], e1 = B.he[c];
@@ -86,16 +89,23 @@ __device__ __forceinline__ Sv blk_high_sum(const BlkMeta &B, int c, const unsign
     int e = e0;
     if constexpr (NH == 4) {
         const uint4 *h4 = reinterpret_cast<const uint4 *>(B.hbi);
-        constexpr bool kPred = sizeof(Sv) == 4;
-        for (; kPred ? e < e1 : e + 4 <= e1; e += 4) {
+        for (; PRED ? e < e1 : e + 4 <= e1; e += 4) {
             const uint4 t = h4[e >> 2];
-            const Sv v0 = gx(Xg + (size_t)(t.x + r) * sizeof(Sv));
-            const Sv v1 = !kPred || e + 1 < e1 ? gx(Xg + (size_t)(t.y + r) * sizeof(Sv)) : Sv(0);
-            const Sv v2 = !kPred || e + 2 < e1 ? gx(Xg + (size_t)(t.z + r) * sizeof(Sv)) : Sv(0);
-            const Sv v3 = !kPred || e + 3 < e1 ? gx(Xg + (size_t)(t.w + r) * sizeof(Sv)) : Sv(0);
-            a += (v0 + v1) + (v2 + v3);
+            if constexpr (PRED && sizeof(Sv) == 8) {
+                const uint32_t tt[4] = {t.x, t.y, t.z, t.w};
+                Sv v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = e + i < e1 ? gx(Xg + (size_t)(tt[i] + r) * sizeof(Sv)) : Sv(0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a += v[i];
+            } else {
+                const Sv v0 = gx(Xg + (size_t)(t.x + r) * sizeof(Sv));
+                const Sv v1 = !PRED || e + 1 < e1 ? gx(Xg + (size_t)(t.y + r) * sizeof(Sv)) : Sv(0);
+                const Sv v2 = !PRED || e + 2 < e1 ? gx(Xg + (size_t)(t.z + r) * sizeof(Sv)) : Sv(0);
+                const Sv v3 = !PRED || e + 3 < e1 ? gx(Xg + (size_t)(t.w + r) * sizeof(Sv)) : Sv(0);
+                a += (v0 + v1) + (v2 + v3);
+            }
         }
-        if constexpr (kPred) return a;
     } else if constexpr (NH == 2) {
         const uint2 *h2 = reinterpret_cast<const uint2 *>(B.hbi);
         for (; e + 2 <= e1; e += 2) {
@@ -103,7 +113,8 @@ __device__ __forceinline__ Sv blk_high_sum(const BlkMeta &B, int c, const unsign
             a += gx(Xg + (size_t)(t.x + r) * sizeof(Sv)) + gx(Xg + (size_t)(t.y + r) * sizeof(Sv));
         }
     }
-    for (; e < e1; ++e) a += gx(Xg + (size_t)(B.hbi[e] + r) * sizeof(Sv));
+    if constexpr (!(NH == 4 && PRED))
+        for (; e < e1; ++e) a += gx(Xg + (size_t)(B.hbi[e] + r) * sizeof(Sv));
     return a;
 }
 

@@ -268,13 +268,15 @@ std::string gen_row_table(const BlkParams &P) {
     // registers (and local-memory spills) down
     int nh = 4;
     if (const char *v = getenv("HM_JIT_HIGH")) nh = atoi(v) == 1 ? 1 : atoi(v) == 2 ? 2 : 4;
+    // the last round predicated (blk_high_sum's PRED): FP32 rows and the FP64 rows of the
+    // sector product; the FP64 spin-flip rows keep the tail loop
     for (int c = 0; c < P.nc; ++c) {
         if (P.par)
             put(s, "    acc[%d] = a%d + hm::blk_high_sum<Sv, %d>(B, %d, Xg, r, gx) %s hm::blk_flip_sum<Sv>(B, %d, Xg, r, gx);\n"
                    "    cnt[%d] = m%d + (B.he[%d] - B.hs[%d]) + (B.x->fe[%d] - B.x->fs[%d]);\n",
                 c, c, nh, c, P.par < 0 ? "-" : "+", c, c, c, c, c, c, c);
         else
-            put(s, "    acc[%d] = a%d + hm::blk_high_sum<Sv, %d>(B, %d, Xg, r, gx);\n    cnt[%d] = m%d + (B.he[%d] - B.hs[%d]);\n",
+            put(s, "    acc[%d] = a%d + hm::blk_high_sum<Sv, %d, true>(B, %d, Xg, r, gx);\n    cnt[%d] = m%d + (B.he[%d] - B.hs[%d]);\n",
                 c, c, nh, c, c, c, c, c);
     }
     s += "#undef XS\n}\n};\n";
