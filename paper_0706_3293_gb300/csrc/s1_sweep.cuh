@@ -186,10 +186,23 @@ __device__ __forceinline__ void s1j_body32(const S1Plan &P, const float *__restr
             const float xo = Xs[r];
             float dg = sb.bdiag, acc = 0.0f;
             Row::row32(l, Xs, x, P.rl + g, P.rx + g, sb.cb, sb.cc, dg, acc);
-#pragma unroll 4
-            for (int e = 0; e < nh; ++e) {
-                const S1Hi<float> he = sb.hx[e];
-                acc = fmaf(he.c, __ldg(x + (he.t + (uint32_t)r)), acc);
+            // four high gathers a round, the last round's loads past the list predicated off
+            // (no serial tail); the multiply-adds keep the list order
+            for (int e = 0; e < nh; e += 4) {
+                float cv[4], xv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (e + i < nh) {
+                        const S1Hi<float> he = sb.hx[e + i];
+                        cv[i] = he.c;
+                        xv[i] = __ldg(x + (he.t + (uint32_t)r));
+                    } else {
+                        cv[i] = 0.0f;
+                        xv[i] = 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc = fmaf(cv[i], xv[i], acc);
             }
             const float hv = fmaf(dg, xo, acc);
             if constexpr (LZ) {
