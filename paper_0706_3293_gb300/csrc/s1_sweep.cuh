@@ -270,10 +270,22 @@ __device__ __forceinline__ void s1j_body64(const S1Plan &P, const long long *__r
             long long dg = sb.bdiag;
             __int128 a = 0;
             Row::row64(l, Xs, Xc, P.rl + g, P.rx + g, sb.cb, sb.cc, dg, a);
-#pragma unroll 2
-            for (int e = 0; e < nh; ++e) {
-                const S1Hi<long long> he = sb.hx[e];
-                a += (__int128)__ldg(Xc + (he.t + (uint32_t)r)) * he.c;
+            // two high gathers a round, the last round's second load predicated off
+            for (int e = 0; e < nh; e += 2) {
+                long long cv[2], xv[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    if (e + i < nh) {
+                        const S1Hi<long long> he = sb.hx[e + i];
+                        cv[i] = he.c;
+                        xv[i] = __ldg(Xc + (he.t + (uint32_t)r));
+                    } else {
+                        cv[i] = 0;
+                        xv[i] = 0;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) a += (__int128)xv[i] * cv[i];
             }
             const __int128 t = a + (__int128)dg * xo;
             const unsigned long long yb = ef::d2u(s1_i128_to_double(t) * sy);
