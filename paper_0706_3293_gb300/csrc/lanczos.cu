@@ -43,7 +43,7 @@ constexpr int NT = 256;
 struct LzLayout {
     size_t buf[2], part, sc, alpha, beta, ritz, psi, coef, res, gout, tri, bpart, total;
     size_t ybuf, xs[2];     // FP64 block path: y = H q and the fixed-point copies of q
-    size_t qqp;             // FP64 block path: partials of q_cur . q_prev (k_fix)
+    size_t qqp;             // FP64 block path: partials of q_cur . q_prev (update kernel)
     size_t hpart;           // s = 1/2 block path: per-block partial sums, 2 x 2^hpart_H doubles
     int hpart_H;
     size_t s1part;          // s = 1 block path: one partial sum per block, s1n of them
@@ -124,7 +124,7 @@ struct hm_lanczos {
     hm::LzScalars *sc;
     double *alpha, *beta, *part, *psi, *coef;
     double *hpart;          // per-block partials of the block path (entries of absent blocks stay 0)
-    double *qqp;            // partials of q_cur . q_prev (FP64 block path)
+    double *qqp;            // partials of q_cur . q_prev (FP64 block path, from the update)
 };
 
 namespace hm {
@@ -314,8 +314,9 @@ k_fix(const unsigned long long *__restrict__ w, long long *__restrict__ X, const
 }
 
 // alpha_j = sigma^2 (q.Hq) - sigma gamma (q.q_prev): q.Hq from the per-block partials of
-// the FP64 block product, q.q_prev from those of the fixed-point copy (k_fix) of q (the
-// Paige form v.(Hv - beta v_prev))
+// the FP64 block product (exact integer dots of the fixed-point copy), q.q_prev from those
+// of the update kernel that made q (double-float), zero at the start (the Paige form
+// v.(Hv - beta v_prev))
 __global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int nblk, const double *__restrict__ qqp,
                             int nq, double *alpha, int pprev) {
     if (S->done) return;
@@ -339,21 +340,29 @@ __global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int n
 // FP64 block path.  The Lanczos vectors are kept as double-float pairs (hi, lo floats,
 // 8 bytes): the update computes in double-float, so a pair holds all it produces and
 // needs no conversion to or from binary64.
+// Resident CTAs per SM of the FP64 block path's update: 40 registers a thread (at 8 CTAs
+// and 32 registers its double-float dots spill; N = 32 step 20.21 against 20.09 ms with the
+// spills and 19.82 ms here).  The update, the copy and the beta reduction of that path run
+// on a grid of this many CTAs per SM (upd64_blocks).
+constexpr int UPD64_CTAS = 6;
+static int upd64_blocks(uint64_t dim) { return std::min(grid_blocks(dim, NT), sm_count() * UPD64_CTAS); }
+
 // w = sigma y - alpha sigma q - gamma q_prev over q_prev (y: binary64 bits of H q);
-// part = |w|^2; largest exponent of w, as a binary64 exponent field, to S->emax[pprev];
-// psi += coef_j q if PSI
+// part = |w|^2; qqp = w . q (the stored new and current vectors, for the next alpha; both
+// dots in double-float per thread, binary64 over the block); largest exponent of w, as a
+// binary64 exponent field, to S->emax[pprev]; psi += coef_j q if PSI
 template <bool PSI>
-__global__ void __launch_bounds__(NT, 2048 / NT)
+__global__ void __launch_bounds__(NT, UPD64_CTAS)
 k_lz_update_y(const unsigned long long *__restrict__ Y, const float2 *__restrict__ qc, float2 *__restrict__ qp,
               uint64_t n, LzScalars *S, const double *__restrict__ alpha, double *__restrict__ part,
-              double *__restrict__ psi, const double *__restrict__ coef, int pprev) {
+              double *__restrict__ qqp, double *__restrict__ psi, const double *__restrict__ coef, int pprev) {
     if (S->done) return;
     __shared__ double red[NT / 32];
     const double sg = S->sigma_cur, gm = S->beta_prev * S->sigma_prev, as = alpha[S->j] * sg;
     const double cj = psi ? coef[S->j] * sg : 0.0;
     auto todf = [](double v) { const float h = (float)v; return ef::df{h, (float)(v - (double)h)}; };
     const ef::df sg_d = todf(sg), as_d = todf(as), gm_d = todf(gm);
-    ef::df s{0.0f, 0.0f};
+    ef::df s{0.0f, 0.0f}, dq{0.0f, 0.0f};
     uint32_t eh = 0;
     const uint64_t stride = (uint64_t)gridDim.x * NT;
     uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x;
@@ -365,17 +374,22 @@ k_lz_update_y(const unsigned long long *__restrict__ Y, const float2 *__restrict
         const unsigned long long yb = yn;
         const float2 q2 = qn, p2 = pn;
         if (r + stride < n) { yn = __ldcs(Y + r + stride); qn = __ldcs(qc + r + stride); pn = qp[r + stride]; }
+        const ef::df q = ef::df{q2.x, q2.y};
         const ef::df t1 = ef::df_mul(sg_d, ef::df_from_bits(yb, 0));
-        const ef::df t2 = ef::df_mul(as_d, ef::df{q2.x, q2.y});
+        const ef::df t2 = ef::df_mul(as_d, q);
         const ef::df t3 = ef::df_mul(gm_d, ef::df{p2.x, p2.y});
         const ef::df w = ef::df_add(t1, ef::df_neg(ef::df_add(t2, t3)));
         qp[r] = make_float2(w.hi, w.lo);
         eh = max(eh, (ef::f2u(w.hi) >> 23) & 0xFFu);
         s = ef::df_add(s, ef::df_mul(w, w));
+        dq = ef::df_add(dq, ef::df_mul(w, q));
         if constexpr (PSI) psi[r] += cj * ((double)q2.x + (double)q2.y);
     }
     const double tot = block_sum<NT>((double)s.hi + (double)s.lo, red);
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    __syncthreads();
+    const double tq = block_sum<NT>((double)dq.hi + (double)dq.lo, red);
+    if (threadIdx.x == 0) qqp[blockIdx.x] = tq;
     for (int o = 16; o > 0; o >>= 1) eh = max(eh, __shfl_down_sync(0xffffffffu, eh, o));
     // |hi| < 2^(eh - 126): the binary64 field eh - 127 + 1023 bounds hi, and hi + lo up
     // to a factor 1 + 2^-24 (the fixed-point copy then stays within 2^53 + 2^29 units)
@@ -392,32 +406,20 @@ __global__ void __launch_bounds__(NT) k_to_df(unsigned long long *__restrict__ b
 }
 
 // fixed-point copy X of the new vector w (double-float pairs), unit from its largest
-// exponent, and the exact dot X . Xo with the copy Xo of the vector before it:
-// qqp[blk] = (q_new . q_cur) in true units, for the next alpha
+// exponent (the dot with the current vector for the next alpha comes from the update)
 __global__ void __launch_bounds__(NT, 2048 / NT)
-k_fixd(const float2 *__restrict__ w, long long *__restrict__ X, const long long *__restrict__ Xo, uint64_t n,
-       const LzScalars *S, int slot, double *__restrict__ qqp) {
+k_fixd(const float2 *__restrict__ w, long long *__restrict__ X, uint64_t n, const LzScalars *S, int slot) {
     if (S->done) return;
-    __shared__ double red[NT / 32];
-    const int E = S->emax[slot], Eo = S->emax[slot ^ 1];
-    __int128 d = 0;
+    const int E = S->emax[slot];
     const uint64_t stride = (uint64_t)gridDim.x * NT;
     uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x;
     float2 vn = make_float2(0.0f, 0.0f);
-    long long on = 0;
-    if (r < n) { vn = __ldcs(w + r); on = __ldcs(Xo + r); }
-    for (; r < n; r += stride) {                       // next row's operands loaded first
+    if (r < n) vn = __ldcs(w + r);
+    for (; r < n; r += stride) {                       // next row's operand loaded first
         const float2 v = vn;
-        const long long o = on;
-        if (r + stride < n) { vn = __ldcs(w + r + stride); on = __ldcs(Xo + r + stride); }
-        const long long x = (long long)ef::fix_from_df(ef::df{v.x, v.y}, E, 0);
-        __stcs(X + r, x);
-        d += (__int128)x * o;
+        if (r + stride < n) vn = __ldcs(w + r + stride);
+        __stcs(X + r, (long long)ef::fix_from_df(ef::df{v.x, v.y}, E, 0));
     }
-    const long long hi = (long long)(d >> 64);
-    const double dd = (double)hi * 18446744073709551616.0 + (double)(unsigned long long)d;
-    const double t = block_sum<NT>(ldexp(dd, (E - 1022 - ef::FIX_BITS) + (Eo - 1022 - ef::FIX_BITS)), red);
-    if (threadIdx.x == 0) qqp[blockIdx.x] = t;
 }
 
 __global__ void k_lz_beta(LzScalars *S, const double *__restrict__ part, int nblk, double *beta, double tol) {
@@ -592,6 +594,7 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
     const int nblk = grid_blocks(sv.dim, NT);
     const int pprev = parity ^ 1;   // buffer of q_prev, receives u then w
     const bool b64 = (R->use_blk || R->use_s1) && R->dtype == HM_F64;
+    const int nblk64 = upd64_blocks(sv.dim);   // grid of the FP64 block path's update kernels
     long long *xs[2] = {R->L.shadow ? (long long *)(R->work + R->L.xs[0]) : nullptr,
                         R->L.shadow ? (long long *)(R->work + R->L.xs[1]) : nullptr};
     unsigned long long *Y = R->L.shadow ? (unsigned long long *)(R->work + R->L.ybuf) : nullptr;
@@ -604,12 +607,12 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
         } else if (b64 && R->use_s1) {
             double *s1part = (double *)(R->work + R->L.s1part);
             HM_TRY(s1_lz64(R->s1, xs[parity], Y, R->sc, parity, s1part, st));
-            k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, s1part, R->s1.nblocks, R->qqp, nblk, R->alpha, pprev);
+            k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, s1part, R->s1.nblocks, R->qqp, nblk64, R->alpha, pprev);
         } else if (b64) {
             HM_TRY(blk_lz64_launch(R->blk, xs[parity], Y, R->sc, parity, R->hpart, R->blk_blocks, st, R->jit));
             if (R->split)
                 HM_TRY(blk_lz64_launch(R->blk2, xs[parity], Y, R->sc, parity, R->hpart, R->blk_blocks2, st, R->jit2));
-            k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->qqp, nblk, R->alpha, pprev);
+            k_lz_alpha2<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->qqp, nblk64, R->alpha, pprev);
         } else if (R->use_blk) {
             HM_TRY(blk_lz32_launch(R->blk, (const float *)qc, (float *)qp, R->sc, R->hpart, R->blk_blocks, st, R->jit));
             k_lz_alpha<<<1, NT, 0, st>>>(R->sc, R->hpart, 1 << R->blk.H, R->alpha, pprev);
@@ -624,13 +627,13 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
         }
     } else if (b64) {
         if (R->psi)
-            k_lz_update_y<true><<<nblk, NT, 0, st>>>(Y, (const float2 *)qc, (float2 *)qp, sv.dim, R->sc, R->alpha,
-                                                     R->part, R->psi, R->coef, pprev);
+            k_lz_update_y<true><<<nblk64, NT, 0, st>>>(Y, (const float2 *)qc, (float2 *)qp, sv.dim, R->sc, R->alpha,
+                                                       R->part, R->qqp, R->psi, R->coef, pprev);
         else
-            k_lz_update_y<false><<<nblk, NT, 0, st>>>(Y, (const float2 *)qc, (float2 *)qp, sv.dim, R->sc, R->alpha,
-                                                      R->part, nullptr, R->coef, pprev);
-        k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
-        k_fixd<<<nblk, NT, 0, st>>>((const float2 *)qp, xs[pprev], xs[parity], sv.dim, R->sc, pprev, R->qqp);
+            k_lz_update_y<false><<<nblk64, NT, 0, st>>>(Y, (const float2 *)qc, (float2 *)qp, sv.dim, R->sc,
+                                                        R->alpha, R->part, R->qqp, nullptr, R->coef, pprev);
+        k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk64, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
+        k_fixd<<<nblk64, NT, 0, st>>>((const float2 *)qp, xs[pprev], sv.dim, R->sc, pprev);
     } else {
         if (R->psi)
             k_lz_update<T, true><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
