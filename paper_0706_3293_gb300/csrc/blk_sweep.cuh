@@ -486,6 +486,18 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
 
 // T_c = 2 acc_c + (ntot_c - 2 cnt_c) x_i: the class sum of Eq. (E-2-1) rows in units of
 // -J_c / 4 (s = 1/2: s^z s^z = +-1/4, exchange element 1/2)
+// s 2^k as binary64 bits, rounded to nearest even: the conversion unit's correctly rounded
+// int64 -> binary64 conversion with its exponent field moved by k, exact while the result
+// is a normal number; otherwise (zero, underflow, overflow) the integer rounding of
+// ef::bits_from_int.  Both give the same bits wherever both apply; this one keeps about
+// twenty integer instructions a row off the integer pipe.
+__device__ __forceinline__ unsigned long long blk_bits_pow2(int64_t s, int k) {
+    const unsigned long long b = ef::d2u(__ll2double_rn((long long)s));
+    const int e = (int)((b >> 52) & 0x7FFu) + k;
+    if (s != 0 && e >= 1 && e <= 2046) return b + ((unsigned long long)(long long)k << 52);
+    return ef::bits_from_int(s, k);
+}
+
 template <int NC>
 __device__ __forceinline__ void blk_classes(const BlkParams &P, const int64_t *acc, const int *cnt, int64_t Xo,
                                             int64_t *T) {
@@ -502,7 +514,7 @@ __device__ __forceinline__ unsigned long long blk_y_bits(const BlkParams &P, con
 #pragma unroll
         for (int c = 0; c < NC; ++c) s += (int64_t)P.Kc[c] * T[c];
         *Tsum = s;
-        if (P.g0_pow2) return ef::bits_from_int(s, u + P.g0_exp);
+        if (P.g0_pow2) return blk_bits_pow2(s, u + P.g0_exp);
         const ef::df t = ef::df_from_fix(s, u + 1022 + ef::FIX_BITS, 0, 0);
         return ef::bits_from_df(ef::df_mul(t, ef::df{P.g0_hi, P.g0_lo}), 0);
     }
@@ -618,7 +630,7 @@ __device__ __forceinline__ void lz64_body(const BlkParams &P, const long long *_
                 [&](uint32_t i) { return (long long)__ldcs(Y + i); },
                 [&](uint32_t off, uint32_t r, int64_t xo, const int64_t *acc, const int *cnt, long long sa) {
                     const int64_t s = (int64_t)sa + tsum(xo, acc, cnt);
-                    __stcs(Y + off + r, ef::bits_from_int(s, u + P.g0_exp));
+                    __stcs(Y + off + r, blk_bits_pow2(s, u + P.g0_exp));
                     d1 += (__int128)xo * s;
                 },
                 [&](int it) {
@@ -655,7 +667,7 @@ __device__ __forceinline__ void lz64_body(const BlkParams &P, const long long *_
             const int64_t ts = 2 * a + (int64_t)m * xo;
             unsigned long long yb;
             if (P.g0_pow2) {
-                yb = ef::bits_from_int(ts, u + P.g0_exp);
+                yb = blk_bits_pow2(ts, u + P.g0_exp);
             } else {
                 const ef::df t = ef::df_from_fix(ts, u + 1022 + ef::FIX_BITS, 0, 0);
                 yb = ef::bits_from_df(ef::df_mul(t, ef::df{P.g0_hi, P.g0_lo}), 0);
