@@ -803,3 +803,50 @@ def test_four_class_triangles_vs_oracle(hm, dtype):
     tol = 1e-11 if dtype == "f64" else 2e-5
     np.testing.assert_allclose(al, oal, rtol=0, atol=tol * np.abs(oal).max())
     np.testing.assert_allclose(be, obe, rtol=0, atol=tol * np.abs(oal).max())
+
+
+@pytest.mark.parametrize("N,j2", [(20, -0.5), (24, -0.25)])
+def test_block_rows_correctly_rounded(hm, N, j2, monkeypatch):
+    """FP64 block rows with integer-ratio couplings and a power-of-two unit (J2 = J1/2,
+    J1/4) are the exact row sums of Eq. (E-2-1) rounded once to binary64.  With
+    x_i = k_i 2^-40 (|k_i| < 2^40), which the fixed-point copy holds exactly, each sampled
+    row of y = H x equals, bit for bit, the correctly rounded exact rational sum
+    sum_b -J_b/4 (+-1) x_i + sum over the allowed exchanges of -J_b/2 x_t (s = 1/2), built
+    from the oracle's decode and encode; with and without run-time compilation (class plans
+    run the block kernel either way)."""
+    from fractions import Fraction
+    inst = W.small_ring(N, -1.0, j2)
+    b = hm.Basis(N, 1, 0)
+    ob = oracle.Basis(N, 1, N // 2)
+    bl = hm.bonds_of(inst)
+    rng = np.random.default_rng(N)
+    k = rng.integers(-(1 << 40) + 1, 1 << 40, size=b.dim, dtype=np.int64)
+    x = k.astype(np.float64) * 2.0 ** -40
+    assert np.array_equal((x * 2.0 ** 40).astype(np.int64), k)
+    rows = np.unique(np.concatenate([rng.integers(0, b.dim, 300), [0, b.dim - 1]]))
+    want = {}
+    for i in rows:
+        i = int(i)
+        d = [int(a) for a in ob.decode(i)]
+        acc = Fraction(0)
+        for p, q, J in zip(inst.u, inst.v, inst.J):
+            p, q, J = int(p), int(q), Fraction(float(J))
+            if d[p] == d[q]:
+                acc += -J / 4 * Fraction(int(k[i]), 1 << 40)
+            else:
+                acc += J / 4 * Fraction(int(k[i]), 1 << 40)
+                t = list(d)
+                t[p], t[q] = d[q], d[p]
+                acc += -J / 2 * Fraction(int(k[ob.encode(t)]), 1 << 40)
+        want[i] = float(acc)              # int / int true division: correctly rounded
+    xt = torch.from_numpy(x).cuda()
+    for jit in ("1", "0"):
+        monkeypatch.setenv("HM_JIT", jit)
+        name = hm.matvec_kernel_name(b, bl)
+        assert name.startswith("k_blk_matvec"), name
+        y = hm.matvec(b, bl, xt).cpu().numpy()
+        got = y[rows]
+        exp = np.array([want[int(i)] for i in rows])
+        bad = np.nonzero(got.view(np.uint64) != exp.view(np.uint64))[0]
+        assert bad.size == 0, (name, [(int(rows[j]), got[j], exp[j]) for j in bad[:5]])
+    monkeypatch.setenv("HM_JIT", "1")
