@@ -342,8 +342,8 @@ __global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int n
 // needs no conversion to or from binary64.
 // Resident CTAs per SM of the FP64 block path's update: 40 registers a thread (at 8 CTAs
 // and 32 registers its double-float dots spill; N = 32 step 20.21 against 20.09 ms with the
-// spills and 19.82 ms here).  The update, the copy and the beta reduction of that path run
-// on a grid of this many CTAs per SM (upd64_blocks).
+// spills and 19.82 ms here).  The update and the reductions of its partials run on a grid
+// of this many CTAs per SM (upd64_blocks).
 constexpr int UPD64_CTAS = 6;
 static int upd64_blocks(uint64_t dim) { return std::min(grid_blocks(dim, NT), sm_count() * UPD64_CTAS); }
 
@@ -633,7 +633,7 @@ static int enqueue_phase_t(hm_lanczos *R, int parity, int phase, cudaStream_t st
             k_lz_update_y<false><<<nblk64, NT, 0, st>>>(Y, (const float2 *)qc, (float2 *)qp, sv.dim, R->sc,
                                                         R->alpha, R->part, R->qqp, nullptr, R->coef, pprev);
         k_lz_beta<<<1, NT, 0, st>>>(R->sc, R->part, nblk64, R->beta, R->dtype == HM_F64 ? LZ_TOL : LZ_TOL32);
-        k_fixd<<<nblk64, NT, 0, st>>>((const float2 *)qp, xs[pprev], sv.dim, R->sc, pprev);
+        k_fixd<<<nblk, NT, 0, st>>>((const float2 *)qp, xs[pprev], sv.dim, R->sc, pprev);
     } else {
         if (R->psi)
             k_lz_update<T, true><<<nblk, NT, 0, st>>>(qc, qp, sv.dim, R->sc, R->alpha, R->part, R->psi, R->coef, pprev);
