@@ -385,25 +385,39 @@ k_lz_update_y(const unsigned long long *__restrict__ Y, const float2 *__restrict
     const ef::df sg_d = todf(sg), as_d = todf(as), gm_d = todf(gm);
     ef::df s{0.0f, 0.0f}, dq{0.0f, 0.0f};
     uint32_t eh = 0;
-    const uint64_t stride = (uint64_t)gridDim.x * NT;
-    uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x;
-    // operands of the next row are loaded before the current row is computed
-    unsigned long long yn = 0;
-    float2 qn = make_float2(0.0f, 0.0f), pn = qn;
-    if (r < n) { yn = __ldcs(Y + r); qn = __ldcs(qc + r); pn = qp[r]; }
-    for (; r < n; r += stride) {
-        const unsigned long long yb = yn;
-        const float2 q2 = qn, p2 = pn;
-        if (r + stride < n) { yn = __ldcs(Y + r + stride); qn = __ldcs(qc + r + stride); pn = qp[r + stride]; }
+    auto row = [&](unsigned long long yb, float2 q2, float2 p2) {
         const ef::df q = ef::df{q2.x, q2.y};
         const ef::df t1 = ef::df_mul(sg_d, ef::df_from_bits(yb, 0));
         const ef::df t2 = ef::df_mul(as_d, q);
         const ef::df t3 = ef::df_mul(gm_d, ef::df{p2.x, p2.y});
         const ef::df w = ef::df_add(t1, ef::df_neg(ef::df_add(t2, t3)));
-        qp[r] = make_float2(w.hi, w.lo);
         eh = max(eh, (ef::f2u(w.hi) >> 23) & 0xFFu);
         s = ef::df_add(s, ef::df_mul(w, w));
         dq = ef::df_add(dq, ef::df_mul(w, q));
+        return make_float2(w.hi, w.lo);
+    };
+    const uint64_t stride = (uint64_t)gridDim.x * NT;
+    uint64_t r0 = 0;
+    if constexpr (!PSI) {
+        // two rows per 16-byte access of each operand (the buffers are 256-byte aligned), so
+        // that each thread keeps more bytes in flight; an odd last row goes through the loop
+        // below
+        const uint64_t n2 = n / 2;
+        const ulonglong2 *Y2 = reinterpret_cast<const ulonglong2 *>(Y);
+        const float4 *qc2 = reinterpret_cast<const float4 *>(qc);
+        float4 *qp2 = reinterpret_cast<float4 *>(qp);
+        for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n2; r += stride) {
+            const ulonglong2 yb = __ldcs(Y2 + r);
+            const float4 q4 = __ldcs(qc2 + r), p4 = qp2[r];
+            const float2 w0 = row(yb.x, make_float2(q4.x, q4.y), make_float2(p4.x, p4.y));
+            const float2 w1 = row(yb.y, make_float2(q4.z, q4.w), make_float2(p4.z, p4.w));
+            qp2[r] = make_float4(w0.x, w0.y, w1.x, w1.y);
+        }
+        r0 = 2 * n2;
+    }
+    for (uint64_t r = r0 + blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += stride) {
+        const float2 q2 = __ldcs(qc + r);
+        qp[r] = row(__ldcs(Y + r), q2, qp[r]);
         if constexpr (PSI) psi[r] += cj * ((double)q2.x + (double)q2.y);
     }
     const double tot = block_sum<NT>((double)s.hi + (double)s.lo, red);
@@ -433,14 +447,19 @@ k_fixd(const float2 *__restrict__ w, long long *__restrict__ X, uint64_t n, cons
     if (S->done) return;
     const int E = S->emax[slot];
     const uint64_t stride = (uint64_t)gridDim.x * NT;
-    uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x;
-    float2 vn = make_float2(0.0f, 0.0f);
-    if (r < n) vn = __ldcs(w + r);
-    for (; r < n; r += stride) {                       // next row's operand loaded first
-        const float2 v = vn;
-        if (r + stride < n) vn = __ldcs(w + r + stride);
-        __stcs(X + r, (long long)ef::fix_from_df(ef::df{v.x, v.y}, E, 0));
+    // two rows per 16-byte access (256-byte aligned buffers); an odd last row after
+    const uint64_t n2 = n / 2;
+    const float4 *w2 = reinterpret_cast<const float4 *>(w);
+    longlong2 *X2 = reinterpret_cast<longlong2 *>(X);
+    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n2; r += stride) {
+        const float4 v = __ldcs(w2 + r);
+        longlong2 x;
+        x.x = (long long)ef::fix_from_df(ef::df{v.x, v.y}, E, 0);
+        x.y = (long long)ef::fix_from_df(ef::df{v.z, v.w}, E, 0);
+        __stcs(X2 + r, x);
     }
+    for (uint64_t r = 2 * n2 + blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += stride)
+        __stcs(X + r, (long long)ef::fix_from_df(ef::df{w[r].x, w[r].y}, E, 0));
 }
 
 __global__ void k_lz_beta(LzScalars *S, const double *__restrict__ part, int nblk, double *beta, double tol) {
