@@ -313,26 +313,6 @@ k_lz_update(const T *__restrict__ qc, T *__restrict__ qp, uint64_t n, LzScalars 
     }
 }
 
-// fixed-point copy X of the new vector w (FP64 block path), unit from its largest
-// exponent, and the exact dot X . Xo with the fixed-point copy Xo of the vector before
-// it: qqp[blk] = (q_new . q_cur) in true units, for the next alpha
-__global__ void __launch_bounds__(NT)
-k_fix(const unsigned long long *__restrict__ w, long long *__restrict__ X, const long long *__restrict__ Xo,
-      uint64_t n, const LzScalars *S, int slot, double *__restrict__ qqp) {
-    if (S->done) return;
-    __shared__ double red[NT / 32];
-    const int E = S->emax[slot], Eo = S->emax[slot ^ 1];
-    __int128 d = 0;
-    for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
-        const long long x = (long long)ef::fix_from_bits(__ldcs(w + r), E);
-        __stcs(X + r, x);
-        d += (__int128)x * __ldcs(Xo + r);
-    }
-    const long long hi = (long long)(d >> 64);
-    const double dd = (double)hi * 18446744073709551616.0 + (double)(unsigned long long)d;
-    const double t = block_sum<NT>(ldexp(dd, (E - 1022 - ef::FIX_BITS) + (Eo - 1022 - ef::FIX_BITS)), red);
-    if (threadIdx.x == 0) qqp[blockIdx.x] = t;
-}
 
 // alpha_j = sigma^2 (q.Hq) - sigma gamma (q.q_prev): q.Hq from the per-block partials of
 // the FP64 block product (exact integer dots of the fixed-point copy), q.q_prev from those
@@ -431,13 +411,20 @@ k_lz_update_y(const unsigned long long *__restrict__ Y, const float2 *__restrict
     if ((threadIdx.x & 31) == 0 && eh) atomicMax(&S->emax[pprev], (int)eh - 127 + 1023);
 }
 
-// start vector, binary64 -> double-float pairs in place (FP64 block path; integer
-// conversion, no FP64 instruction)
-__global__ void __launch_bounds__(NT) k_to_df(unsigned long long *__restrict__ b, uint64_t n) {
+// start vector of the FP64 block path, one pass: its fixed-point copy X (unit from its
+// largest exponent field, S->emax[0]) and the binary64 values turned into double-float
+// pairs in place (integer conversion, no FP64 instruction); there is no vector before it,
+// so its q.q_prev partials are zero
+__global__ void __launch_bounds__(NT) k_fix_start(unsigned long long *__restrict__ b, long long *__restrict__ X,
+                                                  uint64_t n, const LzScalars *S, double *__restrict__ qqp) {
+    const int E = S->emax[0];
     for (uint64_t r = blockIdx.x * (uint64_t)NT + threadIdx.x; r < n; r += (uint64_t)gridDim.x * NT) {
-        const ef::df v = ef::df_from_bits(b[r], 0);
-        ((float2 *)b)[r] = make_float2(v.hi, v.lo);
+        const unsigned long long v = b[r];
+        __stcs(X + r, (long long)ef::fix_from_bits(v, E));
+        const ef::df d = ef::df_from_bits(v, 0);
+        ((float2 *)b)[r] = make_float2(d.hi, d.lo);
     }
+    if (threadIdx.x == 0) qqp[blockIdx.x] = 0.0;
 }
 
 // fixed-point copy X of the new vector w (double-float pairs), unit from its largest
@@ -733,10 +720,8 @@ static int enqueue_start(hm_lanczos *R, const void *v0, uint64_t seed, cudaStrea
     else k_sumsq<float><<<nblk, NT, 0, st>>>((const float *)b0, sv.dim, R->part, nullptr);
     k_lz_start<<<1, NT, 0, st>>>(R->sc, R->part, nblk);
     if ((R->use_blk || R->use_s1) && R->dtype == HM_F64) {
-        HM_CUDA(cudaMemsetAsync(R->work + R->L.xs[1], 0, sv.dim * 8, st));
-        k_fix<<<nblk, NT, 0, st>>>((const unsigned long long *)b0, (long long *)(R->work + R->L.xs[0]),
-                                   (const long long *)(R->work + R->L.xs[1]), sv.dim, R->sc, 0, R->qqp);
-        k_to_df<<<nblk, NT, 0, st>>>((unsigned long long *)b0, sv.dim);
+        k_fix_start<<<nblk, NT, 0, st>>>((unsigned long long *)b0, (long long *)(R->work + R->L.xs[0]), sv.dim, R->sc,
+                                         R->qqp);
     }
     HM_CUDA(cudaGetLastError());
     R->host_j = 0;
