@@ -484,8 +484,6 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
     }
 }
 
-// T_c = 2 acc_c + (ntot_c - 2 cnt_c) x_i: the class sum of Eq. (E-2-1) rows in units of
-// -J_c / 4 (s = 1/2: s^z s^z = +-1/4, exchange element 1/2)
 // s 2^k as binary64 bits, rounded to nearest even: the conversion unit's correctly rounded
 // int64 -> binary64 conversion with its exponent field moved by k, exact while the result
 // is a normal number; otherwise (zero, underflow, overflow) the integer rounding of
@@ -498,6 +496,8 @@ __device__ __forceinline__ unsigned long long blk_bits_pow2(int64_t s, int k) {
     return ef::bits_from_int(s, k);
 }
 
+// T_c = 2 acc_c + (ntot_c - 2 cnt_c) x_i: the class sum of Eq. (E-2-1) rows in units of
+// -J_c / 4 (s = 1/2: s^z s^z = +-1/4, exchange element 1/2)
 template <int NC>
 __device__ __forceinline__ void blk_classes(const BlkParams &P, const int64_t *acc, const int *cnt, int64_t Xo,
                                             int64_t *T) {

@@ -313,7 +313,6 @@ k_lz_update(const T *__restrict__ qc, T *__restrict__ qp, uint64_t n, LzScalars 
     }
 }
 
-
 // alpha_j = sigma^2 (q.Hq) - sigma gamma (q.q_prev): q.Hq from the per-block partials of
 // the FP64 block product (exact integer dots of the fixed-point copy), q.q_prev from those
 // of the update kernel that made q (double-float), zero at the start (the Paige form
@@ -338,9 +337,6 @@ __global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int n
     }
 }
 
-// FP64 block path.  The Lanczos vectors are kept as double-float pairs (hi, lo floats,
-// 8 bytes): the update computes in double-float, so a pair holds all it produces and
-// needs no conversion to or from binary64.
 // Resident CTAs per SM of the FP64 block path's update: 40 registers a thread (at 8 CTAs
 // and 32 registers its double-float dots spill; N = 32 step 20.21 against 20.09 ms with the
 // spills and 19.82 ms here).  The update and the reductions of its partials run on a grid
@@ -348,6 +344,9 @@ __global__ void k_lz_alpha2(LzScalars *S, const double *__restrict__ part, int n
 constexpr int UPD64_CTAS = 6;
 static int upd64_blocks(uint64_t dim) { return std::min(grid_blocks(dim, NT), sm_count() * UPD64_CTAS); }
 
+// FP64 block path.  The Lanczos vectors are kept as double-float pairs (hi, lo floats,
+// 8 bytes): the update computes in double-float, so a pair holds all it produces and
+// needs no conversion to or from binary64.
 // w = sigma y - alpha sigma q - gamma q_prev over q_prev (y: binary64 bits of H q);
 // part = |w|^2; qqp = w . q (the stored new and current vectors, for the next alpha; both
 // dots in double-float per thread, binary64 over the block); largest exponent of w, as a
