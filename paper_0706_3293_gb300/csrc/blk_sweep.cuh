@@ -185,8 +185,16 @@ __host__ __device__ __forceinline__ size_t blk_row_xs_bytes(const BlkParams &P, 
 __host__ __device__ __forceinline__ size_t blk_x_bytes(const BlkParams &P) {
     return P.perbond ? al16(sizeof(BlkMetaX)) : P.par ? al16(sizeof(BlkMetaXF)) : 0;
 }
+// the table C (binomials D(p, c), p <= N, c <= A) staged in shared memory when it takes at
+// most 4 KB (2.2 KB for N = 32, M = 0): the block set-up's offsets off(h) read it in a loop
+// over the high word's ones, a chain of dependent-issue loads between two CTA barriers
+__host__ __device__ __forceinline__ size_t blk_c_bytes(const BlkParams &P) {
+    const size_t b = (size_t)(P.N + 1) * (P.A + 1) * sizeof(uint32_t);
+    return b <= 4096 ? al16(b) : 0;
+}
+
 __host__ __device__ __forceinline__ size_t blk_row_smem_bytes(const BlkParams &P, int esize, int pad) {
-    return blk_row_xs_bytes(P, esize, pad) + 2 * al16(sizeof(BlkMeta)) + 2 * blk_x_bytes(P);
+    return blk_row_xs_bytes(P, esize, pad) + 2 * al16(sizeof(BlkMeta)) + 2 * blk_x_bytes(P) + blk_c_bytes(P);
 }
 
 __device__ __forceinline__ bool blk_h_valid(const BlkParams &P, uint32_t h) {
@@ -345,6 +353,12 @@ __device__ __forceinline__ void blk_sweep(const BlkParams &P, const unsigned cha
         const uint8_t *R0g = (const uint8_t *)P.tab + P.off_R0;
         for (int i = tid; i < 256; i += BLK_NT) s_R0S[i] = (uint32_t)R0g[i] * (uint32_t)sizeof(Sv);
         Row::template stage<Sv>(P, smem);
+        if (blk_c_bytes(P)) {
+            uint32_t *Cs = (uint32_t *)(smem + blk_row_xs_bytes(P, sizeof(Sv), Row::kPad) + 2 * al16(sizeof(BlkMeta)) +
+                                        2 * blk_x_bytes(P));
+            for (int i = tid; i < (P.N + 1) * (P.A + 1); i += BLK_NT) Cs[i] = Cg[i];
+            Cg = Cs;
+        }
     }
     BlkTabs tb;
     tb.U = nullptr; tb.R0 = nullptr; tb.C = Cg;
