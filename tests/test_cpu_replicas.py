@@ -269,3 +269,50 @@ def test_triangle_encoding_of_low_exchanges(K):
             cls_b = [o2] if second_is_e3 else []
             assert sorted(cls_a) == sorted(t for t, v in zip(tg[:2], ok[:2]) if v)
             assert sorted(cls_b) == sorted(t for t, v in zip(tg[2:], ok[2:]) if v)
+
+
+# ---- the row value's rounding through the conversion unit ------------------------------------
+
+def test_exponent_shift_rounding_matches_exact():
+    """The block rows round s 2^k (s the exact int64 row sum, k the fixed-point unit) as
+    round-to-nearest-even binary64 of s with its exponent field moved by k, whenever the
+    result is a normal number.  Replica: Python's int -> float conversion (correctly
+    rounded) with the field moved by k, against the exact rational s 2^k rounded by
+    Fraction -> float, for random s over the whole int64 range and k over the range the
+    kernels use; plus the cases at the ends of that range, which must fall back."""
+    import struct
+    from fractions import Fraction
+
+    def bits(x):
+        return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+    def shifted(s, k):
+        """the kernel's fast path, or None where it hands over to the integer rounding"""
+        if s == 0:
+            return None
+        b = bits(float(s))
+        e = ((b >> 52) & 0x7FF) + k
+        if not 1 <= e <= 2046:
+            return None
+        return (b + (k << 52)) & 0xFFFFFFFFFFFFFFFF
+
+    rng = np.random.default_rng(5)
+    n_fast = 0
+    for _ in range(20000):
+        nb = int(rng.integers(1, 64))
+        s = int(rng.integers(0, 1 << 62)) >> (62 - nb) if nb < 62 else int(rng.integers(0, 1 << 62))
+        s = -s if rng.integers(0, 2) else s
+        # the kernels' k is the unit exponent E - 1075 (E about 1000..1023) plus that of g0;
+        # a wide range besides, down to where the results leave the normal numbers
+        k = int(rng.integers(-90, -40)) if rng.integers(0, 2) else int(rng.integers(-1140, 900))
+        got = shifted(s, k)
+        if got is None:
+            continue
+        n_fast += 1
+        assert got == bits(float(Fraction(s) * Fraction(2) ** k)), (s, k)
+    assert n_fast > 12000
+    # ties: s with exactly 54 significant bits ending in ...1 (halfway), both parities
+    for s in ((1 << 53) + 1, (1 << 53) + 3, -((1 << 60) + (1 << 7)), (1 << 62) + (1 << 8) + (1 << 9)):
+        assert shifted(s, -1075) == bits(float(Fraction(s) * Fraction(2) ** -1075))
+    # out of the normal range: the kernel hands over to the integer rounding
+    assert shifted(1, -1075) is None and shifted(0, -1000) is None and shifted(1 << 62, 1000) is None
