@@ -262,8 +262,11 @@ int sector_ground_energies(int n_sites, int two_s, int n_bonds, const int32_t *u
  * eigenvector c is found on the device (bisection + inverse iteration), a second pass
  * regenerates the same v_j and accumulates psi0 = sum_j c_j v_j, which is normalised;
  * then bond_corr(psi0, psi0).  Host outputs: *e0, dE0_dJ[n_bonds]; psi_out (device,
- * double[dim]) optional.  Returns HM_DEGENERATE when the gap to the second Ritz value is
- * below 1e-8 |E0| (the gradient is then one of many).  Workspace: e0_grad_workspace. */
+ * double[dim]) optional.  Returns HM_DEGENERATE when the gap to the second Ritz value of
+ * that T is below 1e-8 |E0| (the gradient is then one of many).  One Krylov space holds
+ * only one direction of an exactly degenerate eigenspace (the two dimer singlets of the
+ * J2 = J1/2 ring), so such a degeneracy is not seen by one run: the result is then the
+ * gradient at the ground state the start vector selects.  Workspace: e0_grad_workspace. */
 int e0_grad_workspace(const hm_basis *basis, int n_bonds, int steps, size_t *bytes);
 int e0_grad(const hm_basis *basis, int n_bonds, const int32_t *u, const int32_t *v,
             const double *J, const void *v0, uint64_t seed, int steps, void *work,
